@@ -1,0 +1,250 @@
+/*
+ * msketch.h — C ABI of libmsketch: GPU CountSketch, Count-Gauss multisketch
+ * and sketched least squares on one GB300 (sm_103a).
+ *
+ * The operations follow "A High Performance GPU CountSketch Implementation
+ * and Its Application to Multisketching and Least Squares Problems"
+ * (Higgins, Boman, Yamazaki, arXiv 2508.14209):
+ *   - CountSketch, Definition 3 and its row form (Section 4), applied by a
+ *     signed scatter-add of rows as in Algorithm 2;
+ *   - the multisketch S2 (S1 x) with S1 a CountSketch and S2 a Gaussian
+ *     sketch ("Count-Gauss", Section 1, Section 6.2);
+ *   - sketch-and-solve least squares, Algorithm 1 (Section 2), with the
+ *     Householder-QR solve of Section 6.1;
+ *   - the normal-equations baseline of Section 6.3 (Gram matrix, Cholesky,
+ *     two triangular solves).
+ * The random sketch entries are not stored (Section 8 names an on-the-fly
+ * hashed CountSketch as future work): bucket and sign of row i, and every
+ * Gaussian entry, are recomputed from a 64-bit seed by a splitmix64 counter
+ * generator, defined below, so that any party can regenerate them.
+ *
+ * Conventions for every entry point
+ *   - Matrices are dense with a leading dimension.  A and Z are column-major;
+ *     the CountSketch output Y is row-major (bucket-major, the layout in
+ *     which Algorithm 2 accumulates rows, Section 6.1).
+ *   - Array arguments are DEVICE pointers owned by the caller unless marked
+ *     "host".  The library never allocates device memory: scratch space is
+ *     the caller's `ws` buffer, sized by the matching *_workspace() query
+ *     (ws may be NULL when the query returns 0).  ws must be 256-byte aligned.
+ *   - Work is enqueued on `stream` (a cudaStream_t passed as void*; NULL is
+ *     the legacy default stream) and is asynchronous, except where an entry
+ *     point says it synchronises the stream to fill a host-side result.
+ *   - Return value: MSK_OK (0); -i when argument i (1-based) is invalid;
+ *     a positive MSK_E* code below; or, for numerical breakdown, the
+ *     positive value documented at the entry point.
+ *   - No entry point falls back to the CPU.
+ *
+ * Counter generator (splitmix64, Steele, Lea and Flood, OOPSLA 2014):
+ *   mix(z):  z ^= z>>30; z *= 0xBF58476D1CE4E5B9; z ^= z>>27;
+ *            z *= 0x94D049BB133111EB; z ^= z>>31
+ *   key(seed, tag) = mix(seed ^ (tag * 0xD1B54A32D192ED03))
+ *   draw(key, i)   = mix(key + (i+1) * 0x9E3779B97F4A7C15)   (mod 2^64)
+ *   CountSketch (tag 0): z = draw(key(seed,0), i) for 0-based row i;
+ *     bucket h(i) = ((z >> 32) * k) >> 32,  sign s(i) = (z & 1) ? -1 : +1.
+ *   Gaussian (tag 2): entry (r, c) of the p x k matrix G is number r*k + c of
+ *     the polar-method sampler in binary32 (attempt a uses draw index
+ *     (r*k+c)*2^16 + a; U = z>>40, V = (z>>16) & 0xFFFFFF,
+ *     u = (2U+1-2^24)*2^-24, v likewise; accept s = u*u+v*v < 1; result
+ *     u*sqrt(-2*ln(s)/s) with ln(m*2^e) = e*ln2 + 2t(1 + t^2/3 + t^4/5 +
+ *     t^6/7 + t^8/9), t = (m-1)/(m+1), m in [sqrt(1/2), sqrt(2)); every step
+ *     one round-to-nearest binary32 operation), divided by sqrt(p) so the
+ *     entries are N(0, 1/p).
+ */
+#ifndef MSKETCH_H
+#define MSKETCH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Element type of A (and of the CountSketch output Y). */
+typedef enum { MSK_F64 = 0, MSK_F32 = 1 } msk_dtype;
+
+/* Arithmetic of the Gaussian stage Z = G Y.
+ *   F64    : G widened exactly from binary32, FP64 multiply-add (CUDA cores).
+ *   F32    : G and Y in binary32, FP32 multiply-add (CUDA cores).
+ *   BF16   : G and Y rounded to bfloat16, tensor cores (tcgen05), FP32 accum.
+ *   F16    : G and Y rounded to binary16, tensor cores, FP32 accumulation.
+ *   BF16X3 : G rounded to bfloat16; Y split exactly into Y1+Y2+Y3 bfloat16
+ *            parts (Henry, Tang, Heinecke, ARITH 2019); the three products
+ *            accumulate in one FP32 tensor-memory accumulator.  Keeps Z at
+ *            FP32 accuracy, which the least-squares preconditioner needs. */
+typedef enum {
+  MSK_GEMM_F64 = 0,
+  MSK_GEMM_F32 = 1,
+  MSK_GEMM_BF16 = 2,
+  MSK_GEMM_F16 = 3,
+  MSK_GEMM_BF16X3 = 4
+} msk_gemm_prec;
+
+/* CountSketch strategy.
+ *   ATOMIC : rows streamed once, each added to its bucket row by L2
+ *            reductions (Algorithm 2's atomics, coalesced per row).
+ *   SORTED : rows grouped by bucket (counting sort on h(i), each bucket's
+ *            rows in increasing order), then each bucket summed in
+ *            increasing row order: deterministic, bitwise reproducible. */
+typedef enum { MSK_CS_ATOMIC = 0, MSK_CS_SORTED = 1 } msk_cs_strategy;
+
+#define MSK_OK 0
+#define MSK_ENOCONV 1001  /* refinement stopped at max_iter (x is returned) */
+#define MSK_ENOMEM 1002   /* ws too small, or a request over the memory budget */
+#define MSK_ETIMEOUT 1003 /* a bounded device wait gave up */
+#define MSK_ECUDA 1004    /* a CUDA runtime call failed */
+#define MSK_ENOTSUP 1005  /* unsupported combination (e.g. alignment) */
+#define MSK_EBUSY 1006    /* server queue full */
+
+/* Result summary of a least-squares solve (host struct). */
+typedef struct {
+  int32_t iters;      /* refinement iterations taken (0 for plain SnS) */
+  int32_t converged;  /* 1 when the stopping test held */
+  double relres;      /* ||b - A x|| / ||b|| of the returned x (FP64) */
+  double relres_sns;  /* the same for the sketch-and-solve start x0 */
+} msk_lstsq_info;
+
+/* ---- Version / self description ---------------------------------------- */
+
+/* Library version string (static storage). */
+const char *msk_version(void);
+
+/* Last CUDA error string seen by the library on this host thread (static
+ * storage, empty when none). */
+const char *msk_last_error(void);
+
+/* ---- Sketch randomness (test hooks) ------------------------------------ */
+
+/* Bucket h(i) in [0, k) and sign s(i) in {-1, +1} of rows i0 .. i0+count-1,
+ * from the counter generator above (Definition 3, Section 4; tag 0).
+ *   h: device uint32[count]; s: device int8[count] (either may be NULL).
+ * Errors: -3 count < 0, -4 k < 1 or k > 2^32-1. */
+int cs_hash(uint64_t seed, int64_t i0, int64_t count, int64_t k, uint32_t *h,
+            int8_t *s, void *stream);
+
+/* The p x k Gaussian G of the multisketch's second stage (Section 1; N(0,1/p)
+ * entries from the sampler above), written row-major with leading dimension
+ * ldg >= k in the element type `out_prec`: MSK_GEMM_F64 (double),
+ * MSK_GEMM_F32 (float), MSK_GEMM_BF16 (bfloat16, round-to-nearest-even of the
+ * binary32 value), MSK_GEMM_F16 (binary16, likewise).
+ * Errors: -2 p < 1, -3 k < 1, -4 bad out_prec, -6 ldg < k. */
+int ms_gaussian(uint64_t seed, int64_t p, int64_t k, int out_prec, void *G,
+                int64_t ldg, void *stream);
+
+/* ---- CountSketch (Definition 3; Algorithm 2) --------------------------- */
+
+/* Scratch bytes cs_sketch needs (0 for MSK_CS_ATOMIC). */
+size_t msk_cs_workspace(int64_t d, int64_t n, int64_t k, int dtype,
+                        int strategy);
+
+/* Y = S [A b]: the k x ncol CountSketch of the d x n matrix A, with the
+ * optional column b appended (ncol = n + (b != NULL)), so that
+ *   Y[m, j] = sum_{i : h(i) = m} s(i) [A b][i, j]       (Section 4).
+ *   A : device, column-major d x n, leading dimension lda >= max(d,1), of
+ *       type dtype (MSK_F64 double / MSK_F32 float); 16-byte aligned.
+ *   b : device double[d] or NULL (rounded to float when dtype = MSK_F32).
+ *   Y : device, row-major k x ncol, leading dimension ldy >= ncol, type dtype;
+ *       overwritten (the kernel zeroes it first).  16-byte aligned.
+ *   strategy : msk_cs_strategy; ws/ws_bytes : scratch (msk_cs_workspace).
+ * Errors: -1 A NULL, -2 bad dtype, -3 d < 0, -4 n < 0, -5 lda < d,
+ *   -7 k < 1, -9 Y NULL, -10 ldy < ncol, -11 bad strategy,
+ *   MSK_ENOMEM ws too small, MSK_ENOTSUP d >= 2^31 for SORTED. */
+int cs_sketch(const void *A, int dtype, int64_t d, int64_t n, int64_t lda,
+              const double *b, int64_t k, uint64_t seed, void *Y, int64_t ldy,
+              int strategy, void *ws, size_t ws_bytes, void *stream);
+
+/* ---- Multisketch (Count-Gauss) ----------------------------------------- */
+
+/* Scratch bytes ms_sketch needs for these sizes (ncol = n + with_b). */
+size_t msk_ms_workspace(int64_t d, int64_t n, int with_b, int64_t k, int64_t p,
+                        int dtype, int gemm_prec, int strategy);
+
+/* Z = G (S [A b]): CountSketch to k rows, then the p x k Gaussian G
+ * (Section 1 "Count-Gauss"; Section 6.2 uses k = 2n^2).  A, b, dtype, k,
+ * seed, strategy as in cs_sketch; the Gaussian uses the same seed (tag 2).
+ *   gemm_prec : msk_gemm_prec, the arithmetic of Z = G Y.
+ *   Z : device double, column-major p x ncol, leading dimension ldz >= p.
+ * Errors as cs_sketch, plus -8 p < 1, -10 bad gemm_prec, -11 Z NULL,
+ *   -12 ldz < p, MSK_ENOTSUP gemm_prec F64 with dtype F32 is allowed, every
+ *   other combination too; MSK_ENOTSUP only for tensor paths on sizes over
+ *   the documented limits (p <= 2^20, ncol <= 512). */
+int ms_sketch(const void *A, int dtype, int64_t d, int64_t n, int64_t lda,
+              const double *b, int64_t k, int64_t p, uint64_t seed,
+              int gemm_prec, void *Z, int64_t ldz, int strategy, void *ws,
+              size_t ws_bytes, void *stream);
+
+/* ---- Dense building blocks (Algorithm 1 steps 2-3) ----------------------- */
+
+/* Scratch bytes msk_gemm needs. */
+size_t msk_gemm_workspace(int64_t p, int64_t k, int64_t ncol, int gemm_prec);
+
+/* Z = G Y with G the counter-generated p x k Gaussian of `seed` (generated
+ * into ws) and Y given: the second stage of ms_sketch on its own.
+ *   Y : device, row-major k x ncol (ldy), double when gemm_prec = F64, float
+ *       otherwise; Z : device double column-major p x ncol (ldz). */
+int msk_gemm(uint64_t seed, int64_t p, int64_t k, int64_t ncol, const void *Y,
+             int64_t ldy, int gemm_prec, double *Z, int64_t ldz, void *ws,
+             size_t ws_bytes, void *stream);
+
+/* In-place Householder QR of the m x c column-major FP64 matrix W (ldw >= m,
+ * m >= c): on return the upper triangle of W[0:c, 0:c] holds R with
+ * R[j][j] = -sign(x_0) ||x|| (sign(0) = +1), the GeQRF step of Section 6.1;
+ * the strictly lower part is overwritten with zeros.  One thread-block
+ * cluster of up to 16 CTAs factors the matrix with the columns split across
+ * the CTAs' shared memory.  Limits: m <= 2048, c <= 512.
+ * Errors: -2 m < c or m > 2048, -3 c < 1 or c > 512, -4 ldw < m. */
+int msk_householder_qr(double *W, int64_t m, int64_t c, int64_t ldw,
+                       void *stream);
+
+/* Solve R x = rhs (upper triangular n x n, column-major, ldr; x may alias
+ * rhs).  Returns j+1 (positive) on an exactly zero pivot R[j][j] — the value
+ * is only known after the stream is synchronised, so this entry point
+ * synchronises `stream`. */
+int msk_trsv_upper(const double *R, int64_t n, int64_t ldr, const double *rhs,
+                   double *x, void *stream);
+
+/* ---- Least squares -------------------------------------------------------- */
+
+/* Scratch bytes ms_lstsq needs. */
+size_t msk_lstsq_workspace(int64_t d, int64_t n, int64_t k, int64_t p,
+                           int dtype, int gemm_prec, int refine);
+
+/* Multisketched least squares min ||b - A x||.
+ *   refine = 0 : sketch-and-solve, Algorithm 1: Z = G S [A b] (p x (n+1)),
+ *     Householder QR of Z, x = R11^{-1} (Q^T z) with Q^T z = R[0:n, n].
+ *   refine = 1 : then sketch-and-precondition refinement (the iterative
+ *     route Section 6 cites, Blendenpik / LSRN): conjugate gradients on the
+ *     normal equations right-preconditioned by R11, with residuals
+ *     r = b - A x and A^T r accumulated in FP64, until the relative residual
+ *     changes by at most tol * relres, or max_iter iterations.
+ *   A : device column-major d x n (lda), dtype F64 or F32; b : device double[d].
+ *   x : device double[n] (output).
+ *   info : host msk_lstsq_info* or NULL; when non-NULL the stream is
+ *     synchronised and relres fields are filled.
+ * Returns MSK_OK; MSK_ENOCONV if refinement hit max_iter; j+1 if R11 has an
+ * exactly zero pivot at column j; negative for bad arguments (-1 A, -2 dtype,
+ * -3 d < n, -4 n < 1, -5 lda, -6 b, -7 k < n+1, -8 p < n+1 or p > k,
+ * -10 gemm_prec, -11 refine, -14 x, MSK_ENOMEM ws). */
+int ms_lstsq(const void *A, int dtype, int64_t d, int64_t n, int64_t lda,
+             const double *b, int64_t k, int64_t p, uint64_t seed,
+             int gemm_prec, int refine, double tol, int32_t max_iter,
+             double *x, msk_lstsq_info *info, void *ws, size_t ws_bytes,
+             void *stream);
+
+/* Scratch bytes ne_lstsq needs. */
+size_t msk_ne_workspace(int64_t d, int64_t n);
+
+/* Normal equations (Section 6.3): Gm = A^T A and y = A^T b in one FP64 pass,
+ * Cholesky Gm = R^T R, x = R^{-1} (R^{-T} y).
+ *   A : device double column-major d x n (lda); b : device double[d];
+ *   x : device double[n].  Synchronises `stream` to read the Cholesky status.
+ * Returns MSK_OK, or j+1 when pivot j of the Cholesky factorisation is not
+ * positive (A^T A numerically not positive definite; x is then NaN). */
+int ne_lstsq(const double *A, int64_t d, int64_t n, int64_t lda,
+             const double *b, double *x, void *ws, size_t ws_bytes,
+             void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MSKETCH_H */
