@@ -1,0 +1,298 @@
+"""Python binding of libmsketch (include/msketch.h): GPU CountSketch,
+Count-Gauss multisketch and sketched least squares on GB300.
+
+Argument marshalling only: every numeric step runs in the CUDA library.  The
+functions take torch CUDA tensors (PyTorch provides device memory and
+streams), check shapes/layouts, allocate the caller-side workspace the C ABI
+asks for, and raise MskError on a non-zero status.  There is no CPU path: if
+libmsketch.so is missing, importing the library raises.
+
+Layouts: A is d x n column-major (a tensor with stride (1, lda), e.g. the
+transpose of a contiguous (n, lda) tensor sliced to d columns); Y is k x ncol
+row-major (stride (ldy, 1)); Z is p x ncol column-major.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmsketch.so")
+
+MSK_F64, MSK_F32 = 0, 1
+GEMM_F64, GEMM_F32, GEMM_BF16, GEMM_F16, GEMM_BF16X3 = 0, 1, 2, 3, 4
+CS_ATOMIC, CS_SORTED = 0, 1
+MSK_OK, MSK_ENOCONV, MSK_ENOMEM, MSK_ETIMEOUT, MSK_ECUDA, MSK_ENOTSUP, MSK_EBUSY = (
+    0, 1001, 1002, 1003, 1004, 1005, 1006)
+
+GEMM_PRECS = {"f64": GEMM_F64, "f32": GEMM_F32, "bf16": GEMM_BF16, "f16": GEMM_F16,
+              "bf16x3": GEMM_BF16X3}
+
+# Names of every function include/msketch.h declares (checked by the tests).
+EXPORTS = ("msk_version", "msk_last_error", "cs_hash", "ms_gaussian", "msk_cs_workspace",
+           "cs_sketch", "msk_ms_workspace", "ms_sketch", "msk_gemm_workspace", "msk_gemm",
+           "msk_householder_qr", "msk_trsv_upper", "msk_lstsq_workspace", "ms_lstsq",
+           "msk_ne_workspace", "ne_lstsq")
+
+
+class MskError(RuntimeError):
+    def __init__(self, fn, code, detail=""):
+        self.code = code
+        super().__init__(f"{fn} returned {code}{(': ' + detail) if detail else ''}")
+
+
+class LstsqInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("relres", ctypes.c_double), ("relres_sns", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libmsketch.so (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise OSError(f"libmsketch.so not built at {path}; run paper_2508_14209_gb300.build.build()")
+        L = ctypes.CDLL(path)
+        _declare(L)
+        _lib = L
+    return _lib
+
+
+_p, _i64, _u64, _int, _sz, _dbl, _i32 = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64,
+                                         ctypes.c_int, ctypes.c_size_t, ctypes.c_double,
+                                         ctypes.c_int32)
+
+
+def _declare(L):
+    sig = {
+        "msk_version": (ctypes.c_char_p, []),
+        "msk_last_error": (ctypes.c_char_p, []),
+        "cs_hash": (_int, [_u64, _i64, _i64, _i64, _p, _p, _p]),
+        "ms_gaussian": (_int, [_u64, _i64, _i64, _int, _p, _i64, _p]),
+        "msk_cs_workspace": (_sz, [_i64, _i64, _i64, _int, _int]),
+        "cs_sketch": (_int, [_p, _int, _i64, _i64, _i64, _p, _i64, _u64, _p, _i64, _int, _p, _sz, _p]),
+        "msk_ms_workspace": (_sz, [_i64, _i64, _int, _i64, _i64, _int, _int, _int]),
+        "ms_sketch": (_int, [_p, _int, _i64, _i64, _i64, _p, _i64, _i64, _u64, _int, _p, _i64, _int,
+                             _p, _sz, _p]),
+        "msk_gemm_workspace": (_sz, [_i64, _i64, _i64, _int]),
+        "msk_gemm": (_int, [_u64, _i64, _i64, _i64, _p, _i64, _int, _p, _i64, _p, _sz, _p]),
+        "msk_householder_qr": (_int, [_p, _i64, _i64, _i64, _p]),
+        "msk_trsv_upper": (_int, [_p, _i64, _i64, _p, _p, _p]),
+        "msk_lstsq_workspace": (_sz, [_i64, _i64, _i64, _i64, _int, _int, _int]),
+        "ms_lstsq": (_int, [_p, _int, _i64, _i64, _i64, _p, _i64, _i64, _u64, _int, _int, _dbl, _i32,
+                            _p, ctypes.POINTER(LstsqInfo), _p, _sz, _p]),
+        "msk_ne_workspace": (_sz, [_i64, _i64]),
+        "ne_lstsq": (_int, [_p, _i64, _i64, _i64, _p, _p, _p, _sz, _p]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+
+
+def version() -> str:
+    return load().msk_version().decode()
+
+
+def _check(fn, rc, ok=(MSK_OK,)):
+    if rc not in ok:
+        raise MskError(fn, rc, load().msk_last_error().decode())
+    return rc
+
+
+def _stream(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _dtype_code(t):
+    if t.dtype == torch.float64:
+        return MSK_F64
+    if t.dtype == torch.float32:
+        return MSK_F32
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def _colmajor(A):
+    """(lda) of a d x n column-major tensor view."""
+    if A.dim() != 2:
+        raise ValueError("A must be 2-D")
+    d, n = A.shape
+    if d > 1 and A.stride(0) != 1:
+        raise ValueError("A must be column-major (stride(0) == 1)")
+    lda = A.stride(1) if n > 1 else max(d, 1)
+    return max(lda, max(d, 1))
+
+
+def _cuda(t, name):
+    if t is not None and not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+
+
+def workspace(nbytes, device):
+    return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
+
+
+def colmajor(d, n, dtype, device, lda=None):
+    """Uninitialised d x n column-major tensor (leading dimension lda)."""
+    lda = d if lda is None else lda
+    buf = torch.empty((max(n, 1), max(lda, 1)), dtype=dtype, device=device)
+    return buf[:n, :d].t()
+
+
+# ---------------------------------------------------------------------------
+
+def cs_hash(seed, i0, count, k, h=None, s=None, stream=None, device="cuda"):
+    """Buckets h(i) (uint32 stored in int32 tensor) and signs s(i) of rows
+    i0..i0+count-1."""
+    if h is None:
+        h = torch.empty(count, dtype=torch.int32, device=device)
+    if s is None:
+        s = torch.empty(count, dtype=torch.int8, device=device)
+    _check("cs_hash", load().cs_hash(seed & (2**64 - 1), i0, count, k, _ptr(h), _ptr(s), _stream(stream)))
+    return h, s
+
+
+_PREC_DTYPE = {GEMM_F64: torch.float64, GEMM_F32: torch.float32, GEMM_BF16: torch.bfloat16,
+               GEMM_F16: torch.float16}
+
+
+def ms_gaussian(seed, p, k, out_prec=GEMM_F32, G=None, stream=None, device="cuda"):
+    """The p x k Gaussian (row-major) of the multisketch's second stage."""
+    if G is None:
+        G = torch.empty((p, k), dtype=_PREC_DTYPE[out_prec], device=device)
+    _check("ms_gaussian", load().ms_gaussian(seed & (2**64 - 1), p, k, out_prec, _ptr(G), G.stride(0),
+                                             _stream(stream)))
+    return G
+
+
+def msk_cs_workspace(d, n, k, dtype, strategy):
+    return load().msk_cs_workspace(d, n, k, dtype, strategy)
+
+
+def cs_sketch(A, k, seed, b=None, Y=None, strategy=CS_ATOMIC, ws=None, stream=None):
+    """Y = S [A b] (k x ncol, row-major, A's dtype)."""
+    _cuda(A, "A"), _cuda(b, "b")
+    d, n = A.shape
+    lda = _colmajor(A)
+    dt = _dtype_code(A)
+    ncol = n + (0 if b is None else 1)
+    if b is not None and (b.dtype != torch.float64 or b.numel() != d):
+        raise ValueError("b must be float64 of length d")
+    if Y is None:
+        Y = torch.empty((k, ncol), dtype=A.dtype, device=A.device)
+    need = msk_cs_workspace(d, n, k, dt, strategy)
+    if ws is None and need:
+        ws = workspace(need, A.device)
+    _check("cs_sketch", load().cs_sketch(_ptr(A), dt, d, n, lda, _ptr(b), k, seed & (2**64 - 1), _ptr(Y),
+                                         Y.stride(0), strategy, _ptr(ws),
+                                         0 if ws is None else ws.numel(), _stream(stream)))
+    return Y
+
+
+def msk_ms_workspace(d, n, with_b, k, p, dtype, gemm_prec, strategy=CS_ATOMIC):
+    return load().msk_ms_workspace(d, n, int(with_b), k, p, dtype, gemm_prec, strategy)
+
+
+def ms_sketch(A, k, p, seed, b=None, gemm_prec=GEMM_F64, Z=None, strategy=CS_ATOMIC, ws=None,
+              stream=None):
+    """Z = G S [A b] (p x ncol, column-major FP64)."""
+    _cuda(A, "A"), _cuda(b, "b")
+    d, n = A.shape
+    lda = _colmajor(A)
+    dt = _dtype_code(A)
+    ncol = n + (0 if b is None else 1)
+    if Z is None:
+        Z = colmajor(p, ncol, torch.float64, A.device)
+    need = msk_ms_workspace(d, n, b is not None, k, p, dt, gemm_prec, strategy)
+    if ws is None:
+        ws = workspace(need, A.device)
+    _check("ms_sketch", load().ms_sketch(_ptr(A), dt, d, n, lda, _ptr(b), k, p, seed & (2**64 - 1),
+                                         gemm_prec, _ptr(Z), _colmajor(Z), strategy, _ptr(ws), ws.numel(),
+                                         _stream(stream)))
+    return Z
+
+
+def msk_gemm_workspace(p, k, ncol, gemm_prec):
+    return load().msk_gemm_workspace(p, k, ncol, gemm_prec)
+
+
+def msk_gemm(seed, p, Y, gemm_prec=GEMM_F64, Z=None, ws=None, stream=None):
+    """Z = G Y with G the seed's p x k Gaussian; Y row-major k x ncol
+    (float64 for GEMM_F64, float32 otherwise)."""
+    k, ncol = Y.shape
+    if Z is None:
+        Z = colmajor(p, ncol, torch.float64, Y.device)
+    if ws is None:
+        ws = workspace(msk_gemm_workspace(p, k, ncol, gemm_prec), Y.device)
+    _check("msk_gemm", load().msk_gemm(seed & (2**64 - 1), p, k, ncol, _ptr(Y), Y.stride(0), gemm_prec,
+                                       _ptr(Z), _colmajor(Z), _ptr(ws), ws.numel(), _stream(stream)))
+    return Z
+
+
+def msk_householder_qr(W, stream=None):
+    """In-place Householder QR of the m x c column-major FP64 W; returns W."""
+    m, c = W.shape
+    _check("msk_householder_qr", load().msk_householder_qr(_ptr(W), m, c, _colmajor(W), _stream(stream)))
+    return W
+
+
+def msk_trsv_upper(R, rhs, x=None, stream=None):
+    n = R.shape[0]
+    if x is None:
+        x = torch.empty(n, dtype=torch.float64, device=R.device)
+    rc = load().msk_trsv_upper(_ptr(R), n, _colmajor(R), _ptr(rhs), _ptr(x), _stream(stream))
+    if rc < 0 or rc >= 1000:
+        _check("msk_trsv_upper", rc)
+    return x, rc
+
+
+def msk_lstsq_workspace(d, n, k, p, dtype, gemm_prec, refine):
+    return load().msk_lstsq_workspace(d, n, k, p, dtype, gemm_prec, int(refine))
+
+
+def ms_lstsq(A, b, k, p, seed, gemm_prec=GEMM_F64, refine=False, tol=1e-10, max_iter=50, x=None,
+             ws=None, stream=None, want_info=True):
+    """Multisketched least squares; returns (x, info dict, status)."""
+    _cuda(A, "A"), _cuda(b, "b")
+    d, n = A.shape
+    dt = _dtype_code(A)
+    if x is None:
+        x = torch.empty(n, dtype=torch.float64, device=A.device)
+    if ws is None:
+        ws = workspace(msk_lstsq_workspace(d, n, k, p, dt, gemm_prec, refine), A.device)
+    info = LstsqInfo()
+    rc = load().ms_lstsq(_ptr(A), dt, d, n, _colmajor(A), _ptr(b), k, p, seed & (2**64 - 1), gemm_prec,
+                         int(refine), tol, max_iter, _ptr(x), ctypes.byref(info) if want_info else None,
+                         _ptr(ws), ws.numel(), _stream(stream))
+    if rc < 0 or rc in (MSK_ENOMEM, MSK_ECUDA, MSK_ENOTSUP, MSK_ETIMEOUT):
+        _check("ms_lstsq", rc)
+    return x, {"iters": info.iters, "converged": info.converged, "relres": info.relres,
+               "relres_sns": info.relres_sns}, rc
+
+
+def msk_ne_workspace(d, n):
+    return load().msk_ne_workspace(d, n)
+
+
+def ne_lstsq(A, b, x=None, ws=None, stream=None):
+    """Normal-equations least squares; returns (x, status) — status j+1 > 0
+    when the Cholesky pivot j is not positive."""
+    d, n = A.shape
+    if x is None:
+        x = torch.empty(n, dtype=torch.float64, device=A.device)
+    if ws is None:
+        ws = workspace(msk_ne_workspace(d, n), A.device)
+    rc = load().ne_lstsq(_ptr(A), d, n, _colmajor(A), _ptr(b), _ptr(x), _ptr(ws), ws.numel(), _stream(stream))
+    if rc < 0 or rc >= 1000:
+        _check("ne_lstsq", rc)
+    return x, rc

@@ -1,0 +1,196 @@
+// api.cu — the extern "C" entry points of libmsketch for the sketching steps
+// (hash hook, Gaussian hook, CountSketch, multisketch, Gaussian-stage GEMM):
+// argument checks, workspace carving, and the launch sequence on the caller's
+// stream.  Every numeric step runs in this library's kernels.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+
+#include "msk_device.cuh"
+#include "msk_internal.h"
+
+namespace msk {
+
+static thread_local char g_last_error[256] = {0};
+
+int cuda_fail(cudaError_t e, const char* where) {
+  std::snprintf(g_last_error, sizeof(g_last_error), "%s: %s", where, cudaGetErrorString(e));
+  return MSK_ECUDA;
+}
+
+int num_sms() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
+  return sms > 0 ? sms : 1;
+}
+
+static size_t dtype_size(int dtype) { return dtype == MSK_F64 ? 8 : 4; }
+
+// Row pitch of the CountSketch Y inside ms_sketch's workspace: FP32 rows are
+// padded to 4 elements so the vector reductions stay 16-byte aligned.
+static int64_t ws_ldy(int64_t ncol, int dtype) {
+  return dtype == MSK_F32 ? (ncol + 3) / 4 * 4 : ncol;
+}
+
+static bool is_tensor_prec(int prec) {
+  return prec == MSK_GEMM_BF16 || prec == MSK_GEMM_F16 || prec == MSK_GEMM_BF16X3;
+}
+
+}  // namespace msk
+
+namespace msk {
+size_t tc_gemm_workspace(int64_t p, int64_t k, int64_t ncol, int prec);
+// Z = G Y for a Y of element type y_dtype (FP64 or FP32); the tensor-core
+// precisions take FP32 Y only.
+int gemm_stage(uint64_t seed, int64_t p, int64_t k, int64_t ncol, const void* Y, int y_dtype,
+               int64_t ldy, int gemm_prec, double* Z, int64_t ldz, void* ws, size_t ws_bytes,
+               cudaStream_t st) {
+  const uint64_t gkey = stream_key(seed, kTagGauss);
+  if (is_tensor_prec(gemm_prec)) {
+    if (y_dtype != MSK_F32) return MSK_ENOTSUP;
+    return launch_tc_gemm(gkey, p, k, ncol, static_cast<const float*>(Y), ldy, gemm_prec, Z, ldz,
+                          ws, ws_bytes, st);
+  }
+  Carve cv(ws, ws_bytes);
+  float* G = static_cast<float*>(cv.take((size_t)p * k * sizeof(float)));
+  if (!G) return MSK_ENOMEM;
+  int rc = launch_gaussian(gkey, p, k, MSK_GEMM_F32, G, k, st);
+  if (rc) return rc;
+  const size_t rest_off = align_up(cv.used, 256);
+  if (rest_off > ws_bytes) return MSK_ENOMEM;
+  return launch_gemm_simt(G, k, Y, y_dtype == MSK_F64, ldy, gemm_prec == MSK_GEMM_F64, p, k, ncol,
+                          Z, ldz, cv.base + rest_off, ws_bytes - rest_off, st);
+}
+}  // namespace msk
+
+using namespace msk;
+
+extern "C" {
+
+const char* msk_version(void) { return "msketch 0.1 (sm_103a)"; }
+
+const char* msk_last_error(void) { return g_last_error; }
+
+int cs_hash(uint64_t seed, int64_t i0, int64_t count, int64_t k, uint32_t* h, int8_t* s,
+            void* stream) {
+  if (count < 0) return -3;
+  if (k < 1 || k > 0xFFFFFFFFLL) return -4;
+  if (i0 < 0) return -2;
+  return launch_cs_hash(stream_key(seed, kTagHash), i0, count, (uint32_t)k, h, s,
+                        as_stream(stream));
+}
+
+int ms_gaussian(uint64_t seed, int64_t p, int64_t k, int out_prec, void* G, int64_t ldg,
+                void* stream) {
+  if (p < 1 || p >= (1LL << 24)) return -2;
+  if (k < 1) return -3;
+  if (out_prec < MSK_GEMM_F64 || out_prec > MSK_GEMM_F16) return -4;
+  if (!G) return -5;
+  if (ldg < k) return -6;
+  return launch_gaussian(stream_key(seed, kTagGauss), p, k, out_prec, G, ldg, as_stream(stream));
+}
+
+size_t msk_cs_workspace(int64_t d, int64_t n, int64_t k, int dtype, int strategy) {
+  (void)n;
+  (void)dtype;
+  if (strategy == MSK_CS_SORTED) return cs_sorted_workspace(d, k);
+  return 0;
+}
+
+int cs_sketch(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, const double* b,
+              int64_t k, uint64_t seed, void* Y, int64_t ldy, int strategy, void* ws,
+              size_t ws_bytes, void* stream) {
+  if (!A && d > 0 && n > 0) return -1;
+  if (dtype != MSK_F64 && dtype != MSK_F32) return -2;
+  if (d < 0) return -3;
+  if (n < 0) return -4;
+  if (lda < (d > 1 ? d : 1)) return -5;
+  if (k < 1 || k > 0xFFFFFFFFLL) return -7;
+  const int64_t ncol = n + (b ? 1 : 0);
+  if (!Y) return -9;
+  if (ldy < ncol) return -10;
+  if (strategy != MSK_CS_ATOMIC && strategy != MSK_CS_SORTED) return -11;
+  cudaStream_t st = as_stream(stream);
+  const uint64_t key = stream_key(seed, kTagHash);
+  if (strategy == MSK_CS_ATOMIC)
+    return launch_cs_atomic(A, dtype, d, n, lda, b, (uint32_t)k, key, Y, ldy, st);
+  if (d >= (1LL << 31) || k >= (1LL << 31)) return MSK_ENOTSUP;
+  if (ws_bytes < cs_sorted_workspace(d, k)) return MSK_ENOMEM;
+  return launch_cs_sorted(A, dtype, d, n, lda, b, (uint32_t)k, key, Y, ldy, ws, ws_bytes, st);
+}
+
+size_t msk_gemm_workspace(int64_t p, int64_t k, int64_t ncol, int gemm_prec) {
+  Need nd;
+  if (is_tensor_prec(gemm_prec)) {
+    nd.add(tc_gemm_workspace(p, k, ncol, gemm_prec));
+  } else {
+    nd.add((size_t)p * k * sizeof(float));  // G in binary32
+    nd.add(gemm_simt_workspace(p, k, ncol, gemm_prec == MSK_GEMM_F64));
+  }
+  return nd.used;
+}
+
+int msk_gemm(uint64_t seed, int64_t p, int64_t k, int64_t ncol, const void* Y, int64_t ldy,
+             int gemm_prec, double* Z, int64_t ldz, void* ws, size_t ws_bytes, void* stream) {
+  if (p < 1 || p >= (1LL << 24)) return -2;
+  if (k < 1) return -3;
+  if (ncol < 1) return -4;
+  if (!Y) return -5;
+  if (ldy < ncol) return -6;
+  if (gemm_prec < MSK_GEMM_F64 || gemm_prec > MSK_GEMM_BF16X3) return -7;
+  if (!Z) return -8;
+  if (ldz < p) return -9;
+  if (ws_bytes < msk_gemm_workspace(p, k, ncol, gemm_prec)) return MSK_ENOMEM;
+  const int y_dtype = gemm_prec == MSK_GEMM_F64 ? MSK_F64 : MSK_F32;
+  return gemm_stage(seed, p, k, ncol, Y, y_dtype, ldy, gemm_prec, Z, ldz, ws, ws_bytes,
+                    as_stream(stream));
+}
+
+size_t msk_ms_workspace(int64_t d, int64_t n, int with_b, int64_t k, int64_t p, int dtype,
+                        int gemm_prec, int strategy) {
+  const int64_t ncol = n + (with_b ? 1 : 0);
+  const int ydt = is_tensor_prec(gemm_prec) ? MSK_F32 : dtype;
+  Need nd;
+  nd.add((size_t)k * ws_ldy(ncol, ydt) * dtype_size(ydt));  // Y
+  nd.add(msk_cs_workspace(d, n, k, ydt, strategy));
+  nd.add(msk_gemm_workspace(p, k, ncol, gemm_prec));
+  return nd.used;
+}
+
+int ms_sketch(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, const double* b,
+              int64_t k, int64_t p, uint64_t seed, int gemm_prec, void* Z, int64_t ldz,
+              int strategy, void* ws, size_t ws_bytes, void* stream) {
+  if (!A && d > 0 && n > 0) return -1;
+  if (dtype != MSK_F64 && dtype != MSK_F32) return -2;
+  if (d < 0) return -3;
+  if (n < 0) return -4;
+  if (lda < (d > 1 ? d : 1)) return -5;
+  if (k < 1 || k > 0xFFFFFFFFLL) return -7;
+  if (p < 1 || p >= (1LL << 24)) return -8;
+  if (gemm_prec < MSK_GEMM_F64 || gemm_prec > MSK_GEMM_BF16X3) return -10;
+  if (!Z) return -11;
+  if (ldz < p) return -12;
+  if (strategy != MSK_CS_ATOMIC && strategy != MSK_CS_SORTED) return -13;
+  const int64_t ncol = n + (b ? 1 : 0);
+  if (ncol < 1) return -4;
+  if (ws_bytes < msk_ms_workspace(d, n, b ? 1 : 0, k, p, dtype, gemm_prec, strategy))
+    return MSK_ENOMEM;
+  // The tensor-core paths take an FP32 CountSketch (dtype F32).
+  if (is_tensor_prec(gemm_prec) && dtype != MSK_F32) return MSK_ENOTSUP;
+  cudaStream_t st = as_stream(stream);
+  Carve cv(ws, ws_bytes);
+  const int64_t ldy = ws_ldy(ncol, dtype);
+  void* Y = cv.take((size_t)k * ldy * dtype_size(dtype));
+  const size_t cs_ws = msk_cs_workspace(d, n, k, dtype, strategy);
+  void* csw = cv.take(cs_ws);
+  if (!Y) return MSK_ENOMEM;
+  int rc = cs_sketch(A, dtype, d, n, lda, b, k, seed, Y, ldy, strategy, csw, cs_ws, stream);
+  if (rc) return rc;
+  const size_t rest_off = align_up(cv.used, 256);
+  return gemm_stage(seed, p, k, ncol, Y, dtype, ldy, gemm_prec, static_cast<double*>(Z), ldz,
+                    cv.base + rest_off, ws_bytes - rest_off, st);
+}
+
+}  // extern "C"

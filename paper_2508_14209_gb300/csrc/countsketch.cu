@@ -1,0 +1,454 @@
+// countsketch.cu — the CountSketch Y = S [A b] (Definition 3 and its row form,
+// Section 4) for column-major A, row-major Y.
+//
+// ATOMIC strategy (the scatter-add of Algorithm 2, rebuilt for GB300):
+//   A tile of 32 consecutive rows x all columns is read with coalesced column
+//   loads (lane = row), transposed through shared memory, and each row is added
+//   to its bucket row Y[h(i), :] by one warp with coalesced L2 reductions
+//   (lane = column), so every reduction instruction covers whole 32-byte
+//   sectors of Y.  Bucket and sign are hashed on the fly (Section 8's hashed
+//   CountSketch); nothing but A is read.  FP64 uses red.add.f64; FP32 uses
+//   4-wide red.add.v4.f32 on 16-byte aligned rows of Y.
+//   Two shared-memory buffers alternate, so one __syncthreads per tile
+//   suffices; the grid is persistent over tiles.
+//
+// SORTED strategy (deterministic): a counting sort of the rows by bucket
+//   (histogram, exclusive scan, scatter, then each bucket's row list sorted in
+//   increasing row order), then one warp per bucket sums its rows in that
+//   order, lane = column.  Same result bit for bit on every run.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "msk_device.cuh"
+#include "msk_internal.h"
+
+namespace msk {
+
+// ---------------------------------------------------------------------------
+// cs_hash hook: materialise h(i), s(i).
+__global__ void cs_hash_kernel(uint64_t key, int64_t i0, int64_t count, uint32_t k,
+                               uint32_t* __restrict__ h, int8_t* __restrict__ s) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t z = draw(key, (uint64_t)(i0 + t));
+    if (h) h[t] = bucket_of(z, k);
+    if (s) s[t] = negative_of(z) ? (int8_t)-1 : (int8_t)1;
+  }
+}
+
+int launch_cs_hash(uint64_t key, int64_t i0, int64_t count, uint32_t k, uint32_t* h,
+                   int8_t* s, cudaStream_t st) {
+  if (count == 0) return MSK_OK;
+  int64_t blocks = std::min<int64_t>((count + 255) / 256, (int64_t)num_sms() * 16);
+  cs_hash_kernel<<<(unsigned)blocks, 256, 0, st>>>(key, i0, count, k, h, s);
+  MSK_CHECK_LAUNCH("cs_hash_kernel");
+  return MSK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// ATOMIC strategy.
+constexpr int kCsRows = 32;    // rows per tile (one per lane in the load phase)
+constexpr int kCsWarps = 8;    // warps per CTA
+constexpr int kCsThreads = kCsWarps * 32;
+// Columns per launch (wider problems are split): two FP64 tiles of 32 rows x
+// 385 columns, or two FP32 tiles of 32 x 516, fit in 227 KB of shared memory.
+constexpr int kCsMaxColsF64 = 384;
+constexpr int kCsMaxColsF32 = 512;
+
+template <typename T>
+struct CsParams {
+  const T* A;
+  int64_t d, lda;
+  int ncol_a;          // columns taken from A in this launch
+  const double* b;     // extra column (after the A columns) or null
+  int ncol;            // ncol_a + (b != null)
+  uint32_t k;
+  uint64_t key;
+  T* Y;
+  int64_t ldy;
+  int pitch;           // shared-memory row pitch (elements)
+};
+
+__device__ __forceinline__ void red_add(double* p, double v) {
+  asm volatile("red.relaxed.gpu.global.add.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+__device__ __forceinline__ void red_add(float* p, float v) {
+  asm volatile("red.relaxed.gpu.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+__device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, float d) {
+  asm volatile("red.relaxed.gpu.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a),
+               "f"(b), "f"(c), "f"(d)
+               : "memory");
+}
+
+// Shared-memory tile layout: row r at r * pitch.  FP64: one column per
+// store, odd pitch, so the 32 transposing stores of a warp (lane = row) and
+// the row reads (lane = column) are both conflict-free.  FP32: a lane stores
+// 4 consecutive columns of its row as one 16-byte vector and pitch/4 is odd,
+// so the 8 lanes of each store wavefront hit 8 distinct 16-byte bank groups;
+// the row reads are 16-byte vectors of consecutive chunks.
+template <typename T>
+__device__ __forceinline__ T load_col(const CsParams<T>& P, int64_t i, int j) {
+  if (j < P.ncol_a) return __ldcs(P.A + i + (int64_t)j * P.lda);
+  if (j < P.ncol) return (T)__ldcs(P.b + i);
+  return (T)0;
+}
+
+// QMAX = column slots (FP64) or 4-column groups (FP32) per lane in the load
+// phase.
+template <typename T, int QMAX, bool VEC4>
+__global__ void __launch_bounds__(kCsThreads) cs_atomic_kernel(const CsParams<T> P) {
+  extern __shared__ __align__(16) unsigned char cs_smem[];
+  T* tiles = reinterpret_cast<T*>(cs_smem);
+  uint64_t* hz = reinterpret_cast<uint64_t*>(cs_smem + 2 * sizeof(T) * kCsRows * P.pitch);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t ntiles = (P.d + kCsRows - 1) / kCsRows;
+  constexpr bool kF32 = sizeof(T) == 4;
+  const int ngroups = (P.ncol + 3) >> 2;
+  int buf = 0;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, buf ^= 1) {
+    const int64_t i0 = t * kCsRows;
+    const int64_t i = i0 + lane;
+    const bool row_ok = i < P.d;
+    T* tile = tiles + buf * kCsRows * P.pitch;
+    if constexpr (kF32) {
+      // load phase: warp w fetches column groups w, w+8, ... (4 columns each)
+      float4 v[QMAX];
+#pragma unroll
+      for (int q = 0; q < QMAX; ++q) {
+        const int g = warp + q * kCsWarps;
+        float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (row_ok && g < ngroups) {
+          x.x = load_col(P, i, 4 * g);
+          x.y = load_col(P, i, 4 * g + 1);
+          x.z = load_col(P, i, 4 * g + 2);
+          x.w = load_col(P, i, 4 * g + 3);
+        }
+        v[q] = x;
+      }
+      if (warp == 0) hz[buf * kCsRows + lane] = row_ok ? draw(P.key, (uint64_t)i) : 0ull;
+#pragma unroll
+      for (int q = 0; q < QMAX; ++q) {
+        const int g = warp + q * kCsWarps;
+        if (g < ngroups) *reinterpret_cast<float4*>(&tile[lane * P.pitch + 4 * g]) = v[q];
+      }
+    } else {
+      // load phase: warp w fetches columns w, w+8, ... for rows i0..i0+31
+      T v[QMAX];
+#pragma unroll
+      for (int q = 0; q < QMAX; ++q) {
+        const int j = warp + q * kCsWarps;
+        v[q] = (row_ok && j < P.ncol) ? load_col(P, i, j) : (T)0;
+      }
+      if (warp == 0) hz[buf * kCsRows + lane] = row_ok ? draw(P.key, (uint64_t)i) : 0ull;
+#pragma unroll
+      for (int q = 0; q < QMAX; ++q) {
+        const int j = warp + q * kCsWarps;
+        if (j < P.ncol) tile[lane * P.pitch + j] = v[q];
+      }
+    }
+    __syncthreads();
+    // reduction phase: warp w adds rows w, w+8, w+16, w+24 into their buckets
+#pragma unroll
+    for (int rr = 0; rr < kCsRows / kCsWarps; ++rr) {
+      const int r = warp + rr * kCsWarps;
+      if (i0 + r >= P.d) break;
+      const uint64_t z = hz[buf * kCsRows + r];
+      T* yrow = P.Y + (int64_t)bucket_of(z, P.k) * P.ldy;
+      const bool neg = negative_of(z);
+      const T* trow = tile + r * P.pitch;
+      if constexpr (VEC4) {
+        const int full = P.ncol & ~3;
+        for (int c = lane * 4; c < full; c += 128) {
+          const float4 x = *reinterpret_cast<const float4*>(&trow[c]);
+          if (neg)
+            red_add_v4(reinterpret_cast<float*>(yrow) + c, -x.x, -x.y, -x.z, -x.w);
+          else
+            red_add_v4(reinterpret_cast<float*>(yrow) + c, x.x, x.y, x.z, x.w);
+        }
+        if (lane < P.ncol - full) {
+          const T x = trow[full + lane];
+          red_add(yrow + full + lane, neg ? -x : x);
+        }
+      } else {
+        for (int c = lane; c < P.ncol; c += 32) {
+          const T x = trow[c];
+          red_add(yrow + c, neg ? -x : x);
+        }
+      }
+    }
+  }
+}
+
+template <typename T, int QMAX, bool VEC4>
+static int launch_cs_atomic_t(const CsParams<T>& P, cudaStream_t st) {
+  const size_t smem = 2 * sizeof(T) * kCsRows * P.pitch + 2 * kCsRows * sizeof(uint64_t);
+  auto kern = cs_atomic_kernel<T, QMAX, VEC4>;
+  MSK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  MSK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kCsThreads, smem));
+  per_sm = std::max(per_sm, 1);
+  const int64_t ntiles = (P.d + kCsRows - 1) / kCsRows;
+  const int64_t grid = std::min<int64_t>(ntiles, (int64_t)num_sms() * per_sm);
+  if (grid <= 0) return MSK_OK;
+  kern<<<(unsigned)grid, kCsThreads, smem, st>>>(P);
+  MSK_CHECK_LAUNCH("cs_atomic_kernel");
+  return MSK_OK;
+}
+
+template <typename T>
+static int cs_atomic_chunk(CsParams<T> P, cudaStream_t st) {
+  if (sizeof(T) == 4) {
+    const bool vec4 = (P.ldy % 4 == 0) && ((reinterpret_cast<uintptr_t>(P.Y) & 15) == 0);
+    const int ngroups = (P.ncol + 3) / 4;
+    P.pitch = 4 * (ngroups | 1);  // pitch / 4 odd
+    const int q = (ngroups + kCsWarps - 1) / kCsWarps;
+    if (vec4) {
+      if (q <= 1) return launch_cs_atomic_t<T, 1, true>(P, st);
+      if (q <= 2) return launch_cs_atomic_t<T, 2, true>(P, st);
+      if (q <= 4) return launch_cs_atomic_t<T, 4, true>(P, st);
+      if (q <= 9) return launch_cs_atomic_t<T, 9, true>(P, st);
+      return launch_cs_atomic_t<T, 16, true>(P, st);
+    }
+    if (q <= 1) return launch_cs_atomic_t<T, 1, false>(P, st);
+    if (q <= 2) return launch_cs_atomic_t<T, 2, false>(P, st);
+    if (q <= 4) return launch_cs_atomic_t<T, 4, false>(P, st);
+    if (q <= 9) return launch_cs_atomic_t<T, 9, false>(P, st);
+    return launch_cs_atomic_t<T, 16, false>(P, st);
+  }
+  P.pitch = P.ncol | 1;  // odd pitch
+  const int q = (P.ncol + kCsWarps - 1) / kCsWarps;
+  if (q <= 1) return launch_cs_atomic_t<T, 1, false>(P, st);
+  if (q <= 4) return launch_cs_atomic_t<T, 4, false>(P, st);
+  if (q <= 8) return launch_cs_atomic_t<T, 8, false>(P, st);
+  if (q <= 17) return launch_cs_atomic_t<T, 17, false>(P, st);
+  if (q <= 33) return launch_cs_atomic_t<T, 33, false>(P, st);
+  return launch_cs_atomic_t<T, 64, false>(P, st);
+}
+
+template <typename T>
+static int cs_atomic_typed(const T* A, int64_t d, int64_t n, int64_t lda, const double* b,
+                           uint32_t k, uint64_t key, T* Y, int64_t ldy, cudaStream_t st) {
+  const int64_t ncol = n + (b ? 1 : 0);
+  MSK_CUDA(cudaMemset2DAsync(Y, (size_t)ldy * sizeof(T), 0, (size_t)ncol * sizeof(T), (size_t)k, st));
+  if (d == 0 || ncol == 0) return MSK_OK;
+  // Column chunks of at most kCsMaxColsF64/F32; b rides with the last chunk.
+  const int64_t maxc = sizeof(T) == 8 ? kCsMaxColsF64 : kCsMaxColsF32;
+  for (int64_t c0 = 0; c0 < ncol; c0 += maxc) {
+    const int64_t c1 = std::min<int64_t>(ncol, c0 + maxc);
+    CsParams<T> P{};
+    P.A = A + c0 * lda;
+    P.d = d;
+    P.lda = lda;
+    P.ncol_a = (int)(std::min<int64_t>(c1, n) - std::min<int64_t>(c0, n));
+    P.b = (b && c1 == ncol) ? b : nullptr;
+    P.ncol = (int)(c1 - c0);
+    P.k = k;
+    P.key = key;
+    P.Y = Y + c0;
+    P.ldy = ldy;
+    int rc = cs_atomic_chunk<T>(P, st);
+    if (rc) return rc;
+  }
+  return MSK_OK;
+}
+
+int launch_cs_atomic(const void* A, int dtype, int64_t d, int64_t n, int64_t lda,
+                     const double* b, uint32_t k, uint64_t key, void* Y, int64_t ldy,
+                     cudaStream_t st) {
+  if (dtype == MSK_F64)
+    return cs_atomic_typed<double>(static_cast<const double*>(A), d, n, lda, b, k, key,
+                                   static_cast<double*>(Y), ldy, st);
+  return cs_atomic_typed<float>(static_cast<const float*>(A), d, n, lda, b, k, key,
+                                static_cast<float*>(Y), ldy, st);
+}
+
+// ---------------------------------------------------------------------------
+// SORTED strategy (deterministic).
+//   ws layout: count[k] (u32), offs[k+1] (u32), cursor[k] (u32), perm[d] (u32)
+size_t cs_sorted_workspace(int64_t d, int64_t k) {
+  Need n;
+  n.add((size_t)k * 4);
+  n.add((size_t)(k + 1) * 4);
+  n.add((size_t)k * 4);
+  n.add((size_t)std::max<int64_t>(d, 1) * 4);
+  return n.used;
+}
+
+__global__ void cs_hist_kernel(uint64_t key, int64_t d, uint32_t k, uint32_t* __restrict__ count) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d;
+       i += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&count[bucket_of(draw(key, (uint64_t)i), k)], 1u);
+}
+
+// Single-CTA exclusive scan of count[0..k) into offs[0..k] (offs[k] = d).
+__global__ void cs_scan_kernel(const uint32_t* __restrict__ count, uint32_t k,
+                               uint32_t* __restrict__ offs) {
+  __shared__ uint32_t part[1024];
+  const uint32_t per = (k + blockDim.x - 1) / blockDim.x;
+  const uint32_t lo = threadIdx.x * per, hi = min(k, lo + per);
+  uint32_t s = 0;
+  for (uint32_t m = lo; m < hi; ++m) s += count[m];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+    uint32_t x = threadIdx.x >= (unsigned)off ? part[threadIdx.x - off] : 0u;
+    __syncthreads();
+    part[threadIdx.x] += x;
+    __syncthreads();
+  }
+  uint32_t run = part[threadIdx.x] - s;  // exclusive prefix of this thread's range
+  for (uint32_t m = lo; m < hi; ++m) {
+    offs[m] = run;
+    run += count[m];
+  }
+  if (threadIdx.x == blockDim.x - 1) offs[k] = part[threadIdx.x];
+}
+
+__global__ void cs_scatter_kernel(uint64_t key, int64_t d, uint32_t k,
+                                  const uint32_t* __restrict__ offs, uint32_t* __restrict__ cursor,
+                                  uint32_t* __restrict__ perm) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t m = bucket_of(draw(key, (uint64_t)i), k);
+    perm[offs[m] + atomicAdd(&cursor[m], 1u)] = (uint32_t)i;
+  }
+}
+
+// Sort each bucket's row list ascending (launched with 256 threads): bitonic
+// sort in shared memory for lists up to kSortCap, selection sort otherwise.
+constexpr int kSortCap = 2048;
+__global__ void cs_segsort_kernel(const uint32_t* __restrict__ offs, uint32_t k,
+                                  uint32_t* __restrict__ perm) {
+  __shared__ uint32_t keys[kSortCap];
+  for (uint32_t m = blockIdx.x; m < k; m += gridDim.x) {
+    const uint32_t lo = offs[m], len = offs[m + 1] - offs[m];
+    if (len <= 1) continue;
+    if (len <= (uint32_t)kSortCap) {
+      uint32_t P2 = 1;
+      while (P2 < len) P2 <<= 1;
+      for (uint32_t t = threadIdx.x; t < P2; t += blockDim.x)
+        keys[t] = t < len ? perm[lo + t] : 0xFFFFFFFFu;
+      __syncthreads();
+      for (uint32_t size = 2; size <= P2; size <<= 1)
+        for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+          for (uint32_t t = threadIdx.x; t < P2; t += blockDim.x) {
+            const uint32_t u = t ^ stride;
+            if (u > t) {
+              const bool up = (t & size) == 0;
+              const uint32_t a = keys[t], c = keys[u];
+              if ((a > c) == up) {
+                keys[t] = c;
+                keys[u] = a;
+              }
+            }
+          }
+          __syncthreads();
+        }
+      for (uint32_t t = threadIdx.x; t < len; t += blockDim.x) perm[lo + t] = keys[t];
+      __syncthreads();
+    } else {
+      // long list: selection sort, one block-wide argmin per position
+      __shared__ uint32_t rb[256], ra[256];
+      for (uint32_t pos = 0; pos + 1 < len; ++pos) {
+        uint32_t best = 0xFFFFFFFFu, best_at = pos;
+        for (uint32_t t = pos + threadIdx.x; t < len; t += blockDim.x) {
+          const uint32_t x = perm[lo + t];
+          if (x < best) {
+            best = x;
+            best_at = t;
+          }
+        }
+        rb[threadIdx.x] = best;
+        ra[threadIdx.x] = best_at;
+        __syncthreads();
+        for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+          if ((int)threadIdx.x < off && rb[threadIdx.x + off] < rb[threadIdx.x]) {
+            rb[threadIdx.x] = rb[threadIdx.x + off];
+            ra[threadIdx.x] = ra[threadIdx.x + off];
+          }
+          __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+          const uint32_t at = ra[0];
+          const uint32_t tmp = perm[lo + pos];
+          perm[lo + pos] = perm[lo + at];
+          perm[lo + at] = tmp;
+        }
+        __syncthreads();
+      }
+    }
+  }
+}
+
+// One warp per bucket: Y[m, c] = sum over the bucket's rows (ascending) of
+// s(i) [A b][i, c]; lane = column.
+template <typename T>
+__global__ void cs_bucket_sum_kernel(const T* __restrict__ A, int64_t lda, int64_t n,
+                                     const double* __restrict__ b, int ncol, uint32_t k,
+                                     uint64_t key, const uint32_t* __restrict__ offs,
+                                     const uint32_t* __restrict__ perm, T* __restrict__ Y,
+                                     int64_t ldy) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp_g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t m = warp_g; m < k; m += nwarps) {
+    const uint32_t lo = offs[m], hi = offs[m + 1];
+    for (int c0 = 0; c0 < ncol; c0 += 32) {
+      const int c = c0 + lane;
+      T acc = 0;
+      for (uint32_t t = lo; t < hi; ++t) {
+        const uint32_t i = perm[t];
+        const bool neg = negative_of(draw(key, (uint64_t)i));
+        if (c < ncol) {
+          const T x = c < n ? A[(int64_t)i + (int64_t)c * lda] : (T)b[i];
+          acc += neg ? -x : x;
+        }
+      }
+      if (c < ncol) Y[m * ldy + c] = acc;
+    }
+  }
+}
+
+int launch_cs_sorted(const void* A, int dtype, int64_t d, int64_t n, int64_t lda,
+                     const double* b, uint32_t k, uint64_t key, void* Y, int64_t ldy,
+                     void* ws, size_t ws_bytes, cudaStream_t st) {
+  Carve cv(ws, ws_bytes);
+  uint32_t* count = static_cast<uint32_t*>(cv.take((size_t)k * 4));
+  uint32_t* offs = static_cast<uint32_t*>(cv.take((size_t)(k + 1) * 4));
+  uint32_t* cursor = static_cast<uint32_t*>(cv.take((size_t)k * 4));
+  uint32_t* perm = static_cast<uint32_t*>(cv.take((size_t)std::max<int64_t>(d, 1) * 4));
+  if (!count || !offs || !cursor || !perm) return MSK_ENOMEM;
+  const int ncol = (int)(n + (b ? 1 : 0));
+  MSK_CUDA(cudaMemsetAsync(count, 0, (size_t)k * 4, st));
+  MSK_CUDA(cudaMemsetAsync(cursor, 0, (size_t)k * 4, st));
+  const int sms = num_sms();
+  const unsigned gb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((d + 255) / 256, sms * 16));
+  if (d > 0) {
+    cs_hist_kernel<<<gb, 256, 0, st>>>(key, d, k, count);
+    MSK_CHECK_LAUNCH("cs_hist_kernel");
+  }
+  cs_scan_kernel<<<1, 1024, 0, st>>>(count, k, offs);
+  MSK_CHECK_LAUNCH("cs_scan_kernel");
+  if (d > 0) {
+    cs_scatter_kernel<<<gb, 256, 0, st>>>(key, d, k, offs, cursor, perm);
+    MSK_CHECK_LAUNCH("cs_scatter_kernel");
+    cs_segsort_kernel<<<(unsigned)std::min<int64_t>(k, sms * 8), 256, 0, st>>>(offs, k, perm);
+    MSK_CHECK_LAUNCH("cs_segsort_kernel");
+  }
+  const unsigned gw = (unsigned)std::max<int64_t>(1, std::min<int64_t>((k + 7) / 8, sms * 16));
+  if (dtype == MSK_F64)
+    cs_bucket_sum_kernel<double><<<gw, 256, 0, st>>>(static_cast<const double*>(A), lda, n, b,
+                                                     ncol, k, key, offs, perm,
+                                                     static_cast<double*>(Y), ldy);
+  else
+    cs_bucket_sum_kernel<float><<<gw, 256, 0, st>>>(static_cast<const float*>(A), lda, n, b,
+                                                    ncol, k, key, offs, perm,
+                                                    static_cast<float*>(Y), ldy);
+  MSK_CHECK_LAUNCH("cs_bucket_sum_kernel");
+  return MSK_OK;
+}
+
+}  // namespace msk

@@ -1,0 +1,143 @@
+// gemm_simt.cu — the Gaussian stage Z = G Y on CUDA cores, in FP64 (G widened
+// exactly from binary32) or FP32 (Section 1 "Count-Gauss"; Section 6.1 does
+// this with a cuBLAS GEMM).  The output is tiny (p x ncol) and K = k is long,
+// so the K dimension is split across CTAs: CTA (mt, nt, s) computes a 64 x 64
+// tile of the partial product over K-slice s and writes it to the workspace;
+// a second kernel sums the slices in a fixed order (deterministic).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "msk_internal.h"
+
+namespace msk {
+
+constexpr int kGBM = 64, kGBN = 64, kGBK = 32, kGThreads = 256;
+
+struct GemmSplit {
+  int mt, nt, s;
+  int64_t kchunk;
+};
+
+static GemmSplit gemm_split(int64_t p, int64_t k, int64_t ncol) {
+  GemmSplit g;
+  g.mt = (int)((p + kGBM - 1) / kGBM);
+  g.nt = (int)((ncol + kGBN - 1) / kGBN);
+  const int64_t target = 2LL * num_sms();
+  int64_t s = std::max<int64_t>(1, target / std::max(1, g.mt * g.nt));
+  s = std::min<int64_t>(s, std::max<int64_t>(1, (k + kGBK - 1) / kGBK));
+  int64_t chunk = (k + s - 1) / s;
+  chunk = (chunk + kGBK - 1) / kGBK * kGBK;
+  g.kchunk = std::max<int64_t>(chunk, kGBK);
+  g.s = (int)((k + g.kchunk - 1) / g.kchunk);
+  if (g.s < 1) g.s = 1;
+  return g;
+}
+
+size_t gemm_simt_workspace(int64_t p, int64_t k, int64_t ncol, bool /*f64*/) {
+  GemmSplit g = gemm_split(p, k, ncol);
+  Need n;
+  n.add((size_t)g.s * p * ncol * sizeof(double));
+  return n.used;
+}
+
+// Partial tile: part[s][c * p + r] = sum_{m in slice s} G[r, m] Y[m, c].
+template <typename T, typename TY>
+__global__ void __launch_bounds__(kGThreads) gemm_simt_kernel(const float* __restrict__ G, int64_t ldg,
+                                                           const TY* __restrict__ Y, int64_t ldy,
+                                                           int64_t p, int64_t k, int64_t ncol,
+                                                           int64_t kchunk, double* __restrict__ part) {
+  __shared__ T Gs[kGBK][kGBM + 1];
+  __shared__ T Ys[kGBK][kGBN];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int64_t m0 = (int64_t)blockIdx.x * kGBM, n0 = (int64_t)blockIdx.y * kGBN;
+  const int64_t kb = (int64_t)blockIdx.z * kchunk, ke = (kb + kchunk < k) ? kb + kchunk : k;
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[a][c] = (T)0;
+  for (int64_t k0 = kb; k0 < ke; k0 += kGBK) {
+#pragma unroll
+    for (int q = 0; q < (kGBM * kGBK) / kGThreads; ++q) {
+      const int e = threadIdx.x + q * kGThreads;
+      const int r = e / kGBK, kk = e % kGBK;
+      const int64_t gr = m0 + r, gk = k0 + kk;
+      Gs[kk][r] = (gr < p && gk < ke) ? (T)G[gr * ldg + gk] : (T)0;
+    }
+#pragma unroll
+    for (int q = 0; q < (kGBN * kGBK) / kGThreads; ++q) {
+      const int e = threadIdx.x + q * kGThreads;
+      const int kk = e / kGBN, c = e % kGBN;
+      const int64_t gk = k0 + kk, gc = n0 + c;
+      Ys[kk][c] = (gk < ke && gc < ncol) ? (T)Y[gk * ldy + gc] : (T)0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < kGBK; ++kk) {
+      T av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = Gs[kk][ty + 16 * a];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) bv[c] = Ys[kk][tx + 16 * c];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[a][c] = fma(av[a], bv[c], acc[a][c]);
+    }
+    __syncthreads();
+  }
+  double* out = part + (int64_t)blockIdx.z * p * ncol;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int64_t r = m0 + ty + 16 * a, cc = n0 + tx + 16 * c;
+      if (r < p && cc < ncol) out[cc * p + r] = (double)acc[a][c];
+    }
+}
+
+// Z[r + c*ldz] = sum_{s=0}^{S-1} part[s][c*p + r], slices added in order.
+__global__ void splitk_reduce_kernel(const double* __restrict__ part, int S, int64_t p, int64_t ncol,
+                                     double* __restrict__ Z, int64_t ldz) {
+  const int64_t total = p * ncol;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int q = 0; q < S; ++q) s += part[(int64_t)q * total + e];
+    const int64_t c = e / p, r = e - c * p;
+    Z[r + c * ldz] = s;
+  }
+}
+
+int launch_gemm_simt(const float* G, int64_t ldg, const void* Y, bool y_f64, int64_t ldy, bool f64,
+                     int64_t p, int64_t k, int64_t ncol, double* Z, int64_t ldz, void* ws,
+                     size_t ws_bytes, cudaStream_t st) {
+  if (p == 0 || ncol == 0) return MSK_OK;
+  GemmSplit g = gemm_split(p, k, ncol);
+  Carve cv(ws, ws_bytes);
+  double* part = static_cast<double*>(cv.take((size_t)g.s * p * ncol * sizeof(double)));
+  if (!part) return MSK_ENOMEM;
+  dim3 grid(g.mt, g.nt, g.s);
+  if (f64 && y_f64)
+    gemm_simt_kernel<double, double><<<grid, kGThreads, 0, st>>>(
+        G, ldg, static_cast<const double*>(Y), ldy, p, k, ncol, g.kchunk, part);
+  else if (f64)
+    gemm_simt_kernel<double, float><<<grid, kGThreads, 0, st>>>(
+        G, ldg, static_cast<const float*>(Y), ldy, p, k, ncol, g.kchunk, part);
+  else if (y_f64)
+    gemm_simt_kernel<float, double><<<grid, kGThreads, 0, st>>>(
+        G, ldg, static_cast<const double*>(Y), ldy, p, k, ncol, g.kchunk, part);
+  else
+    gemm_simt_kernel<float, float><<<grid, kGThreads, 0, st>>>(
+        G, ldg, static_cast<const float*>(Y), ldy, p, k, ncol, g.kchunk, part);
+  MSK_CHECK_LAUNCH("gemm_simt_kernel");
+  const int64_t total = p * ncol;
+  splitk_reduce_kernel<<<(unsigned)std::min<int64_t>((total + 255) / 256, num_sms() * 8), 256, 0,
+                         st>>>(part, g.s, p, ncol, Z, ldz);
+  MSK_CHECK_LAUNCH("splitk_reduce_kernel");
+  return MSK_OK;
+}
+
+}  // namespace msk

@@ -1,0 +1,84 @@
+// msk_internal.h — host-side internals of libmsketch shared by the .cu files:
+// status propagation, stream casts, workspace carving, launch declarations.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/msketch.h"
+
+namespace msk {
+
+// Records the CUDA error text for msk_last_error() and returns MSK_ECUDA.
+int cuda_fail(cudaError_t e, const char* where);
+
+#define MSK_CUDA(call)                                  \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return ::msk::cuda_fail(e_, #call); \
+  } while (0)
+
+#define MSK_CHECK_LAUNCH(where)                         \
+  do {                                                  \
+    cudaError_t e_ = cudaGetLastError();                \
+    if (e_ != cudaSuccess) return ::msk::cuda_fail(e_, where); \
+  } while (0)
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Bump allocator over the caller's workspace (256-byte aligned pieces).
+struct Carve {
+  char* base;
+  size_t cap;
+  size_t used = 0;
+  Carve(void* b, size_t c) : base(static_cast<char*>(b)), cap(c) {}
+  // Returns nullptr when the piece does not fit (or base is null).
+  void* take(size_t bytes) {
+    size_t off = align_up(used, 256);
+    if (bytes == 0) return base ? base + off : nullptr;
+    if (!base || off + bytes > cap) return nullptr;
+    used = off + bytes;
+    return base + off;
+  }
+};
+// Size accounting twin of Carve.
+struct Need {
+  size_t used = 0;
+  void add(size_t bytes) { used = align_up(used, 256) + bytes; }
+};
+
+int num_sms();
+
+// ---- kernels launched across translation units -------------------------
+// countsketch.cu
+int launch_cs_hash(uint64_t key, int64_t i0, int64_t count, uint32_t k, uint32_t* h,
+                   int8_t* s, cudaStream_t st);
+int launch_cs_atomic(const void* A, int dtype, int64_t d, int64_t n, int64_t lda,
+                     const double* b, uint32_t k, uint64_t key, void* Y, int64_t ldy,
+                     cudaStream_t st);
+size_t cs_sorted_workspace(int64_t d, int64_t k);
+int launch_cs_sorted(const void* A, int dtype, int64_t d, int64_t n, int64_t lda,
+                     const double* b, uint32_t k, uint64_t key, void* Y, int64_t ldy,
+                     void* ws, size_t ws_bytes, cudaStream_t st);
+// gaussian.cu
+int launch_gaussian(uint64_t key, int64_t p, int64_t k, int out_prec, void* G, int64_t ldg,
+                    cudaStream_t st);
+// gemm_simt.cu
+size_t gemm_simt_workspace(int64_t p, int64_t k, int64_t ncol, bool f64);
+int launch_gemm_simt(const float* G, int64_t ldg, const void* Y, bool y_f64, int64_t ldy, bool f64,
+                     int64_t p, int64_t k, int64_t ncol, double* Z, int64_t ldz, void* ws,
+                     size_t ws_bytes, cudaStream_t st);
+
+// gemm_tc.cu (tcgen05 tensor-core Gaussian stage)
+size_t tc_gemm_workspace(int64_t p, int64_t k, int64_t ncol, int prec);
+int launch_tc_gemm(uint64_t gkey, int64_t p, int64_t k, int64_t ncol, const float* Y, int64_t ldy,
+                   int prec, double* Z, int64_t ldz, void* ws, size_t ws_bytes, cudaStream_t st);
+// api.cu
+int gemm_stage(uint64_t seed, int64_t p, int64_t k, int64_t ncol, const void* Y, int y_dtype,
+               int64_t ldy, int gemm_prec, double* Z, int64_t ldz, void* ws, size_t ws_bytes,
+               cudaStream_t st);
+
+}  // namespace msk
