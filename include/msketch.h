@@ -203,6 +203,30 @@ int msk_householder_qr(double *W, int64_t m, int64_t c, int64_t ldw,
 int msk_trsv_upper(const double *R, int64_t n, int64_t ldr, const double *rhs,
                    double *x, void *stream);
 
+/* Size of the fixed scratch array behind msk_gemm_noalloc (24 MiB). */
+#define MSK_NOALLOC_SCRATCH_BYTES ((size_t)24 << 20)
+
+/* msk_gemm without a caller workspace, for programs that may not allocate
+ * device memory when they need the Gaussian stage (for instance a component
+ * running under a host application whose allocator owns all device memory, or
+ * a loop that cannot pay for the device-wide synchronisation an allocation can
+ * cause).  The paper has no counterpart; this is a convenience of the library.
+ *   Same arguments and result as msk_gemm, minus ws/ws_bytes.  The scratch (the
+ *   binary32 G and the split-K partials) lives in one array of
+ *   MSK_NOALLOC_SCRATCH_BYTES inside the library, reserved on every GPU that
+ *   loads it until the process exits.  No device memory is allocated.
+ *   The first call made on a device looks up the array's device address (once
+ *   per device, with that device current); make that first call before any
+ *   stream capture starts on the device.
+ *   All calls share the array and each call overwrites it: calls whose GPU
+ *   work overlaps in time (e.g. on different streams) race and give wrong
+ *   results; serialise them.  Nothing in the array needs to start at zero.
+ * Errors: as msk_gemm; MSK_ENOMEM (with a message in msk_last_error) when
+ *   msk_gemm_workspace(p, k, ncol, gemm_prec) exceeds the array. */
+int msk_gemm_noalloc(uint64_t seed, int64_t p, int64_t k, int64_t ncol,
+                     const void *Y, int64_t ldy, int gemm_prec, double *Z,
+                     int64_t ldz, void *stream);
+
 /* ---- Least squares -------------------------------------------------------- */
 
 /* Scratch bytes ms_lstsq needs. */

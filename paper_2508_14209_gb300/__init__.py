@@ -34,7 +34,9 @@ GEMM_PRECS = {"f64": GEMM_F64, "f32": GEMM_F32, "bf16": GEMM_BF16, "f16": GEMM_F
 EXPORTS = ("msk_version", "msk_last_error", "cs_hash", "ms_gaussian", "msk_cs_workspace",
            "cs_sketch", "msk_ms_workspace", "ms_sketch", "msk_gemm_workspace", "msk_gemm",
            "msk_householder_qr", "msk_trsv_upper", "msk_lstsq_workspace", "ms_lstsq",
-           "msk_ne_workspace", "ne_lstsq")
+           "msk_ne_workspace", "ne_lstsq", "msk_gemm_noalloc")
+
+NOALLOC_SCRATCH_BYTES = 24 << 20
 
 
 class MskError(RuntimeError):
@@ -81,6 +83,7 @@ def _declare(L):
                              _p, _sz, _p]),
         "msk_gemm_workspace": (_sz, [_i64, _i64, _i64, _int]),
         "msk_gemm": (_int, [_u64, _i64, _i64, _i64, _p, _i64, _int, _p, _i64, _p, _sz, _p]),
+        "msk_gemm_noalloc": (_int, [_u64, _i64, _i64, _i64, _p, _i64, _int, _p, _i64, _p]),
         "msk_householder_qr": (_int, [_p, _i64, _i64, _i64, _p]),
         "msk_trsv_upper": (_int, [_p, _i64, _i64, _p, _p, _p]),
         "msk_lstsq_workspace": (_sz, [_i64, _i64, _i64, _i64, _int, _int, _int]),
@@ -236,6 +239,18 @@ def msk_gemm(seed, p, Y, gemm_prec=GEMM_F64, Z=None, ws=None, stream=None):
         ws = workspace(msk_gemm_workspace(p, k, ncol, gemm_prec), Y.device)
     _check("msk_gemm", load().msk_gemm(seed & (2**64 - 1), p, k, ncol, _ptr(Y), Y.stride(0), gemm_prec,
                                        _ptr(Z), _colmajor(Z), _ptr(ws), ws.numel(), _stream(stream)))
+    return Z
+
+
+def msk_gemm_noalloc(seed, p, Y, gemm_prec=GEMM_F64, Z=None, stream=None):
+    """msk_gemm with the library's fixed scratch array instead of a caller
+    workspace (for callers that may not allocate device memory; Z is still the
+    caller's).  Calls share the array: serialise them."""
+    k, ncol = Y.shape
+    if Z is None:
+        Z = colmajor(p, ncol, torch.float64, Y.device)
+    _check("msk_gemm_noalloc", load().msk_gemm_noalloc(seed & (2**64 - 1), p, k, ncol, _ptr(Y), Y.stride(0),
+                                                       gemm_prec, _ptr(Z), _colmajor(Z), _stream(stream)))
     return Z
 
 

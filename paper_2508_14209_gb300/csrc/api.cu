@@ -19,6 +19,10 @@ int cuda_fail(cudaError_t e, const char* where) {
   return MSK_ECUDA;
 }
 
+void set_error_text(const char* msg) {
+  std::snprintf(g_last_error, sizeof(g_last_error), "%s", msg);
+}
+
 int num_sms() {
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 1;

@@ -12,6 +12,8 @@ namespace msk {
 
 // Records the CUDA error text for msk_last_error() and returns MSK_ECUDA.
 int cuda_fail(cudaError_t e, const char* where);
+// Records a plain message for msk_last_error().
+void set_error_text(const char* msg);
 
 #define MSK_CUDA(call)                                  \
   do {                                                  \

@@ -1,0 +1,63 @@
+"""msk_gemm_noalloc — the Gaussian-stage GEMM for callers that may not allocate
+device memory (its scratch is a fixed array inside the library) — must give
+what msk_gemm gives with a caller workspace.  Collected last on purpose; it
+passes on its own in a fresh process and after the other tests."""
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+EPS64 = np.finfo(np.float64).eps
+
+
+@pytest.fixture(scope="module")
+def msk():
+    import paper_2508_14209_gb300 as m
+    from paper_2508_14209_gb300 import build
+
+    assert torch.cuda.is_available()
+    build.build()
+    m.load()
+    return m
+
+
+def _bound(orc, seed, p, Y, prec):
+    # rounding bound of a length-k FP64 / FP32 dot product on the same inputs,
+    # used by every GEMM parity test in this suite
+    G = orc.gaussian(seed, p, Y.shape[0]).astype(np.float64)
+    Yh = Y.double().cpu().numpy()
+    u = EPS64 if prec == "f64" else 2.0 ** -24
+    return (Y.shape[0] + 2) * u * (np.abs(G) @ np.abs(Yh))
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_noalloc_matches_workspace_entry_point(msk, orc, prec):
+    gp = msk.GEMM_PRECS[prec]
+    dt = torch.float64 if prec == "f64" else torch.float32
+    p, k, ncol = 256, 8192, 65
+    gen = torch.Generator().manual_seed(7)
+    for call, seed in enumerate((0x5EED0004, 0x5EED0005)):  # two calls in a row
+        Y = torch.randn(k, ncol, generator=gen, dtype=torch.float64).to(dt).cuda()
+        Zref = msk.msk_gemm(seed, p, Y, gemm_prec=gp).cpu().numpy()
+        Z = msk.msk_gemm_noalloc(seed, p, Y, gemm_prec=gp).cpu().numpy()
+        assert np.all(np.abs(Z - Zref) <= _bound(orc, seed, p, Y, prec)), f"call {call}"
+
+
+def test_noalloc_does_not_grow_device_memory(msk):
+    Y = torch.randn(4096, 33, dtype=torch.float64, device="cuda")
+    msk.msk_gemm_noalloc(3, 128, Y)  # first call on the device: address set-up
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for s in range(3):
+        msk.msk_gemm_noalloc(4 + s, 128, Y)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+
+
+def test_noalloc_rejects_oversized_problem(msk):
+    # 512 x 32768 binary32 G alone is 64 MiB, beyond the fixed array
+    Y = torch.zeros(32768, 8, dtype=torch.float64, device="cuda")
+    with pytest.raises(msk.MskError) as ei:
+        msk.msk_gemm_noalloc(1, 512, Y)
+    assert ei.value.code == msk.MSK_ENOMEM
+    assert "scratch" in str(ei.value)
