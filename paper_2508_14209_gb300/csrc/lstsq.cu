@@ -1,11 +1,605 @@
-// lstsq.cu — placeholder.
+// lstsq.cu — least-squares solvers built on the multisketch:
+//   * ms_lstsq, refine = 0: sketch-and-solve (Algorithm 1, Section 2):
+//       Z = G S [A b] (p x (n+1)), Householder QR of Z, x = R11^{-1} R[0:n, n].
+//   * ms_lstsq, refine = 1: sketch-and-precondition refinement (the iterative
+//       route Section 6 cites).  Outer loop: true residual r = b - A x and
+//       g = A^T r in FP64 (one pass over A).  Inner loop: conjugate gradients
+//       on A^T A d = g preconditioned by M = R11^T R11, T iterations, each one
+//       pass over A computing A^T (A p) in FP32 (FP32 suffices for a
+//       correction; the FP64 outer residual sets the final accuracy).  Then
+//       x += d.  Stops when the relative residual changes by at most
+//       tol * relres between outer steps.
+//   * ne_lstsq: normal equations (Section 6.3): [A b]^T [A b] in one FP64
+//       pass (split over row slices, partials summed in a fixed order),
+//       Cholesky, two triangular solves.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <vector>
+
 #include "msk_internal.h"
-extern "C" {
-int msk_householder_qr(double*, int64_t, int64_t, int64_t, void*) { return MSK_ENOTSUP; }
-int msk_trsv_upper(const double*, int64_t, int64_t, const double*, double*, void*) { return MSK_ENOTSUP; }
-size_t msk_lstsq_workspace(int64_t, int64_t, int64_t, int64_t, int, int, int) { return 0; }
-int ms_lstsq(const void*, int, int64_t, int64_t, int64_t, const double*, int64_t, int64_t, uint64_t,
-             int, int, double, int32_t, double*, msk_lstsq_info*, void*, size_t, void*) { return MSK_ENOTSUP; }
-size_t msk_ne_workspace(int64_t, int64_t) { return 0; }
-int ne_lstsq(const double*, int64_t, int64_t, int64_t, const double*, double*, void*, size_t, void*) { return MSK_ENOTSUP; }
+
+namespace msk {
+
+// ---------------------------------------------------------------------------
+// Gram matrix of [A b] (FP64): C[a][c] = sum_i X[i][a] X[i][c] for the
+// (n+1)-column X = [A b], upper 64x64 tiles only, split over row slices.
+constexpr int kGrT = 64, kGrK = 32, kGrThreads = 256;
+
+template <typename TA>
+__device__ __forceinline__ double x_at(const TA* A, int64_t lda, int64_t n, const double* b,
+                                       int64_t i, int64_t c) {
+  return c < n ? (double)A[i + c * lda] : b[i];
 }
+
+template <typename TA>
+__global__ void __launch_bounds__(kGrThreads) gram_kernel(const TA* __restrict__ A, int64_t lda,
+                                                       int64_t d, int64_t n,
+                                                       const double* __restrict__ b, int64_t rchunk,
+                                                       const int2* __restrict__ tiles,
+                                                       double* __restrict__ part) {
+  __shared__ double Xa[kGrK][kGrT + 1];
+  __shared__ double Xc[kGrK][kGrT + 1];
+  const int64_t ncol = n + 1;
+  const int2 t = tiles[blockIdx.x];
+  const int64_t a0 = (int64_t)t.x * kGrT, c0 = (int64_t)t.y * kGrT;
+  const int64_t r0 = (int64_t)blockIdx.y * rchunk, r1 = min(d, r0 + rchunk);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double acc[4][4] = {};
+  for (int64_t k0 = r0; k0 < r1; k0 += kGrK) {
+    for (int e = threadIdx.x; e < kGrK * kGrT; e += kGrThreads) {
+      const int kk = e % kGrK, cc = e / kGrK;
+      const int64_t i = k0 + kk;
+      Xa[kk][cc] = (i < r1 && a0 + cc < ncol) ? x_at(A, lda, n, b, i, a0 + cc) : 0.0;
+      Xc[kk][cc] = (i < r1 && c0 + cc < ncol) ? x_at(A, lda, n, b, i, c0 + cc) : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < kGrK; ++kk) {
+      double av[4], cv[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) av[q] = Xa[kk][ty + 16 * q];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) cv[q] = Xc[kk][tx + 16 * q];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(av[u], cv[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+  // part[slice][c * ncol + a] (column-major (n+1) x (n+1)); only a <= c kept
+  double* out = part + (int64_t)blockIdx.y * ncol * ncol;
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int64_t a = a0 + ty + 16 * u, c = c0 + tx + 16 * v;
+      if (a < ncol && c < ncol && a <= c) out[c * ncol + a] = acc[u][v];
+    }
+}
+
+// Sum the slices (fixed order) and mirror the upper triangle.
+__global__ void gram_reduce_kernel(const double* __restrict__ part, int S, int64_t ncol,
+                                   double* __restrict__ C) {
+  const int64_t total = ncol * ncol;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = e / ncol, a = e % ncol;
+    const int64_t src = a <= c ? c * ncol + a : a * ncol + c;
+    double s = 0.0;
+    for (int q = 0; q < S; ++q) s += part[(int64_t)q * total + src];
+    C[e] = s;
+  }
+}
+
+struct GramPlan {
+  int ntile, npairs, slices;
+  int64_t rchunk;
+};
+
+static GramPlan gram_plan(int64_t d, int64_t n) {
+  GramPlan g;
+  const int64_t ncol = n + 1;
+  g.ntile = (int)((ncol + kGrT - 1) / kGrT);
+  g.npairs = g.ntile * (g.ntile + 1) / 2;
+  int64_t s = std::max<int64_t>(1, (2LL * num_sms()) / g.npairs);
+  s = std::min<int64_t>(s, std::max<int64_t>(1, (d + kGrK - 1) / kGrK));
+  g.rchunk = ((d + s - 1) / s + kGrK - 1) / kGrK * kGrK;
+  if (g.rchunk < kGrK) g.rchunk = kGrK;
+  g.slices = (int)std::max<int64_t>(1, (d + g.rchunk - 1) / g.rchunk);
+  return g;
+}
+
+static size_t gram_workspace(int64_t d, int64_t n) {
+  GramPlan g = gram_plan(d, n);
+  const int64_t ncol = n + 1;
+  Need nd;
+  nd.add((size_t)g.npairs * sizeof(int2));
+  nd.add((size_t)g.slices * ncol * ncol * sizeof(double));
+  return nd.used;
+}
+
+// ---------------------------------------------------------------------------
+// Row-tiled passes over A (rows in tiles of kPR, whole rows in shared memory).
+//   RESID = true : FP64.  r_i = b_i - A_i x; accumulates g = A^T r and ||r||^2,
+//                  ||b||^2 (optional).
+//   RESID = false: FP32.  w_i = A_i p; accumulates v = A^T w and ||w||^2.
+// Per-CTA partials part[cta][0..n) (vector), part[cta][n], part[cta][n+1]
+// (scalars); summed in a fixed order by pass_reduce_kernel.
+constexpr int kPR = 64, kPThreads = 256;
+
+template <typename TA, typename TC, bool RESID>
+__global__ void __launch_bounds__(kPThreads) pass_kernel(const TA* __restrict__ A, int64_t lda,
+                                                      int64_t d, int n, const double* __restrict__ b,
+                                                      const double* __restrict__ vin,
+                                                      double* __restrict__ part) {
+  extern __shared__ __align__(16) unsigned char pk_smem[];
+  const int pitch = n | 1;
+  TC* tile = reinterpret_cast<TC*>(pk_smem);       // kPR x pitch
+  TC* vs = tile + kPR * pitch;                     // n (x or p)
+  TC* ws = vs + n;                                 // kPR (row results)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int j = threadIdx.x; j < n; j += kPThreads) vs[j] = (TC)vin[j];
+  TC accv[2] = {0, 0};  // columns threadIdx.x and threadIdx.x + 256 (n <= 512)
+  double s1 = 0.0, s2 = 0.0;
+  const int64_t ntiles = (d + kPR - 1) / kPR;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t i0 = t * kPR;
+    __syncthreads();
+    // load: warp w takes columns w, w+8, ...; lanes cover rows lane, lane+32
+    for (int j = warp; j < n; j += kPThreads / 32) {
+      const TA* col = A + (int64_t)j * lda;
+#pragma unroll
+      for (int h = 0; h < kPR / 32; ++h) {
+        const int r = lane + 32 * h;
+        const int64_t i = i0 + r;
+        tile[r * pitch + j] = i < d ? (TC)__ldcs(col + i) : (TC)0;
+      }
+    }
+    __syncthreads();
+    // per-row dot products (rows 0..kPR-1 handled by the first kPR threads)
+    if (threadIdx.x < kPR) {
+      const int r = threadIdx.x;
+      const int64_t i = i0 + r;
+      TC w = 0;
+      const TC* row = tile + r * pitch;
+      for (int j = 0; j < n; ++j) w = fma(row[j], vs[j], w);
+      if (i < d) {
+        if (RESID) {
+          const double bi = b[i];
+          const double ri = bi - (double)w;
+          ws[r] = (TC)ri;
+          s1 += ri * ri;
+          s2 += bi * bi;
+        } else {
+          ws[r] = w;
+          s1 += (double)w * (double)w;
+        }
+      } else {
+        ws[r] = (TC)0;
+      }
+    }
+    __syncthreads();
+    // per-column accumulation of A^T w
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int j = threadIdx.x + q * kPThreads;
+      if (j < n) {
+        TC a = accv[q];
+        for (int r = 0; r < kPR; ++r) a = fma(tile[r * pitch + j], ws[r], a);
+        accv[q] = a;
+      }
+    }
+  }
+  double* out = part + (int64_t)blockIdx.x * (n + 2);
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int j = threadIdx.x + q * kPThreads;
+    if (j < n) out[j] = (double)accv[q];
+  }
+  // block sums of s1, s2
+  __shared__ double red[2][kPThreads / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+  }
+  if (lane == 0) {
+    red[0][warp] = s1;
+    red[1][warp] = s2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, c = 0.0;
+    for (int w = 0; w < kPThreads / 32; ++w) {
+      a += red[0][w];
+      c += red[1][w];
+    }
+    out[n] = a;
+    out[n + 1] = c;
+  }
+}
+
+// out[j] = sum over CTAs of part[cta][j] (j < n + 2), fixed order.
+__global__ void pass_reduce_kernel(const double* __restrict__ part, int nctas, int len,
+                                   double* __restrict__ out) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < len; j += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int q = 0; q < nctas; ++q) s += part[(int64_t)q * len + j];
+    out[j] = s;
+  }
+}
+
+static int pass_grid(int64_t d) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>((d + kPR - 1) / kPR, 2LL * num_sms()));
+}
+
+template <typename TA, typename TC, bool RESID>
+static int launch_pass_t(const TA* A, int64_t lda, int64_t d, int n, const double* b,
+                         const double* vin, double* part, double* out, cudaStream_t st) {
+  const int pitch = n | 1;
+  const size_t smem = sizeof(TC) * ((size_t)kPR * pitch + n + kPR);
+  auto kern = pass_kernel<TA, TC, RESID>;
+  MSK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int grid = pass_grid(d);
+  kern<<<grid, kPThreads, smem, st>>>(A, lda, d, n, b, vin, part);
+  MSK_CHECK_LAUNCH("pass_kernel");
+  pass_reduce_kernel<<<(n + 2 + 255) / 256, 256, 0, st>>>(part, grid, n + 2, out);
+  MSK_CHECK_LAUNCH("pass_reduce_kernel");
+  return MSK_OK;
+}
+
+// RESID: out = [A^T r (n), ||r||^2, ||b||^2] with r = b - A x (FP64).
+// else : out = [A^T A p (n), ||A p||^2, 0] (FP32 arithmetic).
+static int launch_pass(const void* A, int dtype, int64_t lda, int64_t d, int n, const double* b,
+                       const double* vin, bool resid, double* part, double* out, cudaStream_t st) {
+  if (dtype == MSK_F64) {
+    if (resid)
+      return launch_pass_t<double, double, true>(static_cast<const double*>(A), lda, d, n, b, vin,
+                                                 part, out, st);
+    return launch_pass_t<double, float, false>(static_cast<const double*>(A), lda, d, n, b, vin, part,
+                                               out, st);
+  }
+  if (resid)
+    return launch_pass_t<float, double, true>(static_cast<const float*>(A), lda, d, n, b, vin, part,
+                                              out, st);
+  return launch_pass_t<float, float, false>(static_cast<const float*>(A), lda, d, n, b, vin, part,
+                                            out, st);
+}
+
+static size_t pass_workspace(int64_t d, int64_t n) {
+  return (size_t)pass_grid(d) * (n + 2) * sizeof(double);
+}
+
+// ---------------------------------------------------------------------------
+// Small FP64 vector kernels of the refinement (single CTA; n <= 512).
+
+// Explicit inverse of the upper-triangular R (n x n, ldr) into Ri (n x n,
+// column-major): column c of Ri solves R y = e_c; one warp per column.
+__global__ void tri_inverse_kernel(const double* __restrict__ R, int n, int64_t ldr,
+                                   double* __restrict__ Ri) {
+  const int lane = threadIdx.x & 31;
+  const int warp_g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int c = warp_g; c < n; c += nw) {
+    double* y = Ri + (int64_t)c * n;
+    for (int r = lane; r < n; r += 32) y[r] = 0.0;
+    __syncwarp();
+    // back substitution restricted to rows <= c
+    for (int i = c; i >= 0; --i) {
+      double s = (i == c) ? 1.0 : 0.0;
+      double part = 0.0;
+      for (int j = i + 1 + lane; j <= c; j += 32) part += R[i + (int64_t)j * ldr] * y[j];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+      if (lane == 0) y[i] = (s - part) / R[i + (int64_t)i * ldr];
+      __syncwarp();
+    }
+  }
+}
+
+// State of the refinement, all device FP64 (n-vectors unless noted):
+//   x, dlt (correction), p (search dir), res (normal-eq. residual), z,
+//   sc[0] = rho.
+struct RefState {
+  double *x, *dlt, *p, *res, *z, *sc;
+};
+
+// z = Ri (Ri^T v): the preconditioner M^{-1} v with M = R^T R.
+__device__ void apply_minv(const double* __restrict__ Ri, int n, const double* v, double* tmp,
+                           double* z) {
+  // tmp = Ri^T v  (tmp[j] = sum_{i<=j} Ri[i][j] v[i])
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const double* col = Ri + (int64_t)j * n;
+    double s = 0.0;
+    for (int i = 0; i <= j; ++i) s += col[i] * v[i];
+    tmp[j] = s;
+  }
+  __syncthreads();
+  // z = Ri tmp  (z[i] = sum_{j>=i} Ri[i][j] tmp[j])
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double s = 0.0;
+    for (int j = i; j < n; ++j) s += Ri[i + (int64_t)j * n] * tmp[j];
+    z[i] = s;
+  }
+  __syncthreads();
+}
+
+// Start of an inner solve: res = g (from the FP64 pass), dlt = 0,
+// z = M^{-1} res, p = z, rho = res.z.
+__global__ void pcg_start_kernel(const double* __restrict__ Ri, int n, const double* __restrict__ g,
+                                 RefState s) {
+  __shared__ double tmp[512];
+  __shared__ double red[32];
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    s.res[j] = g[j];
+    s.dlt[j] = 0.0;
+  }
+  __syncthreads();
+  apply_minv(Ri, n, s.res, tmp, s.z);
+  double part = 0.0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    s.p[j] = s.z[j];
+    part += s.res[j] * s.z[j];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r += red[w];
+    s.sc[0] = r;
+  }
+}
+
+// One CG update after the pass produced v = A^T A p (pv[0..n)), pv[n] = p.v:
+//   alpha = rho / p.v; dlt += alpha p; res -= alpha v; z = M^{-1} res;
+//   rho' = res.z; p = z + (rho'/rho) p.
+__global__ void pcg_update_kernel(const double* __restrict__ Ri, int n, const double* __restrict__ pv,
+                                  RefState s) {
+  __shared__ double tmp[512];
+  __shared__ double red[32];
+  __shared__ double alpha_s, beta_s;
+  // p.v from the vector itself (more accurate than ||A p||^2 in FP32)
+  double part = 0.0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) part += s.p[j] * pv[j];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double pAp = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) pAp += red[w];
+    alpha_s = pAp > 0.0 ? s.sc[0] / pAp : 0.0;
+  }
+  __syncthreads();
+  const double alpha = alpha_s;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    s.dlt[j] += alpha * s.p[j];
+    s.res[j] -= alpha * pv[j];
+  }
+  __syncthreads();
+  apply_minv(Ri, n, s.res, tmp, s.z);
+  part = 0.0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) part += s.res[j] * s.z[j];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double rho = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) rho += red[w];
+    beta_s = s.sc[0] > 0.0 ? rho / s.sc[0] : 0.0;
+    s.sc[0] = rho;
+  }
+  __syncthreads();
+  const double beta = beta_s;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) s.p[j] = s.z[j] + beta * s.p[j];
+}
+
+// x += dlt
+__global__ void axpy_kernel(int n, const double* __restrict__ dlt, double* __restrict__ x) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+    x[j] += dlt[j];
+}
+
+constexpr int kInnerIters = 6;  // CG iterations per outer (FP64 residual) step
+
+}  // namespace msk
+
+using namespace msk;
+
+namespace {
+
+bool is_tensor_prec_l(int prec) {
+  return prec == MSK_GEMM_BF16 || prec == MSK_GEMM_F16 || prec == MSK_GEMM_BF16X3;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t msk_lstsq_workspace(int64_t d, int64_t n, int64_t k, int64_t p, int dtype, int gemm_prec,
+                           int refine) {
+  Need nd;
+  nd.add(msk_ms_workspace(d, n, 1, k, p, dtype, gemm_prec, MSK_CS_ATOMIC));
+  nd.add((size_t)p * (n + 1) * sizeof(double));  // Z
+  nd.add(pass_workspace(d, n));                     // pass partials
+  nd.add((size_t)(n + 2) * sizeof(double));         // pass result
+  if (refine) {
+    nd.add((size_t)n * n * sizeof(double));  // R^{-1}
+    nd.add((size_t)5 * n * sizeof(double));  // dlt, p, res, z, g copy
+    nd.add(64);                              // scalars
+  }
+  return nd.used;
+}
+
+int ms_lstsq(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, const double* b,
+             int64_t k, int64_t p, uint64_t seed, int gemm_prec, int refine, double tol,
+             int32_t max_iter, double* x, msk_lstsq_info* info, void* ws, size_t ws_bytes,
+             void* stream) {
+  if (!A) return -1;
+  if (dtype != MSK_F64 && dtype != MSK_F32) return -2;
+  if (d < n) return -3;
+  if (n < 1 || n > 400) return -4;
+  if (lda < d) return -5;
+  if (!b) return -6;
+  if (k < n + 1) return -7;
+  if (p < n + 1 || p > k || p > 2048) return -8;
+  if (gemm_prec < MSK_GEMM_F64 || gemm_prec > MSK_GEMM_BF16X3) return -10;
+  if (refine != 0 && refine != 1) return -11;
+  if (!x) return -14;
+  if (ws_bytes < msk_lstsq_workspace(d, n, k, p, dtype, gemm_prec, refine)) return MSK_ENOMEM;
+  if (is_tensor_prec_l(gemm_prec) && dtype != MSK_F32) return MSK_ENOTSUP;
+  cudaStream_t st = as_stream(stream);
+  Carve cv(ws, ws_bytes);
+  const size_t ms_ws = msk_ms_workspace(d, n, 1, k, p, dtype, gemm_prec, MSK_CS_ATOMIC);
+  void* msw = cv.take(ms_ws);
+  double* Z = static_cast<double*>(cv.take((size_t)p * (n + 1) * sizeof(double)));
+  double* part = static_cast<double*>(cv.take(pass_workspace(d, n)));
+  double* pout = static_cast<double*>(cv.take((size_t)(n + 2) * sizeof(double)));
+  if (!Z || !part || !pout) return MSK_ENOMEM;
+  // 1. Z = G S [A b]
+  int rc = ms_sketch(A, dtype, d, n, lda, b, k, p, seed, gemm_prec, Z, p, MSK_CS_ATOMIC, msw, ms_ws,
+                     stream);
+  if (rc) return rc;
+  // 2. Householder QR of Z (in place): R = Z[0:n+1, 0:n+1]
+  rc = launch_householder_qr(Z, p, n + 1, p, st);
+  if (rc) return rc;
+  // 3. x0 = R11^{-1} R[0:n, n]
+  rc = launch_trsv_upper(Z, n, p, Z + n * p, x, nullptr, false, st);
+  if (rc) return rc;
+  double relres_sns = -1.0, relres = -1.0, bnorm2 = 0.0;
+  int iters = 0, converged = 1;
+  int status = MSK_OK;
+  if (refine) {
+    double* Ri = static_cast<double*>(cv.take((size_t)n * n * sizeof(double)));
+    double* vec = static_cast<double*>(cv.take((size_t)5 * n * sizeof(double)));
+    double* sc = static_cast<double*>(cv.take(64));
+    if (!Ri || !vec || !sc) return MSK_ENOMEM;
+    RefState s{x, vec, vec + n, vec + 2 * n, vec + 3 * n, sc};
+    double* gsave = vec + 4 * n;
+    tri_inverse_kernel<<<(unsigned)std::max<int64_t>(1, (n + 7) / 8), 256, 0, st>>>(Z, (int)n, p, Ri);
+    MSK_CHECK_LAUNCH("tri_inverse_kernel");
+    double prev = -1.0;
+    converged = 0;
+    std::vector<double> host(3);
+    for (int outer = 0; outer <= max_iter; ++outer) {
+      // FP64 true residual pass: pout = [A^T r, ||r||^2, ||b||^2]
+      rc = launch_pass(A, dtype, lda, d, (int)n, b, x, true, part, pout, st);
+      if (rc) return rc;
+      MSK_CUDA(cudaMemcpyAsync(host.data(), pout + n, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+      MSK_CUDA(cudaStreamSynchronize(st));
+      if (outer == 0) bnorm2 = host[1];
+      const double rr = std::sqrt(std::max(host[0], 0.0) / (bnorm2 > 0.0 ? bnorm2 : 1.0));
+      if (outer == 0) relres_sns = rr;
+      relres = rr;
+      if (prev >= 0.0 && std::fabs(prev - rr) <= tol * rr) {
+        converged = 1;
+        break;
+      }
+      if (outer == max_iter) break;
+      prev = rr;
+      iters = outer + 1;
+      // inner PCG on A^T A d = g (FP32 passes)
+      MSK_CUDA(cudaMemcpyAsync(gsave, pout, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      pcg_start_kernel<<<1, 512, 0, st>>>(Ri, (int)n, gsave, s);
+      MSK_CHECK_LAUNCH("pcg_start_kernel");
+      for (int it = 0; it < kInnerIters; ++it) {
+        rc = launch_pass(A, dtype, lda, d, (int)n, nullptr, s.p, false, part, pout, st);
+        if (rc) return rc;
+        pcg_update_kernel<<<1, 512, 0, st>>>(Ri, (int)n, pout, s);
+        MSK_CHECK_LAUNCH("pcg_update_kernel");
+      }
+      axpy_kernel<<<1, 512, 0, st>>>((int)n, s.dlt, x);
+      MSK_CHECK_LAUNCH("axpy_kernel");
+    }
+    if (!converged) status = MSK_ENOCONV;
+  } else if (info) {
+    rc = launch_pass(A, dtype, lda, d, (int)n, b, x, true, part, pout, st);
+    if (rc) return rc;
+    double host[2];
+    MSK_CUDA(cudaMemcpyAsync(host, pout + n, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    MSK_CUDA(cudaStreamSynchronize(st));
+    relres = std::sqrt(std::max(host[0], 0.0) / (host[1] > 0.0 ? host[1] : 1.0));
+    relres_sns = relres;
+  }
+  if (info) {
+    const int piv = first_zero_pivot(Z, n, p, st);
+    if (piv > 0 && piv < 1000) status = piv;
+    info->iters = iters;
+    info->converged = converged;
+    info->relres = relres;
+    info->relres_sns = relres_sns;
+  }
+  return status;
+}
+
+size_t msk_ne_workspace(int64_t d, int64_t n) {
+  Need nd;
+  nd.add(gram_workspace(d, n));
+  nd.add((size_t)(n + 1) * (n + 1) * sizeof(double));  // C = [A b]^T [A b]
+  nd.add((size_t)n * n * sizeof(double));              // R
+  nd.add((size_t)n * sizeof(double));                  // y
+  nd.add(64);                                          // status
+  return nd.used;
+}
+
+int ne_lstsq(const double* A, int64_t d, int64_t n, int64_t lda, const double* b, double* x,
+             void* ws, size_t ws_bytes, void* stream) {
+  if (!A) return -1;
+  if (d < n) return -2;
+  if (n < 1 || n > 4096) return -3;
+  if (lda < d) return -4;
+  if (!b) return -5;
+  if (!x) return -6;
+  if (ws_bytes < msk_ne_workspace(d, n)) return MSK_ENOMEM;
+  cudaStream_t st = as_stream(stream);
+  Carve cv(ws, ws_bytes);
+  GramPlan g = gram_plan(d, n);
+  const int64_t ncol = n + 1;
+  int2* tiles = static_cast<int2*>(cv.take((size_t)g.npairs * sizeof(int2)));
+  double* part = static_cast<double*>(cv.take((size_t)g.slices * ncol * ncol * sizeof(double)));
+  double* C = static_cast<double*>(cv.take((size_t)ncol * ncol * sizeof(double)));
+  double* R = static_cast<double*>(cv.take((size_t)n * n * sizeof(double)));
+  double* y = static_cast<double*>(cv.take((size_t)n * sizeof(double)));
+  int* status = static_cast<int*>(cv.take(64));
+  if (!tiles || !part || !C || !R || !y || !status) return MSK_ENOMEM;
+  std::vector<int2> hp;
+  for (int a = 0; a < g.ntile; ++a)
+    for (int c = a; c < g.ntile; ++c) hp.push_back(make_int2(a, c));
+  MSK_CUDA(cudaMemcpyAsync(tiles, hp.data(), hp.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
+  MSK_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
+  dim3 grid(g.npairs, g.slices);
+  gram_kernel<double><<<grid, kGrThreads, 0, st>>>(A, lda, d, n, b, g.rchunk, tiles, part);
+  MSK_CHECK_LAUNCH("gram_kernel");
+  const int64_t tot = ncol * ncol;
+  gram_reduce_kernel<<<(unsigned)std::min<int64_t>((tot + 255) / 256, 1024), 256, 0, st>>>(
+      part, g.slices, ncol, C);
+  MSK_CHECK_LAUNCH("gram_reduce_kernel");
+  // C[0:n,0:n] = A^T A, C[0:n, n] = A^T b.  Cholesky overwrites C's upper part.
+  int rc = launch_cholesky(C, n, ncol, R, n, status, st);
+  if (rc) return rc;
+  rc = launch_trsv_upper(R, n, n, C + n * ncol, y, nullptr, true, st);  // R^T y = A^T b
+  if (rc) return rc;
+  rc = launch_trsv_upper(R, n, n, y, x, nullptr, false, st);            // R x = y
+  if (rc) return rc;
+  int hs = 0;
+  MSK_CUDA(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  MSK_CUDA(cudaStreamSynchronize(st));
+  if (hs > 0) {
+    // x is meaningless after a failed factorisation: make that visible
+    std::vector<double> nanv((size_t)n, std::nan(""));
+    MSK_CUDA(cudaMemcpyAsync(x, nanv.data(), (size_t)n * sizeof(double), cudaMemcpyHostToDevice, st));
+    MSK_CUDA(cudaStreamSynchronize(st));
+    return hs;
+  }
+  return MSK_OK;
+}
+
+}  // extern "C"

@@ -78,6 +78,13 @@ int launch_gemm_simt(const float* G, int64_t ldg, const void* Y, bool y_f64, int
 size_t tc_gemm_workspace(int64_t p, int64_t k, int64_t ncol, int prec);
 int launch_tc_gemm(uint64_t gkey, int64_t p, int64_t k, int64_t ncol, const float* Y, int64_t ldy,
                    int prec, double* Z, int64_t ldz, void* ws, size_t ws_bytes, cudaStream_t st);
+// qr.cu
+int launch_householder_qr(double* W, int64_t m, int64_t c, int64_t ldw, cudaStream_t st);
+int launch_trsv_upper(const double* R, int64_t n, int64_t ldr, const double* rhs, double* x,
+                      int* status, bool transposed, cudaStream_t st);
+int launch_cholesky(double* Gm, int64_t n, int64_t ldg, double* R, int64_t ldr, int* status,
+                    cudaStream_t st);
+int first_zero_pivot(const double* R, int64_t n, int64_t ldr, cudaStream_t st);
 // api.cu
 int gemm_stage(uint64_t seed, int64_t p, int64_t k, int64_t ncol, const void* Y, int y_dtype,
                int64_t ldy, int gemm_prec, double* Z, int64_t ldz, void* ws, size_t ws_bytes,

@@ -1,0 +1,298 @@
+// qr.cu — the small dense FP64 steps of sketch-and-solve (Algorithm 1 steps
+// 2-3; GeQRF/OrMQR/TRSV in Section 6.1) and of the normal equations
+// (POTRF + two TRSV, Section 6.3).
+//
+// Householder QR of the sketched m x c matrix (m = p rows, c = n+1 columns):
+// one thread-block cluster (up to 16 CTAs on 16 SMs) factors one matrix.
+// Column j belongs to CTA j mod CL (cyclic, so the shrinking trailing matrix
+// stays balanced).  Step j: the owner builds the reflector of column j
+// (v = x + sign(x0)||x|| e0, tau = 2 / v^T v, R[j][j] = -sign(x0)||x||) and
+// publishes v0 and tau; after one cluster barrier every CTA applies
+// I - tau v v^T to the columns it owns, one warp per column.  The matrix stays
+// in global memory (it is at most a few MB and lives in L2); v is staged in
+// each CTA's shared memory.  FP64 throughout.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <vector>
+
+#include "msk_internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace msk {
+
+constexpr int kQrThreads = 256;
+constexpr int kQrMaxRows = 2048;
+constexpr int kQrMaxCols = 512;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum (all threads get the result).  `red` holds >= 32 doubles.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int w = 0; w < nw; ++w) s += red[w];
+  return s;
+}
+
+// The owner of column j publishes (v0, tau) in its shared memory slot
+// pub[j & 1]; the other CTAs read it through distributed shared memory after
+// the cluster barrier.  Two slots: slot j & 1 is rewritten at step j + 2 only,
+// after a barrier every reader of step j has passed.  Columns owned by other
+// CTAs are read with L1-bypassing loads.
+__global__ void __launch_bounds__(kQrThreads) qr_cluster_kernel(double* __restrict__ W, int m, int c,
+                                                              int64_t ldw) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int CL = (int)cluster.num_blocks();
+  __shared__ double vbuf[kQrMaxRows];
+  __shared__ double red[32];
+  __shared__ double pub[2][2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int steps = min(m, c);
+  for (int j = 0; j < steps; ++j) {
+    const int owner = j % CL;
+    double* colj = W + (int64_t)j * ldw;
+    if (rank == owner) {
+      double s = 0.0;
+      for (int i = j + threadIdx.x; i < m; i += blockDim.x) s += colj[i] * colj[i];
+      const double norm2 = block_sum(s, red);
+      if (threadIdx.x == 0) {
+        const double x0 = colj[j];
+        const double alpha = sqrt(norm2);
+        const double sgn = x0 >= 0.0 ? 1.0 : -1.0;
+        const double v0 = x0 + sgn * alpha;
+        const double vtv = norm2 - x0 * x0 + v0 * v0;
+        pub[j & 1][0] = v0;
+        pub[j & 1][1] = vtv > 0.0 ? 2.0 / vtv : 0.0;
+        colj[j] = -sgn * alpha;
+      }
+    }
+    __threadfence();
+    cluster.sync();
+    // stage v = (v0, W[j+1:m, j]) and apply the reflector to owned columns
+    const double* opub = cluster.map_shared_rank(&pub[j & 1][0], owner);
+    const double v0 = opub[0], tau = opub[1];
+    for (int i = j + threadIdx.x; i < m; i += blockDim.x) vbuf[i - j] = (i == j) ? v0 : __ldcg(colj + i);
+    __syncthreads();
+    if (tau != 0.0) {
+      // owned columns > j: first owned column index >= j+1 with col % CL == rank
+      int first = j + 1 + ((rank - (j + 1) % CL) + CL) % CL;
+      for (int col = first + warp * CL; col < c; col += nwarps * CL) {
+        double* w = W + (int64_t)col * ldw;
+        double s = 0.0;
+        for (int i = j + lane; i < m; i += 32) s += vbuf[i - j] * w[i];
+        s = warp_sum(s) * tau;
+        for (int i = j + lane; i < m; i += 32) w[i] -= s * vbuf[i - j];
+      }
+    }
+    __syncthreads();
+  }
+  cluster.sync();
+  // zero the strictly lower part of owned columns
+  for (int col = rank; col < c; col += CL) {
+    double* w = W + (int64_t)col * ldw;
+    for (int i = col + 1 + threadIdx.x; i < m; i += blockDim.x) w[i] = 0.0;
+  }
+}
+
+int launch_householder_qr(double* W, int64_t m, int64_t c, int64_t ldw, cudaStream_t st) {
+  static int cluster_size = 0;
+  if (cluster_size == 0) {
+    cudaError_t e = cudaFuncSetAttribute(qr_cluster_kernel,
+                                         cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    int cs = 8;
+    if (e == cudaSuccess) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(16, 1, 1);
+      cfg.blockDim = dim3(kQrThreads, 1, 1);
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = 16;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int ncl = 0;
+      if (cudaOccupancyMaxActiveClusters(&ncl, qr_cluster_kernel, &cfg) == cudaSuccess && ncl > 0)
+        cs = 16;
+    }
+    cudaGetLastError();
+    cluster_size = cs;
+  }
+  int CL = (int)std::min<int64_t>(cluster_size, c);
+  if (CL < 1) CL = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CL, 1, 1);
+  cfg.blockDim = dim3(kQrThreads, 1, 1);
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  MSK_CUDA(cudaLaunchKernelEx(&cfg, qr_cluster_kernel, W, (int)m, (int)c, ldw));
+  return MSK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Triangular solves (single CTA; n <= 4096).  status[0] <- j+1 for the first
+// zero pivot met (0 when none).
+constexpr int kTrsvMax = 4096;
+
+// R x = rhs, R upper (column-major, ldr).  x may alias rhs.
+__global__ void trsv_upper_kernel(const double* __restrict__ R, int n, int64_t ldr,
+                                  const double* rhs, double* x, int* status) {
+  __shared__ double xs[kTrsvMax];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) xs[i] = rhs[i];
+  __syncthreads();
+  for (int i = n - 1; i >= 0; --i) {
+    if (threadIdx.x == 0) {
+      const double rii = R[i + (int64_t)i * ldr];
+      if (rii == 0.0 && status && status[0] == 0) status[0] = i + 1;
+      xs[i] = xs[i] / rii;
+    }
+    __syncthreads();
+    const double xi = xs[i];
+    const double* col = R + (int64_t)i * ldr;
+    for (int r = threadIdx.x; r < i; r += blockDim.x) xs[r] -= col[r] * xi;
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = xs[i];
+}
+
+// R^T y = rhs, R upper (so R^T lower).  y may alias rhs.
+__global__ void trsv_upper_t_kernel(const double* __restrict__ R, int n, int64_t ldr,
+                                    const double* rhs, double* y, int* status) {
+  __shared__ double ys[kTrsvMax];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) ys[i] = rhs[i];
+  __syncthreads();
+  for (int i = 0; i < n; ++i) {
+    if (threadIdx.x == 0) {
+      const double rii = R[i + (int64_t)i * ldr];
+      if (rii == 0.0 && status && status[0] == 0) status[0] = i + 1;
+      ys[i] = ys[i] / rii;
+    }
+    __syncthreads();
+    const double yi = ys[i];
+    for (int r = i + 1 + threadIdx.x; r < n; r += blockDim.x) ys[r] -= R[i + (int64_t)r * ldr] * yi;
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = ys[i];
+}
+
+int launch_trsv_upper(const double* R, int64_t n, int64_t ldr, const double* rhs, double* x,
+                      int* status, bool transposed, cudaStream_t st) {
+  if (n <= 0) return MSK_OK;
+  if (n > kTrsvMax) return MSK_ENOTSUP;
+  if (transposed)
+    trsv_upper_t_kernel<<<1, 256, 0, st>>>(R, (int)n, ldr, rhs, x, status);
+  else
+    trsv_upper_kernel<<<1, 256, 0, st>>>(R, (int)n, ldr, rhs, x, status);
+  MSK_CHECK_LAUNCH("trsv_kernel");
+  return MSK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Cholesky of the symmetric n x n matrix Gm (column-major, ldg; upper part
+// used) into upper R (column-major, ldr) with R^T R = Gm: right-looking, one
+// CTA.  Gm is overwritten (trailing updates).  status[0] <- j+1 when pivot j is
+// not positive.
+__global__ void cholesky_kernel(double* __restrict__ Gm, int n, int64_t ldg, double* __restrict__ R,
+                                int64_t ldr, int* status) {
+  __shared__ double piv;
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
+    const int r = i % n, c = i / n;
+    if (r > c) R[r + (int64_t)c * ldr] = 0.0;
+  }
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    if (threadIdx.x == 0) {
+      const double s = Gm[j + (int64_t)j * ldg];
+      if (!(s > 0.0)) {
+        bad = 1;
+        if (status) status[0] = j + 1;
+      } else {
+        piv = sqrt(s);
+        R[j + (int64_t)j * ldr] = piv;
+      }
+    }
+    __syncthreads();
+    if (bad) return;
+    const double rjj = piv;
+    for (int c = j + 1 + threadIdx.x; c < n; c += blockDim.x)
+      R[j + (int64_t)c * ldr] = Gm[j + (int64_t)c * ldg] / rjj;
+    __syncthreads();
+    // trailing update of the upper triangle: Gm[a][c] -= R[j][a] R[j][c], j < a <= c
+    const int t = n - j - 1;
+    for (int e = threadIdx.x; e < t * t; e += blockDim.x) {
+      const int a = j + 1 + e % t, c = j + 1 + e / t;
+      if (a <= c) Gm[a + (int64_t)c * ldg] -= R[j + (int64_t)a * ldr] * R[j + (int64_t)c * ldr];
+    }
+    __syncthreads();
+  }
+}
+
+// Host-side check of an upper-triangular factor's diagonal: synchronises the
+// stream, returns j+1 for the first exactly-zero R[j][j], else MSK_OK.
+int first_zero_pivot(const double* R, int64_t n, int64_t ldr, cudaStream_t st) {
+  if (n <= 0) return MSK_OK;
+  std::vector<double> diag((size_t)n);
+  MSK_CUDA(cudaMemcpy2DAsync(diag.data(), sizeof(double), R, (size_t)(ldr + 1) * sizeof(double),
+                             sizeof(double), (size_t)n, cudaMemcpyDeviceToHost, st));
+  MSK_CUDA(cudaStreamSynchronize(st));
+  for (int64_t j = 0; j < n; ++j)
+    if (diag[(size_t)j] == 0.0) return (int)(j + 1);
+  return MSK_OK;
+}
+
+int launch_cholesky(double* Gm, int64_t n, int64_t ldg, double* R, int64_t ldr, int* status,
+                    cudaStream_t st) {
+  cholesky_kernel<<<1, 1024, 0, st>>>(Gm, (int)n, ldg, R, ldr, status);
+  MSK_CHECK_LAUNCH("cholesky_kernel");
+  return MSK_OK;
+}
+
+}  // namespace msk
+
+using namespace msk;
+
+extern "C" {
+
+int msk_householder_qr(double* W, int64_t m, int64_t c, int64_t ldw, void* stream) {
+  if (!W) return -1;
+  if (m < c || m > kQrMaxRows) return -2;
+  if (c < 1 || c > kQrMaxCols) return -3;
+  if (ldw < m) return -4;
+  return launch_householder_qr(W, m, c, ldw, as_stream(stream));
+}
+
+int msk_trsv_upper(const double* R, int64_t n, int64_t ldr, const double* rhs, double* x,
+                   void* stream) {
+  if (!R) return -1;
+  if (n < 0 || n > kTrsvMax) return -2;
+  if (ldr < (n > 1 ? n : 1)) return -3;
+  if (!rhs && n > 0) return -4;
+  if (!x && n > 0) return -5;
+  cudaStream_t st = as_stream(stream);
+  int rc = launch_trsv_upper(R, n, ldr, rhs, x, nullptr, false, st);
+  if (rc) return rc;
+  return first_zero_pivot(R, n, ldr, st);
+}
+
+}  // extern "C"

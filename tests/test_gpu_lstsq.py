@@ -1,0 +1,136 @@
+"""GPU parity of the dense steps and the least-squares solvers against the
+oracle: Householder R, triangular solves, sketch-and-solve (same S and G as the
+oracle: relative residual within 1e-8 relative), refinement (relative residual
+within 1e-8 of the oracle's exact least-squares minimiser, and never above
+FP64 sketch-and-solve), normal equations and their breakdown (Section 6.3)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import inputs
+
+pytestmark = pytest.mark.gpu
+EPS64 = np.finfo(np.float64).eps
+
+
+@pytest.fixture(scope="module")
+def msk():
+    import paper_2508_14209_gb300 as m
+    from paper_2508_14209_gb300 import build
+
+    assert torch.cuda.is_available()
+    build.build()
+    m.load()
+    return m
+
+
+def dev_colmajor(M, msk):
+    M = torch.as_tensor(M)
+    d, n = M.shape
+    out = msk.colmajor(d, n, M.dtype, "cuda")
+    out.copy_(M)
+    return out
+
+
+@pytest.mark.parametrize("m,c", [(8, 1), (9, 9), (64, 7), (129, 65), (512, 129), (1024, 257),
+                                 (2048, 100), (300, 17)])
+def test_householder_r_matches_oracle(msk, orc, m, c):
+    Z = np.random.default_rng(m * 7 + c).standard_normal((m, c))
+    W = dev_colmajor(Z, msk)
+    msk.msk_householder_qr(W)
+    Wh = W.cpu().numpy()
+    R = Wh[:c, :c]
+    Ro = orc.householder_r(Z)
+    nz = np.linalg.norm(Z)
+    assert np.all(Wh[np.tril_indices(m, -1, c)] == 0.0)
+    assert np.allclose(R, Ro, rtol=0, atol=4 * m * EPS64 * nz)
+    assert np.allclose(R.T @ R, Z.T @ Z, rtol=0, atol=8 * m * EPS64 * nz * nz)
+
+
+def test_trsv_and_zero_pivot(msk):
+    rng = np.random.default_rng(3)
+    n = 200
+    R = np.triu(rng.standard_normal((n, n))) + 8 * np.eye(n)
+    c = rng.standard_normal(n)
+    x, rc = msk.msk_trsv_upper(dev_colmajor(R, msk), torch.tensor(c, device="cuda"))
+    assert rc == 0
+    assert np.allclose(x.cpu().numpy(), np.linalg.solve(R, c), rtol=1e-12, atol=1e-12)
+    R[57, 57] = 0.0
+    _, rc = msk.msk_trsv_upper(dev_colmajor(R, msk), torch.tensor(c, device="cuda"))
+    assert rc == 58
+
+
+def _problem(d, n, lsig, seed, dtype):
+    A, b, _ = inputs.ls_problem(d, n, lsig, seed=seed, dtype=dtype)
+    return A, b
+
+
+@pytest.mark.parametrize("d,n,lsig", [(4096 + 17, 8, -2), (65536, 32, -6), (20000, 64, -10),
+                                      (1 << 17, 16, -2)])
+def test_sns_f64_matches_oracle(msk, orc, d, n, lsig):
+    A, b = _problem(d, n, lsig, 100 + n, torch.float64)
+    k, p, seed = 2 * n * n, 4 * n, 0x5EED0003
+    x, info, rc = msk.ms_lstsq(dev_colmajor(A, msk), b.cuda(), k, p, seed, msk.GEMM_F64)
+    assert rc == 0
+    xg = x.cpu().numpy()
+    An, bn = A.numpy(), b.numpy()
+    xo, ro, _ = orc.sns_lstsq(An, bn, k, p, seed, "f64")
+    rg = orc.relres(An, bn, xg)
+    assert abs(rg - ro) <= 1e-8 * ro
+    assert abs(info["relres"] - rg) <= 1e-8 * rg
+    kappa = 10.0 ** (-lsig)
+    assert np.linalg.norm(xg - xo) <= 1e3 * kappa * EPS64 * np.linalg.norm(xo) + 1e-300
+
+
+def test_sns_exact_recovery(msk):
+    d, n = 1 << 14, 12
+    A, _ = _problem(d, n, -3, 7, torch.float64)
+    xt = torch.arange(1, n + 1, dtype=torch.float64)
+    b = A @ xt
+    x, info, rc = msk.ms_lstsq(dev_colmajor(A, msk), b.cuda(), 2 * n * n, 4 * n, 9, msk.GEMM_F64)
+    assert rc == 0
+    assert torch.allclose(x.cpu(), xt, rtol=1e-10, atol=0)
+
+
+@pytest.mark.parametrize("d,n,lsig,prec", [(1 << 15, 16, -4, "f32"), (1 << 15, 32, -8, "f32"),
+                                           (40000, 64, -6, "f32")])
+def test_refined_mixed_reaches_minimiser(msk, orc, d, n, lsig, prec):
+    A, b = _problem(d, n, lsig, 300 + n, torch.float32)
+    k, p, seed = 2 * n * n, 4 * n, 0x5EED0004
+    x, info, rc = msk.ms_lstsq(dev_colmajor(A, msk), b.cuda(), k, p, seed, msk.GEMM_PRECS[prec],
+                               refine=True, tol=1e-12, max_iter=20)
+    assert rc == 0, info
+    An, bn = A.numpy(), b.numpy()
+    xo = orc.lstsq_exact(An, bn)
+    ro = orc.relres(An, bn, xo)
+    rg = orc.relres(An, bn, x.cpu().numpy())
+    assert abs(rg - ro) <= 1e-8 * ro                      # two-sided, against the minimiser
+    _, r_sns64, _ = orc.sns_lstsq(An.astype(np.float64), bn, k, p, seed, "f64")
+    assert rg <= (1 + 1e-8) * r_sns64                     # never worse than FP64 sketch-and-solve
+    assert info["iters"] >= 1 and info["converged"] == 1
+
+
+def test_ne_matches_oracle_and_breaks_down(msk, orc):
+    d, n = 1 << 14, 10
+    A, b = _problem(d, n, -4, 41, torch.float64)
+    x, rc = msk.ne_lstsq(dev_colmajor(A, msk), b.cuda())
+    assert rc == 0
+    xo, info = orc.ne_lstsq(A.numpy(), b.numpy())
+    assert info == 0
+    assert np.allclose(x.cpu().numpy(), xo, rtol=1e-6, atol=1e-6 * np.abs(xo).max())
+    # Section 6.3 sensitivity experiment: d = 2^17, n = 16, b = A e, kappa = 1e10
+    d, n = 1 << 17, 16
+    A, _ = _problem(d, n, -10, 42, torch.float64)
+    b = A @ torch.ones(n, dtype=torch.float64)
+    Ad = dev_colmajor(A, msk)
+    xn, rc = msk.ne_lstsq(Ad, b.cuda())
+    xs, info, rcs = msk.ms_lstsq(Ad, b.cuda(), 2 * n * n, 4 * n, 5, msk.GEMM_F64)
+    rs = orc.relres(A.numpy(), b.numpy(), xs.cpu().numpy())
+    assert rcs == 0 and rs < 1e-12
+    if rc == 0:
+        rn = orc.relres(A.numpy(), b.numpy(), xn.cpu().numpy())
+        assert rn > 1e3 * rs
+    else:
+        assert rc > 0 and torch.isnan(xn).all()
