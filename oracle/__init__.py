@@ -158,6 +158,20 @@ def round_bf16(x) -> np.ndarray:
     return out.reshape(np.shape(x))
 
 
+def split_bf16x3(y32) -> np.ndarray:
+    """y1 + y2 + y3 for the split of float32 y into three bfloat16 parts
+    (Henry, Tang, Heinecke, ARITH 2019): y1 = bf16(y), y2 = bf16(y - y1),
+    y3 = bf16(y - y1 - y2), each difference exact in binary32.  Returned as the
+    float64 sum (exact: the parts have disjoint significant bits)."""
+    y = np.asarray(y32, dtype=np.float32)
+    y1 = round_bf16(y)
+    r1 = (y - y1).astype(np.float32)
+    y2 = round_bf16(r1)
+    r2 = (r1 - y2).astype(np.float32)
+    y3 = round_bf16(r2)
+    return y1.astype(np.float64) + y2.astype(np.float64) + y3.astype(np.float64)
+
+
 def round_fp16(x) -> np.ndarray:
     """IEEE round-to-nearest-even of float32 values to binary16 (numpy's
     conversion), returned as float32 values."""
@@ -233,7 +247,8 @@ def multisketch(A, k: int, p: int, seed: int, b=None, gemm_prec: str = "f64"):
     """Z = G (S [A b]) with the Gaussian and the sketch rounded to the GEMM's
     input precision first ("f64": G widened exactly from float32, Y as is;
     "f32": Y rounded to float32; "bf16"/"f16": G and Y rounded to the 16-bit
-    type).  Returns (Z, G_used, Y_used) as FP64 arrays."""
+    type; "bf16x3": G rounded to bfloat16, float32 Y split into three
+    bfloat16 parts).  Returns (Z, G_used, Y_used) as FP64 arrays."""
     Y = countsketch(A, k, seed, b)
     G = gaussian(seed, p, k)
     if gemm_prec == "f64":
@@ -246,6 +261,9 @@ def multisketch(A, k: int, p: int, seed: int, b=None, gemm_prec: str = "f64"):
     elif gemm_prec == "f16":
         Gu = round_fp16(G).astype(np.float64)
         Yu = round_fp16(Y.astype(np.float32)).astype(np.float64)
+    elif gemm_prec == "bf16x3":
+        Gu = round_bf16(G).astype(np.float64)
+        Yu = split_bf16x3(Y.astype(np.float32)).astype(np.float64)
     else:
         raise ValueError(gemm_prec)
     return gemm(Gu, Yu), Gu, Yu

@@ -1,9 +1,451 @@
-// gemm_tc.cu — placeholder for the tcgen05 tensor-core Gaussian stage.
+// gemm_tc.cu — the Gaussian stage Z = G Y on the 5th-generation tensor cores
+// (tcgen05, kind::f16, FP32 accumulation in tensor memory), the only dense
+// contraction of the multisketch (Section 1 "Count-Gauss"; the paper runs it
+// as a cuBLAS GEMM, Section 6.1).
+//
+// Operands (both K-major, bf16 or fp16):
+//   A = G, p x k row-major, generated directly in the 16-bit type;
+//   B = Y^T split into PARTS 16-bit parts, Yt[t][n][k]:
+//     PARTS = 1 for BF16 / F16 (Y rounded once);
+//     PARTS = 3 for BF16X3: Y = Y1 + Y2 + Y3 exactly up to 2^-24 |Y|, each
+//     Yt a bfloat16 rounding of what the previous parts left (Henry, Tang,
+//     Heinecke, ARITH 2019); G is exactly bfloat16, so every product is exact
+//     and the three MMAs accumulate into one FP32 accumulator.
+// Tiling: a CTA owns a 128 x NT tile of Z and a slice of the K tiles (split-K:
+// the output is tiny, K = k is long).  Warp 0 (one lane) streams 128x64 A tiles
+// and NTx64 B tiles with TMA (128-byte swizzle) through a ring of shared-memory
+// stages; warp 1 (one lane) issues tcgen05.mma (K = 16 per instruction, four
+// per 64-wide K tile, times PARTS) into a TMEM accumulator and frees each stage
+// with tcgen05.commit; all four warps then read the accumulator back with
+// tcgen05.ld and write FP32 partial tiles, which a second kernel sums in FP64
+// in a fixed order.  Every mbarrier wait is bounded (1 s): on expiry the kernel
+// records a timeout flag, waits (bounded) for its own copies in flight, frees
+// its tensor memory and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
 #include "msk_internal.h"
+
 namespace msk {
-size_t tc_gemm_workspace(int64_t, int64_t, int64_t, int) { return 0; }
-int launch_tc_gemm(uint64_t, int64_t, int64_t, int64_t, const float*, int64_t, int, double*,
-                   int64_t, void*, size_t, cudaStream_t) {
-  return MSK_ENOTSUP;
+
+constexpr int kTcBM = 128;       // M per CTA (one UMMA M)
+constexpr int kTcBK = 64;        // K per stage: 64 x 2 bytes = one 128-byte swizzle row
+constexpr int kTcThreads = 128;  // 4 warps
+constexpr uint64_t kTcWaitNs = 1000000000ull;
+constexpr uint32_t kTcWaitIters = 1u << 28;
+constexpr int kTcSmemBudget = 220 * 1024;
+
+__device__ int g_tc_timeout = 0;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
 }
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait on an mbarrier phase: false (and the timeout flag set) after
+// kTcWaitNs nanoseconds or kTcWaitIters polls.
+__device__ bool mbar_wait(uint32_t a, uint32_t parity) {
+  if (mbar_try(a, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t i = 0; i < kTcWaitIters; ++i) {
+    if (mbar_try(a, parity)) return true;
+    if (global_ns() - t0 > kTcWaitNs) break;
+  }
+  atomicExch(&g_tc_timeout, 1);
+  return false;
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
+                                            int c2, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms of
+// 1024 bytes (stride byte offset 1024), descriptor version 1.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)(16u >> 4) << 16;
+  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Instruction descriptor of kind::f16 with FP32 accumulation, K-major A and B:
+// bits 4-5 D format (1 = F32), 7-9 A format, 10-12 B format (0 = F16,
+// 1 = BF16), 17-22 N >> 3, 24-28 M >> 4.
+static uint32_t make_idesc(int M, int N, bool bf16) {
+  return (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+template <int PARTS>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   int p, int ncol, int NT, int KT, int kt_per, int stages, uint32_t idesc,
+                   float* __restrict__ part) {
+  extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
+  unsigned char* smem =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~uintptr_t(1023));
+  const uint32_t a_bytes = kTcBM * kTcBK * 2;
+  const uint32_t b_bytes = (uint32_t)NT * kTcBK * 2;
+  const uint32_t stage_bytes = a_bytes + PARTS * b_bytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)stages * stage_bytes);
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * stages + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * kTcBM, n0 = blockIdx.y * NT;
+  const int kt0 = blockIdx.z * kt_per;
+  const int nk = min(KT, kt0 + kt_per) - kt0;
+  const uint32_t tmem_cols = NT <= 32 ? 32u : NT <= 64 ? 64u : NT <= 128 ? 128u : 256u;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < stages; ++s) {
+      mbar_init(smem_u32(&bars[s]), 1);
+      mbar_init(smem_u32(&bars[stages + s]), 1);
+    }
+    mbar_init(smem_u32(&bars[2 * stages]), 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_holder)),
+                 "r"(tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_holder;
+
+  if (warp == 0 && lane == 0) {
+    // TMA producer
+    int issued = 0;
+    for (int it = 0; it < nk; ++it) {
+      const int s = it % stages;
+      if (it >= stages && !mbar_wait(smem_u32(&bars[stages + s]), ((it / stages) & 1) ^ 1)) {
+        *abort_flag = 1;
+        break;
+      }
+      if (*abort_flag) break;
+      const uint32_t full = smem_u32(&bars[s]);
+      mbar_expect_tx(full, stage_bytes);
+      unsigned char* st = smem + (size_t)s * stage_bytes;
+      const int kc = (kt0 + it) * kTcBK;
+      tma_load_2d(smem_u32(st), &tmA, kc, m0, full);
+#pragma unroll
+      for (int t = 0; t < PARTS; ++t)
+        tma_load_3d(smem_u32(st + a_bytes + t * b_bytes), &tmB, kc, n0, t, full);
+      ++issued;
+    }
+    if (*abort_flag) {
+      // let this CTA's copies in flight land before leaving (bounded waits)
+      for (int it = (issued > stages ? issued - stages : 0); it < issued; ++it)
+        mbar_wait(smem_u32(&bars[it % stages]), (it / stages) & 1);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    for (int it = 0; it < nk; ++it) {
+      const int s = it % stages;
+      if (!mbar_wait(smem_u32(&bars[s]), (it / stages) & 1)) {
+        *abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t a_base = smem_u32(smem + (size_t)s * stage_bytes);
+#pragma unroll
+      for (int kk = 0; kk < kTcBK / 16; ++kk) {
+        const uint64_t ad = sw128_desc(a_base + kk * 32);
+#pragma unroll
+        for (int t = 0; t < PARTS; ++t) {
+          const uint64_t bd = sw128_desc(a_base + a_bytes + t * b_bytes + kk * 32);
+          umma_f16(tmem, ad, bd, idesc, (it > 0 || kk > 0 || t > 0) ? 1u : 0u);
+        }
+      }
+      umma_commit(smem_u32(&bars[stages + s]));
+    }
+    umma_commit(smem_u32(&bars[2 * stages]));
+  }
+  __syncwarp();
+  // epilogue: TMEM lane (warp*32 + lane) holds row m0 + warp*32 + lane
+  const bool done = mbar_wait(smem_u32(&bars[2 * stages]), 0);
+  tc_fence_after();
+  // tcgen05.ld is warp-collective: take the decision per warp
+  if (__all_sync(0xffffffffu, done && !*abort_flag && nk > 0)) {
+    const int row = m0 + warp * 32 + lane;
+    float* out = part + (int64_t)blockIdx.z * p * ncol;
+    for (int c0 = 0; c0 < NT; c0 += 16) {
+      uint32_t v[16];
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int col = n0 + c0 + q;
+        if (row < p && col < ncol) out[(int64_t)col * p + row] = __uint_as_float(v[q]);
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 2)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols)
+                 : "memory");
+}
+
+// Yt[t][n][kk] (row pitch kpitch) from the FP32 row-major Y (k x ncol, ldy):
+// PARTS = 1: round once (bf16 or fp16); PARTS = 3: bf16 split of the residues.
+// Rows n >= ncol (up to npad) are zero.  32x32 tiles transposed in shared memory.
+template <int PARTS, bool BF16>
+__global__ void split_transpose_kernel(const float* __restrict__ Y, int64_t ldy, int64_t k, int ncol,
+                                       int npad, int64_t kpitch, uint16_t* __restrict__ Yt) {
+  __shared__ float tile[32][33];
+  const int64_t k0 = (int64_t)blockIdx.x * 32;
+  const int n0 = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t kk = k0 + r;
+    const int n = n0 + tx;
+    tile[r][tx] = (kk < k && n < ncol) ? Y[kk * ldy + n] : 0.0f;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int n = n0 + r;
+    const int64_t kk = k0 + tx;
+    if (n >= npad || kk >= k) continue;
+    float y = tile[tx][r];
+#pragma unroll
+    for (int t = 0; t < PARTS; ++t) {
+      uint16_t bits;
+      float back;
+      if (BF16) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(y);
+        bits = __bfloat16_as_ushort(h);
+        back = __bfloat162float(h);
+      } else {
+        const __half h = __float2half_rn(y);
+        bits = __half_as_ushort(h);
+        back = __half2float(h);
+      }
+      Yt[((int64_t)t * npad + n) * kpitch + kk] = bits;
+      y = y - back;  // exact in binary32 (the rounded part shares y's leading bits)
+    }
+  }
+}
+
+// Z[r + c*ldz] = sum_s part[s][c*p + r] in FP64, slices in order.
+__global__ void tc_reduce_kernel(const float* __restrict__ part, int S, int64_t p, int64_t ncol,
+                                 double* __restrict__ Z, int64_t ldz) {
+  const int64_t total = p * ncol;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int q = 0; q < S; ++q) s += (double)part[(int64_t)q * total + e];
+    const int64_t c = e / p, r = e - c * p;
+    Z[r + c * ldz] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+struct TcPlan {
+  int parts, npad, NT, Mt, Nt, KT, kt_per, S, stages;
+  int64_t kpitch;
+};
+
+static int tc_parts(int prec) { return prec == MSK_GEMM_BF16X3 ? 3 : 1; }
+
+static TcPlan tc_plan(int64_t p, int64_t k, int64_t ncol, int prec) {
+  TcPlan t;
+  t.parts = tc_parts(prec);
+  t.npad = (int)((ncol + 15) / 16 * 16);
+  const int nt_max = t.parts == 3 ? 144 : 256;
+  const int ntiles = (t.npad + nt_max - 1) / nt_max;
+  t.NT = (int)(((t.npad + ntiles - 1) / ntiles + 15) / 16 * 16);
+  t.Nt = (t.npad + t.NT - 1) / t.NT;
+  t.Mt = (int)((p + kTcBM - 1) / kTcBM);
+  t.KT = (int)((k + kTcBK - 1) / kTcBK);
+  t.kpitch = (k + 7) / 8 * 8;
+  const int tiles = t.Mt * t.Nt;
+  int s = std::max(1, num_sms() / std::max(1, tiles));
+  s = std::min(s, t.KT);
+  t.kt_per = (t.KT + s - 1) / s;
+  t.S = (t.KT + t.kt_per - 1) / t.kt_per;
+  const int stage_bytes = kTcBM * kTcBK * 2 + t.parts * t.NT * kTcBK * 2;
+  t.stages = std::max(1, std::min(6, (kTcSmemBudget - 2048) / stage_bytes));
+  return t;
+}
+
+size_t tc_gemm_workspace(int64_t p, int64_t k, int64_t ncol, int prec) {
+  TcPlan t = tc_plan(p, k, ncol, prec);
+  Need nd;
+  nd.add((size_t)p * t.kpitch * 2);                        // G (16-bit)
+  nd.add((size_t)t.parts * t.npad * t.kpitch * 2);         // Yt parts (16-bit)
+  nd.add((size_t)t.S * p * ncol * sizeof(float));          // FP32 partials
+  return nd.used;
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+  }
+  return fn;
+}
+
+int launch_tc_gemm(uint64_t gkey, int64_t p, int64_t k, int64_t ncol, const float* Y, int64_t ldy,
+                   int prec, double* Z, int64_t ldz, void* ws, size_t ws_bytes, cudaStream_t st) {
+  if (p < 1 || ncol < 1 || k < 1) return MSK_OK;
+  if (ncol > 512) return MSK_ENOTSUP;
+  TcPlan t = tc_plan(p, k, ncol, prec);
+  const bool bf16 = prec != MSK_GEMM_F16;
+  Carve cv(ws, ws_bytes);
+  uint16_t* G = static_cast<uint16_t*>(cv.take((size_t)p * t.kpitch * 2));
+  uint16_t* Yt = static_cast<uint16_t*>(cv.take((size_t)t.parts * t.npad * t.kpitch * 2));
+  float* part = static_cast<float*>(cv.take((size_t)t.S * p * ncol * sizeof(float)));
+  if (!G || !Yt || !part) return MSK_ENOMEM;
+  int rc = launch_gaussian(gkey, p, k, bf16 ? MSK_GEMM_BF16 : MSK_GEMM_F16, G, t.kpitch, st);
+  if (rc) return rc;
+  {
+    dim3 grid((unsigned)((k + 31) / 32), (unsigned)((t.npad + 31) / 32));
+    if (t.parts == 3)
+      split_transpose_kernel<3, true><<<grid, 256, 0, st>>>(Y, ldy, k, (int)ncol, t.npad, t.kpitch, Yt);
+    else if (bf16)
+      split_transpose_kernel<1, true><<<grid, 256, 0, st>>>(Y, ldy, k, (int)ncol, t.npad, t.kpitch, Yt);
+    else
+      split_transpose_kernel<1, false><<<grid, 256, 0, st>>>(Y, ldy, k, (int)ncol, t.npad, t.kpitch, Yt);
+    MSK_CHECK_LAUNCH("split_transpose_kernel");
+  }
+  auto enc = encode_fn();
+  if (!enc) {
+    set_error_text("cuTensorMapEncodeTiled entry point not available");
+    return MSK_ECUDA;
+  }
+  const CUtensorMapDataType dt = bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  CUtensorMap tmA, tmB;
+  {
+    cuuint64_t dims[2] = {(cuuint64_t)k, (cuuint64_t)p};
+    cuuint64_t strides[1] = {(cuuint64_t)t.kpitch * 2};
+    cuuint32_t box[2] = {(cuuint32_t)kTcBK, (cuuint32_t)kTcBM};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(&tmA, dt, 2, G, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+      set_error_text("cuTensorMapEncodeTiled failed for G");
+      return MSK_ECUDA;
+    }
+  }
+  {
+    cuuint64_t dims[3] = {(cuuint64_t)k, (cuuint64_t)t.npad, (cuuint64_t)t.parts};
+    cuuint64_t strides[2] = {(cuuint64_t)t.kpitch * 2, (cuuint64_t)t.npad * t.kpitch * 2};
+    cuuint32_t box[3] = {(cuuint32_t)kTcBK, (cuuint32_t)t.NT, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(&tmB, dt, 3, Yt, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+      set_error_text("cuTensorMapEncodeTiled failed for Y");
+      return MSK_ECUDA;
+    }
+  }
+  const uint32_t idesc = make_idesc(kTcBM, t.NT, bf16);
+  const int stage_bytes = kTcBM * kTcBK * 2 + t.parts * t.NT * kTcBK * 2;
+  const size_t smem = (size_t)t.stages * stage_bytes + 1024 + 256;
+  dim3 grid(t.Mt, t.Nt, t.S);
+  if (t.parts == 3) {
+    MSK_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    tc_gemm_kernel<3><<<grid, kTcThreads, smem, st>>>(tmA, tmB, (int)p, (int)ncol, t.NT, t.KT, t.kt_per,
+                                                      t.stages, idesc, part);
+  } else {
+    MSK_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    tc_gemm_kernel<1><<<grid, kTcThreads, smem, st>>>(tmA, tmB, (int)p, (int)ncol, t.NT, t.KT, t.kt_per,
+                                                      t.stages, idesc, part);
+  }
+  MSK_CHECK_LAUNCH("tc_gemm_kernel");
+  const int64_t total = p * ncol;
+  tc_reduce_kernel<<<(unsigned)std::min<int64_t>((total + 255) / 256, num_sms() * 8), 256, 0, st>>>(
+      part, t.S, p, ncol, Z, ldz);
+  MSK_CHECK_LAUNCH("tc_reduce_kernel");
+  return MSK_OK;
+}
+
+// Reads and clears the timeout flag of the tensor-core kernel (synchronises).
+int tc_take_timeout(cudaStream_t st) {
+  int h = 0, zero = 0;
+  MSK_CUDA(cudaStreamSynchronize(st));
+  MSK_CUDA(cudaMemcpyFromSymbol(&h, g_tc_timeout, sizeof(int)));
+  if (h) MSK_CUDA(cudaMemcpyToSymbol(g_tc_timeout, &zero, sizeof(int)));
+  return h ? MSK_ETIMEOUT : MSK_OK;
+}
+
 }  // namespace msk

@@ -91,3 +91,13 @@ def test_cholesky(orc):
     assert np.allclose(R, np.linalg.cholesky(Gm).T, atol=1e-12)
     _, info = orc.cholesky_upper(np.diag([1.0, -1.0, 2.0]))
     assert info == 2
+
+
+def test_split_bf16x3(orc):
+    y = (np.random.default_rng(9).standard_normal(20000) * 10.0 ** np.random.default_rng(10).integers(-8, 8, 20000)).astype(np.float32)
+    s = orc.split_bf16x3(y)
+    # three bfloat16 parts carry 24 significant bits: y is recovered to 2^-24 |y|
+    assert np.all(np.abs(s - y.astype(np.float64)) <= 2.0 ** -24 * np.abs(y))
+    # values already in bfloat16 are their own first part
+    yb = orc.round_bf16(y)
+    assert np.array_equal(orc.split_bf16x3(yb), yb.astype(np.float64))
