@@ -98,7 +98,8 @@ typedef enum { MSK_CS_ATOMIC = 0, MSK_CS_SORTED = 1 } msk_cs_strategy;
 
 /* Result summary of a least-squares solve (host struct). */
 typedef struct {
-  int32_t iters;      /* refinement iterations taken (0 for plain SnS) */
+  int32_t iters;      /* inner refinement iterations (= passes over A besides
+                         the FP64 residual passes); 0 for plain SnS */
   int32_t converged;  /* 1 when the stopping test held */
   double relres;      /* ||b - A x|| / ||b|| of the returned x (FP64) */
   double relres_sns;  /* the same for the sketch-and-solve start x0 */
@@ -112,6 +113,17 @@ const char *msk_version(void);
 /* Last CUDA error string seen by the library on this host thread (static
  * storage, empty when none). */
 const char *msk_last_error(void);
+
+/* ---- Tuning registry (set by the autotuner, read by the launchers) ------- */
+
+/* Named integer knobs, e.g. "cs.f64.variant" (0 = warp reductions,
+ * 1 = TMA bulk reductions per row), "tc.kt_per" (K tiles per CTA of the
+ * tensor-core GEMM).  Unset knobs mean "launcher default".  Process-wide and
+ * thread-safe; they change speed only, never results beyond rounding order.
+ * msk_tune_set returns -1 for an empty name; msk_tune_clear(NULL) clears all. */
+int msk_tune_set(const char *name, long long value);
+long long msk_tune_get(const char *name, long long dflt);
+int msk_tune_clear(const char *name);
 
 /* ---- Sketch randomness (test hooks) ------------------------------------ */
 
@@ -237,10 +249,13 @@ size_t msk_lstsq_workspace(int64_t d, int64_t n, int64_t k, int64_t p,
  *   refine = 0 : sketch-and-solve, Algorithm 1: Z = G S [A b] (p x (n+1)),
  *     Householder QR of Z, x = R11^{-1} (Q^T z) with Q^T z = R[0:n, n].
  *   refine = 1 : then sketch-and-precondition refinement (the iterative
- *     route Section 6 cites, Blendenpik / LSRN): conjugate gradients on the
- *     normal equations right-preconditioned by R11, with residuals
- *     r = b - A x and A^T r accumulated in FP64, until the relative residual
- *     changes by at most tol * relres, or max_iter iterations.
+ *     route Section 6 cites, Blendenpik / LSRN).  Each outer step forms the
+ *     residual r = b - A x and g = A^T r in FP64 (one pass over A), then runs
+ *     conjugate gradients on A^T A d = g preconditioned by R11^T R11 (one pass
+ *     over A per iteration; FP64 for FP64 A, double-single arithmetic on the
+ *     FP32 units for FP32 A) until the preconditioned residual drops by 1e-6,
+ *     and sets x += d.  Stops when the relative residual changes by at most
+ *     tol * relres between outer steps, or after max_iter outer steps.
  *   A : device column-major d x n (lda), dtype F64 or F32; b : device double[d].
  *   x : device double[n] (output).
  *   info : host msk_lstsq_info* or NULL; when non-NULL the stream is

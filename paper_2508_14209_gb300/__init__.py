@@ -34,7 +34,8 @@ GEMM_PRECS = {"f64": GEMM_F64, "f32": GEMM_F32, "bf16": GEMM_BF16, "f16": GEMM_F
 EXPORTS = ("msk_version", "msk_last_error", "cs_hash", "ms_gaussian", "msk_cs_workspace",
            "cs_sketch", "msk_ms_workspace", "ms_sketch", "msk_gemm_workspace", "msk_gemm",
            "msk_householder_qr", "msk_trsv_upper", "msk_lstsq_workspace", "ms_lstsq",
-           "msk_ne_workspace", "ne_lstsq", "msk_gemm_noalloc")
+           "msk_ne_workspace", "ne_lstsq", "msk_gemm_noalloc", "msk_tune_set", "msk_tune_get",
+           "msk_tune_clear")
 
 NOALLOC_SCRATCH_BYTES = 24 << 20
 
@@ -83,6 +84,9 @@ def _declare(L):
                              _p, _sz, _p]),
         "msk_gemm_workspace": (_sz, [_i64, _i64, _i64, _int]),
         "msk_gemm": (_int, [_u64, _i64, _i64, _i64, _p, _i64, _int, _p, _i64, _p, _sz, _p]),
+        "msk_tune_set": (_int, [ctypes.c_char_p, ctypes.c_longlong]),
+        "msk_tune_get": (ctypes.c_longlong, [ctypes.c_char_p, ctypes.c_longlong]),
+        "msk_tune_clear": (_int, [ctypes.c_char_p]),
         "msk_gemm_noalloc": (_int, [_u64, _i64, _i64, _i64, _p, _i64, _int, _p, _i64, _p]),
         "msk_householder_qr": (_int, [_p, _i64, _i64, _i64, _p]),
         "msk_trsv_upper": (_int, [_p, _i64, _i64, _p, _p, _p]),
@@ -96,6 +100,18 @@ def _declare(L):
         f = getattr(L, name)
         f.restype = res
         f.argtypes = args
+
+
+def tune_set(name: str, value: int) -> None:
+    _check("msk_tune_set", load().msk_tune_set(name.encode(), int(value)))
+
+
+def tune_get(name: str, default: int = -1) -> int:
+    return int(load().msk_tune_get(name.encode(), int(default)))
+
+
+def tune_clear(name: str | None = None) -> None:
+    load().msk_tune_clear(None if name is None else name.encode())
 
 
 def version() -> str:

@@ -35,7 +35,7 @@ static size_t dtype_size(int dtype) { return dtype == MSK_F64 ? 8 : 4; }
 // Row pitch of the CountSketch Y inside ms_sketch's workspace: FP32 rows are
 // padded to 4 elements so the vector reductions stay 16-byte aligned.
 static int64_t ws_ldy(int64_t ncol, int dtype) {
-  return dtype == MSK_F32 ? (ncol + 3) / 4 * 4 : ncol;
+  return dtype == MSK_F32 ? (ncol + 3) / 4 * 4 : (ncol + 1) / 2 * 2;
 }
 
 static bool is_tensor_prec(int prec) {
@@ -106,6 +106,16 @@ size_t msk_cs_workspace(int64_t d, int64_t n, int64_t k, int dtype, int strategy
 int cs_sketch(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, const double* b,
               int64_t k, uint64_t seed, void* Y, int64_t ldy, int strategy, void* ws,
               size_t ws_bytes, void* stream) {
+  return cs_sketch_internal(A, dtype, d, n, lda, b, k, seed, Y, ldy, strategy, ws, ws_bytes,
+                            false, as_stream(stream));
+}
+
+}  // extern "C"
+
+int msk::cs_sketch_internal(const void* A, int dtype, int64_t d, int64_t n, int64_t lda,
+                            const double* b, int64_t k, uint64_t seed, void* Y, int64_t ldy,
+                            int strategy, void* ws, size_t ws_bytes, bool pad_ok,
+                            cudaStream_t st) {
   if (!A && d > 0 && n > 0) return -1;
   if (dtype != MSK_F64 && dtype != MSK_F32) return -2;
   if (d < 0) return -3;
@@ -116,14 +126,15 @@ int cs_sketch(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, const
   if (!Y) return -9;
   if (ldy < ncol) return -10;
   if (strategy != MSK_CS_ATOMIC && strategy != MSK_CS_SORTED) return -11;
-  cudaStream_t st = as_stream(stream);
   const uint64_t key = stream_key(seed, kTagHash);
   if (strategy == MSK_CS_ATOMIC)
-    return launch_cs_atomic(A, dtype, d, n, lda, b, (uint32_t)k, key, Y, ldy, st);
+    return launch_cs_atomic(A, dtype, d, n, lda, b, (uint32_t)k, key, Y, ldy, pad_ok, st);
   if (d >= (1LL << 31) || k >= (1LL << 31)) return MSK_ENOTSUP;
   if (ws_bytes < cs_sorted_workspace(d, k)) return MSK_ENOMEM;
   return launch_cs_sorted(A, dtype, d, n, lda, b, (uint32_t)k, key, Y, ldy, ws, ws_bytes, st);
 }
+
+extern "C" {
 
 size_t msk_gemm_workspace(int64_t p, int64_t k, int64_t ncol, int gemm_prec) {
   Need nd;
@@ -190,7 +201,8 @@ int ms_sketch(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, const
   const size_t cs_ws = msk_cs_workspace(d, n, k, dtype, strategy);
   void* csw = cv.take(cs_ws);
   if (!Y) return MSK_ENOMEM;
-  int rc = cs_sketch(A, dtype, d, n, lda, b, k, seed, Y, ldy, strategy, csw, cs_ws, stream);
+  int rc = cs_sketch_internal(A, dtype, d, n, lda, b, k, seed, Y, ldy, strategy, csw, cs_ws,
+                              true, st);
   if (rc) return rc;
   const size_t rest_off = align_up(cv.used, 256);
   return gemm_stage(seed, p, k, ncol, Y, dtype, ldy, gemm_prec, static_cast<double*>(Z), ldz,

@@ -228,28 +228,322 @@ static int cs_atomic_chunk(CsParams<T> P, cudaStream_t st) {
   return launch_cs_atomic_t<T, 64, false>(P, st);
 }
 
+// FP64 variant with TMA bulk reductions: a lane loads two columns of its row,
+// applies the row's sign and stores them as one 16-byte vector (pitch/2 odd:
+// conflict-free); then warp 0 hands each row of the tile to the TMA unit with
+// one cp.reduce.async.bulk .add.f64 (Y row = 16-byte aligned, length a
+// multiple of 16 bytes), so the SM issues one instruction per row instead of
+// one reduction per element.  A row buffer is rewritten two tiles later, after
+// its bulk reads have drained (cp.async.bulk.wait_group.read 1, then a CTA
+// barrier).  nbulk = columns handed to the bulk unit (even); an odd last
+// column that may not be padded goes through a warp reduction.
+template <int QMAX>
+__global__ void __launch_bounds__(kCsThreads) cs_bulk_f64_kernel(const CsParams<double> P, int nbulk) {
+  extern __shared__ __align__(16) unsigned char cs_smem[];
+  double* tiles = reinterpret_cast<double*>(cs_smem);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int npairs = (P.ncol + 1) >> 1;
+  const int64_t ntiles = (P.d + kCsRows - 1) / kCsRows;
+  int buf = 0;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, buf ^= 1) {
+    const int64_t i0 = t * kCsRows;
+    const int64_t i = i0 + lane;
+    const bool row_ok = i < P.d;
+    const uint64_t z = row_ok ? draw(P.key, (uint64_t)i) : 0ull;
+    const unsigned long long sgn = negative_of(z) ? 0x8000000000000000ull : 0ull;
+    double* tile = tiles + buf * kCsRows * P.pitch;
+    double2 v[QMAX];
+#pragma unroll
+    for (int q = 0; q < QMAX; ++q) {
+      const int g = warp + q * kCsWarps;
+      double2 x = make_double2(0.0, 0.0);
+      if (row_ok && g < npairs) {
+        x.x = load_col(P, i, 2 * g);
+        x.y = load_col(P, i, 2 * g + 1);
+      }
+      x.x = __longlong_as_double(__double_as_longlong(x.x) ^ sgn);
+      x.y = __longlong_as_double(__double_as_longlong(x.y) ^ sgn);
+      v[q] = x;
+    }
+    if (warp == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+    __syncthreads();  // buffer `buf` no longer read by the bulk unit
+#pragma unroll
+    for (int q = 0; q < QMAX; ++q) {
+      const int g = warp + q * kCsWarps;
+      if (g < npairs) *reinterpret_cast<double2*>(&tile[lane * P.pitch + 2 * g]) = v[q];
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+      if (row_ok) {
+        double* yrow = P.Y + (int64_t)bucket_of(z, P.k) * P.ldy;
+        const uint32_t src = (uint32_t)__cvta_generic_to_shared(tile + lane * P.pitch);
+        if (nbulk > 0)
+          asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f64 [%0], [%1], %2;"
+                       ::"l"(yrow), "r"(src), "r"(nbulk * 8)
+                       : "memory");
+        if (nbulk < P.ncol) red_add(yrow + nbulk, tile[lane * P.pitch + nbulk]);
+      }
+      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    }
+  }
+  if (warp == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+template <int QMAX>
+static int launch_cs_bulk_t(const CsParams<double>& P, int nbulk, cudaStream_t st) {
+  const size_t smem = 2 * sizeof(double) * kCsRows * P.pitch;
+  auto kern = cs_bulk_f64_kernel<QMAX>;
+  MSK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  MSK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kCsThreads, smem));
+  per_sm = std::max(per_sm, 1);
+  const int64_t ntiles = (P.d + kCsRows - 1) / kCsRows;
+  const int64_t grid = std::min<int64_t>(ntiles, (int64_t)num_sms() * per_sm);
+  if (grid <= 0) return MSK_OK;
+  kern<<<(unsigned)grid, kCsThreads, smem, st>>>(P, nbulk);
+  MSK_CHECK_LAUNCH("cs_bulk_f64_kernel");
+  return MSK_OK;
+}
+
+// Returns 1 when the bulk variant ran, 0 when it does not apply.
+static int cs_bulk_f64_chunk(CsParams<double> P, bool pad_ok, cudaStream_t st, int* rc) {
+  *rc = MSK_OK;
+  if (tune_get("cs.f64.variant", 0) != 1) return 0;
+  if ((reinterpret_cast<uintptr_t>(P.Y) & 15) != 0 || (P.ldy & 1) != 0) return 0;
+  int nbulk = P.ncol & ~1;
+  if ((P.ncol & 1) && pad_ok && P.ldy >= P.ncol + 1) nbulk = P.ncol + 1;
+  const int npairs = (P.ncol + 1) >> 1;
+  P.pitch = 2 * (npairs | 1);  // pitch/2 odd, pitch >= ncol (+1 pad column, zero)
+  const int q = (npairs + kCsWarps - 1) / kCsWarps;
+  if (q <= 1) *rc = launch_cs_bulk_t<1>(P, nbulk, st);
+  else if (q <= 2) *rc = launch_cs_bulk_t<2>(P, nbulk, st);
+  else if (q <= 4) *rc = launch_cs_bulk_t<4>(P, nbulk, st);
+  else if (q <= 9) *rc = launch_cs_bulk_t<9>(P, nbulk, st);
+  else if (q <= 17) *rc = launch_cs_bulk_t<17>(P, nbulk, st);
+  else *rc = launch_cs_bulk_t<24>(P, nbulk, st);
+  return 1;
+}
+
+// Fixed-width variants (NCA = A columns per launch, known at compile time,
+// plus an optional b column): fully unrolled loads, the row's sign applied
+// by XOR of the sign bit while transposing, fixed reduction offsets.  Same
+// tile scheme as cs_atomic_kernel.  FP64: lane = column, red.add.f64.
+// FP32: 4 columns per lane, red.add.v4.f32 (a row of 4*L columns takes L
+// lanes; several rows per warp instruction when 4*L < 128).
+__device__ __forceinline__ double flip(double x, unsigned long long s) {
+  return __longlong_as_double(__double_as_longlong(x) ^ s);
+}
+__device__ __forceinline__ float flip(float x, unsigned s) {
+  return __uint_as_float(__float_as_uint(x) ^ s);
+}
+
+template <int NCA, bool HAS_B>
+__global__ void __launch_bounds__(kCsThreads) cs_fixed_f64_kernel(const CsParams<double> P) {
+  constexpr int NCOL = NCA + (HAS_B ? 1 : 0);
+  constexpr int PITCH = NCOL | 1;
+  constexpr int Q = (NCA + kCsWarps - 1) / kCsWarps;
+  __shared__ double tiles[2][kCsRows][PITCH];
+  __shared__ uint64_t hz[2][kCsRows];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t ntiles = (P.d + kCsRows - 1) / kCsRows;
+  int buf = 0;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, buf ^= 1) {
+    const int64_t i0 = t * kCsRows;
+    const int64_t i = i0 + lane;
+    const bool row_ok = i < P.d;
+    double v[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const int j = warp + q * kCsWarps;
+      v[q] = (row_ok && j < NCA) ? __ldcs(P.A + i + (int64_t)j * P.lda) : 0.0;
+    }
+    double vb = 0.0;
+    if (HAS_B && warp == kCsWarps - 1) vb = row_ok ? __ldcs(P.b + i) : 0.0;
+    if (warp == 0) hz[buf][lane] = row_ok ? draw(P.key, (uint64_t)i) : 0ull;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const int j = warp + q * kCsWarps;
+      if (j < NCA) tiles[buf][lane][j] = v[q];
+    }
+    if (HAS_B && warp == kCsWarps - 1) tiles[buf][lane][NCA] = vb;
+    __syncthreads();
+#pragma unroll
+    for (int rr = 0; rr < kCsRows / kCsWarps; ++rr) {
+      const int r = warp + rr * kCsWarps;
+      if (i0 + r >= P.d) break;
+      const uint64_t z = hz[buf][r];
+      double* yrow = P.Y + (int64_t)bucket_of(z, P.k) * P.ldy;
+      const unsigned long long sg = negative_of(z) ? 0x8000000000000000ull : 0ull;
+#pragma unroll
+      for (int c = lane; c < NCA; c += 32) red_add(yrow + c, flip(tiles[buf][r][c], sg));
+      if (HAS_B && lane == 0) red_add(yrow + NCA, flip(tiles[buf][r][NCA], sg));
+    }
+  }
+}
+
+template <int NCA, bool HAS_B>
+__global__ void __launch_bounds__(kCsThreads) cs_fixed_f32_kernel(const CsParams<float> P) {
+  constexpr int NG = (NCA + 3) / 4;             // 4-column groups of A
+  constexpr int PITCH = 4 * ((NG + 1) | 1);     // room for b's group, pitch/4 odd
+  constexpr int QG = (NG + kCsWarps - 1) / kCsWarps;
+  constexpr int LPR = NCA / 4 < 32 ? NCA / 4 : 32;  // lanes per row in the reduction phase
+  constexpr int RPI = 32 / LPR;                 // rows per warp instruction
+  __shared__ __align__(16) float tiles[2][kCsRows][PITCH];
+  __shared__ uint64_t hz[2][kCsRows];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t ntiles = (P.d + kCsRows - 1) / kCsRows;
+  int buf = 0;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, buf ^= 1) {
+    const int64_t i0 = t * kCsRows;
+    const int64_t i = i0 + lane;
+    const bool row_ok = i < P.d;
+    float4 v[QG];
+#pragma unroll
+    for (int q = 0; q < QG; ++q) {
+      const int g = warp + q * kCsWarps;
+      float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (row_ok && g < NG) {
+        const float* a = P.A + i + (int64_t)(4 * g) * P.lda;
+        x.x = __ldcs(a);
+        x.y = __ldcs(a + P.lda);
+        x.z = __ldcs(a + 2 * P.lda);
+        x.w = __ldcs(a + 3 * P.lda);
+      }
+      v[q] = x;
+    }
+    float vb = 0.f;
+    if (HAS_B && warp == kCsWarps - 1) vb = row_ok ? (float)__ldcs(P.b + i) : 0.f;
+    if (warp == 0) hz[buf][lane] = row_ok ? draw(P.key, (uint64_t)i) : 0ull;
+#pragma unroll
+    for (int q = 0; q < QG; ++q) {
+      const int g = warp + q * kCsWarps;
+      if (g < NG) *reinterpret_cast<float4*>(&tiles[buf][lane][4 * g]) = v[q];
+    }
+    if (HAS_B && warp == kCsWarps - 1) tiles[buf][lane][NCA] = vb;
+    __syncthreads();
+    // reduction phase: RPI rows per warp instruction, row groups spread over warps
+#pragma unroll
+    for (int r0 = warp * RPI; r0 < kCsRows; r0 += kCsWarps * RPI) {
+      const int r = r0 + lane / LPR;
+      const int cl = lane % LPR;
+      const bool ok = i0 + r < P.d;
+      const uint64_t z = hz[buf][r];
+      float* yrow = P.Y + (int64_t)bucket_of(z, P.k) * P.ldy;
+      const unsigned sg = negative_of(z) ? 0x80000000u : 0u;
+      if (ok) {
+#pragma unroll
+        for (int c = 4 * cl; c < NCA; c += 4 * LPR) {
+          const float4 x = *reinterpret_cast<const float4*>(&tiles[buf][r][c]);
+          red_add_v4(yrow + c, flip(x.x, sg), flip(x.y, sg), flip(x.z, sg), flip(x.w, sg));
+        }
+        if (HAS_B && cl == 0) red_add(yrow + NCA, flip(tiles[buf][r][NCA], sg));
+      }
+    }
+  }
+}
+
+template <typename KernT, typename ParT>
+static int launch_fixed(KernT kern, const ParT& P, cudaStream_t st) {
+  int per_sm = 0;
+  MSK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kCsThreads, 0));
+  per_sm = std::max(per_sm, 1);
+  const int64_t ntiles = (P.d + kCsRows - 1) / kCsRows;
+  const int64_t grid = std::min<int64_t>(ntiles, (int64_t)num_sms() * per_sm);
+  if (grid <= 0) return MSK_OK;
+  kern<<<(unsigned)grid, kCsThreads, 0, st>>>(P);
+  MSK_CHECK_LAUNCH("cs_fixed_kernel");
+  return MSK_OK;
+}
+
+// Returns 1 when a fixed-width kernel covered this chunk.
+template <typename T>
+static int cs_fixed_chunk(const CsParams<T>& P, cudaStream_t st, int* rc) {
+  *rc = MSK_OK;
+  if (tune_get("cs.fixed", 1) == 0) return 0;
+  const bool hb = P.b != nullptr;
+  if (P.ncol != P.ncol_a + (hb ? 1 : 0)) return 0;
+  const int nca = P.ncol_a;
+  if constexpr (sizeof(T) == 8) {
+#define MSK_FIX64(N)                                                          \
+  if (nca == N) {                                                             \
+    *rc = hb ? launch_fixed(cs_fixed_f64_kernel<N, true>, P, st)              \
+             : launch_fixed(cs_fixed_f64_kernel<N, false>, P, st);            \
+    return 1;                                                                 \
+  }
+    MSK_FIX64(16) MSK_FIX64(32) MSK_FIX64(64) MSK_FIX64(128) MSK_FIX64(256)
+#undef MSK_FIX64
+  } else {
+    // v4 reductions need 16-byte aligned Y rows
+    if ((P.ldy % 4) != 0 || (reinterpret_cast<uintptr_t>(P.Y) & 15) != 0) return 0;
+#define MSK_FIX32(N)                                                          \
+  if (nca == N) {                                                             \
+    *rc = hb ? launch_fixed(cs_fixed_f32_kernel<N, true>, P, st)              \
+             : launch_fixed(cs_fixed_f32_kernel<N, false>, P, st);            \
+    return 1;                                                                 \
+  }
+    MSK_FIX32(16) MSK_FIX32(32) MSK_FIX32(64) MSK_FIX32(128) MSK_FIX32(256)
+#undef MSK_FIX32
+  }
+  return 0;
+}
+
 template <typename T>
 static int cs_atomic_typed(const T* A, int64_t d, int64_t n, int64_t lda, const double* b,
-                           uint32_t k, uint64_t key, T* Y, int64_t ldy, cudaStream_t st) {
+                           uint32_t k, uint64_t key, T* Y, int64_t ldy, bool pad_ok,
+                           cudaStream_t st) {
   const int64_t ncol = n + (b ? 1 : 0);
   MSK_CUDA(cudaMemset2DAsync(Y, (size_t)ldy * sizeof(T), 0, (size_t)ncol * sizeof(T), (size_t)k, st));
   if (d == 0 || ncol == 0) return MSK_OK;
   // Column chunks of at most kCsMaxColsF64/F32; b rides with the last chunk.
-  const int64_t maxc = sizeof(T) == 8 ? kCsMaxColsF64 : kCsMaxColsF32;
-  for (int64_t c0 = 0; c0 < ncol; c0 += maxc) {
-    const int64_t c1 = std::min<int64_t>(ncol, c0 + maxc);
+  // Column chunks: at most the shared-memory limit, and narrow enough that the
+  // chunk's slice of Y (k x chunk) stays resident in L2 (about 40% of it) —
+  // reductions that miss L2 turn into DRAM read-modify-writes.  A is still read
+  // once: each chunk reads only its own columns.
+  int64_t maxc = sizeof(T) == 8 ? kCsMaxColsF64 : kCsMaxColsF32;
+  {
+    static int l2_bytes = 0;
+    if (l2_bytes == 0) {
+      int dev = 0;
+      if (cudaGetDevice(&dev) != cudaSuccess ||
+          cudaDeviceGetAttribute(&l2_bytes, cudaDevAttrL2CacheSize, dev) != cudaSuccess ||
+          l2_bytes <= 0)
+        l2_bytes = 64 << 20;
+    }
+    const int64_t budget = tune_get("cs.l2_budget_bytes", (long long)l2_bytes * 2 / 5);
+    int64_t fit = budget / ((int64_t)k * (int64_t)sizeof(T));
+    fit = fit / 16 * 16;
+    if (fit >= 16 && fit < maxc) maxc = fit;
+  }
+  // chunks of A columns; b rides with the last one
+  const int64_t nchunks = n > 0 ? (n + maxc - 1) / maxc : 1;
+  for (int64_t ch = 0; ch < nchunks; ++ch) {
+    const int64_t c0 = ch * maxc, c1 = std::min<int64_t>(n, c0 + maxc);
+    const bool last = ch == nchunks - 1;
     CsParams<T> P{};
     P.A = A + c0 * lda;
     P.d = d;
     P.lda = lda;
-    P.ncol_a = (int)(std::min<int64_t>(c1, n) - std::min<int64_t>(c0, n));
-    P.b = (b && c1 == ncol) ? b : nullptr;
-    P.ncol = (int)(c1 - c0);
+    P.ncol_a = (int)(c1 - c0);
+    P.b = (b && last) ? b : nullptr;
+    P.ncol = P.ncol_a + (P.b ? 1 : 0);
+    if (P.ncol == 0) continue;
     P.k = k;
     P.key = key;
     P.Y = Y + c0;
     P.ldy = ldy;
-    int rc = cs_atomic_chunk<T>(P, st);
+    int rc = MSK_OK;
+    if (cs_fixed_chunk<T>(P, st, &rc)) {
+      if (rc) return rc;
+      continue;
+    }
+    if constexpr (sizeof(T) == 8) {
+      if (cs_bulk_f64_chunk(P, pad_ok && last, st, &rc)) {
+        if (rc) return rc;
+        continue;
+      }
+    }
+    rc = cs_atomic_chunk<T>(P, st);
     if (rc) return rc;
   }
   return MSK_OK;
@@ -257,12 +551,12 @@ static int cs_atomic_typed(const T* A, int64_t d, int64_t n, int64_t lda, const 
 
 int launch_cs_atomic(const void* A, int dtype, int64_t d, int64_t n, int64_t lda,
                      const double* b, uint32_t k, uint64_t key, void* Y, int64_t ldy,
-                     cudaStream_t st) {
+                     bool pad_ok, cudaStream_t st) {
   if (dtype == MSK_F64)
     return cs_atomic_typed<double>(static_cast<const double*>(A), d, n, lda, b, k, key,
-                                   static_cast<double*>(Y), ldy, st);
+                                   static_cast<double*>(Y), ldy, pad_ok, st);
   return cs_atomic_typed<float>(static_cast<const float*>(A), d, n, lda, b, k, key,
-                                static_cast<float*>(Y), ldy, st);
+                                static_cast<float*>(Y), ldy, pad_ok, st);
 }
 
 // ---------------------------------------------------------------------------

@@ -258,6 +258,193 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                  : "memory");
 }
 
+// ---------------------------------------------------------------------------
+// BF16X3 with per-K-tile draining.  A single FP32 accumulator over a CTA's
+// whole K slice loses about sqrt(C/2) ulps over a chain of C products
+// (C ~ 4e4 here), which made R too inexact to precondition kappa(A) ~ 1e8.
+// So the MMA warp restarts the accumulator every 64-wide K tile (C = 192 exact
+// products) in one of two TMEM buffers, and 16 drain warps read each finished
+// buffer (tcgen05.ld) and add it into double-single registers (hi + lo binary32
+// pairs, TwoSum), while the MMA warp fills the other buffer.  Drain warp w
+// covers TMEM lanes 32 (w mod 4) .. +31 and a quarter of the NT columns.
+// Per-CTA results are written as FP64 partials.
+constexpr int kDsDrainWarps = 16;
+constexpr int kDsThreads = (2 + kDsDrainWarps) * 32;
+constexpr int kDsMaxCpw = 24;  // columns per drain warp (NT <= 96): keeps hi/lo in registers
+
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&v)[4]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
+               : "r"(taddr));
+}
+__device__ __forceinline__ void ds_accum(float& hi, float& lo, float v) {
+  const float s = hi + v;
+  const float bb = s - hi;
+  const float e = (hi - (s - bb)) + (v - bb);  // TwoSum error of hi + v
+  const float t = lo + e;
+  hi = s + t;
+  lo = t - (hi - s);
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
+
+__global__ void __launch_bounds__(kDsThreads, 1)
+    tc_gemm_ds_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                      int p, int ncol, int NT, int KT, int kt_per, int stages, uint32_t idesc,
+                      double* __restrict__ part) {
+  constexpr int PARTS = 3;
+  extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
+  unsigned char* smem =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~uintptr_t(1023));
+  const uint32_t a_bytes = kTcBM * kTcBK * 2;
+  const uint32_t b_bytes = (uint32_t)NT * kTcBK * 2;
+  const uint32_t stage_bytes = a_bytes + PARTS * b_bytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)stages * stage_bytes);
+  // bars: full[stages], empty[stages], accf[2], acce[2]
+  uint64_t* accf = bars + 2 * stages;
+  uint64_t* acce = accf + 2;
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(acce + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * kTcBM, n0 = blockIdx.y * NT;
+  const int kt0 = blockIdx.z * kt_per;
+  const int nk = min(KT, kt0 + kt_per) - kt0;
+  constexpr uint32_t kCols = 512;  // two accumulator buffers at columns 0 and 256
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < stages; ++s) {
+      mbar_init(smem_u32(&bars[s]), 1);
+      mbar_init(smem_u32(&bars[stages + s]), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&accf[b]), 1);
+      mbar_init(smem_u32(&acce[b]), kDsDrainWarps);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_holder)),
+                 "r"(kCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_holder;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int issued = 0;
+      for (int it = 0; it < nk; ++it) {
+        const int s = it % stages;
+        if (it >= stages && !mbar_wait(smem_u32(&bars[stages + s]), ((it / stages) & 1) ^ 1)) {
+          *abort_flag = 1;
+          break;
+        }
+        if (*abort_flag) break;
+        const uint32_t full = smem_u32(&bars[s]);
+        mbar_expect_tx(full, stage_bytes);
+        unsigned char* st = smem + (size_t)s * stage_bytes;
+        const int kc = (kt0 + it) * kTcBK;
+        tma_load_2d(smem_u32(st), &tmA, kc, m0, full);
+#pragma unroll
+        for (int t = 0; t < PARTS; ++t)
+          tma_load_3d(smem_u32(st + a_bytes + t * b_bytes), &tmB, kc, n0, t, full);
+        ++issued;
+      }
+      if (*abort_flag)
+        for (int it = (issued > stages ? issued - stages : 0); it < issued; ++it)
+          mbar_wait(smem_u32(&bars[it % stages]), (it / stages) & 1);
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      for (int it = 0; it < nk; ++it) {
+        const int s = it % stages;
+        const int b = it & 1, u = it >> 1;
+        if (u >= 1 && !mbar_wait(smem_u32(&acce[b]), (u - 1) & 1)) {
+          *abort_flag = 1;
+          break;
+        }
+        if (!mbar_wait(smem_u32(&bars[s]), (it / stages) & 1)) {
+          *abort_flag = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t a_base = smem_u32(smem + (size_t)s * stage_bytes);
+        const uint32_t d = tmem + (uint32_t)b * 256u;
+#pragma unroll
+        for (int kk = 0; kk < kTcBK / 16; ++kk) {
+          const uint64_t ad = sw128_desc(a_base + kk * 32);
+#pragma unroll
+          for (int t = 0; t < PARTS; ++t) {
+            const uint64_t bd = sw128_desc(a_base + a_bytes + t * b_bytes + kk * 32);
+            umma_f16(d, ad, bd, idesc, (kk > 0 || t > 0) ? 1u : 0u);
+          }
+        }
+        umma_commit(smem_u32(&bars[stages + s]));
+        umma_commit(smem_u32(&accf[b]));
+      }
+    }
+    __syncwarp();
+  } else {
+    // drain warps
+    const int dw = warp - 2;
+    const int quad = warp & 3;
+    const int cpw = NT / 4;
+    const int c_begin = (dw >> 2) * cpw;
+    float hi[kDsMaxCpw], lo[kDsMaxCpw];
+#pragma unroll
+    for (int c = 0; c < kDsMaxCpw; ++c) {
+      hi[c] = 0.f;
+      lo[c] = 0.f;
+    }
+    bool ok = true;
+    for (int it = 0; it < nk; ++it) {
+      const int b = it & 1, u = it >> 1;
+      const bool got = mbar_wait(smem_u32(&accf[b]), u & 1);
+      if (!__all_sync(0xffffffffu, got && !*abort_flag)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t base = tmem + (uint32_t)b * 256u + ((uint32_t)(quad * 32) << 16) + (uint32_t)c_begin;
+#pragma unroll
+      for (int c = 0; c < kDsMaxCpw; c += 4) {
+        if (c < cpw) {
+          uint32_t v[4];
+          tmem_ld4(base + (uint32_t)c, v);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int q = 0; q < 4; ++q) ds_accum(hi[c + q], lo[c + q], __uint_as_float(v[q]));
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&acce[b]));
+    }
+    if (ok && nk > 0) {
+      const int row = m0 + quad * 32 + lane;
+      double* out = part + (int64_t)blockIdx.z * p * ncol;
+#pragma unroll
+      for (int c = 0; c < kDsMaxCpw; ++c) {
+        const int col = n0 + c_begin + c;
+        if (c < cpw && row < p && col < ncol)
+          out[(int64_t)col * p + row] = (double)hi[c] + (double)lo[c];
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 2)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols)
+                 : "memory");
+}
+
 // Yt[t][n][kk] (row pitch kpitch) from the FP32 row-major Y (k x ncol, ldy):
 // PARTS = 1: round once (bf16 or fp16); PARTS = 3: bf16 split of the residues.
 // Rows n >= ncol (up to npad) are zero.  32x32 tiles transposed in shared memory.
@@ -323,7 +510,8 @@ static TcPlan tc_plan(int64_t p, int64_t k, int64_t ncol, int prec) {
   TcPlan t;
   t.parts = tc_parts(prec);
   t.npad = (int)((ncol + 15) / 16 * 16);
-  const int nt_max = t.parts == 3 ? 144 : 256;
+  const bool drain = t.parts == 3 && tune_get("tc.drain", 1) != 0;
+  const int nt_max = drain ? 4 * kDsMaxCpw : (t.parts == 3 ? 144 : 256);
   const int ntiles = (t.npad + nt_max - 1) / nt_max;
   t.NT = (int)(((t.npad + ntiles - 1) / ntiles + 15) / 16 * 16);
   t.Nt = (t.npad + t.NT - 1) / t.NT;
@@ -345,7 +533,7 @@ size_t tc_gemm_workspace(int64_t p, int64_t k, int64_t ncol, int prec) {
   Need nd;
   nd.add((size_t)p * t.kpitch * 2);                        // G (16-bit)
   nd.add((size_t)t.parts * t.npad * t.kpitch * 2);         // Yt parts (16-bit)
-  nd.add((size_t)t.S * p * ncol * sizeof(float));          // FP32 partials
+  nd.add((size_t)t.S * p * ncol * sizeof(double));         // partials (FP32 or FP64)
   return nd.used;
 }
 
@@ -371,7 +559,7 @@ int launch_tc_gemm(uint64_t gkey, int64_t p, int64_t k, int64_t ncol, const floa
   Carve cv(ws, ws_bytes);
   uint16_t* G = static_cast<uint16_t*>(cv.take((size_t)p * t.kpitch * 2));
   uint16_t* Yt = static_cast<uint16_t*>(cv.take((size_t)t.parts * t.npad * t.kpitch * 2));
-  float* part = static_cast<float*>(cv.take((size_t)t.S * p * ncol * sizeof(float)));
+  float* part = static_cast<float*>(cv.take((size_t)t.S * p * ncol * sizeof(double)));
   if (!G || !Yt || !part) return MSK_ENOMEM;
   int rc = launch_gaussian(gkey, p, k, bf16 ? MSK_GEMM_BF16 : MSK_GEMM_F16, G, t.kpitch, st);
   if (rc) return rc;
@@ -422,6 +610,18 @@ int launch_tc_gemm(uint64_t gkey, int64_t p, int64_t k, int64_t ncol, const floa
   const int stage_bytes = kTcBM * kTcBK * 2 + t.parts * t.NT * kTcBK * 2;
   const size_t smem = (size_t)t.stages * stage_bytes + 1024 + 256;
   dim3 grid(t.Mt, t.Nt, t.S);
+  const bool drain = t.parts == 3 && tune_get("tc.drain", 1) != 0;
+  if (drain) {
+    MSK_CUDA(cudaFuncSetAttribute(tc_gemm_ds_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    tc_gemm_ds_kernel<<<grid, kDsThreads, smem, st>>>(tmA, tmB, (int)p, (int)ncol, t.NT, t.KT, t.kt_per,
+                                                      t.stages, idesc, reinterpret_cast<double*>(part));
+    MSK_CHECK_LAUNCH("tc_gemm_ds_kernel");
+    const int64_t total = p * ncol;
+    splitk_reduce_kernel<<<(unsigned)std::min<int64_t>((total + 255) / 256, num_sms() * 8), 256, 0, st>>>(
+        reinterpret_cast<const double*>(part), t.S, p, ncol, Z, ldz);
+    MSK_CHECK_LAUNCH("splitk_reduce_kernel");
+    return MSK_OK;
+  }
   if (t.parts == 3) {
     MSK_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     tc_gemm_kernel<3><<<grid, kTcThreads, smem, st>>>(tmA, tmB, (int)p, (int)ncol, t.NT, t.KT, t.kt_per,

@@ -4,10 +4,12 @@
 //   * ms_lstsq, refine = 1: sketch-and-precondition refinement (the iterative
 //       route Section 6 cites).  Outer loop: true residual r = b - A x and
 //       g = A^T r in FP64 (one pass over A).  Inner loop: conjugate gradients
-//       on A^T A d = g preconditioned by M = R11^T R11, T iterations, each one
-//       pass over A computing A^T (A p) in FP32 (FP32 suffices for a
-//       correction; the FP64 outer residual sets the final accuracy).  Then
-//       x += d.  Stops when the relative residual changes by at most
+//       on A^T A d = g preconditioned by M = R11^T R11, each iteration one pass
+//       over A computing A^T (A p) — in FP64 for FP64 A, in double-single
+//       arithmetic on the FP32 units for FP32 A (binary32 alone fails: with
+//       kappa(A) * 2^-24 > 1 the products A p cancel to noise) — until the
+//       preconditioned residual norm drops by 1e-6 (at most 60 iterations).
+//       Then x += d.  Stops when the relative residual changes by at most
 //       tol * relres between outer steps.
 //   * ne_lstsq: normal equations (Section 6.3): [A b]^T [A b] in one FP64
 //       pass (split over row slices, partials summed in a fixed order),
@@ -252,22 +254,148 @@ static int launch_pass_t(const TA* A, int64_t lda, int64_t d, int n, const doubl
   return MSK_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Double-single pass for FP32 A: v = A^T (A p) with every sum carried as an
+// unevaluated pair hi + lo of binary32 numbers (Dekker 1971; Knuth's TwoSum;
+// the exact product a*b = hi + lo from one FMA).  About 48 significant bits,
+// enough for the inner iterations at kappa(A) up to ~1e10, at the cost of
+// ~13 FP32 operations per multiply-add instead of one FP64 operation (GB300's
+// FP64 rate is 1/66 of its FP32 rate).  p arrives in FP64 and is split into
+// hi + lo binary32 parts.
+struct DS {
+  float hi, lo;
+};
+__device__ __forceinline__ DS ds_add(DS a, float bh, float bl) {
+  const float s = a.hi + bh;
+  const float v = s - a.hi;
+  float e = (a.hi - (s - v)) + (bh - v);  // TwoSum error of a.hi + bh
+  e += a.lo + bl;
+  const float h = s + e;
+  return DS{h, e - (h - s)};
+}
+// acc += a * (xh + xl), a exact binary32.
+__device__ __forceinline__ DS ds_fma(DS acc, float a, float xh, float xl) {
+  const float ph = a * xh;
+  float pl = fmaf(a, xh, -ph);  // exact: a*xh = ph + pl
+  pl = fmaf(a, xl, pl);
+  return ds_add(acc, ph, pl);
+}
+__device__ __forceinline__ DS ds_shfl_xor(DS v, int m) {
+  return DS{__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m)};
+}
+
+// Tile: kPR rows x pitch floats, pitch = 4 (mod 32) so that 16-byte stores of
+// 4 columns (lane = row) and the row reads of the dot phase are conflict-free.
+__global__ void __launch_bounds__(kPThreads) pass_ds_kernel(const float* __restrict__ A, int64_t lda,
+                                                         int64_t d, int n, int pitch,
+                                                         const double* __restrict__ vin,
+                                                         double* __restrict__ part) {
+  extern __shared__ __align__(16) unsigned char ds_smem[];
+  float* tile = reinterpret_cast<float*>(ds_smem);  // kPR x pitch
+  float* ph = tile + kPR * pitch;                   // n: p hi
+  float* pl = ph + n;                               // n: p lo
+  float* wh = pl + n;                               // kPR: w hi
+  float* wl = wh + kPR;                             // kPR: w lo
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int j = threadIdx.x; j < n; j += kPThreads) {
+    const double x = vin[j];
+    const float h = (float)x;
+    ph[j] = h;
+    pl[j] = (float)(x - (double)h);
+  }
+  DS acc[2] = {{0.f, 0.f}, {0.f, 0.f}};
+  const int ngroups = (n + 3) >> 2;
+  const int64_t ntiles = (d + kPR - 1) / kPR;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t i0 = t * kPR;
+    __syncthreads();
+    // load: lane = row (two row halves), warp w takes 4-column groups w, w+8, ...
+    for (int g = warp; g < ngroups; g += kPThreads / 32) {
+#pragma unroll
+      for (int h = 0; h < kPR / 32; ++h) {
+        const int r = lane + 32 * h;
+        const int64_t i = i0 + r;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i < d) {
+          const int j = 4 * g;
+          v.x = __ldcs(A + i + (int64_t)j * lda);
+          if (j + 1 < n) v.y = __ldcs(A + i + (int64_t)(j + 1) * lda);
+          if (j + 2 < n) v.z = __ldcs(A + i + (int64_t)(j + 2) * lda);
+          if (j + 3 < n) v.w = __ldcs(A + i + (int64_t)(j + 3) * lda);
+        }
+        *reinterpret_cast<float4*>(&tile[r * pitch + 4 * g]) = v;
+      }
+    }
+    __syncthreads();
+    // dot phase: 4 threads per row, thread q takes columns q, q+4, ...
+    {
+      const int r = threadIdx.x >> 2, q = threadIdx.x & 3;
+      const float* row = tile + r * pitch;
+      DS w{0.f, 0.f};
+      for (int j = q; j < n; j += 4) w = ds_fma(w, row[j], ph[j], pl[j]);
+      DS o = ds_shfl_xor(w, 1);
+      w = ds_add(w, o.hi, o.lo);
+      o = ds_shfl_xor(w, 2);
+      w = ds_add(w, o.hi, o.lo);
+      if (q == 0) {
+        const bool ok = i0 + r < d;
+        wh[r] = ok ? w.hi : 0.f;
+        wl[r] = ok ? w.lo : 0.f;
+      }
+    }
+    __syncthreads();
+    // column phase: v_j += sum_r A[r][j] w_r
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int j = threadIdx.x + c * kPThreads;
+      if (j < n) {
+        DS a = acc[c];
+        for (int r = 0; r < kPR; ++r) a = ds_fma(a, tile[r * pitch + j], wh[r], wl[r]);
+        acc[c] = a;
+      }
+    }
+  }
+  double* out = part + (int64_t)blockIdx.x * (n + 2);
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const int j = threadIdx.x + c * kPThreads;
+    if (j < n) out[j] = (double)acc[c].hi + (double)acc[c].lo;
+  }
+  if (threadIdx.x == 0) {
+    out[n] = 0.0;
+    out[n + 1] = 0.0;
+  }
+}
+
+static int launch_pass_ds(const float* A, int64_t lda, int64_t d, int n, const double* vin,
+                          double* part, double* out, cudaStream_t st) {
+  int pitch = (n + 3) / 4 * 4;
+  while (pitch % 32 != 4) pitch += 4;
+  const size_t smem = sizeof(float) * ((size_t)kPR * pitch + 2 * n + 2 * kPR);
+  MSK_CUDA(cudaFuncSetAttribute(pass_ds_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int grid = pass_grid(d);
+  pass_ds_kernel<<<grid, kPThreads, smem, st>>>(A, lda, d, n, pitch, vin, part);
+  MSK_CHECK_LAUNCH("pass_ds_kernel");
+  pass_reduce_kernel<<<(n + 2 + 255) / 256, 256, 0, st>>>(part, grid, n + 2, out);
+  MSK_CHECK_LAUNCH("pass_reduce_kernel");
+  return MSK_OK;
+}
+
 // RESID: out = [A^T r (n), ||r||^2, ||b||^2] with r = b - A x (FP64).
-// else : out = [A^T A p (n), ||A p||^2, 0] (FP32 arithmetic).
+// else : out = [A^T A p (n), ., .] (FP64 for FP64 A, double-single for FP32 A).
 static int launch_pass(const void* A, int dtype, int64_t lda, int64_t d, int n, const double* b,
                        const double* vin, bool resid, double* part, double* out, cudaStream_t st) {
   if (dtype == MSK_F64) {
     if (resid)
       return launch_pass_t<double, double, true>(static_cast<const double*>(A), lda, d, n, b, vin,
                                                  part, out, st);
-    return launch_pass_t<double, float, false>(static_cast<const double*>(A), lda, d, n, b, vin, part,
-                                               out, st);
+    return launch_pass_t<double, double, false>(static_cast<const double*>(A), lda, d, n, b, vin,
+                                                part, out, st);
   }
   if (resid)
     return launch_pass_t<float, double, true>(static_cast<const float*>(A), lda, d, n, b, vin, part,
                                               out, st);
-  return launch_pass_t<float, float, false>(static_cast<const float*>(A), lda, d, n, b, vin, part,
-                                            out, st);
+  return launch_pass_ds(static_cast<const float*>(A), lda, d, n, vin, part, out, st);
 }
 
 static size_t pass_workspace(int64_t d, int64_t n) {
@@ -408,7 +536,10 @@ __global__ void axpy_kernel(int n, const double* __restrict__ dlt, double* __res
     x[j] += dlt[j];
 }
 
-constexpr int kInnerIters = 6;  // CG iterations per outer (FP64 residual) step
+// Inner CG per outer (FP64 residual) step: stop when the preconditioned
+// residual norm has dropped by kInnerEta, or after kMaxInner iterations.
+constexpr int kMaxInner = 60;
+constexpr double kInnerEta = 1e-6;
 
 }  // namespace msk
 
@@ -475,7 +606,7 @@ int ms_lstsq(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, const 
   rc = launch_trsv_upper(Z, n, p, Z + n * p, x, nullptr, false, st);
   if (rc) return rc;
   double relres_sns = -1.0, relres = -1.0, bnorm2 = 0.0;
-  int iters = 0, converged = 1;
+  int iters = 0, converged = 1, inner_total = 0;
   int status = MSK_OK;
   if (refine) {
     double* Ri = static_cast<double*>(cv.take((size_t)n * n * sizeof(double)));
@@ -505,20 +636,27 @@ int ms_lstsq(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, const 
       }
       if (outer == max_iter) break;
       prev = rr;
-      iters = outer + 1;
-      // inner PCG on A^T A d = g (FP32 passes)
+      // inner PCG on A^T A d = g (double-single passes for FP32 A)
       MSK_CUDA(cudaMemcpyAsync(gsave, pout, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
       pcg_start_kernel<<<1, 512, 0, st>>>(Ri, (int)n, gsave, s);
       MSK_CHECK_LAUNCH("pcg_start_kernel");
-      for (int it = 0; it < kInnerIters; ++it) {
+      double rho0 = 0.0, rho = 0.0;
+      MSK_CUDA(cudaMemcpyAsync(&rho0, sc, sizeof(double), cudaMemcpyDeviceToHost, st));
+      MSK_CUDA(cudaStreamSynchronize(st));
+      for (int it = 0; it < kMaxInner && rho0 > 0.0; ++it) {
         rc = launch_pass(A, dtype, lda, d, (int)n, nullptr, s.p, false, part, pout, st);
         if (rc) return rc;
         pcg_update_kernel<<<1, 512, 0, st>>>(Ri, (int)n, pout, s);
         MSK_CHECK_LAUNCH("pcg_update_kernel");
+        ++inner_total;
+        MSK_CUDA(cudaMemcpyAsync(&rho, sc, sizeof(double), cudaMemcpyDeviceToHost, st));
+        MSK_CUDA(cudaStreamSynchronize(st));
+        if (!(rho > kInnerEta * kInnerEta * rho0)) break;
       }
       axpy_kernel<<<1, 512, 0, st>>>((int)n, s.dlt, x);
       MSK_CHECK_LAUNCH("axpy_kernel");
     }
+    iters = inner_total;
     if (!converged) status = MSK_ENOCONV;
   } else if (info) {
     rc = launch_pass(A, dtype, lda, d, (int)n, b, x, true, part, pout, st);

@@ -53,14 +53,22 @@ struct Need {
 };
 
 int num_sms();
+// Tuning registry lookup (tune.cpp).
+long long tune_get(const char* name, long long dflt);
 
 // ---- kernels launched across translation units -------------------------
 // countsketch.cu
 int launch_cs_hash(uint64_t key, int64_t i0, int64_t count, uint32_t k, uint32_t* h,
                    int8_t* s, cudaStream_t st);
+// pad_ok: the column after the last one of each Y row is scratch (ldy > ncol)
+// and may receive +0.0 from a padded bulk reduction.
 int launch_cs_atomic(const void* A, int dtype, int64_t d, int64_t n, int64_t lda,
                      const double* b, uint32_t k, uint64_t key, void* Y, int64_t ldy,
-                     cudaStream_t st);
+                     bool pad_ok, cudaStream_t st);
+// Internal CountSketch launch used by the multisketch (same checks as cs_sketch).
+int cs_sketch_internal(const void* A, int dtype, int64_t d, int64_t n, int64_t lda,
+                       const double* b, int64_t k, uint64_t seed, void* Y, int64_t ldy,
+                       int strategy, void* ws, size_t ws_bytes, bool pad_ok, cudaStream_t st);
 size_t cs_sorted_workspace(int64_t d, int64_t k);
 int launch_cs_sorted(const void* A, int dtype, int64_t d, int64_t n, int64_t lda,
                      const double* b, uint32_t k, uint64_t key, void* Y, int64_t ldy,
@@ -74,6 +82,9 @@ int launch_gemm_simt(const float* G, int64_t ldg, const void* Y, bool y_f64, int
                      int64_t p, int64_t k, int64_t ncol, double* Z, int64_t ldz, void* ws,
                      size_t ws_bytes, cudaStream_t st);
 
+// Z[r + c*ldz] = sum_s part[s][c*p + r] (FP64 partials, fixed order).
+__global__ void splitk_reduce_kernel(const double* __restrict__ part, int S, int64_t p, int64_t ncol,
+                                     double* __restrict__ Z, int64_t ldz);
 // gemm_tc.cu (tcgen05 tensor-core Gaussian stage)
 size_t tc_gemm_workspace(int64_t p, int64_t k, int64_t ncol, int prec);
 int launch_tc_gemm(uint64_t gkey, int64_t p, int64_t k, int64_t ncol, const float* Y, int64_t ldy,

@@ -20,7 +20,7 @@ def lib():
 def declared_functions():
     src = open(os.path.join(ROOT, "include", "msketch.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*([a-z_0-9]+)\s*\(", src, flags=re.M)
+    names = re.findall(r"^\s*(?:const\s+)?(?:[a-z_0-9]+\s+)*[a-z_0-9]+[\s*]+([a-z_0-9]+)\s*\(", src, flags=re.M)
     return sorted(set(names))
 
 
