@@ -283,6 +283,80 @@ int ne_lstsq(const double *A, int64_t d, int64_t n, int64_t lda,
              const double *b, double *x, void *ws, size_t ws_bytes,
              void *stream);
 
+/* ---- Batched solves (many uneven problems per launch) -------------------- */
+
+/* One least-squares problem of a batch: FP32 A (device, column-major d x n,
+ * lda >= d), FP64 b (device, d), the seed of its sketch, FP64 x (device, n,
+ * output).  The batch uses the paper's sizes k = 2 n^2 (CountSketch) and
+ * p = 4 n (Gaussian), Section 6.2; n must be 16, 32, 64, 128 or 256 and
+ * d >= 4 n. */
+typedef struct {
+  const float *A;
+  int64_t d, n, lda;
+  const double *b;
+  uint64_t seed;
+  double *x;
+} msk_batch_item;
+
+/* Scratch bytes msk_batch_lstsq needs for these items. */
+size_t msk_batch_workspace(const msk_batch_item *items, int nitems, int refine);
+
+/* Solve every problem of the batch with the mixed-precision multisketch path:
+ * FP32 CountSketch, split-BF16 tensor-core Gaussian stage with FP32
+ * accumulators drained into double-single registers, FP64 Householder QR and
+ * solve (Algorithm 1), and with refine = 1 the refinement of ms_lstsq (FP64
+ * residual passes, double-single CG passes) until each problem's relative
+ * residual changes by at most tol * relres, or max_iter outer steps.  Each
+ * stage is one launch over all problems; the CG rounds are replayed from a
+ * CUDA graph.  items: host array of nitems; infos: host array of nitems or
+ * NULL.  Synchronises `stream`.  ws: 256-byte aligned, msk_batch_workspace
+ * bytes.  Returns MSK_OK, MSK_ENOCONV if some problem hit max_iter, or -1
+ * (bad item), -2 (nitems < 1), -3 (bad refine), MSK_ENOMEM. */
+int msk_batch_lstsq(const msk_batch_item *items, int nitems, int refine,
+                    double tol, int32_t max_iter, msk_lstsq_info *infos,
+                    void *ws, size_t ws_bytes, void *stream);
+
+/* ---- Request server (continuous batching) -------------------------------- */
+
+/* A server for msk_batch_item requests.  mem_budget bytes of device memory are
+ * reserved once here and split evenly over `workers` worker threads (each
+ * with its own stream); nothing else is allocated while serving.  A free
+ * worker admits waiting requests in arrival order while their batched
+ * workspace (msk_batch_workspace) fits its share of the budget, at most
+ * max_batch per batch, and solves them with msk_batch_lstsq(refine, tol,
+ * max_iter); batches of different workers overlap on the GPU.  The paper
+ * serves single problems; this is the serving layer around its solver.
+ * Errors: -1 budget < 1 MiB, -2 workers outside 1..16, -3 max_batch < 1,
+ * -4 bad refine, -7 srv NULL, MSK_ENOMEM when the pool cannot be reserved. */
+int ms_server_create(size_t mem_budget, int workers, int max_batch, int refine,
+                     double tol, int32_t max_iter, void **srv);
+
+/* Queue one request (non-blocking).  The request's arrays must stay valid
+ * until it is done; x is written in place.  *ticket identifies it.
+ * MSK_ENOMEM when the request alone exceeds a worker's share of the budget,
+ * MSK_EBUSY when the server is stopping or its queue is full. */
+int ms_server_submit(void *srv, const msk_batch_item *req, uint64_t *ticket);
+
+/* *done = 1 once the request is solved; then info (host, may be NULL) and
+ * latency_s (seconds from submission to completion, may be NULL) are filled
+ * and the return value is the request's status (MSK_OK, or the batch's
+ * error).  -2 for an unknown ticket. */
+int ms_server_poll(void *srv, uint64_t ticket, int *done, msk_lstsq_info *info,
+                   double *latency_s);
+
+/* Block until the queue is empty and no batch is in flight. */
+int ms_server_wait_all(void *srv);
+
+/* Requests solved, batches run, requests waiting (any pointer may be NULL). */
+int ms_server_stats(void *srv, int64_t *solved, int64_t *batches,
+                    int64_t *queued);
+
+/* Text of the last failing batch of this server (empty when none). */
+const char *ms_server_error(void *srv);
+
+/* Finish the queued requests, stop the workers, release the pool. */
+int ms_server_destroy(void *srv);
+
 #ifdef __cplusplus
 }
 #endif

@@ -58,13 +58,14 @@ def integer_matrix(d: int, n: int, seed: int, lo: int = -8, hi: int = 8,
 
 def haar_orthogonal(n: int, seed: int, device="cpu") -> torch.Tensor:
     """n x n Haar-distributed orthogonal matrix: QR of a Gaussian matrix with
-    the signs of diag(R) moved into Q (Mezzadri, Notices AMS 2007)."""
-    g = _gen(seed ^ 0x5A5A5A5A, device)
-    M = torch.randn(n, n, generator=g, device=device, dtype=torch.float64)
+    the signs of diag(R) moved into Q (Mezzadri, Notices AMS 2007).  Drawn and
+    factored on the host (it is small), then moved to `device`."""
+    g = _gen(seed ^ 0x5A5A5A5A, "cpu")
+    M = torch.randn(n, n, generator=g, dtype=torch.float64)
     Q, R = torch.linalg.qr(M)
     sgn = torch.sign(torch.diagonal(R))
     sgn[sgn == 0] = 1
-    return Q * sgn
+    return (Q * sgn).to(device)
 
 
 def log_spaced_sigma(n: int, log10_min: float, device="cpu") -> torch.Tensor:

@@ -35,7 +35,9 @@ EXPORTS = ("msk_version", "msk_last_error", "cs_hash", "ms_gaussian", "msk_cs_wo
            "cs_sketch", "msk_ms_workspace", "ms_sketch", "msk_gemm_workspace", "msk_gemm",
            "msk_householder_qr", "msk_trsv_upper", "msk_lstsq_workspace", "ms_lstsq",
            "msk_ne_workspace", "ne_lstsq", "msk_gemm_noalloc", "msk_tune_set", "msk_tune_get",
-           "msk_tune_clear")
+           "msk_tune_clear", "msk_batch_workspace", "msk_batch_lstsq", "ms_server_create",
+           "ms_server_submit", "ms_server_poll", "ms_server_wait_all", "ms_server_stats",
+           "ms_server_destroy", "ms_server_error")
 
 NOALLOC_SCRATCH_BYTES = 24 << 20
 
@@ -44,6 +46,12 @@ class MskError(RuntimeError):
     def __init__(self, fn, code, detail=""):
         self.code = code
         super().__init__(f"{fn} returned {code}{(': ' + detail) if detail else ''}")
+
+
+class BatchItem(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_void_p), ("d", ctypes.c_int64), ("n", ctypes.c_int64),
+                ("lda", ctypes.c_int64), ("b", ctypes.c_void_p), ("seed", ctypes.c_uint64),
+                ("x", ctypes.c_void_p)]
 
 
 class LstsqInfo(ctypes.Structure):
@@ -95,6 +103,17 @@ def _declare(L):
                             _p, ctypes.POINTER(LstsqInfo), _p, _sz, _p]),
         "msk_ne_workspace": (_sz, [_i64, _i64]),
         "ne_lstsq": (_int, [_p, _i64, _i64, _i64, _p, _p, _p, _sz, _p]),
+        "msk_batch_workspace": (_sz, [ctypes.POINTER(BatchItem), _int, _int]),
+        "ms_server_create": (_int, [_sz, _int, _int, _int, _dbl, _i32, ctypes.POINTER(_p)]),
+        "ms_server_submit": (_int, [_p, ctypes.POINTER(BatchItem), ctypes.POINTER(_u64)]),
+        "ms_server_poll": (_int, [_p, _u64, ctypes.POINTER(_int), ctypes.POINTER(LstsqInfo),
+                                  ctypes.POINTER(_dbl)]),
+        "ms_server_wait_all": (_int, [_p]),
+        "ms_server_stats": (_int, [_p, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
+        "ms_server_destroy": (_int, [_p]),
+        "ms_server_error": (ctypes.c_char_p, [_p]),
+        "msk_batch_lstsq": (_int, [ctypes.POINTER(BatchItem), _int, _int, _dbl, _i32,
+                                   ctypes.POINTER(LstsqInfo), _p, _sz, _p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -327,3 +346,97 @@ def ne_lstsq(A, b, x=None, ws=None, stream=None):
     if rc < 0 or rc >= 1000:
         _check("ne_lstsq", rc)
     return x, rc
+
+
+def _batch_items(problems, xs):
+    arr = (BatchItem * len(problems))()
+    for j, ((A, bb, seed), x) in enumerate(zip(problems, xs)):
+        if A.dtype != torch.float32:
+            raise TypeError("batched problems take FP32 A")
+        d, n = A.shape
+        arr[j] = BatchItem(A.data_ptr(), d, n, _colmajor(A), bb.data_ptr(), seed & (2**64 - 1),
+                           x.data_ptr())
+    return arr
+
+
+def msk_batch_workspace(problems, refine=True):
+    xs = [None] * len(problems)
+    arr = (BatchItem * len(problems))()
+    for j, (A, bb, seed) in enumerate(problems):
+        d, n = A.shape
+        arr[j] = BatchItem(A.data_ptr(), d, n, _colmajor(A), bb.data_ptr(), seed & (2**64 - 1), 0)
+    return load().msk_batch_workspace(arr, len(problems), int(refine))
+
+
+def msk_batch_lstsq(problems, refine=True, tol=1e-10, max_iter=10, ws=None, stream=None):
+    """Solve [(A, b, seed), ...] (FP32 column-major A, FP64 b on the GPU) in one
+    batch.  Returns (xs, infos, status)."""
+    dev = problems[0][0].device
+    xs = [torch.empty(A.shape[1], dtype=torch.float64, device=dev) for A, _, _ in problems]
+    arr = _batch_items(problems, xs)
+    if ws is None:
+        ws = workspace(load().msk_batch_workspace(arr, len(problems), int(refine)), dev)
+    infos = (LstsqInfo * len(problems))()
+    rc = load().msk_batch_lstsq(arr, len(problems), int(refine), tol, max_iter, infos, _ptr(ws),
+                                ws.numel(), _stream(stream))
+    if rc < 0 or rc in (MSK_ENOMEM, MSK_ECUDA, MSK_ENOTSUP, MSK_ETIMEOUT):
+        _check("msk_batch_lstsq", rc)
+    out = [{"iters": i.iters, "converged": i.converged, "relres": i.relres,
+            "relres_sns": i.relres_sns} for i in infos]
+    return xs, out, rc
+
+
+class Server:
+    """Thin wrapper of the C request server (ms_server_*)."""
+
+    def __init__(self, mem_budget, workers=2, max_batch=64, refine=True, tol=1e-10, max_iter=10):
+        h = ctypes.c_void_p()
+        _check("ms_server_create", load().ms_server_create(int(mem_budget), workers, max_batch, int(refine),
+                                                           tol, max_iter, ctypes.byref(h)))
+        self._h = h
+        self._keep = {}
+
+    def submit(self, A, b, seed, x):
+        """Queue (A, b, seed) with output x; returns the ticket."""
+        d, n = A.shape
+        item = BatchItem(A.data_ptr(), d, n, _colmajor(A), b.data_ptr(), seed & (2**64 - 1), x.data_ptr())
+        t = ctypes.c_uint64()
+        _check("ms_server_submit", load().ms_server_submit(self._h, ctypes.byref(item), ctypes.byref(t)))
+        self._keep[t.value] = (A, b, x)
+        return t.value
+
+    def poll(self, ticket):
+        """(done, info dict or None, latency seconds or None, status)."""
+        done = ctypes.c_int()
+        info = LstsqInfo()
+        lat = ctypes.c_double()
+        rc = load().ms_server_poll(self._h, ticket, ctypes.byref(done), ctypes.byref(info), ctypes.byref(lat))
+        if rc < 0:
+            _check("ms_server_poll", rc)
+        if not done.value:
+            return False, None, None, rc
+        self._keep.pop(ticket, None)
+        return True, {"iters": info.iters, "converged": info.converged, "relres": info.relres,
+                      "relres_sns": info.relres_sns}, lat.value, rc
+
+    def error(self):
+        return load().ms_server_error(self._h).decode()
+
+    def wait_all(self):
+        _check("ms_server_wait_all", load().ms_server_wait_all(self._h))
+
+    def stats(self):
+        s, bt, q = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        load().ms_server_stats(self._h, ctypes.byref(s), ctypes.byref(bt), ctypes.byref(q))
+        return {"solved": s.value, "batches": bt.value, "queued": q.value}
+
+    def close(self):
+        if self._h:
+            load().ms_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

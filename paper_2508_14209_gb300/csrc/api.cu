@@ -23,6 +23,22 @@ void set_error_text(const char* msg) {
   std::snprintf(g_last_error, sizeof(g_last_error), "%s", msg);
 }
 
+int smem_optin_max() {
+  int dev = 0, v = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || v <= 0)
+    return 48 * 1024;
+  return v;
+}
+
+cudaError_t allow_max_smem(const void* func) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, func);
+  if (e != cudaSuccess) return e;
+  const int dyn = smem_optin_max() - (int)fa.sharedSizeBytes;
+  return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn > 0 ? dyn : 0);
+}
+
 int num_sms() {
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 1;
@@ -40,6 +56,15 @@ static int64_t ws_ldy(int64_t ncol, int dtype) {
 
 static bool is_tensor_prec(int prec) {
   return prec == MSK_GEMM_BF16 || prec == MSK_GEMM_F16 || prec == MSK_GEMM_BF16X3;
+}
+
+// Element type of the CountSketch inside ms_sketch: the FP64 Gaussian stage
+// gets an FP64-accumulated sketch even from FP32 A (the plain FP64 path);
+// the tensor-core stages take an FP32 sketch; otherwise A's type.
+static int ms_y_dtype(int dtype, int gemm_prec) {
+  if (gemm_prec == MSK_GEMM_F64) return MSK_F64;
+  if (is_tensor_prec(gemm_prec)) return MSK_F32;
+  return dtype;
 }
 
 }  // namespace msk
@@ -166,7 +191,7 @@ int msk_gemm(uint64_t seed, int64_t p, int64_t k, int64_t ncol, const void* Y, i
 size_t msk_ms_workspace(int64_t d, int64_t n, int with_b, int64_t k, int64_t p, int dtype,
                         int gemm_prec, int strategy) {
   const int64_t ncol = n + (with_b ? 1 : 0);
-  const int ydt = is_tensor_prec(gemm_prec) ? MSK_F32 : dtype;
+  const int ydt = ms_y_dtype(dtype, gemm_prec);
   Need nd;
   nd.add((size_t)k * ws_ldy(ncol, ydt) * dtype_size(ydt));  // Y
   nd.add(msk_cs_workspace(d, n, k, ydt, strategy));
@@ -196,16 +221,29 @@ int ms_sketch(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, const
   if (is_tensor_prec(gemm_prec) && dtype != MSK_F32) return MSK_ENOTSUP;
   cudaStream_t st = as_stream(stream);
   Carve cv(ws, ws_bytes);
-  const int64_t ldy = ws_ldy(ncol, dtype);
-  void* Y = cv.take((size_t)k * ldy * dtype_size(dtype));
-  const size_t cs_ws = msk_cs_workspace(d, n, k, dtype, strategy);
+  const int ydt = ms_y_dtype(dtype, gemm_prec);
+  const int64_t ldy = ws_ldy(ncol, ydt);
+  void* Y = cv.take((size_t)k * ldy * dtype_size(ydt));
+  const size_t cs_ws = msk_cs_workspace(d, n, k, ydt, strategy);
   void* csw = cv.take(cs_ws);
   if (!Y) return MSK_ENOMEM;
-  int rc = cs_sketch_internal(A, dtype, d, n, lda, b, k, seed, Y, ldy, strategy, csw, cs_ws,
-                              true, st);
+  int rc = MSK_OK;
+  if (ydt == MSK_F64 && dtype == MSK_F32) {
+    // FP64 sketch of the FP32-stored A
+    if (strategy != MSK_CS_ATOMIC) return MSK_ENOTSUP;
+    MSK_CUDA(cudaMemset2DAsync(Y, (size_t)ldy * 8, 0, (size_t)ncol * 8, (size_t)k, st));
+    int64_t maxc = 256;
+    const int64_t fit = (int64_t)(tune_get("cs.l2_budget_bytes", 48ll << 20)) / (k * 8);
+    if (fit >= 64 && fit / 64 * 64 < maxc) maxc = fit / 64 * 64;
+    rc = launch_cs_f32a_f64y(static_cast<const float*>(A), d, n, lda, b, (uint32_t)k,
+                             stream_key(seed, kTagHash), static_cast<double*>(Y), ldy, maxc, st);
+  } else {
+    rc = cs_sketch_internal(A, dtype, d, n, lda, b, k, seed, Y, ldy, strategy, csw, cs_ws, true,
+                            st);
+  }
   if (rc) return rc;
   const size_t rest_off = align_up(cv.used, 256);
-  return gemm_stage(seed, p, k, ncol, Y, dtype, ldy, gemm_prec, static_cast<double*>(Z), ldz,
+  return gemm_stage(seed, p, k, ncol, Y, ydt, ldy, gemm_prec, static_cast<double*>(Z), ldz,
                     cv.base + rest_off, ws_bytes - rest_off, st);
 }
 

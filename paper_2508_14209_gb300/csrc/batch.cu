@@ -1,0 +1,567 @@
+// batch.cu — many least-squares solves of uneven sizes in one set of launches
+// (msk_batch_lstsq), the engine under the request server.
+//
+// Path per problem (the mixed-precision multisketch of the configurations):
+// FP32 CountSketch of [A b] to k = 2n^2 rows (Section 6.2), Gaussian stage to
+// p = 4n rows as split-BF16 products on the tensor cores with draining FP32
+// accumulators, FP64 Householder QR and triangular solve (Algorithm 1), then
+// sketch-and-precondition refinement (FP64 residual passes, double-single CG
+// passes).  Every stage is ONE launch over all problems of the batch:
+//   CountSketch   one persistent launch per width class (tiles of all problems
+//                 numbered consecutively);
+//   Gaussian, split, GEMM, split-K reduction: one launch each, per-problem
+//                 descriptors (the GEMM reads its tensor maps from global
+//                 memory);
+//   QR + solve    one launch, one thread-block cluster per problem;
+//   refinement    FP64 residual pass, reduction and CG start: one launch each;
+//                 the inner CG rounds (pass, reduction, update) x kRound are
+//                 captured once into a CUDA graph and replayed until every
+//                 problem has met its stopping rule.
+// Problems that stop early are skipped by the later launches (device flags).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "msk_device.cuh"
+#include "msk_internal.h"
+#include "msk_qr.cuh"
+#include "msk_refine.cuh"
+
+namespace msk {
+
+constexpr int kBatchKtPer = 16;   // K tiles per CTA of the batched GEMM
+constexpr int kBatchChunks = 256; // CTAs per problem in the refinement passes
+constexpr int kRound = 4;         // CG iterations per captured graph round
+constexpr int kBatchMaxInner = 200;
+constexpr double kBatchDecFrac = 0.05;
+
+// Per-problem device descriptor (pointers into the caller's workspace).
+struct BatchJob {
+  const float* A;
+  const double* b;
+  double* x;
+  int64_t d, lda;
+  int n, k, p, ncol;
+  uint64_t gkey;
+  float* Y;
+  int ldy;
+  uint16_t* G;
+  uint16_t* Yt;
+  int64_t kpitch;
+  int npad;
+  double* part;  // GEMM partials (S x p x ncol)
+  int S;
+  double* Z;     // p x ncol, then R
+  // refinement
+  double* Ri;
+  double* vec;   // dlt, p, res, z, g: 5n
+  double* sc;    // [0] rho, [1] gain, [2] active, [3] floor, [4] inner iters, [5] bb, [6] rr0
+  double* ppart; // pass partials: nchunks x (n + 2)
+  double* pout;  // reduced pass result: n + 2
+  int nchunks;
+};
+
+__global__ void batch_zero_kernel(const BatchJob* __restrict__ jobs) {
+  const BatchJob& J = jobs[blockIdx.y];
+  const int64_t total = (int64_t)J.k * J.ldy;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x)
+    J.Y[e] = 0.f;
+}
+
+__global__ void batch_gaussian_kernel(const BatchJob* __restrict__ jobs) {
+  const BatchJob& J = jobs[blockIdx.y];
+  const int64_t total = (int64_t)J.p * J.k;
+  const float sqrt_p = __fsqrt_rn((float)J.p);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / J.k, c = e - r * J.k;
+    const float g = __fdiv_rn(gauss_std(J.gkey, (uint64_t)e), sqrt_p);
+    J.G[r * J.kpitch + c] = __bfloat16_as_ushort(__float2bfloat16_rn(g));
+  }
+}
+
+// Yt[t][n][kk] = bf16 split of Y[kk][n] (3 parts), 32x32 transposed tiles.
+__global__ void batch_split_kernel(const BatchJob* __restrict__ jobs) {
+  const BatchJob& J = jobs[blockIdx.z];
+  const int64_t k0 = (int64_t)blockIdx.x * 32;
+  const int n0 = blockIdx.y * 32;
+  if (k0 >= J.k || n0 >= J.npad) return;
+  __shared__ float tile[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t kk = k0 + r;
+    const int n = n0 + tx;
+    tile[r][tx] = (kk < J.k && n < J.ncol) ? J.Y[kk * J.ldy + n] : 0.0f;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int n = n0 + r;
+    const int64_t kk = k0 + tx;
+    if (n >= J.npad || kk >= J.k) continue;
+    float y = tile[tx][r];
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      const __nv_bfloat16 h = __float2bfloat16_rn(y);
+      J.Yt[((int64_t)t * J.npad + n) * J.kpitch + kk] = __bfloat16_as_ushort(h);
+      y = y - __bfloat162float(h);
+    }
+  }
+}
+
+__global__ void batch_gemm_reduce_kernel(const BatchJob* __restrict__ jobs) {
+  const BatchJob& J = jobs[blockIdx.y];
+  const int64_t total = (int64_t)J.p * J.ncol;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int q = 0; q < J.S; ++q) s += J.part[(int64_t)q * total + e];
+    const int64_t c = e / J.p, r = e - c * J.p;
+    J.Z[r + c * J.p] = s;  // Z column-major p x ncol
+  }
+}
+
+// One cluster per problem: Householder QR of Z (p x (n+1)), then
+// x0 = R11^{-1} R[0:n, n] by the cluster's first CTA.
+__global__ void __launch_bounds__(kQrThreads) batch_qr_kernel(const BatchJob* __restrict__ jobs) {
+  const BatchJob& J = jobs[blockIdx.y];
+  qr_cluster_body(J.Z, J.p, J.ncol, J.p);
+  cg::this_cluster().sync();
+  if (cg::this_cluster().block_rank() == 0) {
+    __shared__ double xs[kTrsvMax];
+    trsv_upper_body(J.Z, J.n, J.p, J.Z + (int64_t)J.n * J.p, J.x, nullptr, xs);
+  }
+}
+
+__global__ void batch_tri_inverse_kernel(const BatchJob* __restrict__ jobs) {
+  const BatchJob& J = jobs[blockIdx.y];
+  tri_inverse_body(J.Z, J.n, J.p, J.Ri, blockIdx.x, gridDim.x);
+}
+
+// Refinement passes over all problems: CTA (c, j) is chunk c of problem j.
+template <bool RESID>
+__global__ void __launch_bounds__(kPThreads) batch_pass_kernel(const BatchJob* __restrict__ jobs) {
+  extern __shared__ __align__(16) unsigned char bp_smem[];
+  const BatchJob& J = jobs[blockIdx.y];
+  if ((int)blockIdx.x >= J.nchunks) return;
+  if (!RESID && J.sc[2] == 0.0) return;  // problem already stopped
+  if (RESID) {
+    pass_body<float, true>(J.A, J.lda, J.d, J.n, J.n | 1, J.b, J.x, J.ppart, blockIdx.x, J.nchunks,
+                           bp_smem);
+  } else {
+    int pitch = (J.n + 3) / 4 * 4;
+    while (pitch % 32 != 4) pitch += 4;
+    pass_ds_body(J.A, J.lda, J.d, J.n, pitch, J.vec + J.n, J.ppart, blockIdx.x, J.nchunks, bp_smem);
+  }
+}
+
+template <bool ONLY_ACTIVE>
+__global__ void __launch_bounds__(256) batch_pass_reduce_kernel(const BatchJob* __restrict__ jobs) {
+  const BatchJob& J = jobs[blockIdx.y];
+  if (ONLY_ACTIVE && J.sc[2] == 0.0) return;
+  if ((int)blockIdx.x * 32 >= J.n + 2) return;
+  pass_reduce_body(J.ppart, J.nchunks, J.n + 2, J.pout, blockIdx.x);
+}
+
+__device__ __forceinline__ RefState ref_state(const BatchJob& J) {
+  return RefState{J.x, J.vec, J.vec + J.n, J.vec + 2 * J.n, J.vec + 3 * J.n, J.sc};
+}
+
+// After an FP64 residual pass: start CG on A^T A d = g for every problem that
+// is still refining; record the stopping floor kBatchDecFrac * tol * ||r||^2.
+__global__ void batch_pcg_start_kernel(const BatchJob* __restrict__ jobs, double tol,
+                                       int* __restrict__ active_count) {
+  const BatchJob& J = jobs[blockIdx.x];
+  const double rr = J.pout[J.n];
+  if (J.sc[2] == 0.0) return;
+  double* g = J.vec + 4 * J.n;
+  for (int j = threadIdx.x; j < J.n; j += blockDim.x) g[j] = J.pout[j];
+  __syncthreads();
+  pcg_start_body(J.Ri, J.n, g, ref_state(J));
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    J.sc[3] = kBatchDecFrac * tol * rr;
+    atomicAdd(active_count, 1);
+  }
+}
+
+// One CG step.  A problem stops when a step gains less than its floor; if
+// that happens at the very first step, x is already the minimiser to within
+// tol: it is marked converged (sc[5] = 1) and its correction is not applied.
+__global__ void batch_pcg_update_kernel(const BatchJob* __restrict__ jobs,
+                                        int* __restrict__ active_count, int* __restrict__ refining) {
+  const BatchJob& J = jobs[blockIdx.x];
+  if (J.sc[2] == 0.0) return;
+  pcg_update_body(J.Ri, J.n, J.pout, ref_state(J));
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    J.sc[4] += 1.0;
+    if (!(J.sc[1] > J.sc[3]) || !(J.sc[0] > 0.0) || J.sc[4] >= (double)kBatchMaxInner) {
+      if (J.sc[4] == 1.0) {
+        J.sc[5] = 1.0;
+        refining[blockIdx.x] = 0;
+      }
+      J.sc[2] = 0.0;
+      atomicSub(active_count, 1);
+    }
+  }
+}
+
+// x += dlt for the problems that refined in this outer step; re-arm them.
+__global__ void batch_axpy_kernel(const BatchJob* __restrict__ jobs, const int* __restrict__ refining) {
+  const BatchJob& J = jobs[blockIdx.x];
+  if (!refining[blockIdx.x]) return;
+  for (int j = threadIdx.x; j < J.n; j += blockDim.x) J.x[j] += J.vec[j];
+}
+
+// out[4j..4j+3] = (||r||^2, ||b||^2, inner iterations, first-step stop) of problem j.
+__global__ void batch_gather_kernel(const BatchJob* __restrict__ jobs, int nprob,
+                                    double* __restrict__ out) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nprob; j += gridDim.x * blockDim.x) {
+    const BatchJob& J = jobs[j];
+    out[4 * j] = J.pout[J.n];
+    out[4 * j + 1] = J.pout[J.n + 1];
+    out[4 * j + 2] = J.sc[4];
+    out[4 * j + 3] = J.sc[5];
+  }
+}
+
+// Arm the refinement of an outer step: sc[2] = refining[j], inner counter 0.
+__global__ void batch_arm_kernel(const BatchJob* __restrict__ jobs, int nprob,
+                                 const int* __restrict__ refining, int* __restrict__ active) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nprob; j += gridDim.x * blockDim.x) {
+    const BatchJob& J = jobs[j];
+    J.sc[0] = 0.0;
+    J.sc[1] = 0.0;
+    J.sc[2] = refining[j] ? 1.0 : 0.0;
+    J.sc[4] = 0.0;
+    J.sc[5] = 0.0;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *active = 0;
+}
+
+struct BatchPlan {
+  std::vector<BatchJob> jobs;
+  std::vector<TcJob> tc;
+  std::vector<TcShape> shapes;
+  std::vector<int> widths;  // CountSketch width classes present
+  std::vector<std::vector<CsParams<float>>> cs;
+  std::vector<std::vector<int64_t>> cs_tiles;
+  std::vector<size_t> cs_off, tiles_off;
+  size_t jobs_off = 0, tc_off = 0, flags_off = 0, gather_off = 0;
+  int total_items = 0, max_nt = 16, max_npad = 16, max_n = 1, max_chunks = 1;
+  int64_t max_k = 1, max_pk = 1, max_yk = 1;
+  size_t bytes = 0;
+};
+
+static bool width_ok(int64_t n) {
+  return n == 16 || n == 32 || n == 64 || n == 128 || n == 256;
+}
+
+// Sizes and places every piece of the batch in the workspace (offsets from
+// its base; with base == nullptr only the sizes are computed).
+static void plan_batch(const msk_batch_item* items, int nitems, int refine, char* base,
+                       BatchPlan* P) {
+  Need nd;
+  auto take = [&](size_t bytes) -> size_t {
+    const size_t off = align_up(nd.used, 256);
+    nd.used = off + bytes;
+    return off;
+  };
+  auto ptr = [&](size_t off) -> char* { return base ? base + off : nullptr; };
+  P->jobs_off = take(sizeof(BatchJob) * (size_t)nitems);
+  P->tc_off = take(sizeof(TcJob) * (size_t)nitems);
+  P->flags_off = take(sizeof(int) * (size_t)(nitems + 8));
+  P->gather_off = take(sizeof(double) * 4 * (size_t)nitems);
+  P->jobs.resize(nitems);
+  P->tc.resize(nitems);
+  P->shapes.resize(nitems);
+  for (int j = 0; j < nitems; ++j) {
+    const msk_batch_item& it = items[j];
+    BatchJob& J = P->jobs[j];
+    J.A = it.A;
+    J.b = it.b;
+    J.x = it.x;
+    J.d = it.d;
+    J.lda = it.lda;
+    J.n = (int)it.n;
+    J.k = (int)(2 * it.n * it.n);
+    J.p = (int)(4 * it.n);
+    J.ncol = J.n + 1;
+    J.gkey = stream_key(it.seed, kTagGauss);
+    J.ldy = (J.ncol + 3) / 4 * 4;
+    TcShape& sh = P->shapes[j];
+    tc_ds_shape(J.p, J.k, J.ncol, kBatchKtPer, &sh);
+    J.kpitch = sh.kpitch;
+    J.npad = sh.npad;
+    J.S = sh.S;
+    J.nchunks = (int)std::max<int64_t>(1, std::min<int64_t>((J.d + kPR - 1) / kPR, kBatchChunks));
+    J.Y = reinterpret_cast<float*>(ptr(take((size_t)J.k * J.ldy * 4)));
+    J.G = reinterpret_cast<uint16_t*>(ptr(take((size_t)J.p * sh.kpitch * 2)));
+    J.Yt = reinterpret_cast<uint16_t*>(ptr(take((size_t)3 * sh.npad * sh.kpitch * 2)));
+    J.part = reinterpret_cast<double*>(ptr(take((size_t)sh.S * J.p * J.ncol * 8)));
+    J.Z = reinterpret_cast<double*>(ptr(take((size_t)J.p * J.ncol * 8)));
+    J.Ri = reinterpret_cast<double*>(ptr(take(refine ? (size_t)J.n * J.n * 8 : 0)));
+    J.vec = reinterpret_cast<double*>(ptr(take(refine ? (size_t)5 * J.n * 8 : 0)));
+    J.sc = reinterpret_cast<double*>(ptr(take(8 * 8)));
+    J.ppart = reinterpret_cast<double*>(ptr(take((size_t)J.nchunks * (J.n + 2) * 8)));
+    J.pout = reinterpret_cast<double*>(ptr(take((size_t)(J.n + 2) * 8)));
+    P->max_nt = std::max(P->max_nt, sh.NT);
+    P->max_npad = std::max(P->max_npad, sh.npad);
+    P->max_n = std::max(P->max_n, J.n);
+    P->max_chunks = std::max(P->max_chunks, J.nchunks);
+    P->max_k = std::max<int64_t>(P->max_k, J.k);
+    P->max_pk = std::max<int64_t>(P->max_pk, (int64_t)J.p * J.k);
+    P->max_yk = std::max<int64_t>(P->max_yk, (int64_t)J.k * J.ldy);
+  }
+  for (int w : {16, 32, 64, 128, 256}) {
+    std::vector<CsParams<float>> ps;
+    std::vector<int64_t> tb(1, 0);
+    for (int j = 0; j < nitems; ++j) {
+      const BatchJob& J = P->jobs[j];
+      if (J.n != w) continue;
+      CsParams<float> c{};
+      c.A = J.A;
+      c.d = J.d;
+      c.lda = J.lda;
+      c.ncol_a = J.n;
+      c.b = J.b;
+      c.ncol = J.ncol;
+      c.k = (uint32_t)J.k;
+      c.key = stream_key(items[j].seed, kTagHash);
+      c.Y = J.Y;
+      c.ldy = J.ldy;
+      ps.push_back(c);
+      tb.push_back(tb.back() + (J.d + 31) / 32);
+    }
+    if (ps.empty()) continue;
+    P->widths.push_back(w);
+    P->cs_off.push_back(take(sizeof(CsParams<float>) * ps.size()));
+    P->tiles_off.push_back(take(sizeof(int64_t) * tb.size()));
+    P->cs.push_back(ps);
+    P->cs_tiles.push_back(tb);
+  }
+  P->bytes = nd.used;
+}
+
+}  // namespace msk
+
+using namespace msk;
+
+extern "C" {
+
+size_t msk_batch_workspace(const msk_batch_item* items, int nitems, int refine) {
+  if (!items || nitems <= 0) return 0;
+  BatchPlan P;
+  plan_batch(items, nitems, refine, nullptr, &P);
+  return P.bytes;
+}
+
+int msk_batch_lstsq(const msk_batch_item* items, int nitems, int refine, double tol,
+                    int32_t max_iter, msk_lstsq_info* infos, void* ws, size_t ws_bytes,
+                    void* stream) {
+  if (!items) return -1;
+  if (nitems < 1) return -2;
+  if (refine != 0 && refine != 1) return -3;
+  for (int j = 0; j < nitems; ++j) {
+    const msk_batch_item& it = items[j];
+    if (!it.A || !it.b || !it.x || !width_ok(it.n) || it.d < 4 * it.n || it.lda < it.d)
+      return -1;
+  }
+  char* base = static_cast<char*>(ws);
+  BatchPlan P;
+  plan_batch(items, nitems, refine, base, &P);
+  if (!ws || ws_bytes < P.bytes || (reinterpret_cast<uintptr_t>(ws) & 255) != 0) return MSK_ENOMEM;
+  cudaStream_t st = as_stream(stream);
+  BatchJob* jobs_dev = reinterpret_cast<BatchJob*>(base + P.jobs_off);
+  TcJob* tc_dev = reinterpret_cast<TcJob*>(base + P.tc_off);
+  int* active = reinterpret_cast<int*>(base + P.flags_off);
+  int* refining = active + 8;
+  double* gather = reinterpret_cast<double*>(base + P.gather_off);
+  int item = 0;
+  int rc = MSK_OK;
+  for (int j = 0; j < nitems; ++j) {
+    const BatchJob& J = P.jobs[j];
+    rc = tc_ds_make_job(J.p, J.k, J.ncol, P.shapes[j], J.G, J.Yt, J.part, item, &P.tc[j]);
+    if (rc) return rc;
+    item += P.shapes[j].items;
+  }
+  P.total_items = item;
+  MSK_CUDA(cudaMemcpyAsync(jobs_dev, P.jobs.data(), sizeof(BatchJob) * nitems, cudaMemcpyHostToDevice, st));
+  MSK_CUDA(cudaMemcpyAsync(tc_dev, P.tc.data(), sizeof(TcJob) * nitems, cudaMemcpyHostToDevice, st));
+  for (size_t c = 0; c < P.widths.size(); ++c) {
+    MSK_CUDA(cudaMemcpyAsync(base + P.cs_off[c], P.cs[c].data(), sizeof(CsParams<float>) * P.cs[c].size(),
+                             cudaMemcpyHostToDevice, st));
+    MSK_CUDA(cudaMemcpyAsync(base + P.tiles_off[c], P.cs_tiles[c].data(),
+                             sizeof(int64_t) * P.cs_tiles[c].size(), cudaMemcpyHostToDevice, st));
+  }
+  const int sms = num_sms();
+  // 1. CountSketch: zero every Y, then one launch per width class
+  batch_zero_kernel<<<dim3((unsigned)std::min<int64_t>((P.max_yk + 255) / 256, 64), nitems), 256, 0, st>>>(jobs_dev);
+  MSK_CHECK_LAUNCH("batch_zero_kernel");
+  for (size_t c = 0; c < P.widths.size(); ++c) {
+    rc = launch_cs_batch_f32(P.widths[c], reinterpret_cast<const CsParams<float>*>(base + P.cs_off[c]),
+                             reinterpret_cast<const int64_t*>(base + P.tiles_off[c]),
+                             (int)P.cs[c].size(), P.cs_tiles[c].back(), st);
+    if (rc) return rc;
+  }
+  // 2. Gaussian (bfloat16) and the 3-part bfloat16 split of Y
+  batch_gaussian_kernel<<<dim3((unsigned)std::min<int64_t>((P.max_pk + 255) / 256, 8 * sms), nitems), 256, 0, st>>>(jobs_dev);
+  MSK_CHECK_LAUNCH("batch_gaussian_kernel");
+  batch_split_kernel<<<dim3((unsigned)((P.max_k + 31) / 32), (unsigned)((P.max_npad + 31) / 32), nitems), 256, 0, st>>>(jobs_dev);
+  MSK_CHECK_LAUNCH("batch_split_kernel");
+  // 3. tensor-core Gaussian stage and its split-K reduction
+  rc = launch_tc_ds_batch(tc_dev, nitems, P.total_items, P.max_nt, st);
+  if (rc) return rc;
+  batch_gemm_reduce_kernel<<<dim3(64, nitems), 256, 0, st>>>(jobs_dev);
+  MSK_CHECK_LAUNCH("batch_gemm_reduce_kernel");
+  // 4. QR + triangular solve, one 16-CTA cluster per problem
+  {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(16, nitems, 1);
+    cfg.blockDim = dim3(kQrThreads, 1, 1);
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 16;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    MSK_CUDA(cudaFuncSetAttribute(batch_qr_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    MSK_CUDA(cudaLaunchKernelEx(&cfg, batch_qr_kernel, (const BatchJob*)jobs_dev));
+  }
+  // 5. refinement
+  std::vector<int> iters(nitems, 0), conv(nitems, refine ? 0 : 1);
+  std::vector<double> relres(nitems, -1.0), relres_sns(nitems, -1.0), prev(nitems, -1.0);
+  std::vector<double> hg(4 * (size_t)nitems);
+  const size_t smem_res =
+      sizeof(double) * ((size_t)P.max_n + kPR) + sizeof(float) * (size_t)kPR * (P.max_n | 1);
+  int pitch_ds = (P.max_n + 3) / 4 * 4;
+  while (pitch_ds % 32 != 4) pitch_ds += 4;
+  const size_t smem_ds = sizeof(float) * ((size_t)kPR * pitch_ds + 2 * P.max_n + 2 * kPR);
+  MSK_ALLOW_SMEM(batch_pass_kernel<true>);
+  MSK_ALLOW_SMEM(batch_pass_kernel<false>);
+  const dim3 pgrid(P.max_chunks, nitems), rgrid((P.max_n + 2 + 31) / 32, nitems);
+  const unsigned gblocks = (unsigned)((nitems + 255) / 256);
+  // FP64 residual pass of every problem, then (||r||^2, ||b||^2, iters) to the host
+  auto fp64_pass = [&](bool first) -> int {
+    batch_pass_kernel<true><<<pgrid, kPThreads, smem_res, st>>>(jobs_dev);
+    MSK_CHECK_LAUNCH("batch_pass_kernel");
+    batch_pass_reduce_kernel<false><<<rgrid, 256, 0, st>>>(jobs_dev);
+    MSK_CHECK_LAUNCH("batch_pass_reduce_kernel");
+    batch_gather_kernel<<<gblocks, 256, 0, st>>>(jobs_dev, nitems, gather);
+    MSK_CHECK_LAUNCH("batch_gather_kernel");
+    MSK_CUDA(cudaMemcpyAsync(hg.data(), gather, sizeof(double) * 4 * nitems, cudaMemcpyDeviceToHost, st));
+    MSK_CUDA(cudaStreamSynchronize(st));
+    for (int j = 0; j < nitems; ++j) {
+      const double rr = std::sqrt(std::max(hg[4 * j], 0.0) / (hg[4 * j + 1] > 0.0 ? hg[4 * j + 1] : 1.0));
+      relres[j] = rr;
+      if (first) relres_sns[j] = rr;
+    }
+    return MSK_OK;
+  };
+  int status = MSK_OK;
+  if (refine) {
+    batch_tri_inverse_kernel<<<dim3((P.max_n + 7) / 8, nitems), 256, 0, st>>>(jobs_dev);
+    MSK_CHECK_LAUNCH("batch_tri_inverse_kernel");
+    // one captured round: kRound CG iterations over all problems
+    // Capture records work without running it, on a private stream (the
+    // legacy default stream cannot be captured); the graph is then launched on
+    // the caller's stream, in order with everything above.
+    static thread_local cudaStream_t cap = nullptr;
+    if (!cap) MSK_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    MSK_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    for (int r = 0; r < kRound; ++r) {
+      batch_pass_kernel<false><<<pgrid, kPThreads, smem_ds, cap>>>(jobs_dev);
+      batch_pass_reduce_kernel<true><<<rgrid, 256, 0, cap>>>(jobs_dev);
+      batch_pcg_update_kernel<<<nitems, 512, 0, cap>>>(jobs_dev, active, refining);
+    }
+    cudaError_t ce = cudaStreamEndCapture(cap, &graph);
+    if (ce != cudaSuccess) return cuda_fail(ce, "capture of the refinement round");
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    if (ce != cudaSuccess) {
+      cudaGraphDestroy(graph);
+      return cuda_fail(ce, "cudaGraphInstantiate");
+    }
+    std::vector<int> ref(nitems, 0);
+    for (int outer = 0; outer <= max_iter && !status; ++outer) {
+      rc = fp64_pass(outer == 0);
+      if (rc) {
+        status = rc;
+        break;
+      }
+      int nref = 0;
+      for (int j = 0; j < nitems; ++j) {
+        ref[j] = 0;
+        if (conv[j]) continue;
+        if (prev[j] >= 0.0 && std::fabs(prev[j] - relres[j]) <= tol * relres[j]) {
+          conv[j] = 1;
+          continue;
+        }
+        if (outer == max_iter) continue;
+        prev[j] = relres[j];
+        ref[j] = 1;
+        ++nref;
+      }
+      if (nref == 0) break;
+      ce = cudaMemcpyAsync(refining, ref.data(), sizeof(int) * nitems, cudaMemcpyHostToDevice, st);
+      if (ce != cudaSuccess) {
+        status = cuda_fail(ce, "refinement flags");
+        break;
+      }
+      batch_arm_kernel<<<gblocks, 256, 0, st>>>(jobs_dev, nitems, refining, active);
+      batch_pcg_start_kernel<<<nitems, 512, 0, st>>>(jobs_dev, tol, active);
+      int hact = nref;
+      for (int round = 0; round * kRound < kBatchMaxInner && hact > 0; ++round) {
+        ce = cudaGraphLaunch(exec, st);
+        if (ce == cudaSuccess) ce = cudaMemcpyAsync(&hact, active, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+        if (ce != cudaSuccess) {
+          status = cuda_fail(ce, "refinement round");
+          break;
+        }
+      }
+      if (status) break;
+      batch_gather_kernel<<<gblocks, 256, 0, st>>>(jobs_dev, nitems, gather);
+      ce = cudaMemcpyAsync(hg.data(), gather, sizeof(double) * 4 * nitems, cudaMemcpyDeviceToHost, st);
+      if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+      if (ce != cudaSuccess) {
+        status = cuda_fail(ce, "refinement counters");
+        break;
+      }
+      for (int j = 0; j < nitems; ++j)
+        if (ref[j]) {
+          iters[j] += (int)hg[4 * j + 2];
+          if (hg[4 * j + 3] != 0.0) conv[j] = 1;  // minimiser reached: relres above stands
+        }
+      batch_axpy_kernel<<<nitems, 256, 0, st>>>(jobs_dev, refining);
+    }
+    cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(graph);
+    if (status) return status;
+    for (int j = 0; j < nitems; ++j)
+      if (!conv[j]) status = MSK_ENOCONV;
+  } else if (infos) {
+    rc = fp64_pass(true);
+    if (rc) return rc;
+  }
+  MSK_CUDA(cudaStreamSynchronize(st));  // the uploads above read host vectors
+  if (infos)
+    for (int j = 0; j < nitems; ++j) {
+      infos[j].iters = iters[j];
+      infos[j].converged = conv[j];
+      infos[j].relres = relres[j];
+      infos[j].relres_sns = relres_sns[j];
+    }
+  return status;
+}
+
+}  // extern "C"

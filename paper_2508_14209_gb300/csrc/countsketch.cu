@@ -57,31 +57,6 @@ constexpr int kCsThreads = kCsWarps * 32;
 constexpr int kCsMaxColsF64 = 384;
 constexpr int kCsMaxColsF32 = 512;
 
-template <typename T>
-struct CsParams {
-  const T* A;
-  int64_t d, lda;
-  int ncol_a;          // columns taken from A in this launch
-  const double* b;     // extra column (after the A columns) or null
-  int ncol;            // ncol_a + (b != null)
-  uint32_t k;
-  uint64_t key;
-  T* Y;
-  int64_t ldy;
-  int pitch;           // shared-memory row pitch (elements)
-};
-
-__device__ __forceinline__ void red_add(double* p, double v) {
-  asm volatile("red.relaxed.gpu.global.add.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
-}
-__device__ __forceinline__ void red_add(float* p, float v) {
-  asm volatile("red.relaxed.gpu.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
-}
-__device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, float d) {
-  asm volatile("red.relaxed.gpu.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a),
-               "f"(b), "f"(c), "f"(d)
-               : "memory");
-}
 
 // Shared-memory tile layout: row r at r * pitch.  FP64: one column per
 // store, odd pitch, so the 32 transposing stores of a warp (lane = row) and
@@ -186,7 +161,7 @@ template <typename T, int QMAX, bool VEC4>
 static int launch_cs_atomic_t(const CsParams<T>& P, cudaStream_t st) {
   const size_t smem = 2 * sizeof(T) * kCsRows * P.pitch + 2 * kCsRows * sizeof(uint64_t);
   auto kern = cs_atomic_kernel<T, QMAX, VEC4>;
-  MSK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  MSK_ALLOW_SMEM(kern);
   int per_sm = 0;
   MSK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kCsThreads, smem));
   per_sm = std::max(per_sm, 1);
@@ -294,7 +269,7 @@ template <int QMAX>
 static int launch_cs_bulk_t(const CsParams<double>& P, int nbulk, cudaStream_t st) {
   const size_t smem = 2 * sizeof(double) * kCsRows * P.pitch;
   auto kern = cs_bulk_f64_kernel<QMAX>;
-  MSK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  MSK_ALLOW_SMEM(kern);
   int per_sm = 0;
   MSK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kCsThreads, smem));
   per_sm = std::max(per_sm, 1);
@@ -331,21 +306,18 @@ static int cs_bulk_f64_chunk(CsParams<double> P, bool pad_ok, cudaStream_t st, i
 // tile scheme as cs_atomic_kernel.  FP64: lane = column, red.add.f64.
 // FP32: 4 columns per lane, red.add.v4.f32 (a row of 4*L columns takes L
 // lanes; several rows per warp instruction when 4*L < 128).
-__device__ __forceinline__ double flip(double x, unsigned long long s) {
-  return __longlong_as_double(__double_as_longlong(x) ^ s);
-}
-__device__ __forceinline__ float flip(float x, unsigned s) {
-  return __uint_as_float(__float_as_uint(x) ^ s);
-}
-
-template <int NCA, bool HAS_B>
-__global__ void __launch_bounds__(kCsThreads) cs_fixed_f64_kernel(const CsParams<double> P) {
+// FP64 accumulation; A is FP64, or FP32 widened exactly (TA = float) — the
+// FP64 sketch of a matrix stored in binary32.
+template <int NCA, bool HAS_B, typename TA>
+__global__ void __launch_bounds__(kCsThreads) cs_fixed_f64_kernel(const CsParams<double> P,
+                                                               const TA* __restrict__ Aa) {
   constexpr int NCOL = NCA + (HAS_B ? 1 : 0);
   constexpr int PITCH = NCOL | 1;
   constexpr int Q = (NCA + kCsWarps - 1) / kCsWarps;
   __shared__ double tiles[2][kCsRows][PITCH];
   __shared__ uint64_t hz[2][kCsRows];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nca = P.ncol_a;  // <= NCA: the kernel serves any width up to NCA
   const int64_t ntiles = (P.d + kCsRows - 1) / kCsRows;
   int buf = 0;
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, buf ^= 1) {
@@ -356,7 +328,7 @@ __global__ void __launch_bounds__(kCsThreads) cs_fixed_f64_kernel(const CsParams
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
       const int j = warp + q * kCsWarps;
-      v[q] = (row_ok && j < NCA) ? __ldcs(P.A + i + (int64_t)j * P.lda) : 0.0;
+      v[q] = (row_ok && j < nca) ? (double)__ldcs(Aa + i + (int64_t)j * P.lda) : 0.0;
     }
     double vb = 0.0;
     if (HAS_B && warp == kCsWarps - 1) vb = row_ok ? __ldcs(P.b + i) : 0.0;
@@ -364,9 +336,9 @@ __global__ void __launch_bounds__(kCsThreads) cs_fixed_f64_kernel(const CsParams
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
       const int j = warp + q * kCsWarps;
-      if (j < NCA) tiles[buf][lane][j] = v[q];
+      if (j < nca) tiles[buf][lane][j] = v[q];  // column nca is b's slot
     }
-    if (HAS_B && warp == kCsWarps - 1) tiles[buf][lane][NCA] = vb;
+    if (HAS_B && warp == kCsWarps - 1) tiles[buf][lane][nca] = vb;
     __syncthreads();
 #pragma unroll
     for (int rr = 0; rr < kCsRows / kCsWarps; ++rr) {
@@ -376,26 +348,30 @@ __global__ void __launch_bounds__(kCsThreads) cs_fixed_f64_kernel(const CsParams
       double* yrow = P.Y + (int64_t)bucket_of(z, P.k) * P.ldy;
       const unsigned long long sg = negative_of(z) ? 0x8000000000000000ull : 0ull;
 #pragma unroll
-      for (int c = lane; c < NCA; c += 32) red_add(yrow + c, flip(tiles[buf][r][c], sg));
-      if (HAS_B && lane == 0) red_add(yrow + NCA, flip(tiles[buf][r][NCA], sg));
+      for (int c = lane; c < NCA; c += 32)
+        if (c < nca) red_add(yrow + c, flip(tiles[buf][r][c], sg));
+      if (HAS_B && lane == 0) red_add(yrow + nca, flip(tiles[buf][r][nca], sg));
     }
   }
 }
 
+
+
 template <int NCA, bool HAS_B>
-__global__ void __launch_bounds__(kCsThreads) cs_fixed_f32_kernel(const CsParams<float> P) {
-  constexpr int NG = (NCA + 3) / 4;             // 4-column groups of A
-  constexpr int PITCH = 4 * ((NG + 1) | 1);     // room for b's group, pitch/4 odd
-  constexpr int QG = (NG + kCsWarps - 1) / kCsWarps;
-  constexpr int LPR = NCA / 4 < 32 ? NCA / 4 : 32;  // lanes per row in the reduction phase
-  constexpr int RPI = 32 / LPR;                 // rows per warp instruction
-  __shared__ __align__(16) float tiles[2][kCsRows][PITCH];
-  __shared__ uint64_t hz[2][kCsRows];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t ntiles = (P.d + kCsRows - 1) / kCsRows;
-  int buf = 0;
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, buf ^= 1) {
-    const int64_t i0 = t * kCsRows;
+struct CsF32Tile {
+  static constexpr int NG = (NCA + 3) / 4;           // 4-column groups of A
+  static constexpr int PITCH = 4 * ((NG + 1) | 1);   // room for b's group, pitch/4 odd
+  static constexpr int QG = (NG + kCsWarps - 1) / kCsWarps;
+  static constexpr int LPR = NCA / 4 < 32 ? NCA / 4 : 32;  // lanes per row (reductions)
+  static constexpr int RPI = 32 / LPR;               // rows per warp instruction
+  struct Smem {
+    float tiles[2][kCsRows][PITCH];
+    uint64_t hz[2][kCsRows];
+  };
+  // One 32-row tile starting at row i0 of problem P into buffer `buf`.
+  __device__ __forceinline__ static void run(const CsParams<float>& P, int64_t i0, int buf,
+                                             Smem& sm) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t i = i0 + lane;
     const bool row_ok = i < P.d;
     float4 v[QG];
@@ -414,13 +390,13 @@ __global__ void __launch_bounds__(kCsThreads) cs_fixed_f32_kernel(const CsParams
     }
     float vb = 0.f;
     if (HAS_B && warp == kCsWarps - 1) vb = row_ok ? (float)__ldcs(P.b + i) : 0.f;
-    if (warp == 0) hz[buf][lane] = row_ok ? draw(P.key, (uint64_t)i) : 0ull;
+    if (warp == 0) sm.hz[buf][lane] = row_ok ? draw(P.key, (uint64_t)i) : 0ull;
 #pragma unroll
     for (int q = 0; q < QG; ++q) {
       const int g = warp + q * kCsWarps;
-      if (g < NG) *reinterpret_cast<float4*>(&tiles[buf][lane][4 * g]) = v[q];
+      if (g < NG) *reinterpret_cast<float4*>(&sm.tiles[buf][lane][4 * g]) = v[q];
     }
-    if (HAS_B && warp == kCsWarps - 1) tiles[buf][lane][NCA] = vb;
+    if (HAS_B && warp == kCsWarps - 1) sm.tiles[buf][lane][NCA] = vb;
     __syncthreads();
     // reduction phase: RPI rows per warp instruction, row groups spread over warps
 #pragma unroll
@@ -428,32 +404,87 @@ __global__ void __launch_bounds__(kCsThreads) cs_fixed_f32_kernel(const CsParams
       const int r = r0 + lane / LPR;
       const int cl = lane % LPR;
       const bool ok = i0 + r < P.d;
-      const uint64_t z = hz[buf][r];
+      const uint64_t z = sm.hz[buf][r];
       float* yrow = P.Y + (int64_t)bucket_of(z, P.k) * P.ldy;
       const unsigned sg = negative_of(z) ? 0x80000000u : 0u;
       if (ok) {
 #pragma unroll
         for (int c = 4 * cl; c < NCA; c += 4 * LPR) {
-          const float4 x = *reinterpret_cast<const float4*>(&tiles[buf][r][c]);
+          const float4 x = *reinterpret_cast<const float4*>(&sm.tiles[buf][r][c]);
           red_add_v4(yrow + c, flip(x.x, sg), flip(x.y, sg), flip(x.z, sg), flip(x.w, sg));
         }
-        if (HAS_B && cl == 0) red_add(yrow + NCA, flip(tiles[buf][r][NCA], sg));
+        if (HAS_B && cl == 0) red_add(yrow + NCA, flip(sm.tiles[buf][r][NCA], sg));
       }
     }
   }
+};
+
+template <int NCA, bool HAS_B>
+__global__ void __launch_bounds__(kCsThreads) cs_fixed_f32_kernel(const CsParams<float> P) {
+  __shared__ __align__(16) typename CsF32Tile<NCA, HAS_B>::Smem sm;
+  const int64_t ntiles = (P.d + kCsRows - 1) / kCsRows;
+  int buf = 0;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, buf ^= 1)
+    CsF32Tile<NCA, HAS_B>::run(P, t * kCsRows, buf, sm);
 }
 
-template <typename KernT, typename ParT>
-static int launch_fixed(KernT kern, const ParT& P, cudaStream_t st) {
+// Batched form: many problems of the same width in one persistent launch.
+// Tiles of all problems are numbered consecutively (tile_begin[j] = first
+// global tile of problem j, tile_begin[nprob] = total); a CTA walks global
+// tiles and finds each tile's problem by binary search.
+template <int NCA>
+__global__ void __launch_bounds__(kCsThreads) cs_batch_f32_kernel(const CsParams<float>* __restrict__ Ps,
+                                                               const int64_t* __restrict__ tile_begin,
+                                                               int nprob) {
+  __shared__ __align__(16) typename CsF32Tile<NCA, true>::Smem sm;
+  const int64_t total = tile_begin[nprob];
+  int buf = 0;
+  for (int64_t t = blockIdx.x; t < total; t += gridDim.x, buf ^= 1) {
+    int lo = 0, hi = nprob - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (tile_begin[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    const CsParams<float> P = Ps[lo];
+    CsF32Tile<NCA, true>::run(P, (t - tile_begin[lo]) * kCsRows, buf, sm);
+  }
+}
+
+template <typename KernT, typename ParT, typename... Extra>
+static int launch_fixed(KernT kern, const ParT& P, cudaStream_t st, Extra... extra) {
   int per_sm = 0;
   MSK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kCsThreads, 0));
   per_sm = std::max(per_sm, 1);
   const int64_t ntiles = (P.d + kCsRows - 1) / kCsRows;
   const int64_t grid = std::min<int64_t>(ntiles, (int64_t)num_sms() * per_sm);
   if (grid <= 0) return MSK_OK;
-  kern<<<(unsigned)grid, kCsThreads, 0, st>>>(P);
+  kern<<<(unsigned)grid, kCsThreads, 0, st>>>(P, extra...);
   MSK_CHECK_LAUNCH("cs_fixed_kernel");
   return MSK_OK;
+}
+
+// Batched FP32 CountSketch launch over `nprob` problems of A-width nca with a
+// b column each (Ps, tile_begin in device memory; total tiles known here).
+int launch_cs_batch_f32(int nca, const CsParams<float>* Ps, const int64_t* tile_begin, int nprob,
+                        int64_t total_tiles, cudaStream_t st) {
+  if (total_tiles <= 0 || nprob <= 0) return MSK_OK;
+  auto go = [&](auto kern) -> int {
+    int per_sm = 0;
+    MSK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kCsThreads, 0));
+    per_sm = std::max(per_sm, 1);
+    const int64_t grid = std::min<int64_t>(total_tiles, (int64_t)num_sms() * per_sm);
+    kern<<<(unsigned)grid, kCsThreads, 0, st>>>(Ps, tile_begin, nprob);
+    MSK_CHECK_LAUNCH("cs_batch_f32_kernel");
+    return MSK_OK;
+  };
+  switch (nca) {
+    case 16: return go(cs_batch_f32_kernel<16>);
+    case 32: return go(cs_batch_f32_kernel<32>);
+    case 64: return go(cs_batch_f32_kernel<64>);
+    case 128: return go(cs_batch_f32_kernel<128>);
+    case 256: return go(cs_batch_f32_kernel<256>);
+    default: return MSK_ENOTSUP;
+  }
 }
 
 // Returns 1 when a fixed-width kernel covered this chunk.
@@ -465,11 +496,11 @@ static int cs_fixed_chunk(const CsParams<T>& P, cudaStream_t st, int* rc) {
   if (P.ncol != P.ncol_a + (hb ? 1 : 0)) return 0;
   const int nca = P.ncol_a;
   if constexpr (sizeof(T) == 8) {
-#define MSK_FIX64(N)                                                          \
-  if (nca == N) {                                                             \
-    *rc = hb ? launch_fixed(cs_fixed_f64_kernel<N, true>, P, st)              \
-             : launch_fixed(cs_fixed_f64_kernel<N, false>, P, st);            \
-    return 1;                                                                 \
+#define MSK_FIX64(N)                                                                    \
+  if (nca <= N) {                                                                       \
+    *rc = hb ? launch_fixed(cs_fixed_f64_kernel<N, true, double>, P, st, P.A)           \
+             : launch_fixed(cs_fixed_f64_kernel<N, false, double>, P, st, P.A);         \
+    return 1;                                                                           \
   }
     MSK_FIX64(16) MSK_FIX64(32) MSK_FIX64(64) MSK_FIX64(128) MSK_FIX64(256)
 #undef MSK_FIX64
@@ -486,6 +517,46 @@ static int cs_fixed_chunk(const CsParams<T>& P, cudaStream_t st, int* rc) {
 #undef MSK_FIX32
   }
   return 0;
+}
+
+// FP64 CountSketch of an FP32-stored A (each value widened exactly): the
+// fixed-width FP64 kernels with runtime widths, in column chunks of <= 256
+// (and L2-resident Y slices).
+int launch_cs_f32a_f64y(const float* A, int64_t d, int64_t n, int64_t lda, const double* b,
+                        uint32_t k, uint64_t key, double* Y, int64_t ldy, int64_t maxc,
+                        cudaStream_t st) {
+  const int64_t nchunks = n > 0 ? (n + maxc - 1) / maxc : 1;
+  for (int64_t ch = 0; ch < nchunks; ++ch) {
+    const int64_t c0 = ch * maxc, c1 = std::min<int64_t>(n, c0 + maxc);
+    const bool last = ch == nchunks - 1;
+    CsParams<double> P{};
+    P.A = nullptr;
+    P.d = d;
+    P.lda = lda;
+    P.ncol_a = (int)(c1 - c0);
+    P.b = (b && last) ? b : nullptr;
+    P.ncol = P.ncol_a + (P.b ? 1 : 0);
+    if (P.ncol == 0) continue;
+    P.k = k;
+    P.key = key;
+    P.Y = Y + c0;
+    P.ldy = ldy;
+    const float* Ac = A + c0 * lda;
+    const bool hb = P.b != nullptr;
+    const int w = P.ncol_a;
+    int rc;
+#define MSK_FIXF(N)                                                                     \
+    if (w <= N) {                                                                       \
+      rc = hb ? launch_fixed(cs_fixed_f64_kernel<N, true, float>, P, st, Ac)            \
+              : launch_fixed(cs_fixed_f64_kernel<N, false, float>, P, st, Ac);          \
+      if (rc) return rc;                                                                \
+      continue;                                                                         \
+    }
+    MSK_FIXF(16) MSK_FIXF(32) MSK_FIXF(64) MSK_FIXF(128) MSK_FIXF(256)
+#undef MSK_FIXF
+    return MSK_ENOTSUP;
+  }
+  return MSK_OK;
 }
 
 template <typename T>
@@ -512,8 +583,9 @@ static int cs_atomic_typed(const T* A, int64_t d, int64_t n, int64_t lda, const 
     }
     const int64_t budget = tune_get("cs.l2_budget_bytes", (long long)l2_bytes * 2 / 5);
     int64_t fit = budget / ((int64_t)k * (int64_t)sizeof(T));
-    fit = fit / 16 * 16;
-    if (fit >= 16 && fit < maxc) maxc = fit;
+    // prefer the fixed-width kernels' widths (multiples of 64, or 32/16)
+    fit = fit >= 64 ? fit / 64 * 64 : fit >= 32 ? 32 : 16;
+    if (fit < maxc) maxc = fit;
   }
   // chunks of A columns; b rides with the last one
   const int64_t nchunks = n > 0 ? (n + maxc - 1) / maxc : 1;

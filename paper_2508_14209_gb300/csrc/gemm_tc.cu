@@ -31,111 +31,15 @@
 #include <cstdint>
 
 #include "msk_internal.h"
+#include "msk_tc.cuh"
 
 namespace msk {
+
+__device__ int g_tc_timeout = 0;  // set by a tensor-core kernel whose bounded wait expired
 
 constexpr int kTcBM = 128;       // M per CTA (one UMMA M)
 constexpr int kTcBK = 64;        // K per stage: 64 x 2 bytes = one 128-byte swizzle row
 constexpr int kTcThreads = 128;  // 4 warps
-constexpr uint64_t kTcWaitNs = 1000000000ull;
-constexpr uint32_t kTcWaitIters = 1u << 28;
-constexpr int kTcSmemBudget = 220 * 1024;
-
-__device__ int g_tc_timeout = 0;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(a), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait on an mbarrier phase: false (and the timeout flag set) after
-// kTcWaitNs nanoseconds or kTcWaitIters polls.
-__device__ bool mbar_wait(uint32_t a, uint32_t parity) {
-  if (mbar_try(a, parity)) return true;
-  const uint64_t t0 = global_ns();
-  for (uint32_t i = 0; i < kTcWaitIters; ++i) {
-    if (mbar_try(a, parity)) return true;
-    if (global_ns() - t0 > kTcWaitNs) break;
-  }
-  atomicExch(&g_tc_timeout, 1);
-  return false;
-}
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
-                                            uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
-      : "memory");
-}
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
-                                            int c2, uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
-      : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms of
-// 1024 bytes (stride byte offset 1024), descriptor version 1.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)(16u >> 4) << 16;
-  d |= (uint64_t)(1024u >> 4) << 32;
-  d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
-  return d;
-}
-__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
-                                         uint32_t idesc, uint32_t accum) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
-      : "memory");
-}
-__device__ __forceinline__ void umma_commit(uint32_t bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-      : "memory");
-}
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
-      "%12, %13, %14, %15}, [%16];"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-        "=r"(v[14]), "=r"(v[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
 // Instruction descriptor of kind::f16 with FP32 accumulation, K-major A and B:
 // bits 4-5 D format (1 = F32), 7-9 A format, 10-12 B format (0 = F16,
 // 1 = BF16), 17-22 N >> 3, 24-28 M >> 4.
@@ -190,7 +94,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     int issued = 0;
     for (int it = 0; it < nk; ++it) {
       const int s = it % stages;
-      if (it >= stages && !mbar_wait(smem_u32(&bars[stages + s]), ((it / stages) & 1) ^ 1)) {
+      if (it >= stages && !mbar_wait(smem_u32(&bars[stages + s]), ((it / stages) & 1) ^ 1, &g_tc_timeout)) {
         *abort_flag = 1;
         break;
       }
@@ -208,13 +112,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (*abort_flag) {
       // let this CTA's copies in flight land before leaving (bounded waits)
       for (int it = (issued > stages ? issued - stages : 0); it < issued; ++it)
-        mbar_wait(smem_u32(&bars[it % stages]), (it / stages) & 1);
+        mbar_wait(smem_u32(&bars[it % stages]), (it / stages) & 1, &g_tc_timeout);
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
     for (int it = 0; it < nk; ++it) {
       const int s = it % stages;
-      if (!mbar_wait(smem_u32(&bars[s]), (it / stages) & 1)) {
+      if (!mbar_wait(smem_u32(&bars[s]), (it / stages) & 1, &g_tc_timeout)) {
         *abort_flag = 1;
         break;
       }
@@ -235,7 +139,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   }
   __syncwarp();
   // epilogue: TMEM lane (warp*32 + lane) holds row m0 + warp*32 + lane
-  const bool done = mbar_wait(smem_u32(&bars[2 * stages]), 0);
+  const bool done = mbar_wait(smem_u32(&bars[2 * stages]), 0, &g_tc_timeout);
   tc_fence_after();
   // tcgen05.ld is warp-collective: take the decision per warp
   if (__all_sync(0xffffffffu, done && !*abort_flag && nk > 0)) {
@@ -272,27 +176,12 @@ constexpr int kDsDrainWarps = 16;
 constexpr int kDsThreads = (2 + kDsDrainWarps) * 32;
 constexpr int kDsMaxCpw = 24;  // columns per drain warp (NT <= 96): keeps hi/lo in registers
 
-__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&v)[4]) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
-               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
-               : "r"(taddr));
-}
-__device__ __forceinline__ void ds_accum(float& hi, float& lo, float v) {
-  const float s = hi + v;
-  const float bb = s - hi;
-  const float e = (hi - (s - bb)) + (v - bb);  // TwoSum error of hi + v
-  const float t = lo + e;
-  hi = s + t;
-  lo = t - (hi - s);
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t a) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
-}
-
-__global__ void __launch_bounds__(kDsThreads, 1)
-    tc_gemm_ds_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                      int p, int ncol, int NT, int KT, int kt_per, int stages, uint32_t idesc,
-                      double* __restrict__ part) {
+// One CTA's tile (mt, nt) and K slice sidx of one problem.  tmA / tmB point
+// at tensor maps in parameter or global memory.
+__device__ __forceinline__ void tc_ds_body(const CUtensorMap* tmA, const CUtensorMap* tmB, int p,
+                                           int ncol, int NT, int KT, int kt_per, int stages,
+                                           uint32_t idesc, double* __restrict__ part, int mt,
+                                           int nt, int sidx) {
   constexpr int PARTS = 3;
   extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
   unsigned char* smem =
@@ -307,8 +196,8 @@ __global__ void __launch_bounds__(kDsThreads, 1)
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(acce + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * kTcBM, n0 = blockIdx.y * NT;
-  const int kt0 = blockIdx.z * kt_per;
+  const int m0 = mt * kTcBM, n0 = nt * NT;
+  const int kt0 = sidx * kt_per;
   const int nk = min(KT, kt0 + kt_per) - kt0;
   constexpr uint32_t kCols = 512;  // two accumulator buffers at columns 0 and 256
 
@@ -341,7 +230,7 @@ __global__ void __launch_bounds__(kDsThreads, 1)
       int issued = 0;
       for (int it = 0; it < nk; ++it) {
         const int s = it % stages;
-        if (it >= stages && !mbar_wait(smem_u32(&bars[stages + s]), ((it / stages) & 1) ^ 1)) {
+        if (it >= stages && !mbar_wait(smem_u32(&bars[stages + s]), ((it / stages) & 1) ^ 1, &g_tc_timeout)) {
           *abort_flag = 1;
           break;
         }
@@ -350,15 +239,15 @@ __global__ void __launch_bounds__(kDsThreads, 1)
         mbar_expect_tx(full, stage_bytes);
         unsigned char* st = smem + (size_t)s * stage_bytes;
         const int kc = (kt0 + it) * kTcBK;
-        tma_load_2d(smem_u32(st), &tmA, kc, m0, full);
+        tma_load_2d(smem_u32(st), tmA, kc, m0, full);
 #pragma unroll
         for (int t = 0; t < PARTS; ++t)
-          tma_load_3d(smem_u32(st + a_bytes + t * b_bytes), &tmB, kc, n0, t, full);
+          tma_load_3d(smem_u32(st + a_bytes + t * b_bytes), tmB, kc, n0, t, full);
         ++issued;
       }
       if (*abort_flag)
         for (int it = (issued > stages ? issued - stages : 0); it < issued; ++it)
-          mbar_wait(smem_u32(&bars[it % stages]), (it / stages) & 1);
+          mbar_wait(smem_u32(&bars[it % stages]), (it / stages) & 1, &g_tc_timeout);
     }
     __syncwarp();
   } else if (warp == 1) {
@@ -366,11 +255,11 @@ __global__ void __launch_bounds__(kDsThreads, 1)
       for (int it = 0; it < nk; ++it) {
         const int s = it % stages;
         const int b = it & 1, u = it >> 1;
-        if (u >= 1 && !mbar_wait(smem_u32(&acce[b]), (u - 1) & 1)) {
+        if (u >= 1 && !mbar_wait(smem_u32(&acce[b]), (u - 1) & 1, &g_tc_timeout)) {
           *abort_flag = 1;
           break;
         }
-        if (!mbar_wait(smem_u32(&bars[s]), (it / stages) & 1)) {
+        if (!mbar_wait(smem_u32(&bars[s]), (it / stages) & 1, &g_tc_timeout)) {
           *abort_flag = 1;
           break;
         }
@@ -406,7 +295,7 @@ __global__ void __launch_bounds__(kDsThreads, 1)
     bool ok = true;
     for (int it = 0; it < nk; ++it) {
       const int b = it & 1, u = it >> 1;
-      const bool got = mbar_wait(smem_u32(&accf[b]), u & 1);
+      const bool got = mbar_wait(smem_u32(&accf[b]), u & 1, &g_tc_timeout);
       if (!__all_sync(0xffffffffu, got && !*abort_flag)) {
         ok = false;
         break;
@@ -429,7 +318,7 @@ __global__ void __launch_bounds__(kDsThreads, 1)
     }
     if (ok && nk > 0) {
       const int row = m0 + quad * 32 + lane;
-      double* out = part + (int64_t)blockIdx.z * p * ncol;
+      double* out = part + (int64_t)sidx * p * ncol;
 #pragma unroll
       for (int c = 0; c < kDsMaxCpw; ++c) {
         const int col = n0 + c_begin + c;
@@ -443,6 +332,37 @@ __global__ void __launch_bounds__(kDsThreads, 1)
   if (warp == 2)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols)
                  : "memory");
+}
+
+__global__ void __launch_bounds__(kDsThreads, 1)
+    tc_gemm_ds_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                      int p, int ncol, int NT, int KT, int kt_per, int stages, uint32_t idesc,
+                      double* __restrict__ part) {
+  tc_ds_body(&tmA, &tmB, p, ncol, NT, KT, kt_per, stages, idesc, part, blockIdx.x, blockIdx.y,
+             blockIdx.z);
+}
+
+// Batched form: CTA b takes work item b; jobs[j] covers items
+// [jobs[j].item_begin, jobs[j + 1].item_begin) in (s, nt, mt) order.  The
+// tensor maps live in global memory (64-byte aligned inside TcJob); the
+// producer thread acquires them for the tensor-map proxy before the first TMA.
+__global__ void __launch_bounds__(kDsThreads, 1)
+    tc_gemm_ds_batch_kernel(const TcJob* __restrict__ jobs, int njobs, int stages) {
+  int lo = 0, hi = njobs - 1;
+  const int b = blockIdx.x;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].item_begin <= b) lo = mid; else hi = mid - 1;
+  }
+  const TcJob& J = jobs[lo];
+  const int local = b - J.item_begin;
+  const int mt = local % J.Mt, nt = (local / J.Mt) % J.Nt, sidx = local / (J.Mt * J.Nt);
+  if (threadIdx.x == 0) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&J.mapA) : "memory");
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&J.mapB) : "memory");
+  }
+  tc_ds_body(&J.mapA, &J.mapB, J.p, J.ncol, J.NT, J.KT, J.kt_per, stages, J.idesc, J.part, mt, nt,
+             sidx);
 }
 
 // Yt[t][n][kk] (row pitch kpitch) from the FP32 row-major Y (k x ncol, ldy):
@@ -612,7 +532,7 @@ int launch_tc_gemm(uint64_t gkey, int64_t p, int64_t k, int64_t ncol, const floa
   dim3 grid(t.Mt, t.Nt, t.S);
   const bool drain = t.parts == 3 && tune_get("tc.drain", 1) != 0;
   if (drain) {
-    MSK_CUDA(cudaFuncSetAttribute(tc_gemm_ds_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    MSK_ALLOW_SMEM(tc_gemm_ds_kernel);
     tc_gemm_ds_kernel<<<grid, kDsThreads, smem, st>>>(tmA, tmB, (int)p, (int)ncol, t.NT, t.KT, t.kt_per,
                                                       t.stages, idesc, reinterpret_cast<double*>(part));
     MSK_CHECK_LAUNCH("tc_gemm_ds_kernel");
@@ -623,11 +543,11 @@ int launch_tc_gemm(uint64_t gkey, int64_t p, int64_t k, int64_t ncol, const floa
     return MSK_OK;
   }
   if (t.parts == 3) {
-    MSK_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    MSK_ALLOW_SMEM(tc_gemm_kernel<3>);
     tc_gemm_kernel<3><<<grid, kTcThreads, smem, st>>>(tmA, tmB, (int)p, (int)ncol, t.NT, t.KT, t.kt_per,
                                                       t.stages, idesc, part);
   } else {
-    MSK_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    MSK_ALLOW_SMEM(tc_gemm_kernel<1>);
     tc_gemm_kernel<1><<<grid, kTcThreads, smem, st>>>(tmA, tmB, (int)p, (int)ncol, t.NT, t.KT, t.kt_per,
                                                       t.stages, idesc, part);
   }
@@ -636,6 +556,84 @@ int launch_tc_gemm(uint64_t gkey, int64_t p, int64_t k, int64_t ncol, const floa
   tc_reduce_kernel<<<(unsigned)std::min<int64_t>((total + 255) / 256, num_sms() * 8), 256, 0, st>>>(
       part, t.S, p, ncol, Z, ldz);
   MSK_CHECK_LAUNCH("tc_reduce_kernel");
+  return MSK_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// Batched draining BF16x3 stage (used by the batch engine).
+
+// Shapes of one problem in the batched stage: N tiles of <= 96 columns,
+// K slices of kt_per K tiles.
+void tc_ds_shape(int64_t p, int64_t k, int64_t ncol, int kt_per, TcShape* s) {
+  s->npad = (int)((ncol + 15) / 16 * 16);
+  const int nt_max = 4 * kDsMaxCpw;
+  const int ntiles = (s->npad + nt_max - 1) / nt_max;
+  s->NT = (int)(((s->npad + ntiles - 1) / ntiles + 15) / 16 * 16);
+  s->Nt = (s->npad + s->NT - 1) / s->NT;
+  s->Mt = (int)((p + kTcBM - 1) / kTcBM);
+  s->KT = (int)((k + kTcBK - 1) / kTcBK);
+  s->kpitch = (k + 7) / 8 * 8;
+  s->kt_per = std::max(1, std::min(kt_per, s->KT));
+  s->S = (s->KT + s->kt_per - 1) / s->kt_per;
+  s->items = s->Mt * s->Nt * s->S;
+}
+
+// Fill a TcJob: tensor maps over G (p x k bf16, pitch kpitch) and Yt (3 parts
+// of npad x k bf16).
+int tc_ds_make_job(int64_t p, int64_t k, int64_t ncol, const TcShape& s, const void* G,
+                   const void* Yt, double* part, int item_begin, TcJob* job) {
+  auto enc = encode_fn();
+  if (!enc) {
+    set_error_text("cuTensorMapEncodeTiled entry point not available");
+    return MSK_ECUDA;
+  }
+  {
+    cuuint64_t dims[2] = {(cuuint64_t)k, (cuuint64_t)p};
+    cuuint64_t strides[1] = {(cuuint64_t)s.kpitch * 2};
+    cuuint32_t box[2] = {(cuuint32_t)kTcBK, (cuuint32_t)kTcBM};
+    cuuint32_t estr[2] = {1, 1};
+    if (enc(&job->mapA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(G), dims, strides, box,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
+      set_error_text("cuTensorMapEncodeTiled failed for a batched G");
+      return MSK_ECUDA;
+    }
+  }
+  {
+    cuuint64_t dims[3] = {(cuuint64_t)k, (cuuint64_t)s.npad, 3};
+    cuuint64_t strides[2] = {(cuuint64_t)s.kpitch * 2, (cuuint64_t)s.npad * s.kpitch * 2};
+    cuuint32_t box[3] = {(cuuint32_t)kTcBK, (cuuint32_t)s.NT, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    if (enc(&job->mapB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(Yt), dims, strides, box,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
+      set_error_text("cuTensorMapEncodeTiled failed for a batched Y");
+      return MSK_ECUDA;
+    }
+  }
+  job->part = part;
+  job->p = (int)p;
+  job->ncol = (int)ncol;
+  job->NT = s.NT;
+  job->KT = s.KT;
+  job->kt_per = s.kt_per;
+  job->Mt = s.Mt;
+  job->Nt = s.Nt;
+  job->S = s.S;
+  job->idesc = make_idesc(kTcBM, s.NT, true);
+  job->item_begin = item_begin;
+  return MSK_OK;
+}
+
+int launch_tc_ds_batch(const TcJob* jobs, int njobs, int total_items, int max_nt, cudaStream_t st) {
+  if (total_items <= 0) return MSK_OK;
+  const int stage_bytes = kTcBM * kTcBK * 2 + 3 * max_nt * kTcBK * 2;
+  const int stages = std::max(1, std::min(6, (kTcSmemBudget - 2048) / stage_bytes));
+  const size_t smem = (size_t)stages * stage_bytes + 1024 + 256;
+  MSK_ALLOW_SMEM(tc_gemm_ds_batch_kernel);
+  tc_gemm_ds_batch_kernel<<<total_items, kDsThreads, smem, st>>>(jobs, njobs, stages);
+  MSK_CHECK_LAUNCH("tc_gemm_ds_batch_kernel");
   return MSK_OK;
 }
 

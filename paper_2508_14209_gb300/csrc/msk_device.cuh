@@ -84,4 +84,51 @@ __device__ __forceinline__ float gauss_std(uint64_t key, uint64_t elem) {
   return 0.0f;
 }
 
+// L2 reductions (the atomic adds of Algorithm 2, issued without a return value).
+__device__ __forceinline__ void red_add(double* p, double v) {
+  asm volatile("red.relaxed.gpu.global.add.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+__device__ __forceinline__ void red_add(float* p, float v) {
+  asm volatile("red.relaxed.gpu.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+__device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, float d) {
+  asm volatile("red.relaxed.gpu.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a),
+               "f"(b), "f"(c), "f"(d)
+               : "memory");
+}
+
+// Sign of a CountSketch row applied by flipping the sign bit.
+__device__ __forceinline__ double flip(double x, unsigned long long s) {
+  return __longlong_as_double(__double_as_longlong(x) ^ s);
+}
+__device__ __forceinline__ float flip(float x, unsigned s) {
+  return __uint_as_float(__float_as_uint(x) ^ s);
+}
+
+
+// Double-single arithmetic: a value carried as an unevaluated sum hi + lo of
+// two binary32 numbers (Dekker 1971; Knuth's TwoSum; the exact product
+// a*b = hi + lo from one FMA), about 48 significant bits.
+struct DS {
+  float hi, lo;
+};
+__device__ __forceinline__ DS ds_add(DS a, float bh, float bl) {
+  const float s = a.hi + bh;
+  const float v = s - a.hi;
+  float e = (a.hi - (s - v)) + (bh - v);  // TwoSum error of a.hi + bh
+  e += a.lo + bl;
+  const float h = s + e;
+  return DS{h, e - (h - s)};
+}
+// acc += a * (xh + xl), a exact binary32.
+__device__ __forceinline__ DS ds_fma(DS acc, float a, float xh, float xl) {
+  const float ph = a * xh;
+  float pl = fmaf(a, xh, -ph);  // exact: a*xh = ph + pl
+  pl = fmaf(a, xl, pl);
+  return ds_add(acc, ph, pl);
+}
+__device__ __forceinline__ DS ds_shfl_xor(DS v, int m) {
+  return DS{__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m)};
+}
+
 }  // namespace msk

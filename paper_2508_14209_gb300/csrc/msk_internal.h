@@ -1,6 +1,7 @@
 // msk_internal.h — host-side internals of libmsketch shared by the .cu files:
 // status propagation, stream casts, workspace carving, launch declarations.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstddef>
@@ -53,6 +54,33 @@ struct Need {
 };
 
 int num_sms();
+// Opt-in shared-memory limit per block of the current device (bytes).
+int smem_optin_max();
+// Allow `func` all the dynamic shared memory the device offers next to its
+// static shared memory.  The value is the same for every caller, so
+// concurrent launches from several host threads cannot race on it (occupancy
+// follows the size passed at launch).
+cudaError_t allow_max_smem(const void* func);
+#define MSK_ALLOW_SMEM(kern) \
+  MSK_CUDA(::msk::allow_max_smem(reinterpret_cast<const void*>(kern)))
+
+// One CountSketch launch's problem: rows [0, d) of the A columns
+// [c0, c0 + ncol_a) (A points at column c0) plus the optional b column,
+// accumulated into Y (row-major, ldy; Y points at column c0).
+template <typename T>
+struct CsParams {
+  const T* A;
+  int64_t d, lda;
+  int ncol_a;          // columns taken from A in this launch
+  const double* b;     // extra column (after the A columns) or null
+  int ncol;            // ncol_a + (b != null)
+  uint32_t k;
+  uint64_t key;
+  T* Y;
+  int64_t ldy;
+  int pitch;           // shared-memory row pitch (elements)
+};
+
 // Tuning registry lookup (tune.cpp).
 long long tune_get(const char* name, long long dflt);
 
@@ -85,6 +113,31 @@ int launch_gemm_simt(const float* G, int64_t ldg, const void* Y, bool y_f64, int
 // Z[r + c*ldz] = sum_s part[s][c*p + r] (FP64 partials, fixed order).
 __global__ void splitk_reduce_kernel(const double* __restrict__ part, int S, int64_t p, int64_t ncol,
                                      double* __restrict__ Z, int64_t ldz);
+// countsketch.cu: FP64 CountSketch of FP32 A (column chunks of <= maxc <= 256)
+int launch_cs_f32a_f64y(const float* A, int64_t d, int64_t n, int64_t lda, const double* b,
+                        uint32_t k, uint64_t key, double* Y, int64_t ldy, int64_t maxc,
+                        cudaStream_t st);
+// countsketch.cu: batched FP32 CountSketch (problems of one A width + b)
+int launch_cs_batch_f32(int nca, const CsParams<float>* Ps, const int64_t* tile_begin, int nprob,
+                        int64_t total_tiles, cudaStream_t st);
+// gemm_tc.cu: one problem of the batched draining BF16x3 GEMM.
+struct alignas(64) TcJob {
+  CUtensorMap mapA;  // G, 2D {k, p}
+  CUtensorMap mapB;  // Yt parts, 3D {k, npad, 3}
+  double* part;      // S x p x ncol FP64 partials
+  int p, ncol, NT, KT, kt_per, Mt, Nt, S;
+  uint32_t idesc;
+  int item_begin;    // first work item (CTA) of this job
+};
+struct TcShape {
+  int npad, NT, Nt, Mt, KT, kt_per, S, items;
+  int64_t kpitch;
+};
+void tc_ds_shape(int64_t p, int64_t k, int64_t ncol, int kt_per, TcShape* s);
+int tc_ds_make_job(int64_t p, int64_t k, int64_t ncol, const TcShape& s, const void* G,
+                   const void* Yt, double* part, int item_begin, TcJob* job);
+int launch_tc_ds_batch(const TcJob* jobs, int njobs, int total_items, int max_nt, cudaStream_t st);
+int tc_take_timeout(cudaStream_t st);
 // gemm_tc.cu (tcgen05 tensor-core Gaussian stage)
 size_t tc_gemm_workspace(int64_t p, int64_t k, int64_t ncol, int prec);
 int launch_tc_gemm(uint64_t gkey, int64_t p, int64_t k, int64_t ncol, const float* Y, int64_t ldy,
