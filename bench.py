@@ -12,6 +12,16 @@ the whole step (GB/s); roofline = the CountSketch kernel against the measured
 HBM copy bandwidth; e2e = the same metric through the public ms_sketch call
 with pinned host buffers (host->device copy of A and device->host copy of Z
 inside the timed region); cpu_baseline = the CPU oracle on the machine's host.
+
+The same line carries the served least-squares comparison ("serving"): a pool
+of least-squares problems shaped like the served configuration (n uniform in
+{16, 32, 64, 128}, d log-uniform in [2^14, 2^21], sigma log-spaced from 1 to
+10^-U(2,8), FP32 A), a trace of requests drawn from the pool with fresh seeds
+and Poisson arrivals, solved (a) by the request server with the mixed-precision
+path (FP32 CountSketch, split-BF16 tensor-core Gaussian stage, FP64 QR,
+refinement) and (b) one at a time by plain FP64 sketch-and-solve on the same
+trace; solves/s and p50/p99 latency (arrival to completion) for both, at
+capacity (all requests at t = 0) and at a fixed Poisson rate.
 """
 from __future__ import annotations
 
@@ -214,6 +224,11 @@ def run_ours(args):
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline(args.workload, A)
+    del A
+    torch.cuda.empty_cache()
+    serving = None
+    if args.serve_requests > 0:
+        serving = run_serving(args, dev, rank)
 
     if rank == 0:
         out = {
@@ -226,16 +241,125 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (2 GiB A per step)",
                        "parallelism": f"replicas{ws}"},
             "stages_ms": {"countsketch": round(cs_ms, 5), "gaussian_gemm": round(gemm_ms, 5)},
-            "roofline": {"bound": "hbm", "kernel": "cs_atomic_kernel (+Y zeroing)",
+            "roofline": {"bound": "hbm", "kernel": "cs_fixed_f64_kernel (+Y zeroing memset)" if dts == "f64" else "cs_fixed_f32_kernel (+Y zeroing memset)",
                          "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                          "frac": round(achieved / hbm, 4), "peak_source": peak_src,
                          "traffic": None},
             "clocks": clk, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
             "cpu_baseline": cpu,
+            "serving": serving,
         }
         print(json.dumps(out), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def _serve_pool(dev, seed):
+    import numpy as np
+    import torch
+
+    import inputs
+
+    rng = np.random.default_rng(seed)
+    pool = []
+    for n in (16, 32, 64, 128):
+        for i in range(6):
+            d = int(2 ** rng.uniform(14, 21))
+            e = float(rng.uniform(2, 8))
+            A, b, _ = inputs.ls_problem(d, n, -e, seed=seed + 97 * n + i, dtype=torch.float32, device=dev)
+            pool.append((A, b, d, n))
+    torch.cuda.synchronize()
+    return pool
+
+
+def _serve_mixed(msk, pool, pick, arrivals, dev, tol):
+    import numpy as np
+    import torch
+
+    srv = msk.Server(mem_budget=64 << 30, workers=3, max_batch=32, refine=True, tol=tol, max_iter=4)
+    xs = [torch.empty(pool[j][3], dtype=torch.float64, device=dev) for j in pick]
+    tickets = []
+    t0 = time.perf_counter()
+    for i, j in enumerate(pick):
+        wait = arrivals[i] - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
+        A, b, d, n = pool[j]
+        tickets.append(srv.submit(A, b, 0x5EED0005 + i, xs[i]))
+    srv.wait_all()
+    wall = time.perf_counter() - t0
+    lat, iters, conv = [], [], 0
+    for t in tickets:
+        done, info, l, rc = srv.poll(t)
+        lat.append(l)
+        iters.append(info["iters"])
+        conv += int(info["converged"] == 1 and rc == 0)
+    stats = srv.stats()
+    srv.close()
+    lat = np.array(lat)
+    return {"solves_per_s": round(len(pick) / wall, 1), "p50_ms": round(1e3 * float(np.median(lat)), 3),
+            "p99_ms": round(1e3 * float(np.quantile(lat, 0.99)), 3), "mean_inner_iters": round(float(np.mean(iters)), 2),
+            "converged": conv, "batches": stats["batches"]}
+
+
+def _serve_plain(msk, pool, pick, arrivals, dev):
+    import numpy as np
+    import torch
+
+    ws = {}
+    lat = []
+    t0 = time.perf_counter()
+    for i, j in enumerate(pick):
+        wait = arrivals[i] - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
+        A, b, d, n = pool[j]
+        k, p = 2 * n * n, 4 * n
+        if (d, n) not in ws:
+            ws[(d, n)] = msk.workspace(msk.msk_lstsq_workspace(d, n, k, p, msk.MSK_F32, msk.GEMM_F64, 0), dev)
+        msk.ms_lstsq(A, b, k, p, 0x5EED0005 + i, msk.GEMM_F64, refine=False, ws=ws[(d, n)], want_info=False)
+        torch.cuda.synchronize()
+        lat.append(time.perf_counter() - t0 - arrivals[i])
+    wall = time.perf_counter() - t0
+    lat = np.array(lat)
+    return {"solves_per_s": round(len(pick) / wall, 1), "p50_ms": round(1e3 * float(np.median(lat)), 3),
+            "p99_ms": round(1e3 * float(np.quantile(lat, 0.99)), 3)}
+
+
+def run_serving(args, dev, rank):
+    """Served least squares: mixed-precision server vs plain FP64 one at a time."""
+    import numpy as np
+
+    import paper_2508_14209_gb300 as msk
+
+    pool = _serve_pool(dev, 0x5EED0005 + rank)
+    rng = np.random.default_rng(0x5EED0005 + rank)
+    N = args.serve_requests
+    pick = rng.integers(0, len(pool), N)
+    out = {"requests": N, "pool_problems": len(pool), "tol": args.serve_tol,
+           "workload": "served: n in {16,32,64,128}, d log-uniform [2^14, 2^21], FP32 A, k=2n^2, p=4n"}
+    # warm-up of both paths (module loads, graph machinery, workspace)
+    _serve_mixed(msk, pool, pick[:16], np.zeros(16), dev, args.serve_tol)
+    _serve_plain(msk, pool, pick[:16], np.zeros(16), dev)
+    zero = np.zeros(N)
+    out["capacity"] = {"mixed": _serve_mixed(msk, pool, pick, zero, dev, args.serve_tol),
+                       "plain_fp64": _serve_plain(msk, pool, pick, zero, dev)}
+    rate = args.serve_rate
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, N))
+    out["poisson"] = {"rate_per_s": rate,
+                      "mixed": _serve_mixed(msk, pool, pick, arrivals, dev, args.serve_tol),
+                      "plain_fp64": _serve_plain(msk, pool, pick, arrivals, dev)}
+    # accuracy on a sample: refined mixed relres never above plain FP64 SnS
+    worse = 0
+    for i in range(min(8, N)):
+        A, b, d, n = pool[pick[i]]
+        k, p = 2 * n * n, 4 * n
+        _, ip, _ = msk.ms_lstsq(A, b, k, p, 0x5EED0005 + i, msk.GEMM_F64, refine=False)
+        _, im, _ = msk.ms_lstsq(A, b, k, p, 0x5EED0005 + i, msk.GEMM_BF16X3, refine=True, tol=args.serve_tol,
+                                max_iter=4)
+        worse += int(im["relres"] > (1 + 1e-8) * ip["relres"])
+    out["sample_relres_mixed_above_fp64_sns"] = worse
+    return out
 
 
 def cpu_baseline(workload, A_dev):
@@ -312,6 +436,9 @@ def main():
     ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=4000)
+    ap.add_argument("--serve-rate", type=float, default=400.0)
+    ap.add_argument("--serve-tol", type=float, default=1e-6)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

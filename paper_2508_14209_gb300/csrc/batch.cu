@@ -29,13 +29,13 @@
 
 #include "msk_device.cuh"
 #include "msk_internal.h"
+#include "msk_pass.cuh"
 #include "msk_qr.cuh"
 #include "msk_refine.cuh"
 
 namespace msk {
 
 constexpr int kBatchKtPer = 16;   // K tiles per CTA of the batched GEMM
-constexpr int kBatchChunks = 256; // CTAs per problem in the refinement passes
 constexpr int kRound = 4;         // CG iterations per captured graph round
 constexpr int kBatchMaxInner = 200;
 constexpr double kBatchDecFrac = 0.05;
@@ -63,7 +63,9 @@ struct BatchJob {
   double* sc;    // [0] rho, [1] gain, [2] active, [3] floor, [4] inner iters, [5] bb, [6] rr0
   double* ppart; // pass partials: nchunks x (n + 2)
   double* pout;  // reduced pass result: n + 2
-  int nchunks;
+  int nchunks;      // CTAs of this problem in the refinement passes
+  int chunk_begin;  // its first CTA in the batch-wide pass grid
+  int cw;           // floats per tile copy (pass32_copy_width: 4, 2 or 1)
 };
 
 __global__ void batch_zero_kernel(const BatchJob* __restrict__ jobs) {
@@ -143,27 +145,43 @@ __global__ void batch_tri_inverse_kernel(const BatchJob* __restrict__ jobs) {
   tri_inverse_body(J.Z, J.n, J.p, J.Ri, blockIdx.x, gridDim.x);
 }
 
-// Refinement passes over all problems: CTA (c, j) is chunk c of problem j.
-template <bool RESID>
-__global__ void __launch_bounds__(kPThreads) batch_pass_kernel(const BatchJob* __restrict__ jobs) {
+// Refinement passes, one launch per width class NC: a 1-D grid over the
+// class's problems mem[0..nmem), problem mem[m] owning CTAs
+// [chunk_begin, chunk_begin + nchunks) (found by binary search).  RESID passes
+// run for the problems with only[j] != 0 (all when only is null); the inner
+// passes for the problems whose solve is still active.
+template <int NC, bool RESID>
+__global__ void __launch_bounds__(kP32Threads, pass32_ctas_per_sm(NC))
+    batch_pass_kernel(const BatchJob* __restrict__ jobs, const int* __restrict__ mem, int nmem,
+                      const int* __restrict__ only) {
   extern __shared__ __align__(16) unsigned char bp_smem[];
-  const BatchJob& J = jobs[blockIdx.y];
-  if ((int)blockIdx.x >= J.nchunks) return;
-  if (!RESID && J.sc[2] == 0.0) return;  // problem already stopped
+  const int c = blockIdx.x;
+  int lo = 0, hi = nmem - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mem[mid]].chunk_begin <= c) lo = mid;
+    else hi = mid - 1;
+  }
+  const int j = mem[lo];
+  const BatchJob& J = jobs[j];
+  const int lc = c - J.chunk_begin;
+  if (lc >= J.nchunks) return;
   if (RESID) {
-    pass_body<float, true>(J.A, J.lda, J.d, J.n, J.n | 1, J.b, J.x, J.ppart, blockIdx.x, J.nchunks,
-                           bp_smem);
+    if (only && !only[j]) return;
+    pass32n_body<NC, true>(J.A, J.lda, J.d, J.n, J.cw, J.b, J.x, J.ppart, lc, J.nchunks, bp_smem);
   } else {
-    int pitch = (J.n + 3) / 4 * 4;
-    while (pitch % 32 != 4) pitch += 4;
-    pass_ds_body(J.A, J.lda, J.d, J.n, pitch, J.vec + J.n, J.ppart, blockIdx.x, J.nchunks, bp_smem);
+    if (J.sc[2] == 0.0) return;  // problem already stopped
+    pass32n_body<NC, false>(J.A, J.lda, J.d, J.n, J.cw, nullptr, J.vec + J.n, J.ppart, lc,
+                            J.nchunks, bp_smem);
   }
 }
 
 template <bool ONLY_ACTIVE>
-__global__ void __launch_bounds__(256) batch_pass_reduce_kernel(const BatchJob* __restrict__ jobs) {
+__global__ void __launch_bounds__(256) batch_pass_reduce_kernel(const BatchJob* __restrict__ jobs,
+                                                                const int* __restrict__ only) {
   const BatchJob& J = jobs[blockIdx.y];
   if (ONLY_ACTIVE && J.sc[2] == 0.0) return;
+  if (only && !only[blockIdx.y]) return;
   if ((int)blockIdx.x * 32 >= J.n + 2) return;
   pass_reduce_body(J.ppart, J.nchunks, J.n + 2, J.pout, blockIdx.x);
 }
@@ -173,7 +191,7 @@ __device__ __forceinline__ RefState ref_state(const BatchJob& J) {
 }
 
 // After an FP64 residual pass: start CG on A^T A d = g for every problem that
-// is still refining; record the stopping floor kBatchDecFrac * tol * ||r||^2.
+// is still refining; its stopping floor is kBatchDecFrac * tol * ||r||^2.
 __global__ void batch_pcg_start_kernel(const BatchJob* __restrict__ jobs, double tol,
                                        int* __restrict__ active_count) {
   const BatchJob& J = jobs[blockIdx.x];
@@ -185,30 +203,23 @@ __global__ void batch_pcg_start_kernel(const BatchJob* __restrict__ jobs, double
   pcg_start_body(J.Ri, J.n, g, ref_state(J));
   __syncthreads();
   if (threadIdx.x == 0) {
-    J.sc[3] = kBatchDecFrac * tol * rr;
+    pcg_arm(J.sc, kBatchDecFrac * tol * rr);
     atomicAdd(active_count, 1);
   }
 }
 
-// One CG step.  A problem stops when a step gains less than its floor; if
-// that happens at the very first step, x is already the minimiser to within
-// tol: it is marked converged (sc[5] = 1) and its correction is not applied.
+// One CG step (pcg_stop_check holds the stopping rule).  A problem whose very
+// first step is below its floor is already the minimiser to within tol: its
+// refining flag is cleared so that the correction is not applied.
 __global__ void batch_pcg_update_kernel(const BatchJob* __restrict__ jobs,
                                         int* __restrict__ active_count, int* __restrict__ refining) {
   const BatchJob& J = jobs[blockIdx.x];
   if (J.sc[2] == 0.0) return;
   pcg_update_body(J.Ri, J.n, J.pout, ref_state(J));
   __syncthreads();
-  if (threadIdx.x == 0) {
-    J.sc[4] += 1.0;
-    if (!(J.sc[1] > J.sc[3]) || !(J.sc[0] > 0.0) || J.sc[4] >= (double)kBatchMaxInner) {
-      if (J.sc[4] == 1.0) {
-        J.sc[5] = 1.0;
-        refining[blockIdx.x] = 0;
-      }
-      J.sc[2] = 0.0;
-      atomicSub(active_count, 1);
-    }
+  if (threadIdx.x == 0 && pcg_stop_check(J.sc, kBatchMaxInner)) {
+    if (J.sc[5] != 0.0) refining[blockIdx.x] = 0;
+    atomicSub(active_count, 1);
   }
 }
 
@@ -219,15 +230,20 @@ __global__ void batch_axpy_kernel(const BatchJob* __restrict__ jobs, const int* 
   for (int j = threadIdx.x; j < J.n; j += blockDim.x) J.x[j] += J.vec[j];
 }
 
-// out[4j..4j+3] = (||r||^2, ||b||^2, inner iterations, first-step stop) of problem j.
+// out[kGather j + (0..5)] = (||r||^2, ||b||^2 of the last residual pass,
+// inner steps, first-step stop, sum of gains, ended by the gain rule).
+constexpr int kGather = 6;
 __global__ void batch_gather_kernel(const BatchJob* __restrict__ jobs, int nprob,
                                     double* __restrict__ out) {
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nprob; j += gridDim.x * blockDim.x) {
     const BatchJob& J = jobs[j];
-    out[4 * j] = J.pout[J.n];
-    out[4 * j + 1] = J.pout[J.n + 1];
-    out[4 * j + 2] = J.sc[4];
-    out[4 * j + 3] = J.sc[5];
+    double* o = out + kGather * j;
+    o[0] = J.pout[J.n];
+    o[1] = J.pout[J.n + 1];
+    o[2] = J.sc[4];
+    o[3] = J.sc[5];
+    o[4] = J.sc[6];
+    o[5] = J.sc[7];
   }
 }
 
@@ -236,11 +252,8 @@ __global__ void batch_arm_kernel(const BatchJob* __restrict__ jobs, int nprob,
                                  const int* __restrict__ refining, int* __restrict__ active) {
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nprob; j += gridDim.x * blockDim.x) {
     const BatchJob& J = jobs[j];
-    J.sc[0] = 0.0;
-    J.sc[1] = 0.0;
+    for (int q = 0; q < kScCount; ++q) J.sc[q] = 0.0;
     J.sc[2] = refining[j] ? 1.0 : 0.0;
-    J.sc[4] = 0.0;
-    J.sc[5] = 0.0;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) *active = 0;
 }
@@ -254,7 +267,11 @@ struct BatchPlan {
   std::vector<std::vector<int64_t>> cs_tiles;
   std::vector<size_t> cs_off, tiles_off;
   size_t jobs_off = 0, tc_off = 0, flags_off = 0, gather_off = 0;
-  int total_items = 0, max_nt = 16, max_npad = 16, max_n = 1, max_chunks = 1;
+  int total_items = 0, max_nt = 16, max_npad = 16, max_n = 1;
+  // refinement-pass launches, one per width class present
+  std::vector<int> pass_nc, pass_chunks;
+  std::vector<std::vector<int>> pass_mem;
+  std::vector<size_t> pass_mem_off;
   int64_t max_k = 1, max_pk = 1, max_yk = 1;
   size_t bytes = 0;
 };
@@ -277,7 +294,7 @@ static void plan_batch(const msk_batch_item* items, int nitems, int refine, char
   P->jobs_off = take(sizeof(BatchJob) * (size_t)nitems);
   P->tc_off = take(sizeof(TcJob) * (size_t)nitems);
   P->flags_off = take(sizeof(int) * (size_t)(nitems + 8));
-  P->gather_off = take(sizeof(double) * 4 * (size_t)nitems);
+  P->gather_off = take(sizeof(double) * kGather * (size_t)nitems);
   P->jobs.resize(nitems);
   P->tc.resize(nitems);
   P->shapes.resize(nitems);
@@ -300,7 +317,6 @@ static void plan_batch(const msk_batch_item* items, int nitems, int refine, char
     J.kpitch = sh.kpitch;
     J.npad = sh.npad;
     J.S = sh.S;
-    J.nchunks = (int)std::max<int64_t>(1, std::min<int64_t>((J.d + kPR - 1) / kPR, kBatchChunks));
     J.Y = reinterpret_cast<float*>(ptr(take((size_t)J.k * J.ldy * 4)));
     J.G = reinterpret_cast<uint16_t*>(ptr(take((size_t)J.p * sh.kpitch * 2)));
     J.Yt = reinterpret_cast<uint16_t*>(ptr(take((size_t)3 * sh.npad * sh.kpitch * 2)));
@@ -308,16 +324,44 @@ static void plan_batch(const msk_batch_item* items, int nitems, int refine, char
     J.Z = reinterpret_cast<double*>(ptr(take((size_t)J.p * J.ncol * 8)));
     J.Ri = reinterpret_cast<double*>(ptr(take(refine ? (size_t)J.n * J.n * 8 : 0)));
     J.vec = reinterpret_cast<double*>(ptr(take(refine ? (size_t)5 * J.n * 8 : 0)));
-    J.sc = reinterpret_cast<double*>(ptr(take(8 * 8)));
-    J.ppart = reinterpret_cast<double*>(ptr(take((size_t)J.nchunks * (J.n + 2) * 8)));
+    J.sc = reinterpret_cast<double*>(ptr(take(kScCount * 8)));
     J.pout = reinterpret_cast<double*>(ptr(take((size_t)(J.n + 2) * 8)));
     P->max_nt = std::max(P->max_nt, sh.NT);
     P->max_npad = std::max(P->max_npad, sh.npad);
     P->max_n = std::max(P->max_n, J.n);
-    P->max_chunks = std::max(P->max_chunks, J.nchunks);
     P->max_k = std::max<int64_t>(P->max_k, J.k);
     P->max_pk = std::max<int64_t>(P->max_pk, (int64_t)J.p * J.k);
     P->max_yk = std::max<int64_t>(P->max_yk, (int64_t)J.k * J.ldy);
+  }
+  // Refinement passes: one launch per width class present, each sized to
+  // fill the GPU (pass32_ctas_per_sm CTAs per SM) and shared out among the
+  // class's problems in proportion to their row tiles (every CTA then walks
+  // about the same number of tiles), at least one CTA per problem.
+  for (int nc : {16, 32, 64, 128, 256}) {
+    std::vector<int> mem;
+    int64_t total_tiles = 0;
+    for (int j = 0; j < nitems; ++j)
+      if (pass32_class(P->jobs[j].n) == nc) {
+        mem.push_back(j);
+        total_tiles += (P->jobs[j].d + pass32_rows(nc) - 1) / pass32_rows(nc);
+      }
+    if (mem.empty()) continue;
+    const int64_t cap = (int64_t)pass32_ctas_per_sm(nc) * num_sms();
+    int begin = 0;
+    for (int j : mem) {
+      BatchJob& J = P->jobs[j];
+      const int64_t tiles = (J.d + pass32_rows(nc) - 1) / pass32_rows(nc);
+      const int64_t share = (cap * tiles + total_tiles - 1) / total_tiles;
+      J.nchunks = (int)std::max<int64_t>(1, std::min<int64_t>(share, tiles));
+      J.chunk_begin = begin;
+      begin += J.nchunks;
+      J.cw = pass32_copy_width(J.A, J.lda);
+      J.ppart = reinterpret_cast<double*>(ptr(take((size_t)J.nchunks * (J.n + 2) * 8)));
+    }
+    P->pass_nc.push_back(nc);
+    P->pass_chunks.push_back(begin);
+    P->pass_mem_off.push_back(take(sizeof(int) * mem.size()));
+    P->pass_mem.push_back(mem);
   }
   for (int w : {16, 32, 64, 128, 256}) {
     std::vector<CsParams<float>> ps;
@@ -394,6 +438,9 @@ int msk_batch_lstsq(const msk_batch_item* items, int nitems, int refine, double 
   P.total_items = item;
   MSK_CUDA(cudaMemcpyAsync(jobs_dev, P.jobs.data(), sizeof(BatchJob) * nitems, cudaMemcpyHostToDevice, st));
   MSK_CUDA(cudaMemcpyAsync(tc_dev, P.tc.data(), sizeof(TcJob) * nitems, cudaMemcpyHostToDevice, st));
+  for (size_t c = 0; c < P.pass_nc.size(); ++c)
+    MSK_CUDA(cudaMemcpyAsync(base + P.pass_mem_off[c], P.pass_mem[c].data(), sizeof(int) * P.pass_mem[c].size(),
+                             cudaMemcpyHostToDevice, st));
   for (size_t c = 0; c < P.widths.size(); ++c) {
     MSK_CUDA(cudaMemcpyAsync(base + P.cs_off[c], P.cs[c].data(), sizeof(CsParams<float>) * P.cs[c].size(),
                              cudaMemcpyHostToDevice, st));
@@ -438,35 +485,66 @@ int msk_batch_lstsq(const msk_batch_item* items, int nitems, int refine, double 
   }
   // 5. refinement
   std::vector<int> iters(nitems, 0), conv(nitems, refine ? 0 : 1);
-  std::vector<double> relres(nitems, -1.0), relres_sns(nitems, -1.0), prev(nitems, -1.0);
-  std::vector<double> hg(4 * (size_t)nitems);
-  const size_t smem_res =
-      sizeof(double) * ((size_t)P.max_n + kPR) + sizeof(float) * (size_t)kPR * (P.max_n | 1);
-  int pitch_ds = (P.max_n + 3) / 4 * 4;
-  while (pitch_ds % 32 != 4) pitch_ds += 4;
-  const size_t smem_ds = sizeof(float) * ((size_t)kPR * pitch_ds + 2 * P.max_n + 2 * kPR);
-  MSK_ALLOW_SMEM(batch_pass_kernel<true>);
-  MSK_ALLOW_SMEM(batch_pass_kernel<false>);
-  const dim3 pgrid(P.max_chunks, nitems), rgrid((P.max_n + 2 + 31) / 32, nitems);
+  std::vector<double> relres(nitems, -1.0), relres_sns(nitems, -1.0), rr(nitems, 0.0);
+  std::vector<double> hg(kGather * (size_t)nitems);
+  MSK_ALLOW_SMEM((batch_pass_kernel<16, true>));
+  MSK_ALLOW_SMEM((batch_pass_kernel<32, true>));
+  MSK_ALLOW_SMEM((batch_pass_kernel<64, true>));
+  MSK_ALLOW_SMEM((batch_pass_kernel<128, true>));
+  MSK_ALLOW_SMEM((batch_pass_kernel<256, true>));
+  MSK_ALLOW_SMEM((batch_pass_kernel<16, false>));
+  MSK_ALLOW_SMEM((batch_pass_kernel<32, false>));
+  MSK_ALLOW_SMEM((batch_pass_kernel<64, false>));
+  MSK_ALLOW_SMEM((batch_pass_kernel<128, false>));
+  MSK_ALLOW_SMEM((batch_pass_kernel<256, false>));
+  const dim3 rgrid((P.max_n + 2 + 31) / 32, nitems);
+  // one pass over every problem: a launch per width class
+  auto passes = [&](bool resid, const int* only, cudaStream_t s) {
+    for (size_t c = 0; c < P.pass_nc.size(); ++c) {
+      const int nc = P.pass_nc[c];
+      const unsigned g = (unsigned)P.pass_chunks[c];
+      const size_t sm = pass32_smem(nc);
+      const int* mem = reinterpret_cast<const int*>(base + P.pass_mem_off[c]);
+      const int nm = (int)P.pass_mem[c].size();
+#define MSK_BATCH_PASS(NCV)                                                                     \
+  if (nc == NCV) {                                                                              \
+    if (resid) batch_pass_kernel<NCV, true><<<g, kP32Threads, sm, s>>>(jobs_dev, mem, nm, only);  \
+    else batch_pass_kernel<NCV, false><<<g, kP32Threads, sm, s>>>(jobs_dev, mem, nm, only);      \
+  }
+      MSK_BATCH_PASS(16)
+      MSK_BATCH_PASS(32)
+      MSK_BATCH_PASS(64)
+      MSK_BATCH_PASS(128)
+      MSK_BATCH_PASS(256)
+#undef MSK_BATCH_PASS
+    }
+  };
   const unsigned gblocks = (unsigned)((nitems + 255) / 256);
-  // FP64 residual pass of every problem, then (||r||^2, ||b||^2, iters) to the host
-  auto fp64_pass = [&](bool first) -> int {
-    batch_pass_kernel<true><<<pgrid, kPThreads, smem_res, st>>>(jobs_dev);
+  // FP64 residual pass of the problems with only[j] (all when null), then the
+  // gathered scalars to the host; rr and relres updated for those problems.
+  auto fp64_pass = [&](const int* only_dev, const std::vector<int>* only_host) -> int {
+    passes(true, only_dev, st);
     MSK_CHECK_LAUNCH("batch_pass_kernel");
-    batch_pass_reduce_kernel<false><<<rgrid, 256, 0, st>>>(jobs_dev);
+    batch_pass_reduce_kernel<false><<<rgrid, 256, 0, st>>>(jobs_dev, only_dev);
     MSK_CHECK_LAUNCH("batch_pass_reduce_kernel");
     batch_gather_kernel<<<gblocks, 256, 0, st>>>(jobs_dev, nitems, gather);
     MSK_CHECK_LAUNCH("batch_gather_kernel");
-    MSK_CUDA(cudaMemcpyAsync(hg.data(), gather, sizeof(double) * 4 * nitems, cudaMemcpyDeviceToHost, st));
+    MSK_CUDA(cudaMemcpyAsync(hg.data(), gather, sizeof(double) * kGather * nitems, cudaMemcpyDeviceToHost, st));
     MSK_CUDA(cudaStreamSynchronize(st));
     for (int j = 0; j < nitems; ++j) {
-      const double rr = std::sqrt(std::max(hg[4 * j], 0.0) / (hg[4 * j + 1] > 0.0 ? hg[4 * j + 1] : 1.0));
-      relres[j] = rr;
-      if (first) relres_sns[j] = rr;
+      if (only_host && !(*only_host)[j]) continue;
+      rr[j] = std::max(hg[kGather * j], 0.0);
+      const double bb = hg[kGather * j + 1];
+      relres[j] = std::sqrt(rr[j] / (bb > 0.0 ? bb : 1.0));
     }
     return MSK_OK;
   };
   int status = MSK_OK;
+  if (refine || infos) {
+    rc = fp64_pass(nullptr, nullptr);
+    if (rc) return rc;
+    relres_sns = relres;
+  }
   if (refine) {
     batch_tri_inverse_kernel<<<dim3((P.max_n + 7) / 8, nitems), 256, 0, st>>>(jobs_dev);
     MSK_CHECK_LAUNCH("batch_tri_inverse_kernel");
@@ -480,8 +558,8 @@ int msk_batch_lstsq(const msk_batch_item* items, int nitems, int refine, double 
     cudaGraphExec_t exec = nullptr;
     MSK_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
     for (int r = 0; r < kRound; ++r) {
-      batch_pass_kernel<false><<<pgrid, kPThreads, smem_ds, cap>>>(jobs_dev);
-      batch_pass_reduce_kernel<true><<<rgrid, 256, 0, cap>>>(jobs_dev);
+      passes(false, nullptr, cap);
+      batch_pass_reduce_kernel<true><<<rgrid, 256, 0, cap>>>(jobs_dev, nullptr);
       batch_pcg_update_kernel<<<nitems, 512, 0, cap>>>(jobs_dev, active, refining);
     }
     cudaError_t ce = cudaStreamEndCapture(cap, &graph);
@@ -491,25 +569,12 @@ int msk_batch_lstsq(const msk_batch_item* items, int nitems, int refine, double 
       cudaGraphDestroy(graph);
       return cuda_fail(ce, "cudaGraphInstantiate");
     }
-    std::vector<int> ref(nitems, 0);
-    for (int outer = 0; outer <= max_iter && !status; ++outer) {
-      rc = fp64_pass(outer == 0);
-      if (rc) {
-        status = rc;
-        break;
-      }
+    std::vector<int> ref(nitems, 0), recheck(nitems, 0);
+    for (int outer = 0; outer < max_iter && !status; ++outer) {
       int nref = 0;
       for (int j = 0; j < nitems; ++j) {
-        ref[j] = 0;
-        if (conv[j]) continue;
-        if (prev[j] >= 0.0 && std::fabs(prev[j] - relres[j]) <= tol * relres[j]) {
-          conv[j] = 1;
-          continue;
-        }
-        if (outer == max_iter) continue;
-        prev[j] = relres[j];
-        ref[j] = 1;
-        ++nref;
+        ref[j] = conv[j] ? 0 : 1;
+        nref += ref[j];
       }
       if (nref == 0) break;
       ce = cudaMemcpyAsync(refining, ref.data(), sizeof(int) * nitems, cudaMemcpyHostToDevice, st);
@@ -530,28 +595,45 @@ int msk_batch_lstsq(const msk_batch_item* items, int nitems, int refine, double 
         }
       }
       if (status) break;
+      // x += d for the problems still refining (those whose first step was
+      // below the floor had their flag cleared: already converged)
+      batch_axpy_kernel<<<nitems, 256, 0, st>>>(jobs_dev, refining);
       batch_gather_kernel<<<gblocks, 256, 0, st>>>(jobs_dev, nitems, gather);
-      ce = cudaMemcpyAsync(hg.data(), gather, sizeof(double) * 4 * nitems, cudaMemcpyDeviceToHost, st);
+      ce = cudaMemcpyAsync(hg.data(), gather, sizeof(double) * kGather * nitems, cudaMemcpyDeviceToHost, st);
       if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
       if (ce != cudaSuccess) {
         status = cuda_fail(ce, "refinement counters");
         break;
       }
-      for (int j = 0; j < nitems; ++j)
-        if (ref[j]) {
-          iters[j] += (int)hg[4 * j + 2];
-          if (hg[4 * j + 3] != 0.0) conv[j] = 1;  // minimiser reached: relres above stands
-        }
-      batch_axpy_kernel<<<nitems, 256, 0, st>>>(jobs_dev, refining);
+      std::vector<double> inner(hg);
+      for (int j = 0; j < nitems; ++j) {
+        recheck[j] = 0;
+        if (!ref[j]) continue;
+        iters[j] += (int)inner[kGather * j + 2];
+        if (inner[kGather * j + 3] != 0.0) conv[j] = 1;  // minimiser reached: relres above stands
+        else recheck[j] = 1;
+      }
+      // new FP64 residual of the corrected problems
+      const std::vector<double> rr_prev(rr), relres_prev(relres);
+      rc = fp64_pass(refining, &recheck);
+      if (rc) {
+        status = rc;
+        break;
+      }
+      for (int j = 0; j < nitems; ++j) {
+        if (!recheck[j]) continue;
+        const double predicted = rr_prev[j] - inner[kGather * j + 4];
+        const bool by_rule = inner[kGather * j + 5] != 0.0;
+        if ((by_rule && std::fabs(rr[j] - predicted) <= tol * rr[j]) ||
+            std::fabs(relres_prev[j] - relres[j]) <= tol * relres[j])
+          conv[j] = 1;
+      }
     }
     cudaGraphExecDestroy(exec);
     cudaGraphDestroy(graph);
     if (status) return status;
     for (int j = 0; j < nitems; ++j)
       if (!conv[j]) status = MSK_ENOCONV;
-  } else if (infos) {
-    rc = fp64_pass(true);
-    if (rc) return rc;
   }
   MSK_CUDA(cudaStreamSynchronize(st));  // the uploads above read host vectors
   if (infos)

@@ -9,9 +9,11 @@
 //       arithmetic on the FP32 units for FP32 A (binary32 alone fails: with
 //       kappa(A) * 2^-24 > 1 the products A p cancel to noise) — until a step
 //       lowers ||b - A x||^2 by less than 0.05 tol ||r||^2 (CG on the normal
-//       equations lowers it by alpha*rho per step).  Then x += d.  Stops when
-//       the relative residual changes by at most tol * relres between outer
-//       steps, or when the first inner step already gains less than that.
+//       equations lowers it by alpha*rho per step).  Then x += d and a new
+//       FP64 residual.  Converged when that residual confirms the decrease
+//       the CG recurrences predicted (to tol * ||r||^2), when the relative
+//       residual changes by at most tol * relres between outer steps, or when
+//       the first inner step already gains less than the floor.
 //   * ne_lstsq: normal equations (Section 6.3): [A b]^T [A b] in one FP64
 //       pass (split over row slices, partials summed in a fixed order),
 //       Cholesky, two triangular solves.
@@ -24,6 +26,8 @@
 
 #include "msk_device.cuh"
 #include "msk_internal.h"
+#include "msk_pass.cuh"
+#include "msk_pass.cuh"
 #include "msk_refine.cuh"
 
 namespace msk {
@@ -128,37 +132,54 @@ static size_t gram_workspace(int64_t d, int64_t n) {
 }
 
 // Thin kernels over the bodies in msk_refine.cuh.
+// `active` (optional): the inner solve's running flag; the inner-iteration
+// kernels return at once when it is 0, so that a round of several iterations
+// can be queued without a host round trip per iteration.
 template <typename TA, bool RESID>
 __global__ void __launch_bounds__(kPThreads) pass_kernel(const TA* __restrict__ A, int64_t lda,
                                                       int64_t d, int n, int pitch,
                                                       const double* __restrict__ b,
                                                       const double* __restrict__ vin,
-                                                      double* __restrict__ part) {
+                                                      double* __restrict__ part,
+                                                      const double* __restrict__ active) {
+  if (active && *active == 0.0) return;
   extern __shared__ __align__(16) unsigned char pk_smem[];
   pass_body<TA, RESID>(A, lda, d, n, pitch, b, vin, part, blockIdx.x, gridDim.x, pk_smem);
 }
 __global__ void __launch_bounds__(256) pass_reduce_kernel(const double* __restrict__ part, int nctas,
-                                                          int len, double* __restrict__ out) {
+                                                          int len, double* __restrict__ out,
+                                                          const double* __restrict__ active) {
+  if (active && *active == 0.0) return;
   pass_reduce_body(part, nctas, len, out, blockIdx.x);
 }
-__global__ void __launch_bounds__(kPThreads) pass_ds_kernel(const float* __restrict__ A, int64_t lda,
-                                                         int64_t d, int n, int pitch,
-                                                         const double* __restrict__ vin,
-                                                         double* __restrict__ part) {
-  extern __shared__ __align__(16) unsigned char ds_smem[];
-  pass_ds_body(A, lda, d, n, pitch, vin, part, blockIdx.x, gridDim.x, ds_smem);
+template <int NC, bool RESID>
+__global__ void __launch_bounds__(kP32Threads, pass32_ctas_per_sm(NC))
+    pass32_kernel(const float* __restrict__ A, int64_t lda, int64_t d, int n, int cw,
+                  const double* __restrict__ b, const double* __restrict__ vin,
+                  double* __restrict__ part, const double* __restrict__ active) {
+  if (active && *active == 0.0) return;
+  extern __shared__ __align__(16) unsigned char p32_smem[];
+  if constexpr (NC == 0)
+    pass32g_body<RESID>(A, lda, d, n, cw == 4, b, vin, part, blockIdx.x, gridDim.x, p32_smem);
+  else
+    pass32n_body<NC, RESID>(A, lda, d, n, cw, b, vin, part, blockIdx.x, gridDim.x, p32_smem);
 }
 __global__ void tri_inverse_kernel(const double* __restrict__ R, int n, int64_t ldr,
                                    double* __restrict__ Ri) {
   tri_inverse_body(R, n, ldr, Ri, blockIdx.x, gridDim.x);
 }
 __global__ void pcg_start_kernel(const double* __restrict__ Ri, int n, const double* __restrict__ g,
-                                 RefState s) {
+                                 RefState s, double floor) {
   pcg_start_body(Ri, n, g, s);
+  __syncthreads();
+  if (threadIdx.x == 0) pcg_arm(s.sc, floor);
 }
 __global__ void pcg_update_kernel(const double* __restrict__ Ri, int n, const double* __restrict__ pv,
-                                  RefState s) {
+                                  RefState s, int max_steps) {
+  if (s.sc[2] == 0.0) return;
   pcg_update_body(Ri, n, pv, s);
+  __syncthreads();
+  if (threadIdx.x == 0) pcg_stop_check(s.sc, max_steps);
 }
 // x += dlt
 __global__ void axpy_kernel(int n, const double* __restrict__ dlt, double* __restrict__ x) {
@@ -172,64 +193,92 @@ static int pass_grid(int64_t d) {
 
 template <typename TA, bool RESID>
 static int launch_pass_t(const TA* A, int64_t lda, int64_t d, int n, const double* b,
-                         const double* vin, double* part, double* out, cudaStream_t st) {
+                         const double* vin, double* part, double* out, const double* active,
+                         cudaStream_t st) {
   const int pitch = n | 1;  // odd: conflict-free transposing stores and row reads
   const size_t smem = sizeof(double) * ((size_t)n + kPR) + sizeof(TA) * (size_t)kPR * pitch;
   auto kern = pass_kernel<TA, RESID>;
   MSK_ALLOW_SMEM(kern);
   const int grid = pass_grid(d);
-  kern<<<grid, kPThreads, smem, st>>>(A, lda, d, n, pitch, b, vin, part);
+  kern<<<grid, kPThreads, smem, st>>>(A, lda, d, n, pitch, b, vin, part, active);
   MSK_CHECK_LAUNCH("pass_kernel");
-  pass_reduce_kernel<<<(n + 2 + 31) / 32, 256, 0, st>>>(part, grid, n + 2, out);
+  pass_reduce_kernel<<<(n + 2 + 31) / 32, 256, 0, st>>>(part, grid, n + 2, out, active);
   MSK_CHECK_LAUNCH("pass_reduce_kernel");
   return MSK_OK;
 }
 
-// ---------------------------------------------------------------------------
-// Double-single pass for FP32 A: v = A^T (A p) with every sum carried as an
-// unevaluated pair hi + lo of binary32 numbers (Dekker 1971; Knuth's TwoSum;
-// the exact product a*b = hi + lo from one FMA).  About 48 significant bits,
-// enough for the inner iterations at kappa(A) up to ~1e10, at the cost of
-// ~13 FP32 operations per multiply-add instead of one FP64 operation (GB300's
-// FP64 rate is 1/66 of its FP32 rate).  p arrives in FP64 and is split into
-// hi + lo binary32 parts.
-static int launch_pass_ds(const float* A, int64_t lda, int64_t d, int n, const double* vin,
-                          double* part, double* out, cudaStream_t st) {
-  int pitch = (n + 3) / 4 * 4;
-  while (pitch % 32 != 4) pitch += 4;
-  const size_t smem = sizeof(float) * ((size_t)kPR * pitch + 2 * n + 2 * kPR);
-  MSK_ALLOW_SMEM(pass_ds_kernel);
-  const int grid = pass_grid(d);
-  pass_ds_kernel<<<grid, kPThreads, smem, st>>>(A, lda, d, n, pitch, vin, part);
-  MSK_CHECK_LAUNCH("pass_ds_kernel");
-  pass_reduce_kernel<<<(n + 2 + 31) / 32, 256, 0, st>>>(part, grid, n + 2, out);
+// Passes over an FP32 A (msk_pass.cuh): the FP64 residual pass and the
+// double-single operator pass of the inner iterations.  Persistent CTAs, at
+// most kPassCtasPerSm per SM (the occupancy of the 70 KB shared-memory tile
+// pipeline), each walking every nctas-th tile of R rows.
+constexpr int kPassCtasPerSm = 3;
+
+static int pass32_grid(int64_t d, int n) {
+  const int R = pass32_rows(n);
+  return (int)std::max<int64_t>(1, std::min<int64_t>((d + R - 1) / R, (int64_t)kPassCtasPerSm * num_sms()));
+}
+
+template <int NC, bool RESID>
+static int launch_pass32_nc(const float* A, int64_t lda, int64_t d, int n, const double* b,
+                            const double* vin, double* part, double* out, const double* active,
+                            cudaStream_t st) {
+  const size_t smem = pass32_smem(n);
+  auto kern = pass32_kernel<NC, RESID>;
+  MSK_ALLOW_SMEM(kern);
+  int per_sm = 0;
+  MSK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kP32Threads, smem));
+  per_sm = std::max(1, std::min(per_sm, kPassCtasPerSm));
+  const int R = pass32_rows(n);
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((d + R - 1) / R, (int64_t)per_sm * num_sms()));
+  kern<<<grid, kP32Threads, smem, st>>>(A, lda, d, n, pass32_copy_width(A, lda), b, vin, part, active);
+  MSK_CHECK_LAUNCH("pass32_kernel");
+  pass_reduce_kernel<<<(n + 2 + 31) / 32, 256, 0, st>>>(part, grid, n + 2, out, active);
   MSK_CHECK_LAUNCH("pass_reduce_kernel");
   return MSK_OK;
 }
 
-// RESID: out = [A^T r (n), ||r||^2, ||b||^2] with r = b - A x (FP64).
+template <bool RESID>
+static int launch_pass32(const float* A, int64_t lda, int64_t d, int n, const double* b,
+                         const double* vin, double* part, double* out, const double* active,
+                         cudaStream_t st) {
+  if (n > 2 * kP32Threads) return MSK_ENOTSUP;
+  switch (pass32_class(n)) {
+    case 16: return launch_pass32_nc<16, RESID>(A, lda, d, n, b, vin, part, out, active, st);
+    case 32: return launch_pass32_nc<32, RESID>(A, lda, d, n, b, vin, part, out, active, st);
+    case 64: return launch_pass32_nc<64, RESID>(A, lda, d, n, b, vin, part, out, active, st);
+    case 128: return launch_pass32_nc<128, RESID>(A, lda, d, n, b, vin, part, out, active, st);
+    case 256: return launch_pass32_nc<256, RESID>(A, lda, d, n, b, vin, part, out, active, st);
+    default: return launch_pass32_nc<0, RESID>(A, lda, d, n, b, vin, part, out, active, st);
+  }
+}
+
+// RESID: out = [A^T r (n), ||r||^2, ||b||^2] with r = b - A x (FP64; for FP32 A
+// the sum A^T r in double-single).
 // else : out = [A^T A p (n), ., .] (FP64 for FP64 A, double-single for FP32 A).
 static int launch_pass(const void* A, int dtype, int64_t lda, int64_t d, int n, const double* b,
-                       const double* vin, bool resid, double* part, double* out, cudaStream_t st) {
+                       const double* vin, bool resid, double* part, double* out,
+                       const double* active, cudaStream_t st) {
   if (dtype == MSK_F64) {
     if (resid)
       return launch_pass_t<double, true>(static_cast<const double*>(A), lda, d, n, b, vin, part,
-                                         out, st);
+                                         out, nullptr, st);
     return launch_pass_t<double, false>(static_cast<const double*>(A), lda, d, n, b, vin, part, out,
-                                        st);
+                                        active, st);
   }
   if (resid)
-    return launch_pass_t<float, true>(static_cast<const float*>(A), lda, d, n, b, vin, part, out,
-                                      st);
-  return launch_pass_ds(static_cast<const float*>(A), lda, d, n, vin, part, out, st);
+    return launch_pass32<true>(static_cast<const float*>(A), lda, d, n, b, vin, part, out, nullptr,
+                               st);
+  return launch_pass32<false>(static_cast<const float*>(A), lda, d, n, nullptr, vin, part, out,
+                              active, st);
 }
 
 static size_t pass_workspace(int64_t d, int64_t n) {
-  return (size_t)pass_grid(d) * (n + 2) * sizeof(double);
+  return (size_t)std::max(pass_grid(d), pass32_grid(d, (int)n)) * (n + 2) * sizeof(double);
 }
 
 constexpr int kMaxInner = 200;
 constexpr double kDecFrac = 0.05;
+constexpr int kInnerRound = 4;  // inner iterations queued per host check
 
 }  // namespace msk
 
@@ -301,71 +350,79 @@ int ms_lstsq(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, const 
   if (refine) {
     double* Ri = static_cast<double*>(cv.take((size_t)n * n * sizeof(double)));
     double* vec = static_cast<double*>(cv.take((size_t)5 * n * sizeof(double)));
-    double* sc = static_cast<double*>(cv.take(64));
+    double* sc = static_cast<double*>(cv.take(kScCount * sizeof(double)));
     if (!Ri || !vec || !sc) return MSK_ENOMEM;
     RefState s{x, vec, vec + n, vec + 2 * n, vec + 3 * n, sc};
     double* gsave = vec + 4 * n;
     tri_inverse_kernel<<<(unsigned)std::max<int64_t>(1, (n + 7) / 8), 256, 0, st>>>(Z, (int)n, p, Ri);
     MSK_CHECK_LAUNCH("tri_inverse_kernel");
-    double prev = -1.0;
     converged = 0;
-    std::vector<double> host(3);
-    for (int outer = 0; outer <= max_iter; ++outer) {
-      // FP64 true residual pass: pout = [A^T r, ||r||^2, ||b||^2]
-      rc = launch_pass(A, dtype, lda, d, (int)n, b, x, true, part, pout, st);
-      if (rc) return rc;
-      MSK_CUDA(cudaMemcpyAsync(host.data(), pout + n, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    // FP64 true residual pass: pout = [A^T r, ||r||^2, ||b||^2]; rr = ||r||^2
+    double rr = 0.0;
+    auto residual = [&]() -> int {
+      int e = launch_pass(A, dtype, lda, d, (int)n, b, x, true, part, pout, nullptr, st);
+      if (e) return e;
+      double h[2];
+      MSK_CUDA(cudaMemcpyAsync(h, pout + n, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
       MSK_CUDA(cudaStreamSynchronize(st));
-      if (outer == 0) bnorm2 = host[1];
-      const double rr = std::sqrt(std::max(host[0], 0.0) / (bnorm2 > 0.0 ? bnorm2 : 1.0));
-      if (outer == 0) relres_sns = rr;
-      relres = rr;
-      if (prev >= 0.0 && std::fabs(prev - rr) <= tol * rr) {
-        converged = 1;
-        break;
-      }
-      if (outer == max_iter) break;
-      prev = rr;
-      // inner PCG on A^T A d = g (double-single passes for FP32 A)
+      rr = std::max(h[0], 0.0);
+      bnorm2 = h[1];
+      relres = std::sqrt(rr / (bnorm2 > 0.0 ? bnorm2 : 1.0));
+      return MSK_OK;
+    };
+    rc = residual();
+    if (rc) return rc;
+    relres_sns = relres;
+    for (int outer = 0; outer < max_iter; ++outer) {
+      // Inner PCG on A^T A d = g (double-single passes for FP32 A).  Each CG
+      // step lowers ||b - A x||^2 by alpha*rho; the solve ends once a step
+      // gains no more than kDecFrac * tol * ||r||^2 (the geometric tail is then
+      // below ~2x that).  Iterations are queued kInnerRound at a time; the
+      // kernels of a stopped solve return at once.
       MSK_CUDA(cudaMemcpyAsync(gsave, pout, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-      pcg_start_kernel<<<1, 512, 0, st>>>(Ri, (int)n, gsave, s);
+      pcg_start_kernel<<<1, 512, 0, st>>>(Ri, (int)n, gsave, s, kDecFrac * tol * rr);
       MSK_CHECK_LAUNCH("pcg_start_kernel");
-      // Each CG step lowers ||b - A x||^2 by alpha*rho; stop the inner loop
-      // once a step gains less than kDecFrac * tol * ||r||^2 (the geometric
-      // tail is then below ~2x that), and stop the outer loop when even the
-      // first step of an inner solve would gain that little.
-      const double rr_now = host[0];
-      const double gain_floor = kDecFrac * tol * rr_now;
-      double sch[2] = {0.0, 0.0};
-      int it = 0;
-      bool first_small = false;
-      for (; it < kMaxInner; ++it) {
-        rc = launch_pass(A, dtype, lda, d, (int)n, nullptr, s.p, false, part, pout, st);
-        if (rc) return rc;
-        pcg_update_kernel<<<1, 512, 0, st>>>(Ri, (int)n, pout, s);
-        MSK_CHECK_LAUNCH("pcg_update_kernel");
-        ++inner_total;
-        MSK_CUDA(cudaMemcpyAsync(sch, sc, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
-        MSK_CUDA(cudaStreamSynchronize(st));
-        if (!(sch[1] > gain_floor) || !(sch[0] > 0.0)) {
-          first_small = it == 0;
-          ++it;
-          break;
+      double active = 1.0;
+      for (int queued = 0; active != 0.0 && queued < kMaxInner; queued += kInnerRound) {
+        for (int r = 0; r < kInnerRound; ++r) {
+          rc = launch_pass(A, dtype, lda, d, (int)n, nullptr, s.p, false, part, pout, sc + 2, st);
+          if (rc) return rc;
+          pcg_update_kernel<<<1, 512, 0, st>>>(Ri, (int)n, pout, s, kMaxInner);
+          MSK_CHECK_LAUNCH("pcg_update_kernel");
         }
+        MSK_CUDA(cudaMemcpyAsync(&active, sc + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
+        MSK_CUDA(cudaStreamSynchronize(st));
       }
-      if (first_small) {
-        // x is the minimiser to within tol: keep it (relres above is its FP64
-        // residual) rather than apply a negligible correction
+      double h[kScCount];
+      MSK_CUDA(cudaMemcpyAsync(h, sc, sizeof(h), cudaMemcpyDeviceToHost, st));
+      MSK_CUDA(cudaStreamSynchronize(st));
+      inner_total += (int)h[4];
+      if (h[5] != 0.0) {
+        // even the first step gains no more than the floor: x is the
+        // minimiser to within tol; keep it (relres is its FP64 residual)
         converged = 1;
         break;
       }
       axpy_kernel<<<1, 512, 0, st>>>((int)n, s.dlt, x);
       MSK_CHECK_LAUNCH("axpy_kernel");
+      const double rr_prev = rr, relres_prev = relres;
+      rc = residual();
+      if (rc) return rc;
+      // Converged when the solve ended by its gain rule and the true FP64
+      // residual confirms the decrease the CG recurrences predicted (no loss
+      // to the inner arithmetic), or when the relative residual no longer
+      // moves by more than tol.
+      const double predicted = rr_prev - h[6];
+      if ((h[7] != 0.0 && std::fabs(rr - predicted) <= tol * rr) ||
+          std::fabs(relres_prev - relres) <= tol * relres) {
+        converged = 1;
+        break;
+      }
     }
     iters = inner_total;
     if (!converged) status = MSK_ENOCONV;
   } else if (info) {
-    rc = launch_pass(A, dtype, lda, d, (int)n, b, x, true, part, pout, st);
+    rc = launch_pass(A, dtype, lda, d, (int)n, b, x, true, part, pout, nullptr, st);
     if (rc) return rc;
     double host[2];
     MSK_CUDA(cudaMemcpyAsync(host, pout + n, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));

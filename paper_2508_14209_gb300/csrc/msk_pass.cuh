@@ -1,0 +1,716 @@
+// msk_pass.cuh — refinement passes over an FP32 A (the operator applications
+// of the sketch-and-precondition refinement: A preconditioned by the R of the
+// sketched QR, as in the preconditioned normal equations of Section 6.3):
+//   RESID = true : r_i = b_i - A_i x in FP64 (one DFMA per element);
+//                  accumulates g = A^T r, ||r||^2, ||b||^2.
+//   RESID = false: w_i = A_i p and v = A^T w, both in double-single.
+// Every product of A with a column vector is accumulated as a compensated
+// pair (s, c) of binary32 numbers: s carries the running sum, TwoSum (Knuth)
+// returns its exact rounding error, the exact product error comes from one
+// FMA (Dekker), and all errors are summed into c — the Dot2 scheme of Ogita,
+// Rump and Oishi (SIAM J. Sci. Comput. 2005), about twice the working
+// precision (~48 bits) at 11 binary32 operations per multiply-add.  GB300's
+// FP64 rate is about 1/64 of its FP32 rate, so this is ~5x cheaper than DFMA.
+//
+// Tiling.  A CTA of kP32Threads threads walks row tiles t = cta, cta + nctas,
+// ... of R rows (R a power of two, R * n ~ 8192), staged column-major in shared
+// memory (stride R) by cp.async, two buffers deep so that the next tile streams
+// in while the current one is computed.  Rows beyond d are zero-filled by the
+// copy itself.
+//   dot phase   : thread (r, q) = (t mod R, t / R) sums columns q, q + Q, ...
+//                 of row r (Q = T / R threads per row; rows t, t + T, ... when
+//                 R >= T); the Q partials are merged through shared memory.
+//                 A warp reads 32 consecutive rows of one column: no conflicts.
+//   column phase: thread (g, j) = (t mod G, t / G) accumulates column j over
+//                 rows g + G * ((x + j) mod (R / G)), x = 0 .. R/G - 1 (G row
+//                 groups, G * n <= T).  The rotation by j puts the 32 lanes of a
+//                 warp in 32 different banks although the stride R is a
+//                 multiple of 32.  Accumulators live in registers across tiles
+//                 and are merged over the G groups once per CTA.
+// Output: part[cta][0..n) the CTA's vector partial, part[cta][n], [n+1] the
+// scalars (RESID) or zeros; summed in fixed order by pass_reduce_body.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "msk_device.cuh"
+
+namespace msk {
+
+constexpr int kP32Threads = 256;
+constexpr int kP32TileElems = 8192;  // R * n target (32 KiB per buffer)
+
+// Width class of the specialised bodies: n <= 256 runs as NC = the next power
+// of two >= max(n, 16) columns (the extra columns are zero-filled and
+// contribute nothing); wider n runs the generic body (class 0).
+__host__ __device__ __forceinline__ int pass32_class(int n) {
+  if (n > 256) return 0;
+  int c = 16;
+  while (c < n) c *= 2;
+  return c;
+}
+// Generic body: rows per tile, a power of two in [32, 1024] with R * n ~ 8192.
+__host__ __device__ __forceinline__ int pass32g_rows(int n) {
+  int R = 32;
+  while (R < 1024 && 2 * R * n <= kP32TileElems) R *= 2;
+  return R;
+}
+// Rows per tile of the body that runs for n.
+__host__ __device__ __forceinline__ int pass32_rows(int n) {
+  const int nc = pass32_class(n);
+  return nc ? kP32TileElems / nc : pass32g_rows(n);
+}
+// Dynamic shared memory of a pass CTA for n columns (two tiles + vectors +
+// merge space) of the body that runs for n.
+__host__ __device__ __forceinline__ size_t pass32_smem(int n) {
+  const int nc = pass32_class(n);
+  if (nc) {
+    const int R = kP32TileElems / nc;
+    return sizeof(float) * 2 * (size_t)kP32TileElems + 16 * (size_t)nc +
+           sizeof(double) * kP32Threads + sizeof(float2) * (size_t)R;
+  }
+  const int R = pass32g_rows(n);
+  return sizeof(float) * 2 * (size_t)R * n + sizeof(double) * (size_t)n +
+         sizeof(double) * kP32Threads + sizeof(float) * 2 * (size_t)R + sizeof(double) * kP32Threads;
+}
+
+struct D2 {
+  float s, c;
+};
+// acc += a * (xh + xl) (Dot2 step: TwoProd by FMA, TwoSum, errors into c).
+__device__ __forceinline__ void d2_fma(D2& acc, float a, float xh, float xl) {
+  const float ph = __fmul_rn(a, xh);
+  const float pe = __fmaf_rn(a, xh, -ph);
+  const float s = __fadd_rn(acc.s, ph);
+  const float v = __fsub_rn(s, acc.s);
+  const float e = __fadd_rn(__fsub_rn(acc.s, __fsub_rn(s, v)), __fsub_rn(ph, v));
+  acc.s = s;
+  acc.c = __fadd_rn(acc.c, __fadd_rn(e, __fmaf_rn(a, xl, pe)));
+}
+// (s1, c1) + (s2, c2)
+__device__ __forceinline__ D2 d2_merge(D2 a, D2 b) {
+  const float s = __fadd_rn(a.s, b.s);
+  const float v = __fsub_rn(s, a.s);
+  const float e = __fadd_rn(__fsub_rn(a.s, __fsub_rn(s, v)), __fsub_rn(b.s, v));
+  return D2{s, __fadd_rn(__fadd_rn(a.c, b.c), e)};
+}
+
+// Two binary32 lanes in one 64-bit register for the packed FP32x2
+// instructions of sm_100+ (add/sub/mul/fma .rn.f32x2): each instruction does
+// the same operation on both lanes, halving the instruction count of the
+// compensated sums below.
+typedef unsigned long long f2p;
+__device__ __forceinline__ f2p f2p_make(float lo, float hi) {
+  f2p r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ float2 f2p_split(f2p v) {
+  float lo, hi;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+  return make_float2(lo, hi);
+}
+__device__ __forceinline__ f2p f2p_add(f2p a, f2p b) {
+  f2p r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2p f2p_sub(f2p a, f2p b) {
+  f2p r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2p f2p_mul(f2p a, f2p b) {
+  f2p r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2p f2p_fma(f2p a, f2p b, f2p c) {
+  f2p r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+struct D2P {
+  f2p s, c;  // two independent compensated sums
+};
+// acc += a * (xh + xl) lane-wise, nxh = -xh: the Dot2 step of d2_fma with
+// ph = a xh carried negated (nph = -ph exactly, rounding is sign-symmetric)
+// so that the exact product error is one FMA: a xh + nph.
+__device__ __forceinline__ void d2p_fma(D2P& acc, f2p a, f2p xh, f2p nxh, f2p xl) {
+  const f2p nph = f2p_mul(a, nxh);
+  const f2p pe = f2p_fma(a, xh, nph);
+  const f2p s = f2p_sub(acc.s, nph);
+  const f2p v = f2p_sub(s, acc.s);
+  const f2p e = f2p_sub(f2p_sub(acc.s, f2p_sub(s, v)), f2p_add(nph, v));
+  acc.s = s;
+  acc.c = f2p_add(acc.c, f2p_add(e, f2p_fma(a, xl, pe)));
+}
+// The two lanes of a packed sum as scalar pairs.
+__device__ __forceinline__ void d2p_lanes(const D2P& a, D2& lo, D2& hi) {
+  const float2 s = f2p_split(a.s), c = f2p_split(a.c);
+  lo = D2{s.x, c.x};
+  hi = D2{s.y, c.y};
+}
+
+__device__ __forceinline__ unsigned p32_smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+// 4-byte copy, zero-filled when !valid (the source is then not read).
+__device__ __forceinline__ void p32_cp4(float* dst, const float* src, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(p32_smem_addr(dst)), "l"(src),
+               "r"(valid ? 4 : 0)
+               : "memory");
+}
+// 16-byte copy of `bytes` (0..16) source bytes, the rest zero-filled.
+__device__ __forceinline__ void p32_cp16(float* dst, const float* src, int bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(p32_smem_addr(dst)), "l"(src),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void p32_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void p32_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Stage rows [i0, i0 + R) of columns 0..ns-1 into buf (column-major, stride
+// R); columns >= n and rows >= d are zero-filled without reading A.
+// vec: A 16-byte aligned and lda a multiple of 4 (16-byte copies).
+__device__ __forceinline__ void p32_issue(const float* __restrict__ A, int64_t lda, int64_t d, int n,
+                                          int ns, int R, int lgR, bool vec, int64_t i0, float* buf) {
+  const int t = threadIdx.x;
+  if (vec) {
+    const int lgR4 = lgR - 2, R4 = R >> 2;
+    const int total = ns * R4;
+    for (int e = t; e < total; e += kP32Threads) {
+      const int j = e >> lgR4, r = (e & (R4 - 1)) << 2;
+      const int64_t i = i0 + r;
+      const int64_t left = j < n ? d - i : 0;
+      const int bytes = left >= 4 ? 16 : (left > 0 ? (int)left * 4 : 0);
+      p32_cp16(buf + (size_t)j * R + r, bytes > 0 ? A + i + (int64_t)j * lda : A, bytes);
+    }
+  } else {
+    const int total = ns * R;
+    for (int e = t; e < total; e += kP32Threads) {
+      const int j = e >> lgR, r = e & (R - 1);
+      const int64_t i = i0 + r;
+      const bool ok = i < d && j < n;
+      p32_cp4(buf + (size_t)j * R + r, ok ? A + i + (int64_t)j * lda : A, ok);
+    }
+  }
+  p32_commit();
+}
+
+// Generic body (any n <= 512; used for n > 256).
+// 8-byte copy of `bytes` (0, 4 or 8) source bytes, the rest zero-filled.
+__device__ __forceinline__ void p32_cp8(float* dst, const float* src, int bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(p32_smem_addr(dst)), "l"(src),
+               "r"(bytes)
+               : "memory");
+}
+
+// Copy width (floats per cp.async) usable for A: 4 when A is 16-byte aligned
+// and lda a multiple of 4, 2 when 8-byte aligned with lda even, else 1.
+__host__ __device__ __forceinline__ int pass32_copy_width(const float* A, int64_t lda) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(A);
+  if ((a & 15) == 0 && (lda & 3) == 0) return 4;
+  if ((a & 7) == 0 && (lda & 1) == 0) return 2;
+  return 1;
+}
+
+// Staging of one tile for the specialised bodies: rows [i0, i0 + R) of the NC
+// columns, W floats per copy.  Chunk c = t + 256 k of the tile is column
+// c / (R/W), rows (c mod (R/W)) * W ..; with R/W a power of two each thread's
+// chunks advance by a fixed column step and (when R/W > 256) a fixed row
+// step, so the unrolled loop needs one pointer add per copy.
+template <int NC, int R, int W>
+__device__ __forceinline__ void p32n_issue(const float* __restrict__ A, int64_t lda, int64_t d, int n,
+                                           int64_t i0, float* buf) {
+  constexpr int CPC = R / W;               // chunks per column
+  constexpr int KT = NC * CPC / kP32Threads;  // chunks per thread
+  const int t = threadIdx.x;
+  if constexpr (CPC <= kP32Threads) {
+    constexpr int JS = kP32Threads / CPC;  // column step per chunk
+    const int r = (t % CPC) * W, j0 = t / CPC;
+    const int64_t i = i0 + r;
+    const int64_t left = d - i;
+    const int rbytes = left >= W ? 4 * W : (left > 0 ? (int)left * 4 : 0);
+    const float* src = A + i + (int64_t)j0 * lda;
+    const int64_t step = (int64_t)JS * lda;
+    float* dst = buf + j0 * R + r;
+    int j = j0;
+#pragma unroll 8
+    for (int k = 0; k < KT; ++k) {
+      const int bytes = j < n ? rbytes : 0;
+      if constexpr (W == 4) p32_cp16(dst, bytes > 0 ? src : A, bytes);
+      else if constexpr (W == 2) p32_cp8(dst, bytes > 0 ? src : A, bytes);
+      else p32_cp4(dst, bytes > 0 ? src : A, bytes > 0);
+      src += step;
+      dst += JS * R;
+      j += JS;
+    }
+  } else {
+    constexpr int RS = CPC / kP32Threads;  // chunks of one column per thread
+#pragma unroll
+    for (int k = 0; k < KT; ++k) {
+      const int j = k / RS, r = (t + kP32Threads * (k % RS)) * W;
+      const int64_t i = i0 + r;
+      const int64_t left = j < n ? d - i : 0;
+      const int bytes = left >= W ? 4 * W : (left > 0 ? (int)left * 4 : 0);
+      const float* s = bytes > 0 ? A + i + (int64_t)j * lda : A;
+      if constexpr (W == 4) p32_cp16(buf + j * R + r, s, bytes);
+      else if constexpr (W == 2) p32_cp8(buf + j * R + r, s, bytes);
+      else p32_cp4(buf + j * R + r, s, bytes > 0);
+    }
+  }
+  p32_commit();
+}
+
+// Exact binary32 -> binary64 widening on the integer units (GB300's FP64 pipe,
+// which a conversion instruction would occupy, is 1/64 of the FP32 rate):
+// sign, exponent rebiased by 1023 - 127 (255 -> 2047 for infinities and
+// NaNs), fraction shifted into place.  e == 0: zero keeps only its sign; a
+// subnormal m 2^-149 is renormalised (leading one of m at bit 31 - clz(m),
+// so the value is 1.f 2^(-118 - clz(m))).
+__device__ __forceinline__ double f2d_exact(float a) {
+  const unsigned u = __float_as_uint(a);
+  const unsigned sign = u & 0x80000000u;
+  const unsigned e = (u >> 23) & 0xffu;
+  const unsigned m = u & 0x007fffffu;
+  const unsigned ex = e == 255u ? 2047u : e + 896u;
+  unsigned hi = sign | (ex << 20) | (m >> 3);
+  unsigned lo = m << 29;
+  if (e == 0u) {
+    if (m == 0u) {
+      hi = sign;
+      lo = 0u;
+    } else {
+      const unsigned lz = (unsigned)__clz((int)m);  // 9 .. 31
+      const unsigned f = (m << (lz - 8u)) & 0x007fffffu;
+      hi = sign | ((905u - lz) << 20) | (f >> 3);
+      lo = f << 29;
+    }
+  }
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+template <bool RESID>
+__device__ __forceinline__ void pass32g_body(const float* __restrict__ A, int64_t lda, int64_t d, int n,
+                                             bool vec, const double* __restrict__ b,
+                                             const double* __restrict__ vin,
+                                             double* __restrict__ part, int cta, int nctas,
+                                             unsigned char* smem) {
+  constexpr int T = kP32Threads;
+  const int t = threadIdx.x;
+  const int R = pass32g_rows(n);
+  int lgR = 5;
+  while ((1 << lgR) < R) ++lgR;
+  const int tile_elems = R * n;
+  float* tiles = reinterpret_cast<float*>(smem);
+  double* vd = reinterpret_cast<double*>(tiles + 2 * (size_t)tile_elems);  // n
+  double* wp = vd + n;                                                     // T (dot partials)
+  float* wh = reinterpret_cast<float*>(wp + T);                            // R
+  float* wl = wh + R;                                                      // R
+  double* red = reinterpret_cast<double*>(wl + R);                         // T
+  float* ph = reinterpret_cast<float*>(vd);
+  float* pl = ph + n;
+  if (RESID) {
+    for (int j = t; j < n; j += T) vd[j] = vin[j];
+  } else {
+    // p = ph + pl (n <= 2T)
+    const double x0 = t < n ? vin[t] : 0.0, x1 = t + T < n ? vin[t + T] : 0.0;
+    if (t < n) {
+      const float h = __double2float_rn(x0);
+      ph[t] = h;
+      pl[t] = __double2float_rn(x0 - (double)h);
+    }
+    if (t + T < n) {
+      const float h = __double2float_rn(x1);
+      ph[t + T] = h;
+      pl[t + T] = __double2float_rn(x1 - (double)h);
+    }
+  }
+  // geometry
+  const int Q = R >= T ? 1 : T / R;   // threads per row in the dot phase
+  const int RT = R >= T ? R / T : 1;  // rows per thread in the dot phase
+  const int rq = R >= T ? t : (t & (R - 1));
+  const int q = R >= T ? 0 : t / R;
+  int G = 1;
+  while (2 * G * n <= T) G *= 2;  // column groups (G = 1 when n > T/2)
+  const int RG = R / G;
+  const int g = t & (G - 1);
+  const int jc = t / G;  // column of this thread (n <= T: one column; else t and t + T)
+
+  D2 acc0{0.f, 0.f}, acc1{0.f, 0.f};
+  double s1 = 0.0, s2 = 0.0;
+  const int64_t ntiles = (d + R - 1) / R;
+  int64_t tile = cta;
+  if (tile < ntiles) p32_issue(A, lda, d, n, n, R, lgR, vec, tile * R, tiles);
+  int buf = 0;
+  for (; tile < ntiles; tile += nctas, buf ^= 1) {
+    const int64_t next = tile + nctas;
+    __syncthreads();  // previous tile's readers are done with the other buffer and wh/wl
+    if (next < ntiles) {
+      p32_issue(A, lda, d, n, n, R, lgR, vec, next * R, tiles + (size_t)(buf ^ 1) * tile_elems);
+      p32_wait<1>();
+    } else {
+      p32_wait<0>();
+    }
+    __syncthreads();
+    const float* tl = tiles + (size_t)buf * tile_elems;
+    const int64_t i0 = tile * R;
+    // ---- dot phase
+    for (int m = 0; m < RT; ++m) {
+      const int r = rq + m * T;
+      if (RESID) {
+        double w = 0.0;
+        for (int j = q; j < n; j += Q) w = fma((double)tl[(size_t)j * R + r], vd[j], w);
+        if (Q == 1) {
+          const int64_t i = i0 + r;
+          float h = 0.f, l = 0.f;
+          if (i < d) {
+            const double bi = b[i];
+            const double ri = bi - w;
+            s1 = fma(ri, ri, s1);
+            s2 = fma(bi, bi, s2);
+            h = __double2float_rn(ri);
+            l = __double2float_rn(ri - (double)h);
+          }
+          wh[r] = h;
+          wl[r] = l;
+        } else {
+          wp[q * R + r] = w;
+        }
+      } else {
+        D2 w{0.f, 0.f};
+        for (int j = q; j < n; j += Q) d2_fma(w, tl[(size_t)j * R + r], ph[j], pl[j]);
+        if (Q == 1) {
+          const float h = __fadd_rn(w.s, w.c);
+          wh[r] = h;
+          wl[r] = __fsub_rn(w.c, __fsub_rn(h, w.s));
+        } else {
+          reinterpret_cast<float2*>(wp)[q * R + r] = make_float2(w.s, w.c);
+        }
+      }
+    }
+    if (Q > 1) {
+      __syncthreads();
+      if (t < R) {
+        const int64_t i = i0 + t;
+        if (RESID) {
+          double w = 0.0;
+          for (int qq = 0; qq < Q; ++qq) w += wp[qq * R + t];
+          float h = 0.f, l = 0.f;
+          if (i < d) {
+            const double bi = b[i];
+            const double ri = bi - w;
+            s1 = fma(ri, ri, s1);
+            s2 = fma(bi, bi, s2);
+            h = __double2float_rn(ri);
+            l = __double2float_rn(ri - (double)h);
+          }
+          wh[t] = h;
+          wl[t] = l;
+        } else {
+          const float2* w2 = reinterpret_cast<const float2*>(wp);
+          D2 w{w2[t].x, w2[t].y};
+          for (int qq = 1; qq < Q; ++qq) w = d2_merge(w, D2{w2[qq * R + t].x, w2[qq * R + t].y});
+          const float h = __fadd_rn(w.s, w.c);
+          wh[t] = h;
+          wl[t] = __fsub_rn(w.c, __fsub_rn(h, w.s));
+        }
+      }
+    }
+    __syncthreads();
+    // ---- column phase
+    if (jc < n) {
+      const float* col = tl + (size_t)jc * R;
+      for (int x = 0; x < RG; ++x) {
+        const int r = g + G * ((x + jc) & (RG - 1));
+        d2_fma(acc0, col[r], wh[r], wl[r]);
+      }
+    }
+    if (G == 1 && t + T < n) {
+      const int j = t + T;
+      const float* col = tl + (size_t)j * R;
+      for (int x = 0; x < R; ++x) {
+        const int r = (x + j) & (R - 1);
+        d2_fma(acc1, col[r], wh[r], wl[r]);
+      }
+    }
+  }
+  // ---- per-CTA partials
+  double* out = part + (int64_t)cta * (n + 2);
+  __syncthreads();
+  if (G > 1) {
+    red[t] = jc < n ? (double)acc0.s + (double)acc0.c : 0.0;
+    __syncthreads();
+    if (t < n) {
+      double s = 0.0;
+      for (int gg = 0; gg < G; ++gg) s += red[gg + G * t];
+      out[t] = s;
+    }
+  } else {
+    if (t < n) out[t] = (double)acc0.s + (double)acc0.c;
+    if (t + T < n) out[t + T] = (double)acc1.s + (double)acc1.c;
+  }
+  if (RESID) {
+    __shared__ double sred[2][T / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    if ((t & 31) == 0) {
+      sred[0][t >> 5] = s1;
+      sred[1][t >> 5] = s2;
+    }
+    __syncthreads();
+    if (t == 0) {
+      double a = 0.0, c = 0.0;
+      for (int w = 0; w < T / 32; ++w) {
+        a += sred[0][w];
+        c += sred[1][w];
+      }
+      out[n] = a;
+      out[n + 1] = c;
+    }
+  } else if (t == 0) {
+    out[n] = 0.0;
+    out[n + 1] = 0.0;
+  }
+}
+
+// Specialised body for NC = pass32_class(n) staged columns (n <= NC real).
+// Tile: R = 8192 / NC rows (RB = R / 32 row blocks of 32 rows).
+//   dot phase   : warp w takes row blocks rb0 .. rb0 + DR - 1 and the DC
+//                 columns of column group cg (M = 8 / min(RB, 8) groups share a
+//                 row block; their partials are merged through shared memory);
+//                 lane = row, so a warp reads 32 consecutive rows of a column.
+//   column phase: warp w owns columns w*CC .. w*CC + CC - 1 (CC = NC / 8), lane
+//                 = row within each of the RB row blocks; the CC compensated
+//                 accumulators stay in registers across tiles and are summed
+//                 over the 32 lanes by shuffles once per CTA.
+// Both phases touch 32 elements per thread per tile, fully unrolled with
+// compile-time shared-memory offsets.
+template <int NC, bool RESID>
+__device__ __forceinline__ void pass32n_body(const float* __restrict__ A, int64_t lda, int64_t d, int n,
+                                             int cw, const double* __restrict__ b,
+                                             const double* __restrict__ vin,
+                                             double* __restrict__ part, int cta, int nctas,
+                                             unsigned char* smem) {
+  constexpr int T = kP32Threads;
+  constexpr int R = kP32TileElems / NC, RB = R / 32;
+  constexpr int DR = RB >= 8 ? RB / 8 : 1;   // dot rows per thread
+  constexpr int M = RB >= 8 ? 1 : 8 / RB;    // dot column groups per row block
+  constexpr int DC = NC / M;                 // dot columns per thread
+  constexpr int CC = NC / 8;                 // column-phase columns per thread
+  constexpr int WPB = 8 / M;                 // warps per column group
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  float* tiles = reinterpret_cast<float*>(smem);
+  double* vd = reinterpret_cast<double*>(tiles + 2 * kP32TileElems);  // NC: x (RESID) or (ph, pl)
+  auto issue = [&](int64_t i0, float* buf) {
+    if (cw == 4) p32n_issue<NC, R, 4>(A, lda, d, n, i0, buf);
+    else if (cw == 2) p32n_issue<NC, R, 2>(A, lda, d, n, i0, buf);
+    else p32n_issue<NC, R, 1>(A, lda, d, n, i0, buf);
+  };
+  // vector region (16 NC bytes): x as FP64 (RESID), or for column pairs
+  // (2h, 2h+1) pvx[h] = (xh0, xh1, -xh0, -xh1) and pvl[h] = (xl0, xl1)
+  float4* pvx = reinterpret_cast<float4*>(vd);
+  float2* pvl = reinterpret_cast<float2*>(pvx + NC / 2);
+  double* wpd = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(vd) + 16 * NC);  // T
+  float2* wv = reinterpret_cast<float2*>(wpd + T);                    // R: (hi, lo) per row
+  float2* wpf = reinterpret_cast<float2*>(wpd);
+  if (RESID) {
+    for (int j = t; j < NC; j += T) vd[j] = j < n ? vin[j] : 0.0;
+  } else {
+    for (int h = t; h < NC / 2; h += T) {
+      const double x0 = 2 * h < n ? vin[2 * h] : 0.0, x1 = 2 * h + 1 < n ? vin[2 * h + 1] : 0.0;
+      const float h0 = __double2float_rn(x0), h1 = __double2float_rn(x1);
+      pvx[h] = make_float4(h0, h1, -h0, -h1);
+      pvl[h] = make_float2(__double2float_rn(x0 - (double)h0), __double2float_rn(x1 - (double)h1));
+    }
+  }
+  const int rb0 = (w % WPB) * DR, cg = w / WPB;
+  D2P acc[CC / 2];  // columns (2c, 2c + 1) of this warp's column block
+#pragma unroll
+  for (int c = 0; c < CC / 2; ++c) acc[c] = D2P{0ull, 0ull};
+  double s1 = 0.0, s2 = 0.0;
+  const int64_t ntiles = (d + R - 1) / R;
+  int64_t tile = cta;
+  if (tile < ntiles) issue(tile * R, tiles);
+  int buf = 0;
+  for (; tile < ntiles; tile += nctas, buf ^= 1) {
+    const int64_t next = tile + nctas;
+    __syncthreads();  // the other buffer and wv are free again
+    if (next < ntiles) {
+      issue(next * R, tiles + (buf ^ 1) * kP32TileElems);
+      p32_wait<1>();
+    } else {
+      p32_wait<0>();
+    }
+    __syncthreads();
+    const float* tl = tiles + buf * kP32TileElems;
+    const int64_t i0 = tile * R;
+    // ---- dot phase
+    const float* tdot = tl + cg * DC * R + rb0 * 32 + lane;
+    if (RESID) {
+      // four independent DFMA chains per row (FP64 latency), summed in order
+      constexpr int KS = DC >= 4 ? 4 : DC;
+      double wd[DR], wk[DR][KS];
+#pragma unroll
+      for (int m = 0; m < DR; ++m)
+#pragma unroll
+        for (int q = 0; q < KS; ++q) wk[m][q] = 0.0;
+#pragma unroll
+      for (int jj = 0; jj < DC; ++jj) {
+        const double xj = vd[cg * DC + jj];
+#pragma unroll
+        for (int m = 0; m < DR; ++m)
+          wk[m][jj % KS] = fma(f2d_exact(tdot[jj * R + m * 32]), xj, wk[m][jj % KS]);
+      }
+#pragma unroll
+      for (int m = 0; m < DR; ++m) {
+        wd[m] = wk[m][0];
+#pragma unroll
+        for (int q = 1; q < KS; ++q) wd[m] += wk[m][q];
+      }
+      if (M == 1) {
+#pragma unroll
+        for (int m = 0; m < DR; ++m) {
+          const int r = (rb0 + m) * 32 + lane;
+          const int64_t i = i0 + r;
+          float h = 0.f, l = 0.f;
+          if (i < d) {
+            const double bi = b[i];
+            const double ri = bi - wd[m];
+            s1 = fma(ri, ri, s1);
+            s2 = fma(bi, bi, s2);
+            h = __double2float_rn(ri);
+            l = __double2float_rn(ri - (double)h);
+          }
+          wv[r] = make_float2(h, l);
+        }
+      } else {
+        wpd[cg * R + rb0 * 32 + lane] = wd[0];
+      }
+    } else {
+      // column pairs (jj, jj + 1): lane 0 sums the even columns, lane 1 the odd
+      D2P wq[DR];
+#pragma unroll
+      for (int m = 0; m < DR; ++m) wq[m] = D2P{0ull, 0ull};
+#pragma unroll
+      for (int jj = 0; jj < DC; jj += 2) {
+        const float4 xv = pvx[(cg * DC + jj) / 2];
+        const float2 xl = pvl[(cg * DC + jj) / 2];
+        const f2p xh = f2p_make(xv.x, xv.y), nxh = f2p_make(xv.z, xv.w), xlp = f2p_make(xl.x, xl.y);
+#pragma unroll
+        for (int m = 0; m < DR; ++m)
+          d2p_fma(wq[m], f2p_make(tdot[jj * R + m * 32], tdot[(jj + 1) * R + m * 32]), xh, nxh, xlp);
+      }
+      D2 wd[DR];
+#pragma unroll
+      for (int m = 0; m < DR; ++m) {
+        D2 e, o;
+        d2p_lanes(wq[m], e, o);
+        wd[m] = d2_merge(e, o);
+      }
+      if (M == 1) {
+#pragma unroll
+        for (int m = 0; m < DR; ++m) {
+          const float h = __fadd_rn(wd[m].s, wd[m].c);
+          wv[(rb0 + m) * 32 + lane] = make_float2(h, __fsub_rn(wd[m].c, __fsub_rn(h, wd[m].s)));
+        }
+      } else {
+        wpf[cg * R + rb0 * 32 + lane] = make_float2(wd[0].s, wd[0].c);
+      }
+    }
+    if (M > 1) {
+      __syncthreads();
+      if (t < R) {
+        if (RESID) {
+          double wsum = 0.0;
+#pragma unroll
+          for (int q = 0; q < M; ++q) wsum += wpd[q * R + t];
+          const int64_t i = i0 + t;
+          float h = 0.f, l = 0.f;
+          if (i < d) {
+            const double bi = b[i];
+            const double ri = bi - wsum;
+            s1 = fma(ri, ri, s1);
+            s2 = fma(bi, bi, s2);
+            h = __double2float_rn(ri);
+            l = __double2float_rn(ri - (double)h);
+          }
+          wv[t] = make_float2(h, l);
+        } else {
+          D2 a{wpf[t].x, wpf[t].y};
+#pragma unroll
+          for (int q = 1; q < M; ++q) a = d2_merge(a, D2{wpf[q * R + t].x, wpf[q * R + t].y});
+          const float h = __fadd_rn(a.s, a.c);
+          wv[t] = make_float2(h, __fsub_rn(a.c, __fsub_rn(h, a.s)));
+        }
+      }
+    }
+    __syncthreads();
+    // ---- column phase
+    {
+      const float* tcol = tl + w * CC * R + lane;
+#pragma unroll
+      for (int m = 0; m < RB; ++m) {
+        const float2 wm = wv[m * 32 + lane];
+        const f2p wh = f2p_make(wm.x, wm.x), nwh = f2p_make(-wm.x, -wm.x), wl = f2p_make(wm.y, wm.y);
+#pragma unroll
+        for (int c = 0; c < CC / 2; ++c)
+          d2p_fma(acc[c], f2p_make(tcol[2 * c * R + m * 32], tcol[(2 * c + 1) * R + m * 32]), wh, nwh, wl);
+      }
+    }
+  }
+  // ---- per-CTA partials: sum each column's accumulator over the 32 lanes
+  double* out = part + (int64_t)cta * (n + 2);
+#pragma unroll
+  for (int c = 0; c < CC; ++c) {
+    D2 lo, hi;
+    d2p_lanes(acc[c / 2], lo, hi);
+    D2 a = (c & 1) ? hi : lo;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+      a = d2_merge(a, D2{__shfl_xor_sync(0xffffffffu, a.s, o), __shfl_xor_sync(0xffffffffu, a.c, o)});
+    const int j = w * CC + c;
+    if (lane == 0 && j < n) out[j] = (double)a.s + (double)a.c;
+  }
+  if (RESID) {
+    __shared__ double sred[2][T / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    if (lane == 0) {
+      sred[0][w] = s1;
+      sred[1][w] = s2;
+    }
+    __syncthreads();
+    if (t == 0) {
+      double a = 0.0, c = 0.0;
+      for (int q = 0; q < T / 32; ++q) {
+        a += sred[0][q];
+        c += sred[1][q];
+      }
+      out[n] = a;
+      out[n + 1] = c;
+    }
+  } else if (t == 0) {
+    out[n] = 0.0;
+    out[n + 1] = 0.0;
+  }
+}
+
+// CTAs per SM of each body (the shared-memory pipeline allows three; the
+// 256-wide body's 32 column accumulators per thread need 128 registers).
+__host__ __device__ constexpr int pass32_ctas_per_sm(int nc) { return nc >= 256 ? 2 : 3; }
+
+// Kernel wrappers (one per width class, each compiled for its own occupancy)
+// live in the translation units that launch them.
+}  // namespace msk

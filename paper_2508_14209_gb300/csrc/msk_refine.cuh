@@ -10,8 +10,8 @@
 namespace msk {
 
 // ---------------------------------------------------------------------------
-// Row-tiled FP64 passes over A (tiles of kPR rows, whole rows in shared memory,
-// stored in A's own type — FP32 A is exact in binary32 — and widened on use).
+// Row-tiled FP64 passes over an FP64 A (tiles of kPR rows, whole rows in
+// shared memory).  Passes over an FP32 A are in msk_pass.cuh.
 //   RESID = true : r_i = b_i - A_i x; accumulates g = A^T r, ||r||^2, ||b||^2.
 //   RESID = false: w_i = A_i p;       accumulates v = A^T w, ||w||^2.
 // Dot phase: 4 threads per row (columns q, q+4, ...), combined by shuffles;
@@ -133,90 +133,6 @@ __device__ __forceinline__ void pass_reduce_body(const double* __restrict__ part
 }
 
 // ---------------------------------------------------------------------------
-// Double-single pass for FP32 A (see the comment above the launcher).
-// Tile: kPR rows x pitch floats, pitch = 4 (mod 32) so that 16-byte stores of
-// 4 columns (lane = row) and the row reads of the dot phase are conflict-free.
-__device__ __forceinline__ void pass_ds_body(const float* __restrict__ A, int64_t lda, int64_t d,
-                                             int n, int pitch, const double* __restrict__ vin,
-                                             double* __restrict__ part, int cta, int nctas,
-                                             unsigned char* ds_smem) {
-  float* tile = reinterpret_cast<float*>(ds_smem);  // kPR x pitch
-  float* ph = tile + kPR * pitch;                   // n: p hi
-  float* pl = ph + n;                               // n: p lo
-  float* wh = pl + n;                               // kPR: w hi
-  float* wl = wh + kPR;                             // kPR: w lo
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int j = threadIdx.x; j < n; j += kPThreads) {
-    const double x = vin[j];
-    const float h = (float)x;
-    ph[j] = h;
-    pl[j] = (float)(x - (double)h);
-  }
-  DS acc[2] = {{0.f, 0.f}, {0.f, 0.f}};
-  const int ngroups = (n + 3) >> 2;
-  const int64_t ntiles = (d + kPR - 1) / kPR;
-  for (int64_t t = cta; t < ntiles; t += nctas) {
-    const int64_t i0 = t * kPR;
-    __syncthreads();
-    // load: lane = row (two row halves), warp w takes 4-column groups w, w+8, ...
-    for (int g = warp; g < ngroups; g += kPThreads / 32) {
-#pragma unroll
-      for (int h = 0; h < kPR / 32; ++h) {
-        const int r = lane + 32 * h;
-        const int64_t i = i0 + r;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (i < d) {
-          const int j = 4 * g;
-          v.x = __ldcs(A + i + (int64_t)j * lda);
-          if (j + 1 < n) v.y = __ldcs(A + i + (int64_t)(j + 1) * lda);
-          if (j + 2 < n) v.z = __ldcs(A + i + (int64_t)(j + 2) * lda);
-          if (j + 3 < n) v.w = __ldcs(A + i + (int64_t)(j + 3) * lda);
-        }
-        *reinterpret_cast<float4*>(&tile[r * pitch + 4 * g]) = v;
-      }
-    }
-    __syncthreads();
-    // dot phase: 4 threads per row, thread q takes columns q, q+4, ...
-    {
-      const int r = threadIdx.x >> 2, q = threadIdx.x & 3;
-      const float* row = tile + r * pitch;
-      DS w{0.f, 0.f};
-      for (int j = q; j < n; j += 4) w = ds_fma(w, row[j], ph[j], pl[j]);
-      DS o = ds_shfl_xor(w, 1);
-      w = ds_add(w, o.hi, o.lo);
-      o = ds_shfl_xor(w, 2);
-      w = ds_add(w, o.hi, o.lo);
-      if (q == 0) {
-        const bool ok = i0 + r < d;
-        wh[r] = ok ? w.hi : 0.f;
-        wl[r] = ok ? w.lo : 0.f;
-      }
-    }
-    __syncthreads();
-    // column phase: v_j += sum_r A[r][j] w_r
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      const int j = threadIdx.x + c * kPThreads;
-      if (j < n) {
-        DS a = acc[c];
-        for (int r = 0; r < kPR; ++r) a = ds_fma(a, tile[r * pitch + j], wh[r], wl[r]);
-        acc[c] = a;
-      }
-    }
-  }
-  double* out = part + (int64_t)cta * (n + 2);
-#pragma unroll
-  for (int c = 0; c < 2; ++c) {
-    const int j = threadIdx.x + c * kPThreads;
-    if (j < n) out[j] = (double)acc[c].hi + (double)acc[c].lo;
-  }
-  if (threadIdx.x == 0) {
-    out[n] = 0.0;
-    out[n + 1] = 0.0;
-  }
-}
-
-// ---------------------------------------------------------------------------
 // Small FP64 vector kernels of the refinement (single CTA; n <= 512).
 
 // Explicit inverse of the upper-triangular R (n x n, ldr) into Ri (n x n,
@@ -250,21 +166,37 @@ struct RefState {
   double *x, *dlt, *p, *res, *z, *sc;
 };
 
-// z = Ri (Ri^T v): the preconditioner M^{-1} v with M = R^T R.
-__device__ __forceinline__ void apply_minv(const double* __restrict__ Ri, int n, const double* v, double* tmp,
-                           double* z) {
-  // tmp = Ri^T v  (tmp[j] = sum_{i<=j} Ri[i][j] v[i])
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+// z = Ri (Ri^T v): the preconditioner M^{-1} v with M = R^T R (one CTA).
+//   tmp = Ri^T v : warp w takes columns w, w + nwarps, ...; its lanes read the
+//                  column contiguously and are summed by shuffles;
+//   z = Ri tmp   : G = blockDim / n thread groups split the sum over j
+//                  (j = i + g, i + g + G, ...); reads of Ri[i + j n] are
+//                  contiguous across the threads of a group; partial sums are
+//                  added in group order.
+// scratch: at least max(n, blockDim) + n doubles of shared memory.
+__device__ __forceinline__ void apply_minv(const double* __restrict__ Ri, int n, const double* v,
+                                           double* tmp, double* z, double* scratch) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = warp; j < n; j += nw) {
     const double* col = Ri + (int64_t)j * n;
     double s = 0.0;
-    for (int i = 0; i <= j; ++i) s += col[i] * v[i];
-    tmp[j] = s;
+    for (int i = lane; i <= j; i += 32) s += col[i] * v[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) tmp[j] = s;
   }
   __syncthreads();
-  // z = Ri tmp  (z[i] = sum_{j>=i} Ri[i][j] tmp[j])
+  const int G = (int)blockDim.x >= 2 * n ? (int)blockDim.x / n : 1;
+  for (int idx = threadIdx.x; idx < n * G; idx += blockDim.x) {
+    const int i = idx % n, g = idx / n;
+    double s = 0.0;
+    for (int j = i + g; j < n; j += G) s += Ri[i + (int64_t)j * n] * tmp[j];
+    scratch[idx] = s;
+  }
+  __syncthreads();
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     double s = 0.0;
-    for (int j = i; j < n; ++j) s += Ri[i + (int64_t)j * n] * tmp[j];
+    for (int g = 0; g < G; ++g) s += scratch[g * n + i];
     z[i] = s;
   }
   __syncthreads();
@@ -275,13 +207,14 @@ __device__ __forceinline__ void apply_minv(const double* __restrict__ Ri, int n,
 __device__ __forceinline__ void pcg_start_body(const double* __restrict__ Ri, int n,
                                                const double* __restrict__ g, RefState s) {
   __shared__ double tmp[512];
+  __shared__ double scr[1024];
   __shared__ double red[32];
   for (int j = threadIdx.x; j < n; j += blockDim.x) {
     s.res[j] = g[j];
     s.dlt[j] = 0.0;
   }
   __syncthreads();
-  apply_minv(Ri, n, s.res, tmp, s.z);
+  apply_minv(Ri, n, s.res, tmp, s.z, scr);
   double part = 0.0;
   for (int j = threadIdx.x; j < n; j += blockDim.x) {
     s.p[j] = s.z[j];
@@ -304,6 +237,7 @@ __device__ __forceinline__ void pcg_start_body(const double* __restrict__ Ri, in
 __device__ __forceinline__ void pcg_update_body(const double* __restrict__ Ri, int n,
                                                 const double* __restrict__ pv, RefState s) {
   __shared__ double tmp[512];
+  __shared__ double scr[1024];
   __shared__ double red[32];
   __shared__ double alpha_s, beta_s;
   // p.v from the vector itself (more accurate than ||A p||^2 in FP32)
@@ -325,7 +259,7 @@ __device__ __forceinline__ void pcg_update_body(const double* __restrict__ Ri, i
     s.res[j] -= alpha * pv[j];
   }
   __syncthreads();
-  apply_minv(Ri, n, s.res, tmp, s.z);
+  apply_minv(Ri, n, s.res, tmp, s.z, scr);
   part = 0.0;
   for (int j = threadIdx.x; j < n; j += blockDim.x) part += s.res[j] * s.z[j];
 #pragma unroll
@@ -345,7 +279,38 @@ __device__ __forceinline__ void pcg_update_body(const double* __restrict__ Ri, i
   for (int j = threadIdx.x; j < n; j += blockDim.x) s.p[j] = s.z[j] + beta * s.p[j];
 }
 
+// Refinement scalars (sc, FP64):
+//   [0] rho = res.z            [1] gain of the last step (alpha rho)
+//   [2] active (1 while the inner solve runs)
+//   [3] floor: a step gaining no more than this ends the inner solve
+//   [4] inner steps taken      [5] 1 if the very first step was below the floor
+//   [6] sum of the gains       [7] 1 if the solve ended by the gain rule
+//                                  (rather than by the step limit)
+constexpr int kScCount = 8;
 
-// Inner CG per outer (FP64 residual) step: at most kMaxInner iterations; the
-// gain-based stopping rule (kDecFrac) is in ms_lstsq.
+// Start-of-solve bookkeeping (thread 0, after pcg_start_body).
+__device__ __forceinline__ void pcg_arm(double* sc, double floor) {
+  sc[1] = 0.0;
+  sc[2] = 1.0;
+  sc[3] = floor;
+  sc[4] = 0.0;
+  sc[5] = 0.0;
+  sc[6] = 0.0;
+  sc[7] = 0.0;
+}
+
+// Stopping rule after a CG step (thread 0, after pcg_update_body): returns
+// true when this step ended the inner solve.
+__device__ __forceinline__ bool pcg_stop_check(double* sc, int max_steps) {
+  sc[4] += 1.0;
+  sc[6] += sc[1];
+  const bool by_rule = !(sc[1] > sc[3]) || !(sc[0] > 0.0);
+  if (by_rule || sc[4] >= (double)max_steps) {
+    if (by_rule && sc[4] == 1.0) sc[5] = 1.0;
+    sc[7] = by_rule ? 1.0 : 0.0;
+    sc[2] = 0.0;
+    return true;
+  }
+  return false;
+}
 }  // namespace msk

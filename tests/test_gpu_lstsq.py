@@ -94,12 +94,21 @@ def test_sns_exact_recovery(msk):
     assert torch.allclose(x.cpu(), xt, rtol=1e-10, atol=0)
 
 
-@pytest.mark.parametrize("d,n,lsig,prec", [(1 << 15, 16, -4, "f32"), (1 << 15, 32, -8, "f32"),
-                                           (40000, 64, -6, "f32")])
-def test_refined_mixed_reaches_minimiser(msk, orc, d, n, lsig, prec):
+# Cases also cover the refinement passes' edges: one partial row tile (d below
+# the tile height), d not a multiple of 4, odd leading dimensions (4-byte
+# copies instead of 16-byte ones), n not a power of two, and n = 400 (two
+# columns per thread in the column phase).
+@pytest.mark.parametrize("d,n,lsig,prec,lda_pad,k", [
+    (1 << 15, 16, -4, "f32", 0, None), (1 << 15, 32, -8, "f32", 0, None),
+    (40000, 64, -6, "f32", 0, None), (500, 16, -5, "f32", 0, None),
+    (40003, 100, -7, "bf16x3", 3, None), (30001, 48, -8, "f32", 1, None),
+    (6001, 400, -3, "f32", 0, 4000)])
+def test_refined_mixed_reaches_minimiser(msk, orc, d, n, lsig, prec, lda_pad, k):
     A, b = _problem(d, n, lsig, 300 + n, torch.float32)
-    k, p, seed = 2 * n * n, 4 * n, 0x5EED0004
-    x, info, rc = msk.ms_lstsq(dev_colmajor(A, msk), b.cuda(), k, p, seed, msk.GEMM_PRECS[prec],
+    k, p, seed = k or 2 * n * n, 4 * n, 0x5EED0004
+    Ad = msk.colmajor(d, n, torch.float32, "cuda", lda=d + lda_pad)
+    Ad.copy_(A)
+    x, info, rc = msk.ms_lstsq(Ad, b.cuda(), k, p, seed, msk.GEMM_PRECS[prec],
                                refine=True, tol=1e-12, max_iter=20)
     assert rc == 0, info
     An, bn = A.numpy(), b.numpy()
@@ -110,6 +119,31 @@ def test_refined_mixed_reaches_minimiser(msk, orc, d, n, lsig, prec):
     _, r_sns64, _ = orc.sns_lstsq(An.astype(np.float64), bn, k, p, seed, "f64")
     assert rg <= (1 + 1e-8) * r_sns64                     # never worse than FP64 sketch-and-solve
     assert info["iters"] >= 1 and info["converged"] == 1
+
+
+@pytest.mark.parametrize("n", [8, 100])
+def test_residual_pass_exact_with_subnormal_and_zero_entries(msk, orc, n):
+    """The FP64 residual pass widens FP32 entries to FP64 exactly: a column of
+    subnormal entries (integers below 2^20 times 2^-149) carrying a solution
+    component of 2^130 contributes O(1) to b, so a flushed or misconverted
+    subnormal would change the residual the pass reports; zero entries ride
+    along."""
+    d = 4099
+    A, _ = _problem(d, n, -2, 77 + n, torch.float32)
+    g = torch.Generator().manual_seed(5)
+    A[:, 0] = torch.randint(-2**20, 2**20, (d,), generator=g).to(torch.float32) * 2.0**-149
+    A[::3, 1] = 0.0
+    assert (A[:, 0].abs() < torch.finfo(torch.float32).tiny).float().mean() > 0.9
+    xt = torch.ones(n, dtype=torch.float64)
+    xt[0] = 2.0**130
+    An = A.numpy().astype(np.float64)
+    b = torch.tensor(An @ xt.numpy()) + 1e-3 * torch.randn(d, generator=g, dtype=torch.float64)
+    Ad = msk.colmajor(d, n, torch.float32, "cuda", lda=d)
+    Ad.copy_(A)
+    x, info, rc = msk.ms_lstsq(Ad, b.cuda(), 2 * n * n, 4 * n, 11, msk.GEMM_F64)
+    assert rc == 0
+    r_orc = orc.relres(An, b.numpy(), x.cpu().numpy())
+    assert abs(info["relres"] - r_orc) <= 1e-10 * r_orc
 
 
 def test_ne_matches_oracle_and_breaks_down(msk, orc):
