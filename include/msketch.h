@@ -116,10 +116,17 @@ const char *msk_last_error(void);
 
 /* ---- Tuning registry (set by the autotuner, read by the launchers) ------- */
 
-/* Named integer knobs, e.g. "cs.f64.variant" (0 = warp reductions,
- * 1 = TMA bulk reductions per row), "tc.kt_per" (K tiles per CTA of the
- * tensor-core GEMM).  Unset knobs mean "launcher default".  Process-wide and
- * thread-safe; they change speed only, never results beyond rounding order.
+/* Named integer knobs that the launchers read (unset = launcher default):
+ *   "cs.fixed"            1 = fixed-width CountSketch kernels (default), 0 = generic
+ *   "cs.l2_budget_bytes"  bytes of Y a CountSketch column chunk keeps in L2
+ *                         (default 2/5 of L2)
+ *   "cs.f64.variant"      1 = FP64 CountSketch by TMA bulk reductions per row
+ *   "tc.drain"            0 = split-BF16 GEMM without draining accumulators
+ *   "batch.kt_per"        K tiles per CTA of the batched tensor-core GEMM (16)
+ *   "batch.round"         CG iterations per captured graph round (4)
+ *   "pass.ctas_per_sm"    refinement-pass CTAs per SM (3, at most 3)
+ * Process-wide and thread-safe; they change speed only, never results beyond
+ * rounding order.  msk_autotune (below) sets them from measurements.
  * msk_tune_set returns -1 for an empty name; msk_tune_clear(NULL) clears all. */
 int msk_tune_set(const char *name, long long value);
 long long msk_tune_get(const char *name, long long dflt);
@@ -315,6 +322,30 @@ size_t msk_batch_workspace(const msk_batch_item *items, int nitems, int refine);
 int msk_batch_lstsq(const msk_batch_item *items, int nitems, int refine,
                     double tol, int32_t max_iter, msk_lstsq_info *infos,
                     void *ws, size_t ws_bytes, void *stream);
+
+/* ---- Autotuner ----------------------------------------------------------- */
+
+/* Scratch bytes msk_autotune needs for these items (the batch workspace at
+ * its largest over the tuned split-K settings, plus a CountSketch output). */
+size_t msk_autotune_workspace(const msk_batch_item *items, int nitems, int refine);
+
+/* Time candidate values of the knobs "cs.fixed", "cs.l2_budget_bytes" (on
+ * cs_sketch of the request with the most elements), "batch.kt_per",
+ * "batch.round" and "pass.ctas_per_sm" (on msk_batch_lstsq of the whole
+ * batch with refine, tol, max_iter), one knob at a time in that order, each
+ * candidate as the median of `reps` runs (1..100) after a warm-up run, timed
+ * with CUDA events on `stream`; leave the fastest value of each knob set in
+ * the registry.  The paper has no counterpart (it tunes nothing).
+ *   report: host buffer of report_bytes (may be NULL) receiving a JSON object
+ *     {"knobs": {name: {"chosen": v, "timed_on": ..., "ms": {value: ms}}},
+ *      "reps": r, "requests": nitems}, truncated to fit.
+ *   ws: device scratch (256-byte aligned) of msk_autotune_workspace bytes.
+ * Synchronous.  Errors: -1 items NULL, -2 nitems < 1, -3 refine not 0/1,
+ * -6 reps out of range, MSK_ENOMEM scratch too small, MSK_ECUDA a timed run
+ * failed (the knob being tuned is restored; earlier choices stay set). */
+int msk_autotune(const msk_batch_item *items, int nitems, int refine, double tol,
+                 int32_t max_iter, int reps, char *report, size_t report_bytes,
+                 void *ws, size_t ws_bytes, void *stream);
 
 /* ---- Request server (continuous batching) -------------------------------- */
 

@@ -37,7 +37,7 @@ EXPORTS = ("msk_version", "msk_last_error", "cs_hash", "ms_gaussian", "msk_cs_wo
            "msk_ne_workspace", "ne_lstsq", "msk_gemm_noalloc", "msk_tune_set", "msk_tune_get",
            "msk_tune_clear", "msk_batch_workspace", "msk_batch_lstsq", "ms_server_create",
            "ms_server_submit", "ms_server_poll", "ms_server_wait_all", "ms_server_stats",
-           "ms_server_destroy", "ms_server_error")
+           "ms_server_destroy", "ms_server_error", "msk_autotune_workspace", "msk_autotune")
 
 NOALLOC_SCRATCH_BYTES = 24 << 20
 
@@ -114,6 +114,9 @@ def _declare(L):
         "ms_server_error": (ctypes.c_char_p, [_p]),
         "msk_batch_lstsq": (_int, [ctypes.POINTER(BatchItem), _int, _int, _dbl, _i32,
                                    ctypes.POINTER(LstsqInfo), _p, _sz, _p]),
+        "msk_autotune_workspace": (_sz, [ctypes.POINTER(BatchItem), _int, _int]),
+        "msk_autotune": (_int, [ctypes.POINTER(BatchItem), _int, _int, _dbl, _i32, _int, ctypes.c_char_p,
+                                _sz, _p, _sz, _p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -384,6 +387,22 @@ def msk_batch_lstsq(problems, refine=True, tol=1e-10, max_iter=10, ws=None, stre
     out = [{"iters": i.iters, "converged": i.converged, "relres": i.relres,
             "relres_sns": i.relres_sns} for i in infos]
     return xs, out, rc
+
+
+def msk_autotune(problems, refine=True, tol=1e-6, max_iter=4, reps=3, stream=None):
+    """Time the registry knobs on the batch [(A, b, seed), ...] and leave the
+    fastest values set (msk_autotune); returns the report as a dict."""
+    import json
+
+    dev = problems[0][0].device
+    xs = [torch.empty(A.shape[1], dtype=torch.float64, device=dev) for A, _, _ in problems]
+    arr = _batch_items(problems, xs)
+    ws = workspace(load().msk_autotune_workspace(arr, len(problems), int(refine)), dev)
+    buf = ctypes.create_string_buffer(1 << 16)
+    rc = load().msk_autotune(arr, len(problems), int(refine), tol, max_iter, reps, buf, len(buf), _ptr(ws),
+                             ws.numel(), _stream(stream))
+    _check("msk_autotune", rc)
+    return json.loads(buf.value.decode())
 
 
 class Server:

@@ -14,7 +14,8 @@
 //                 memory);
 //   QR + solve    one launch, one thread-block cluster per problem;
 //   refinement    FP64 residual pass, reduction and CG start: one launch each;
-//                 the inner CG rounds (pass, reduction, update) x kRound are
+//                 the inner CG rounds (pass, reduction, update) x kRound (knob
+//                 "batch.round") are
 //                 captured once into a CUDA graph and replayed until every
 //                 problem has met its stopping rule.
 // Problems that stop early are skipped by the later launches (device flags).
@@ -35,7 +36,7 @@
 
 namespace msk {
 
-constexpr int kBatchKtPer = 16;   // K tiles per CTA of the batched GEMM
+constexpr int kBatchKtPer = 16;   // K tiles per CTA of the batched GEMM (knob "batch.kt_per")
 constexpr int kRound = 4;         // CG iterations per captured graph round
 constexpr int kBatchMaxInner = 200;
 constexpr double kBatchDecFrac = 0.05;
@@ -298,6 +299,7 @@ static void plan_batch(const msk_batch_item* items, int nitems, int refine, char
   P->jobs.resize(nitems);
   P->tc.resize(nitems);
   P->shapes.resize(nitems);
+  const int kt_per = (int)std::min<long long>(64, std::max<long long>(1, tune_get("batch.kt_per", kBatchKtPer)));
   for (int j = 0; j < nitems; ++j) {
     const msk_batch_item& it = items[j];
     BatchJob& J = P->jobs[j];
@@ -313,7 +315,7 @@ static void plan_batch(const msk_batch_item* items, int nitems, int refine, char
     J.gkey = stream_key(it.seed, kTagGauss);
     J.ldy = (J.ncol + 3) / 4 * 4;
     TcShape& sh = P->shapes[j];
-    tc_ds_shape(J.p, J.k, J.ncol, kBatchKtPer, &sh);
+    tc_ds_shape(J.p, J.k, J.ncol, kt_per, &sh);
     J.kpitch = sh.kpitch;
     J.npad = sh.npad;
     J.S = sh.S;
@@ -346,7 +348,9 @@ static void plan_batch(const msk_batch_item* items, int nitems, int refine, char
         total_tiles += (P->jobs[j].d + pass32_rows(nc) - 1) / pass32_rows(nc);
       }
     if (mem.empty()) continue;
-    const int64_t cap = (int64_t)pass32_ctas_per_sm(nc) * num_sms();
+    const int64_t per_sm = std::min<long long>(pass32_ctas_per_sm(nc),
+                                               std::max<long long>(1, tune_get("pass.ctas_per_sm", 3)));
+    const int64_t cap = per_sm * num_sms();
     int begin = 0;
     for (int j : mem) {
       BatchJob& J = P->jobs[j];
@@ -548,7 +552,7 @@ int msk_batch_lstsq(const msk_batch_item* items, int nitems, int refine, double 
   if (refine) {
     batch_tri_inverse_kernel<<<dim3((P.max_n + 7) / 8, nitems), 256, 0, st>>>(jobs_dev);
     MSK_CHECK_LAUNCH("batch_tri_inverse_kernel");
-    // one captured round: kRound CG iterations over all problems
+    // one captured round: `round` CG iterations over all problems
     // Capture records work without running it, on a private stream (the
     // legacy default stream cannot be captured); the graph is then launched on
     // the caller's stream, in order with everything above.
@@ -557,7 +561,8 @@ int msk_batch_lstsq(const msk_batch_item* items, int nitems, int refine, double 
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     MSK_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-    for (int r = 0; r < kRound; ++r) {
+    const int round_len = (int)std::min<long long>(16, std::max<long long>(1, tune_get("batch.round", kRound)));
+    for (int r = 0; r < round_len; ++r) {
       passes(false, nullptr, cap);
       batch_pass_reduce_kernel<true><<<rgrid, 256, 0, cap>>>(jobs_dev, nullptr);
       batch_pcg_update_kernel<<<nitems, 512, 0, cap>>>(jobs_dev, active, refining);
@@ -585,7 +590,7 @@ int msk_batch_lstsq(const msk_batch_item* items, int nitems, int refine, double 
       batch_arm_kernel<<<gblocks, 256, 0, st>>>(jobs_dev, nitems, refining, active);
       batch_pcg_start_kernel<<<nitems, 512, 0, st>>>(jobs_dev, tol, active);
       int hact = nref;
-      for (int round = 0; round * kRound < kBatchMaxInner && hact > 0; ++round) {
+      for (int round = 0; round * round_len < kBatchMaxInner && hact > 0; ++round) {
         ce = cudaGraphLaunch(exec, st);
         if (ce == cudaSuccess) ce = cudaMemcpyAsync(&hact, active, sizeof(int), cudaMemcpyDeviceToHost, st);
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);

@@ -227,7 +227,7 @@ static int launch_pass32_nc(const float* A, int64_t lda, int64_t d, int n, const
   MSK_ALLOW_SMEM(kern);
   int per_sm = 0;
   MSK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kP32Threads, smem));
-  per_sm = std::max(1, std::min(per_sm, kPassCtasPerSm));
+  per_sm = std::max(1, std::min<int>(per_sm, (int)std::min<long long>(kPassCtasPerSm, tune_get("pass.ctas_per_sm", kPassCtasPerSm))));
   const int R = pass32_rows(n);
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((d + R - 1) / R, (int64_t)per_sm * num_sms()));
   kern<<<grid, kP32Threads, smem, st>>>(A, lda, d, n, pass32_copy_width(A, lda), b, vin, part, active);
