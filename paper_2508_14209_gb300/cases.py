@@ -1,0 +1,86 @@
+"""Single-kernel-family cases for profiling and timing (ncu, CUDA events).
+
+    python -m paper_2508_14209_gb300.cases sketch  --d 1048576 --n 64 --dtype f64
+    python -m paper_2508_14209_gb300.cases gemm    --p 1024 --k 32768 --ncol 257 --prec bf16x3
+    python -m paper_2508_14209_gb300.cases refined --d 1333142 --n 128 --log10-sigma -2.7
+
+Each case draws its seeded synthetic input once on the GPU (the generators of
+the `inputs` module), runs the library call `--reps` times and prints one JSON
+line with the mean device time per call (CUDA events on the current stream).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+
+def main(argv=None):
+    import torch
+
+    import inputs
+    import paper_2508_14209_gb300 as msk
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("case", choices=["sketch", "gemm", "refined"])
+    ap.add_argument("--d", type=int, default=1 << 20)
+    ap.add_argument("--n", type=int, default=64)
+    ap.add_argument("--dtype", choices=["f64", "f32"], default="f64")
+    ap.add_argument("--p", type=int, default=1024)
+    ap.add_argument("--k", type=int, default=32768)
+    ap.add_argument("--ncol", type=int, default=257)
+    ap.add_argument("--prec", default="bf16x3", choices=sorted(msk.GEMM_PRECS))
+    ap.add_argument("--log10-sigma", type=float, default=-4.0)
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--seed", type=int, default=0x5EED0004)
+    a = ap.parse_args(argv)
+    dev = torch.device("cuda", 0)
+    msk.load()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    out = {"case": a.case}
+    if a.case == "sketch":
+        dt = torch.float64 if a.dtype == "f64" else torch.float32
+        A = inputs.normal_matrix(a.d, a.n, a.seed, dtype=dt, device=dev)
+        k = 2 * a.n * a.n
+        Y = torch.empty((k, a.n), dtype=dt, device=dev)
+        call = lambda: msk.cs_sketch(A, k, a.seed, Y=Y)  # noqa: E731
+        out.update(d=a.d, n=a.n, k=k, dtype=a.dtype, bytes_per_call=a.d * a.n * A.element_size())
+    elif a.case == "gemm":
+        prec = msk.GEMM_PRECS[a.prec]
+        ydt = torch.float64 if prec == msk.GEMM_F64 else torch.float32
+        Y = inputs.normal_matrix(a.k, a.ncol, a.seed, dtype=ydt, device=dev)
+        Yr = torch.empty((a.k, a.ncol), dtype=ydt, device=dev)  # row-major k x ncol
+        Yr.copy_(Y)
+        Z = msk.colmajor(a.p, a.ncol, torch.float64, dev)
+        ws = msk.workspace(msk.msk_gemm_workspace(a.p, a.k, a.ncol, prec), dev)
+        call = lambda: msk.msk_gemm(a.seed, a.p, Yr, gemm_prec=prec, Z=Z, ws=ws)  # noqa: E731
+        out.update(p=a.p, k=a.k, ncol=a.ncol, prec=a.prec, flops_per_call=2 * a.p * a.k * a.ncol)
+    else:
+        A, b, _ = inputs.ls_problem(a.d, a.n, a.log10_sigma, seed=a.seed, dtype=torch.float32, device=dev)
+        prob = [(A, b, a.seed)]
+        ws = msk.workspace(msk.msk_batch_workspace(prob, True), dev)
+        res = {}
+
+        def call():
+            res["r"] = msk.msk_batch_lstsq(prob, refine=True, tol=a.tol, max_iter=4, ws=ws)
+
+        out.update(d=a.d, n=a.n, tol=a.tol, bytes_per_pass=a.d * a.n * 4)
+    call()
+    torch.cuda.synchronize()
+    ev[0].record()
+    for _ in range(a.reps):
+        call()
+    ev[1].record()
+    torch.cuda.synchronize()
+    out["ms_per_call"] = round(ev[0].elapsed_time(ev[1]) / a.reps, 5)
+    if a.case == "refined":
+        out["info"] = res["r"][1][0]
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()
