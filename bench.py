@@ -47,6 +47,17 @@ WORKLOADS = {
 }
 DEFAULT = "multisketch_f64_4194304x64"
 
+# DRAM bytes (read + write) of one CountSketch kernel launch, from one ncu
+# capture of the same kernel on a quarter-size case (1048576 rows: 541.10 MB
+# read + 3.06 MB written FP64; 270.55 + 3.13 MB FP32), scaled by the rows
+# processed (the kernel streams A once, so traffic grows in proportion).
+CS_TRAFFIC = {
+    "multisketch_f64_4194304x64": 4 * (541.097e6 + 3.062e6),
+    "multisketch_f32_4194304x64": 4 * (270.554e6 + 3.128e6),
+    "multisketch_f64_1048576x64": 541.097e6 + 3.062e6,
+    "multisketch_f32_1048576x64": 270.554e6 + 3.128e6,
+}
+
 
 def _peaks():
     try:
@@ -244,7 +255,8 @@ def run_ours(args):
             "roofline": {"bound": "hbm", "kernel": "cs_fixed_f64_kernel (+Y zeroing memset)" if dts == "f64" else "cs_fixed_f32_kernel (+Y zeroing memset)",
                          "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                          "frac": round(achieved / hbm, 4), "peak_source": peak_src,
-                         "traffic": None},
+                         "traffic": CS_TRAFFIC.get(args.workload),
+                         "traffic_note": "ncu dram bytes of one 1048576-row launch, scaled by rows"},
             "clocks": clk, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
             "cpu_baseline": cpu,
             "serving": serving,
