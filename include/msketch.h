@@ -121,6 +121,9 @@ const char *msk_last_error(void);
  *   "cs.l2_budget_bytes"  bytes of Y a CountSketch column chunk keeps in L2
  *                         (default 2/5 of L2)
  *   "cs.f64.variant"      1 = FP64 CountSketch by TMA bulk reductions per row
+ *   "cs.f64.prefetch"     FP64-output CountSketch loads the next tile during the
+ *                         current one's reductions: 1 on, 0 off (default: on
+ *                         from 128 columns up)
  *   "tc.drain"            0 = split-BF16 GEMM without draining accumulators
  *   "batch.kt_per"        K tiles per CTA of the batched tensor-core GEMM (16)
  *   "batch.round"         CG iterations per captured graph round (4)

@@ -37,11 +37,16 @@ def main(argv=None):
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--seed", type=int, default=0x5EED0004)
+    ap.add_argument("--tune", action="append", default=[], metavar="KNOB=VALUE",
+                    help="set a tuning-registry knob before the run (repeatable)")
     a = ap.parse_args(argv)
     dev = torch.device("cuda", 0)
     msk.load()
+    for kv in a.tune:
+        name, value = kv.split("=", 1)
+        msk.tune_set(name, int(value))
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    out = {"case": a.case}
+    out = {"case": a.case, "tune": a.tune}
     if a.case == "sketch":
         dt = torch.float64 if a.dtype == "f64" else torch.float32
         A = inputs.normal_matrix(a.d, a.n, a.seed, dtype=dt, device=dev)

@@ -57,9 +57,13 @@ int largest(const msk_batch_item* items, int nitems) {
   return best;
 }
 
+// Row pitch of the timing sketch's Y: [A b] columns rounded up to a multiple
+// of 4, as the batched path lays Y out (the fixed-width FP32 kernels need it).
+int64_t cs_ldy(const msk_batch_item& it) { return (it.n + 1 + 3) / 4 * 4; }
+
 size_t cs_scratch(const msk_batch_item& it) {
   const int64_t k = 2 * it.n * it.n;
-  return (size_t)k * (size_t)(it.n + 1) * sizeof(float);
+  return (size_t)k * (size_t)cs_ldy(it) * sizeof(float);
 }
 
 }  // namespace
@@ -119,7 +123,7 @@ int msk_autotune(const msk_batch_item* items, int nitems, int refine, double tol
       if (rc == MSK_ENOCONV) rc = MSK_OK;
     } else {
       const int64_t k = 2 * big.n * big.n;
-      rc = cs_sketch(big.A, MSK_F32, big.d, big.n, big.lda, big.b, k, big.seed, Y, big.n + 1,
+      rc = cs_sketch(big.A, MSK_F32, big.d, big.n, big.lda, big.b, k, big.seed, Y, cs_ldy(big),
                      MSK_CS_ATOMIC, nullptr, 0, st);
     }
     return rc ? -1.0 - std::abs((double)rc) : 0.0;

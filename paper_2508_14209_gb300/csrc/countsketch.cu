@@ -308,7 +308,12 @@ static int cs_bulk_f64_chunk(CsParams<double> P, bool pad_ok, cudaStream_t st, i
 // lanes; several rows per warp instruction when 4*L < 128).
 // FP64 accumulation; A is FP64, or FP32 widened exactly (TA = float) — the
 // FP64 sketch of a matrix stored in binary32.
-template <int NCA, bool HAS_B, typename TA>
+// PF: the next tile's loads are issued right after the barrier, so they are
+// in flight while this tile's reductions go out (one tile of A in registers
+// ahead of the shared-memory tile); without PF a tile's loads start after the
+// previous tile's reductions.  Knob "cs.f64.prefetch": 1 on, 0 off, unset =
+// on from 128 columns up.
+template <int NCA, bool HAS_B, typename TA, bool PF>
 __global__ void __launch_bounds__(kCsThreads) cs_fixed_f64_kernel(const CsParams<double> P,
                                                                const TA* __restrict__ Aa) {
   constexpr int NCOL = NCA + (HAS_B ? 1 : 0);
@@ -319,27 +324,34 @@ __global__ void __launch_bounds__(kCsThreads) cs_fixed_f64_kernel(const CsParams
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nca = P.ncol_a;  // <= NCA: the kernel serves any width up to NCA
   const int64_t ntiles = (P.d + kCsRows - 1) / kCsRows;
-  int buf = 0;
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, buf ^= 1) {
-    const int64_t i0 = t * kCsRows;
-    const int64_t i = i0 + lane;
+  double v[Q];
+  double vb = 0.0;
+  uint64_t zr = 0;
+  auto load = [&](int64_t t) {
+    const int64_t i = t * kCsRows + lane;
     const bool row_ok = i < P.d;
-    double v[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
       const int j = warp + q * kCsWarps;
       v[q] = (row_ok && j < nca) ? (double)__ldcs(Aa + i + (int64_t)j * P.lda) : 0.0;
     }
-    double vb = 0.0;
     if (HAS_B && warp == kCsWarps - 1) vb = row_ok ? __ldcs(P.b + i) : 0.0;
-    if (warp == 0) hz[buf][lane] = row_ok ? draw(P.key, (uint64_t)i) : 0ull;
+    if (warp == 0) zr = row_ok ? draw(P.key, (uint64_t)i) : 0ull;
+  };
+  int buf = 0;
+  if (PF && (int64_t)blockIdx.x < ntiles) load(blockIdx.x);
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, buf ^= 1) {
+    if (!PF) load(t);
+    const int64_t i0 = t * kCsRows;
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
       const int j = warp + q * kCsWarps;
       if (j < nca) tiles[buf][lane][j] = v[q];  // column nca is b's slot
     }
     if (HAS_B && warp == kCsWarps - 1) tiles[buf][lane][nca] = vb;
+    if (warp == 0) hz[buf][lane] = zr;
     __syncthreads();
+    if (PF && t + gridDim.x < ntiles) load(t + gridDim.x);
 #pragma unroll
     for (int rr = 0; rr < kCsRows / kCsWarps; ++rr) {
       const int r = warp + rr * kCsWarps;
@@ -496,11 +508,18 @@ static int cs_fixed_chunk(const CsParams<T>& P, cudaStream_t st, int* rc) {
   if (P.ncol != P.ncol_a + (hb ? 1 : 0)) return 0;
   const int nca = P.ncol_a;
   if constexpr (sizeof(T) == 8) {
-#define MSK_FIX64(N)                                                                    \
-  if (nca <= N) {                                                                       \
-    *rc = hb ? launch_fixed(cs_fixed_f64_kernel<N, true, double>, P, st, P.A)           \
-             : launch_fixed(cs_fixed_f64_kernel<N, false, double>, P, st, P.A);         \
-    return 1;                                                                           \
+    // register prefetch of the next tile: measured faster from 128 columns
+    // up (more loads per thread to hide), slower at 64 and below
+    const long long pf_knob = tune_get("cs.f64.prefetch", -1);
+#define MSK_FIX64(N)                                                                          \
+  if (nca <= N) {                                                                             \
+    if (pf_knob > 0 || (pf_knob < 0 && N >= 128))                                             \
+      *rc = hb ? launch_fixed(cs_fixed_f64_kernel<N, true, double, true>, P, st, P.A)         \
+               : launch_fixed(cs_fixed_f64_kernel<N, false, double, true>, P, st, P.A);       \
+    else                                                                                      \
+      *rc = hb ? launch_fixed(cs_fixed_f64_kernel<N, true, double, false>, P, st, P.A)        \
+               : launch_fixed(cs_fixed_f64_kernel<N, false, double, false>, P, st, P.A);      \
+    return 1;                                                                                 \
   }
     MSK_FIX64(16) MSK_FIX64(32) MSK_FIX64(64) MSK_FIX64(128) MSK_FIX64(256)
 #undef MSK_FIX64
@@ -547,8 +566,8 @@ int launch_cs_f32a_f64y(const float* A, int64_t d, int64_t n, int64_t lda, const
     int rc;
 #define MSK_FIXF(N)                                                                     \
     if (w <= N) {                                                                       \
-      rc = hb ? launch_fixed(cs_fixed_f64_kernel<N, true, float>, P, st, Ac)            \
-              : launch_fixed(cs_fixed_f64_kernel<N, false, float>, P, st, Ac);          \
+      rc = hb ? launch_fixed(cs_fixed_f64_kernel<N, true, float, true>, P, st, Ac)      \
+              : launch_fixed(cs_fixed_f64_kernel<N, false, float, true>, P, st, Ac);    \
       if (rc) return rc;                                                                \
       continue;                                                                         \
     }
