@@ -566,8 +566,8 @@ int launch_cs_f32a_f64y(const float* A, int64_t d, int64_t n, int64_t lda, const
     int rc;
 #define MSK_FIXF(N)                                                                     \
     if (w <= N) {                                                                       \
-      rc = hb ? launch_fixed(cs_fixed_f64_kernel<N, true, float, true>, P, st, Ac)      \
-              : launch_fixed(cs_fixed_f64_kernel<N, false, float, true>, P, st, Ac);    \
+      rc = hb ? launch_fixed(cs_fixed_f64_kernel<N, true, float, (N >= 128)>, P, st, Ac) \
+              : launch_fixed(cs_fixed_f64_kernel<N, false, float, (N >= 128)>, P, st, Ac); \
       if (rc) return rc;                                                                \
       continue;                                                                         \
     }
