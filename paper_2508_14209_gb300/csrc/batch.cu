@@ -131,12 +131,17 @@ __global__ void batch_gemm_reduce_kernel(const BatchJob* __restrict__ jobs) {
 
 // One cluster per problem: Householder QR of Z (p x (n+1)), then
 // x0 = R11^{-1} R[0:n, n] by the cluster's first CTA.
-__global__ void __launch_bounds__(kQrThreads) batch_qr_kernel(const BatchJob* __restrict__ jobs) {
+__global__ void __launch_bounds__(kQrThreads) batch_qr_kernel(const BatchJob* __restrict__ jobs,
+                                                             size_t smem_cap) {
+  extern __shared__ __align__(16) double bqr_dyn[];
   const BatchJob& J = jobs[blockIdx.y];
-  qr_cluster_body(J.Z, J.p, J.ncol, J.p);
+  if (qr_smem_bytes(J.p, J.ncol, (int)cg::this_cluster().num_blocks()) <= smem_cap)
+    qr_cluster_smem_body(J.Z, J.p, J.ncol, J.p, bqr_dyn);
+  else
+    qr_cluster_body(J.Z, J.p, J.ncol, J.p);
   cg::this_cluster().sync();
   if (cg::this_cluster().block_rank() == 0) {
-    __shared__ double xs[kTrsvMax];
+    __shared__ double xs[512];  // n <= 256 in a batch
     trsv_upper_body(J.Z, J.n, J.p, J.Z + (int64_t)J.n * J.p, J.x, nullptr, xs);
   }
 }
@@ -485,7 +490,12 @@ int msk_batch_lstsq(const msk_batch_item* items, int nitems, int refine, double 
     cfg.attrs = at;
     cfg.numAttrs = 1;
     MSK_CUDA(cudaFuncSetAttribute(batch_qr_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-    MSK_CUDA(cudaLaunchKernelEx(&cfg, batch_qr_kernel, (const BatchJob*)jobs_dev));
+    size_t qsm = 0;
+    for (const BatchJob& J : P.jobs)
+      if (qr_smem_fits(J.p, J.ncol, 16)) qsm = std::max(qsm, qr_smem_bytes(J.p, J.ncol, 16));
+    if (qsm) MSK_ALLOW_SMEM(batch_qr_kernel);
+    cfg.dynamicSmemBytes = qsm;
+    MSK_CUDA(cudaLaunchKernelEx(&cfg, batch_qr_kernel, (const BatchJob*)jobs_dev, qsm));
   }
   // 5. refinement
   std::vector<int> iters(nitems, 0), conv(nitems, refine ? 0 : 1);

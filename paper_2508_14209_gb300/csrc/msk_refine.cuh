@@ -136,24 +136,33 @@ __device__ __forceinline__ void pass_reduce_body(const double* __restrict__ part
 // Small FP64 vector kernels of the refinement (single CTA; n <= 512).
 
 // Explicit inverse of the upper-triangular R (n x n, ldr) into Ri (n x n,
-// column-major): column c of Ri solves R y = e_c; one warp per column.
+// column-major; rows below the diagonal zero).  Column c of Ri is R^{-1} e_c,
+// computed by one warp with the column-oriented back substitution
+//   t = e_c;  for j = c .. 0:  y_j = t_j / R_jj;  t_i -= y_j R_ij  (i < j),
+// so every step reads a contiguous piece of R's column j; t lives in shared
+// memory (all lanes read t_j as a broadcast) and 1/R_jj is formed once.
+// Shared memory: kTriMaxN reciprocals + kTriMaxN per warp (blockDim <= 256).
+constexpr int kTriMaxN = 512;
 __device__ __forceinline__ void tri_inverse_body(const double* __restrict__ R, int n, int64_t ldr,
                                                  double* __restrict__ Ri, int blk, int nblk) {
-  const int lane = threadIdx.x & 31;
-  const int warp_g = (blk * blockDim.x + threadIdx.x) >> 5;
-  const int nw = (nblk * blockDim.x) >> 5;
+  __shared__ double rinv[kTriMaxN];
+  __shared__ double tw[8][kTriMaxN];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwb = (int)(blockDim.x >> 5);
+  const int warp_g = blk * nwb + warp, nw = nblk * nwb;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) rinv[j] = 1.0 / R[j + (int64_t)j * ldr];
+  __syncthreads();
+  double* t = tw[warp];
   for (int c = warp_g; c < n; c += nw) {
     double* y = Ri + (int64_t)c * n;
-    for (int r = lane; r < n; r += 32) y[r] = 0.0;
+    for (int i = lane; i <= c; i += 32) t[i] = (i == c) ? 1.0 : 0.0;
+    for (int i = c + 1 + lane; i < n; i += 32) y[i] = 0.0;
     __syncwarp();
-    // back substitution restricted to rows <= c
-    for (int i = c; i >= 0; --i) {
-      double s = (i == c) ? 1.0 : 0.0;
-      double part = 0.0;
-      for (int j = i + 1 + lane; j <= c; j += 32) part += R[i + (int64_t)j * ldr] * y[j];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-      if (lane == 0) y[i] = (s - part) / R[i + (int64_t)i * ldr];
+    for (int j = c; j >= 0; --j) {
+      const double yj = t[j] * rinv[j];
+      if (lane == 0) y[j] = yj;
+      const double* col = R + (int64_t)j * ldr;
+      for (int i = lane; i < j; i += 32) t[i] = fma(-yj, __ldg(col + i), t[i]);
       __syncwarp();
     }
   }

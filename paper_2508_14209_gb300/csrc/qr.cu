@@ -24,9 +24,16 @@
 namespace msk {
 
 
+// smem_cap: dynamic shared memory of the launch; the on-chip form runs when
+// the owned columns fit in it.
 __global__ void __launch_bounds__(kQrThreads) qr_cluster_kernel(double* __restrict__ W, int m, int c,
-                                                              int64_t ldw) {
-  qr_cluster_body(W, m, c, ldw);
+                                                              int64_t ldw, size_t smem_cap) {
+  extern __shared__ __align__(16) double qr_dyn[];
+  const int CL = (int)cg::this_cluster().num_blocks();
+  if (qr_smem_bytes(m, c, CL) <= smem_cap)
+    qr_cluster_smem_body(W, m, c, ldw, qr_dyn);
+  else
+    qr_cluster_body(W, m, c, ldw);
 }
 
 int launch_householder_qr(double* W, int64_t m, int64_t c, int64_t ldw, cudaStream_t st) {
@@ -66,7 +73,10 @@ int launch_householder_qr(double* W, int64_t m, int64_t c, int64_t ldw, cudaStre
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  MSK_CUDA(cudaLaunchKernelEx(&cfg, qr_cluster_kernel, W, (int)m, (int)c, ldw));
+  const size_t smem = qr_smem_fits((int)m, (int)c, CL) ? qr_smem_bytes((int)m, (int)c, CL) : 0;
+  if (smem) MSK_ALLOW_SMEM(qr_cluster_kernel);
+  cfg.dynamicSmemBytes = smem;
+  MSK_CUDA(cudaLaunchKernelEx(&cfg, qr_cluster_kernel, W, (int)m, (int)c, ldw, smem));
   return MSK_OK;
 }
 

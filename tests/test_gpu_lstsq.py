@@ -34,8 +34,10 @@ def dev_colmajor(M, msk):
     return out
 
 
+# Shapes whose owned columns fit in shared memory run the on-chip cluster QR;
+# (2048, 400) exceeds it and runs the global-memory form.
 @pytest.mark.parametrize("m,c", [(8, 1), (9, 9), (64, 7), (129, 65), (512, 129), (1024, 257),
-                                 (2048, 100), (300, 17)])
+                                 (2048, 100), (300, 17), (2048, 400)])
 def test_householder_r_matches_oracle(msk, orc, m, c):
     Z = np.random.default_rng(m * 7 + c).standard_normal((m, c))
     W = dev_colmajor(Z, msk)
