@@ -95,19 +95,26 @@ __device__ __forceinline__ void qr_cluster_body(double* __restrict__ W, int m, i
 
 // Shared-memory form of the cluster QR, for matrices whose owned columns fit
 // on chip (qr_smem_fits): CTA `rank` keeps columns rank, rank + CL, ... of W
-// in its shared memory for the whole factorisation.  At step j the owner of
-// column j forms the reflector (v = x + sign(x0) ||x|| e0, tau = 2 / v^T v)
-// in its own shared memory (two buffers, alternating by step); after one
-// cluster barrier every CTA copies v from the owner through distributed shared
-// memory (the copies spread over all CTAs' threads) and applies the reflector
-// to its owned columns > j.  Buffer j & 1 is rewritten at step j + 2, after
-// every CTA has passed the barrier of step j + 1 and so finished copying v_j.
-// The factor goes back to W at the end, zeros below the diagonal.
-// Dynamic shared memory: (ceil(c / CL) + 3) * m doubles.
+// in its shared memory for the whole factorisation.
+//   step j: the owner of column j forms the reflector v = x + sign(x0)||x|| e0,
+//     tau = 2 / v^T v from ||x||^2, which the warp that last updated column j
+//     accumulated on the way (no block reduction); it publishes (v0, tau) and
+//     writes R_jj into row j of its column.  Rows > j of that column are v's
+//     tail and never change again.
+//   one cluster barrier; every CTA copies v's tail from the owner's column
+//     through distributed shared memory (the copies spread over all CTAs'
+//     threads) and applies the reflector to its owned columns > j, one warp
+//     per column; the warp that updates column j + 1 also sums its new
+//     squares below row j.
+// (v0, tau) use two slots alternating by step: slot j & 1 is rewritten at step
+// j + 2, after every CTA has passed the barrier of step j + 1.  The factor
+// goes back to W at the end, zeros below the diagonal.
+// Dynamic shared memory: (ceil(c / CL) + 1) * m doubles + ceil(c / CL) norms.
 __host__ __device__ __forceinline__ size_t qr_smem_bytes(int m, int c, int CL) {
-  return sizeof(double) * (size_t)((c + CL - 1) / CL + 3) * (size_t)m;
+  const size_t own = (size_t)((c + CL - 1) / CL);
+  return sizeof(double) * ((own + 1) * (size_t)m + own);
 }
-constexpr size_t kQrSmemMax = 160 * 1024;  // 1024 x 257 on a 16-CTA cluster: 155.6 KB
+constexpr size_t kQrSmemMax = 160 * 1024;  // 1024 x 257 on a 16-CTA cluster: 148 KB
 __host__ __device__ __forceinline__ bool qr_smem_fits(int m, int c, int CL) {
   return qr_smem_bytes(m, c, CL) <= kQrSmemMax;
 }
@@ -117,10 +124,11 @@ __device__ __forceinline__ void qr_cluster_smem_body(double* __restrict__ W, int
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   const int CL = (int)cluster.num_blocks();
+  const int own = (c + CL - 1) / CL;
   const int nown = (c - rank + CL - 1) / CL;  // columns rank, rank + CL, ...
-  double* cols = sm;                                  // nown x m
-  double* vb = sm + (size_t)((c + CL - 1) / CL) * m;  // 2 x m: this CTA's published v
-  double* vl = vb + 2 * (size_t)m;                    // m: local copy of the step's v
+  double* cols = sm;                           // own x m
+  double* vl = sm + (size_t)own * m;           // m: local copy of the step's v
+  double* cnorm = vl + m;                      // own: ||column below the pivot row||^2
   __shared__ double vsc[2][2];
   __shared__ double red[32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -128,42 +136,52 @@ __device__ __forceinline__ void qr_cluster_smem_body(double* __restrict__ W, int
     const double* src = W + (int64_t)(rank + lj * CL) * ldw;
     for (int i = threadIdx.x; i < m; i += blockDim.x) cols[(size_t)lj * m + i] = src[i];
   }
+  __syncthreads();
+  if (rank == 0) {  // ||column 0||^2
+    double s = 0.0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) s += cols[i] * cols[i];
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) cnorm[0] = s;
+  }
   const int steps = min(m, c);
   for (int j = 0; j < steps; ++j) {
     const int owner = j % CL, slot = j & 1;
-    __syncthreads();  // the owner's column j is up to date; vl is free
-    if (rank == owner) {
+    __syncthreads();  // column j and its norm are final; vl is free
+    if (rank == owner && threadIdx.x == 0) {
       double* x = cols + (size_t)(j / CL) * m;
-      double s = 0.0;
-      for (int i = j + threadIdx.x; i < m; i += blockDim.x) s += x[i] * x[i];
-      const double norm2 = block_sum(s, red);
+      const double norm2 = cnorm[j / CL];
       const double x0 = x[j];
       const double alpha = sqrt(norm2);
       const double sgn = x0 >= 0.0 ? 1.0 : -1.0;
       const double v0 = x0 + sgn * alpha;
       const double vtv = norm2 - x0 * x0 + v0 * v0;
-      double* v = vb + (size_t)slot * m;
-      for (int i = j + threadIdx.x; i < m; i += blockDim.x) v[i] = (i == j) ? v0 : x[i];
-      __syncthreads();  // every thread has read x[j] before it becomes R_jj
-      if (threadIdx.x == 0) {
-        vsc[slot][0] = v0;
-        vsc[slot][1] = vtv > 0.0 ? 2.0 / vtv : 0.0;
-        x[j] = -sgn * alpha;
-      }
+      vsc[slot][0] = v0;
+      vsc[slot][1] = vtv > 0.0 ? 2.0 / vtv : 0.0;
+      x[j] = -sgn * alpha;
     }
     cluster.sync();
-    const double* ov = cluster.map_shared_rank(vb + (size_t)slot * m, owner);
-    const double tau = *cluster.map_shared_rank(&vsc[slot][1], owner);
-    for (int i = j + threadIdx.x; i < m; i += blockDim.x) vl[i] = ov[i];
+    const double* ox = cluster.map_shared_rank(cols + (size_t)(j / CL) * m, owner);
+    const double* osc = cluster.map_shared_rank(&vsc[slot][0], owner);
+    for (int i = j + threadIdx.x; i < m; i += blockDim.x) vl[i] = (i == j) ? osc[0] : ox[i];
+    const double tau = osc[1];
     __syncthreads();
-    if (tau != 0.0) {
-      // owned columns > j: local index from the first one after j
-      const int lj0 = (j + CL - rank) / CL;
-      for (int lj = lj0 + warp; lj < nown; lj += nwarps) {
-        double* w = cols + (size_t)lj * m;
-        double t = 0.0;
-        for (int i = j + lane; i < m; i += 32) t += vl[i] * w[i];
-        t = warp_sum(t) * tau;
+    // owned columns > j: local index from the first one after j
+    const int lj0 = (j + CL - rank) / CL;
+    for (int lj = lj0 + warp; lj < nown; lj += nwarps) {
+      double* w = cols + (size_t)lj * m;
+      double t = 0.0;
+      for (int i = j + lane; i < m; i += 32) t += vl[i] * w[i];
+      t = warp_sum(t) * tau;
+      if (rank + lj * CL == j + 1) {  // the next pivot column: update and sum squares
+        double s2 = 0.0;
+        for (int i = j + lane; i < m; i += 32) {
+          const double wi = w[i] - t * vl[i];
+          w[i] = wi;
+          if (i > j) s2 += wi * wi;
+        }
+        s2 = warp_sum(s2);
+        if (lane == 0) cnorm[lj] = s2;
+      } else {
         for (int i = j + lane; i < m; i += 32) w[i] -= t * vl[i];
       }
     }
