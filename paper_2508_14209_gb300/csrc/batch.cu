@@ -14,8 +14,9 @@
 //                 memory);
 //   QR + solve    one launch, one thread-block cluster per problem;
 //   refinement    FP64 residual pass, reduction and CG start: one launch each;
-//                 the inner CG rounds (pass, reduction, update) x kRound (knob
-//                 "batch.round") are
+//                 the inner CG rounds (pass per width class, then the CG step
+//                 fused with the partials' reduction on one 8-CTA cluster per
+//                 problem) x kRound (knob "batch.round") are
 //                 captured once into a CUDA graph and replayed until every
 //                 problem has met its stopping rule.
 // Problems that stop early are skipped by the later launches (device flags).
@@ -182,11 +183,10 @@ __global__ void __launch_bounds__(kP32Threads, pass32_ctas_per_sm(NC))
   }
 }
 
-template <bool ONLY_ACTIVE>
+// Sum of the residual pass's per-CTA partials (problems with only[j] set).
 __global__ void __launch_bounds__(256) batch_pass_reduce_kernel(const BatchJob* __restrict__ jobs,
                                                                 const int* __restrict__ only) {
   const BatchJob& J = jobs[blockIdx.y];
-  if (ONLY_ACTIVE && J.sc[2] == 0.0) return;
   if (only && !only[blockIdx.y]) return;
   if ((int)blockIdx.x * 32 >= J.n + 2) return;
   pass_reduce_body(J.ppart, J.nchunks, J.n + 2, J.pout, blockIdx.x);
@@ -214,17 +214,14 @@ __global__ void batch_pcg_start_kernel(const BatchJob* __restrict__ jobs, double
   }
 }
 
-// One CG step (pcg_stop_check holds the stopping rule).  A problem whose very
-// first step is below its floor is already the minimiser to within tol: its
-// refining flag is cleared so that the correction is not applied.
-__global__ void batch_pcg_update_kernel(const BatchJob* __restrict__ jobs,
-                                        int* __restrict__ active_count, int* __restrict__ refining) {
-  const BatchJob& J = jobs[blockIdx.x];
-  if (J.sc[2] == 0.0) return;
-  pcg_update_body(J.Ri, J.n, J.pout, ref_state(J));
-  __syncthreads();
-  if (threadIdx.x == 0 && pcg_stop_check(J.sc, kBatchMaxInner)) {
-    if (J.sc[5] != 0.0) refining[blockIdx.x] = 0;
+// One CG step of every problem, fused with the reduction of its pass
+// partials: one kUpdCL-CTA cluster per problem (blockIdx.y).
+__global__ void __launch_bounds__(kUpdThreads) batch_pcg_cluster_kernel(const BatchJob* __restrict__ jobs,
+                                                                       int* __restrict__ active_count,
+                                                                       int* __restrict__ refining) {
+  const BatchJob& J = jobs[blockIdx.y];
+  if (pcg_cluster_update_body(J.ppart, J.nchunks, J.n + 2, J.Ri, J.n, ref_state(J), kBatchMaxInner)) {
+    if (J.sc[5] != 0.0) refining[blockIdx.y] = 0;
     atomicSub(active_count, 1);
   }
 }
@@ -539,7 +536,7 @@ int msk_batch_lstsq(const msk_batch_item* items, int nitems, int refine, double 
   auto fp64_pass = [&](const int* only_dev, const std::vector<int>* only_host) -> int {
     passes(true, only_dev, st);
     MSK_CHECK_LAUNCH("batch_pass_kernel");
-    batch_pass_reduce_kernel<false><<<rgrid, 256, 0, st>>>(jobs_dev, only_dev);
+    batch_pass_reduce_kernel<<<rgrid, 256, 0, st>>>(jobs_dev, only_dev);
     MSK_CHECK_LAUNCH("batch_pass_reduce_kernel");
     batch_gather_kernel<<<gblocks, 256, 0, st>>>(jobs_dev, nitems, gather);
     MSK_CHECK_LAUNCH("batch_gather_kernel");
@@ -572,10 +569,20 @@ int msk_batch_lstsq(const msk_batch_item* items, int nitems, int refine, double 
     cudaGraphExec_t exec = nullptr;
     MSK_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
     const int round_len = (int)std::min<long long>(16, std::max<long long>(1, tune_get("batch.round", kRound)));
+    cudaLaunchConfig_t ucfg = {};
+    ucfg.gridDim = dim3(kUpdCL, nitems, 1);
+    ucfg.blockDim = dim3(kUpdThreads, 1, 1);
+    ucfg.stream = cap;
+    cudaLaunchAttribute uat[1];
+    uat[0].id = cudaLaunchAttributeClusterDimension;
+    uat[0].val.clusterDim.x = kUpdCL;
+    uat[0].val.clusterDim.y = 1;
+    uat[0].val.clusterDim.z = 1;
+    ucfg.attrs = uat;
+    ucfg.numAttrs = 1;
     for (int r = 0; r < round_len; ++r) {
       passes(false, nullptr, cap);
-      batch_pass_reduce_kernel<true><<<rgrid, 256, 0, cap>>>(jobs_dev, nullptr);
-      batch_pcg_update_kernel<<<nitems, 512, 0, cap>>>(jobs_dev, active, refining);
+      cudaLaunchKernelEx(&ucfg, batch_pcg_cluster_kernel, (const BatchJob*)jobs_dev, active, refining);
     }
     cudaError_t ce = cudaStreamEndCapture(cap, &graph);
     if (ce != cudaSuccess) return cuda_fail(ce, "capture of the refinement round");

@@ -174,12 +174,13 @@ __global__ void pcg_start_kernel(const double* __restrict__ Ri, int n, const dou
   __syncthreads();
   if (threadIdx.x == 0) pcg_arm(s.sc, floor);
 }
-__global__ void pcg_update_kernel(const double* __restrict__ Ri, int n, const double* __restrict__ pv,
-                                  RefState s, int max_steps) {
-  if (s.sc[2] == 0.0) return;
-  pcg_update_body(Ri, n, pv, s);
-  __syncthreads();
-  if (threadIdx.x == 0) pcg_stop_check(s.sc, max_steps);
+
+// One CG step fused with the reduction of the pass partials (one cluster).
+__global__ void __launch_bounds__(kUpdThreads) pcg_cluster_kernel(const double* __restrict__ part,
+                                                                 int nchunks, int stride,
+                                                                 const double* __restrict__ Ri, int n,
+                                                                 RefState s, int max_steps) {
+  pcg_cluster_update_body(part, nchunks, stride, Ri, n, s, max_steps);
 }
 // x += dlt
 __global__ void axpy_kernel(int n, const double* __restrict__ dlt, double* __restrict__ x) {
@@ -191,10 +192,12 @@ static int pass_grid(int64_t d) {
   return (int)std::max<int64_t>(1, std::min<int64_t>((d + kPR - 1) / kPR, 3LL * num_sms()));
 }
 
+// out == nullptr: leave the per-CTA partials unreduced (the fused CG step
+// reduces them); *grid_out receives the number of partials.
 template <typename TA, bool RESID>
 static int launch_pass_t(const TA* A, int64_t lda, int64_t d, int n, const double* b,
                          const double* vin, double* part, double* out, const double* active,
-                         cudaStream_t st) {
+                         cudaStream_t st, int* grid_out) {
   const int pitch = n | 1;  // odd: conflict-free transposing stores and row reads
   const size_t smem = sizeof(double) * ((size_t)n + kPR) + sizeof(TA) * (size_t)kPR * pitch;
   auto kern = pass_kernel<TA, RESID>;
@@ -202,6 +205,8 @@ static int launch_pass_t(const TA* A, int64_t lda, int64_t d, int n, const doubl
   const int grid = pass_grid(d);
   kern<<<grid, kPThreads, smem, st>>>(A, lda, d, n, pitch, b, vin, part, active);
   MSK_CHECK_LAUNCH("pass_kernel");
+  if (grid_out) *grid_out = grid;
+  if (!out) return MSK_OK;
   pass_reduce_kernel<<<(n + 2 + 31) / 32, 256, 0, st>>>(part, grid, n + 2, out, active);
   MSK_CHECK_LAUNCH("pass_reduce_kernel");
   return MSK_OK;
@@ -221,7 +226,7 @@ static int pass32_grid(int64_t d, int n) {
 template <int NC, bool RESID>
 static int launch_pass32_nc(const float* A, int64_t lda, int64_t d, int n, const double* b,
                             const double* vin, double* part, double* out, const double* active,
-                            cudaStream_t st) {
+                            cudaStream_t st, int* grid_out) {
   const size_t smem = pass32_smem(n);
   auto kern = pass32_kernel<NC, RESID>;
   MSK_ALLOW_SMEM(kern);
@@ -232,6 +237,8 @@ static int launch_pass32_nc(const float* A, int64_t lda, int64_t d, int n, const
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((d + R - 1) / R, (int64_t)per_sm * num_sms()));
   kern<<<grid, kP32Threads, smem, st>>>(A, lda, d, n, pass32_copy_width(A, lda), b, vin, part, active);
   MSK_CHECK_LAUNCH("pass32_kernel");
+  if (grid_out) *grid_out = grid;
+  if (!out) return MSK_OK;
   pass_reduce_kernel<<<(n + 2 + 31) / 32, 256, 0, st>>>(part, grid, n + 2, out, active);
   MSK_CHECK_LAUNCH("pass_reduce_kernel");
   return MSK_OK;
@@ -240,15 +247,15 @@ static int launch_pass32_nc(const float* A, int64_t lda, int64_t d, int n, const
 template <bool RESID>
 static int launch_pass32(const float* A, int64_t lda, int64_t d, int n, const double* b,
                          const double* vin, double* part, double* out, const double* active,
-                         cudaStream_t st) {
+                         cudaStream_t st, int* grid_out) {
   if (n > 2 * kP32Threads) return MSK_ENOTSUP;
   switch (pass32_class(n)) {
-    case 16: return launch_pass32_nc<16, RESID>(A, lda, d, n, b, vin, part, out, active, st);
-    case 32: return launch_pass32_nc<32, RESID>(A, lda, d, n, b, vin, part, out, active, st);
-    case 64: return launch_pass32_nc<64, RESID>(A, lda, d, n, b, vin, part, out, active, st);
-    case 128: return launch_pass32_nc<128, RESID>(A, lda, d, n, b, vin, part, out, active, st);
-    case 256: return launch_pass32_nc<256, RESID>(A, lda, d, n, b, vin, part, out, active, st);
-    default: return launch_pass32_nc<0, RESID>(A, lda, d, n, b, vin, part, out, active, st);
+    case 16: return launch_pass32_nc<16, RESID>(A, lda, d, n, b, vin, part, out, active, st, grid_out);
+    case 32: return launch_pass32_nc<32, RESID>(A, lda, d, n, b, vin, part, out, active, st, grid_out);
+    case 64: return launch_pass32_nc<64, RESID>(A, lda, d, n, b, vin, part, out, active, st, grid_out);
+    case 128: return launch_pass32_nc<128, RESID>(A, lda, d, n, b, vin, part, out, active, st, grid_out);
+    case 256: return launch_pass32_nc<256, RESID>(A, lda, d, n, b, vin, part, out, active, st, grid_out);
+    default: return launch_pass32_nc<0, RESID>(A, lda, d, n, b, vin, part, out, active, st, grid_out);
   }
 }
 
@@ -257,19 +264,19 @@ static int launch_pass32(const float* A, int64_t lda, int64_t d, int n, const do
 // else : out = [A^T A p (n), ., .] (FP64 for FP64 A, double-single for FP32 A).
 static int launch_pass(const void* A, int dtype, int64_t lda, int64_t d, int n, const double* b,
                        const double* vin, bool resid, double* part, double* out,
-                       const double* active, cudaStream_t st) {
+                       const double* active, cudaStream_t st, int* grid_out = nullptr) {
   if (dtype == MSK_F64) {
     if (resid)
       return launch_pass_t<double, true>(static_cast<const double*>(A), lda, d, n, b, vin, part,
-                                         out, nullptr, st);
+                                         out, nullptr, st, grid_out);
     return launch_pass_t<double, false>(static_cast<const double*>(A), lda, d, n, b, vin, part, out,
-                                        active, st);
+                                        active, st, grid_out);
   }
   if (resid)
     return launch_pass32<true>(static_cast<const float*>(A), lda, d, n, b, vin, part, out, nullptr,
-                               st);
+                               st, grid_out);
   return launch_pass32<false>(static_cast<const float*>(A), lda, d, n, nullptr, vin, part, out,
-                              active, st);
+                              active, st, grid_out);
 }
 
 static size_t pass_workspace(int64_t d, int64_t n) {
@@ -383,12 +390,25 @@ int ms_lstsq(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, const 
       pcg_start_kernel<<<1, 512, 0, st>>>(Ri, (int)n, gsave, s, kDecFrac * tol * rr);
       MSK_CHECK_LAUNCH("pcg_start_kernel");
       double active = 1.0;
+      cudaLaunchConfig_t ucfg = {};
+      ucfg.gridDim = dim3(kUpdCL, 1, 1);
+      ucfg.blockDim = dim3(kUpdThreads, 1, 1);
+      ucfg.stream = st;
+      cudaLaunchAttribute uat[1];
+      uat[0].id = cudaLaunchAttributeClusterDimension;
+      uat[0].val.clusterDim.x = kUpdCL;
+      uat[0].val.clusterDim.y = 1;
+      uat[0].val.clusterDim.z = 1;
+      ucfg.attrs = uat;
+      ucfg.numAttrs = 1;
       for (int queued = 0; active != 0.0 && queued < kMaxInner; queued += kInnerRound) {
         for (int r = 0; r < kInnerRound; ++r) {
-          rc = launch_pass(A, dtype, lda, d, (int)n, nullptr, s.p, false, part, pout, sc + 2, st);
+          int nparts = 0;
+          rc = launch_pass(A, dtype, lda, d, (int)n, nullptr, s.p, false, part, nullptr, sc + 2, st,
+                           &nparts);
           if (rc) return rc;
-          pcg_update_kernel<<<1, 512, 0, st>>>(Ri, (int)n, pout, s, kMaxInner);
-          MSK_CHECK_LAUNCH("pcg_update_kernel");
+          MSK_CUDA(cudaLaunchKernelEx(&ucfg, pcg_cluster_kernel, (const double*)part, nparts,
+                                      (int)n + 2, (const double*)Ri, (int)n, s, (int)kMaxInner));
         }
         MSK_CUDA(cudaMemcpyAsync(&active, sc + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
         MSK_CUDA(cudaStreamSynchronize(st));

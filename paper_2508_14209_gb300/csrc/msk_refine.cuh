@@ -1,6 +1,7 @@
 // msk_refine.cuh — device bodies of the refinement (sketch-and-precondition)
 // passes and small vector steps, shared by ms_lstsq and the batched engine.
 #pragma once
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -240,54 +241,6 @@ __device__ __forceinline__ void pcg_start_body(const double* __restrict__ Ri, in
   }
 }
 
-// One CG update after the pass produced v = A^T A p (pv[0..n)), pv[n] = p.v:
-//   alpha = rho / p.v; dlt += alpha p; res -= alpha v; z = M^{-1} res;
-//   rho' = res.z; p = z + (rho'/rho) p.
-__device__ __forceinline__ void pcg_update_body(const double* __restrict__ Ri, int n,
-                                                const double* __restrict__ pv, RefState s) {
-  __shared__ double tmp[512];
-  __shared__ double scr[1024];
-  __shared__ double red[32];
-  __shared__ double alpha_s, beta_s;
-  // p.v from the vector itself (more accurate than ||A p||^2 in FP32)
-  double part = 0.0;
-  for (int j = threadIdx.x; j < n; j += blockDim.x) part += s.p[j] * pv[j];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double pAp = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) pAp += red[w];
-    alpha_s = pAp > 0.0 ? s.sc[0] / pAp : 0.0;
-  }
-  __syncthreads();
-  const double alpha = alpha_s;
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    s.dlt[j] += alpha * s.p[j];
-    s.res[j] -= alpha * pv[j];
-  }
-  __syncthreads();
-  apply_minv(Ri, n, s.res, tmp, s.z, scr);
-  part = 0.0;
-  for (int j = threadIdx.x; j < n; j += blockDim.x) part += s.res[j] * s.z[j];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double rho = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) rho += red[w];
-    beta_s = s.sc[0] > 0.0 ? rho / s.sc[0] : 0.0;
-    s.sc[1] = alpha_s * s.sc[0];  // decrease of ||b - A x||^2 by this step (CG identity)
-    s.sc[0] = rho;
-  }
-  __syncthreads();
-  const double beta = beta_s;
-  for (int j = threadIdx.x; j < n; j += blockDim.x) s.p[j] = s.z[j] + beta * s.p[j];
-}
-
 // Refinement scalars (sc, FP64):
 //   [0] rho = res.z            [1] gain of the last step (alpha rho)
 //   [2] active (1 while the inner solve runs)
@@ -308,7 +261,7 @@ __device__ __forceinline__ void pcg_arm(double* sc, double floor) {
   sc[7] = 0.0;
 }
 
-// Stopping rule after a CG step (thread 0, after pcg_update_body): returns
+// Stopping rule after a CG step (one thread, after the step): returns
 // true when this step ended the inner solve.
 __device__ __forceinline__ bool pcg_stop_check(double* sc, int max_steps) {
   sc[4] += 1.0;
@@ -322,4 +275,127 @@ __device__ __forceinline__ bool pcg_stop_check(double* sc, int max_steps) {
   }
   return false;
 }
+// ---------------------------------------------------------------------------
+// One CG step fused with the reduction of the pass partials, on a cluster of
+// kUpdCL CTAs (kUpdThreads threads each; n <= kUpdMaxN).  CTA r owns the
+// slice j0 = r*sl .. j0+sl-1 of the n-vectors (sl = ceil(n / CL)):
+//   1. v_j = sum over pass CTAs of part[c][j] (j in the slice; fixed order),
+//      and the slice's share of p.v;
+//   -- barrier: alpha = rho / p.v from the CL shares, summed in rank order;
+//   2. dlt_j += alpha p_j, res_j -= alpha v_j; res_j to every CTA (DSMEM);
+//   -- barrier: tmp_j = (Ri^T res)_j for the slice (one warp per column);
+//      tmp_j to every CTA;
+//   -- barrier: z_i = (Ri tmp)_i for the slice and its share of rho' = res.z;
+//   -- barrier: rho' from the shares; beta = rho' / rho; p_i = z_i + beta p_i.
+// The FP64 work of M^{-1} (2 n^2 operations, a few microseconds on one SM at
+// GB300's FP64 rate) is split CL ways.  Returns true in CTA 0, thread 0 when
+// this step ended the inner solve (pcg_stop_check).  All CTAs of the cluster
+// see the same sc[2] on entry, so they return together when the solve has
+// already stopped.
+constexpr int kUpdCL = 8, kUpdThreads = 256, kUpdMaxN = 512;
+constexpr int kUpdMaxSlice = kUpdMaxN / kUpdCL;
+
+__device__ __forceinline__ bool pcg_cluster_update_body(const double* __restrict__ part, int nchunks,
+                                                        int stride, const double* __restrict__ Ri,
+                                                        int n, RefState s, int max_steps) {
+  namespace cgr = cooperative_groups;
+  cgr::cluster_group cluster = cgr::this_cluster();
+  const int CL = (int)cluster.num_blocks(), rank = (int)cluster.block_rank();
+  __shared__ double resg[kUpdMaxN], tmpg[kUpdMaxN];
+  __shared__ double pr[kUpdThreads];
+  __shared__ double vsl[kUpdMaxSlice], zsl[kUpdMaxSlice];
+  __shared__ double dotp[kUpdCL], dotr[kUpdCL];
+  __shared__ double red[32];
+  if (s.sc[2] == 0.0) return false;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
+  const int sl = (n + CL - 1) / CL;
+  const int j0 = rank * sl, ns = max(0, min(n, j0 + sl) - j0);
+  const double rho_old = s.sc[0];
+  auto block_total = [&](double v) -> double {  // all threads get the sum (fixed order)
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double r = 0.0;
+    for (int w = 0; w < nw; ++w) r += red[w];
+    return r;
+  };
+  // 1. v on the slice from the pass partials; share of p.v
+  const int G = ns > 0 ? (int)blockDim.x / ns : 1;
+  if (ns > 0 && t < G * ns) {
+    const int jj = t % ns, g = t / ns;
+    double a0 = 0.0, a1 = 0.0;
+    int c = g;
+    for (; c + G < nchunks; c += 2 * G) {
+      a0 += part[(int64_t)c * stride + j0 + jj];
+      a1 += part[(int64_t)(c + G) * stride + j0 + jj];
+    }
+    if (c < nchunks) a0 += part[(int64_t)c * stride + j0 + jj];
+    pr[t] = a0 + a1;
+  }
+  __syncthreads();
+  double pv = 0.0;
+  if (t < ns) {
+    double v = 0.0;
+    for (int g = 0; g < G; ++g) v += pr[g * ns + t];
+    vsl[t] = v;
+    pv = s.p[j0 + t] * v;
+  }
+  pv = block_total(pv);
+  if (t < CL) *cluster.map_shared_rank(&dotp[rank], t) = pv;
+  cluster.sync();
+  double pAp = 0.0;
+  for (int r = 0; r < CL; ++r) pAp += dotp[r];
+  const double alpha = pAp > 0.0 ? rho_old / pAp : 0.0;
+  // 2. dlt, res on the slice; res to every CTA
+  if (t < ns) {
+    const int j = j0 + t;
+    s.dlt[j] += alpha * s.p[j];
+    const double rj = s.res[j] - alpha * vsl[t];
+    s.res[j] = rj;
+    for (int r = 0; r < CL; ++r) *cluster.map_shared_rank(&resg[j], r) = rj;
+  }
+  cluster.sync();
+  // 3. tmp = Ri^T res on the slice (column j of Ri is contiguous)
+  for (int jj = warp; jj < ns; jj += nw) {
+    const int j = j0 + jj;
+    const double* col = Ri + (int64_t)j * n;
+    double a = 0.0;
+    for (int i = lane; i <= j; i += 32) a += col[i] * resg[i];
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane < CL) *cluster.map_shared_rank(&tmpg[j], lane) = a;
+  }
+  cluster.sync();
+  // 4. z = Ri tmp on the slice: thread (ii, g) sums j = i + g, i + g + G, ...
+  if (ns > 0 && t < G * ns) {
+    const int ii = t % ns, g = t / ns, i = j0 + ii;
+    double a = 0.0;
+    for (int j = i + g; j < n; j += G) a += Ri[i + (int64_t)j * n] * tmpg[j];
+    pr[t] = a;
+  }
+  __syncthreads();
+  double rz = 0.0;
+  if (t < ns) {
+    double z = 0.0;
+    for (int g = 0; g < G; ++g) z += pr[g * ns + t];
+    zsl[t] = z;
+    s.z[j0 + t] = z;
+    rz = resg[j0 + t] * z;
+  }
+  rz = block_total(rz);
+  if (t < CL) *cluster.map_shared_rank(&dotr[rank], t) = rz;
+  cluster.sync();
+  double rho = 0.0;
+  for (int r = 0; r < CL; ++r) rho += dotr[r];
+  const double beta = rho_old > 0.0 ? rho / rho_old : 0.0;
+  if (t < ns) s.p[j0 + t] = zsl[t] + beta * s.p[j0 + t];
+  bool stopped = false;
+  if (rank == 0 && t == 0) {
+    s.sc[1] = alpha * rho_old;  // decrease of ||b - A x||^2 by this step (CG identity)
+    s.sc[0] = rho;
+    stopped = pcg_stop_check(s.sc, max_steps);
+  }
+  return stopped;
+}
+
 }  // namespace msk
