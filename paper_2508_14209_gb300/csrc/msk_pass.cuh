@@ -56,18 +56,23 @@ __host__ __device__ __forceinline__ int pass32g_rows(int n) {
   while (R < 1024 && 2 * R * n <= kP32TileElems) R *= 2;
   return R;
 }
+// Specialised bodies: elements per tile and pipeline depth by width class —
+// 16 KiB tiles three deep up to 128 columns (two tiles of compute cover a
+// tile's load latency), 32 KiB tiles two deep at 256 (a tile keeps >= 32 rows).
+__host__ __device__ constexpr int pass32n_tile(int nc) { return nc <= 128 ? 4096 : 8192; }
+__host__ __device__ constexpr int pass32n_stages(int nc) { return nc <= 128 ? 3 : 2; }
 // Rows per tile of the body that runs for n.
 __host__ __device__ __forceinline__ int pass32_rows(int n) {
   const int nc = pass32_class(n);
-  return nc ? kP32TileElems / nc : pass32g_rows(n);
+  return nc ? pass32n_tile(nc) / nc : pass32g_rows(n);
 }
 // Dynamic shared memory of a pass CTA for n columns (two tiles + vectors +
 // merge space) of the body that runs for n.
 __host__ __device__ __forceinline__ size_t pass32_smem(int n) {
   const int nc = pass32_class(n);
   if (nc) {
-    const int R = kP32TileElems / nc;
-    return sizeof(float) * 2 * (size_t)kP32TileElems + 16 * (size_t)nc +
+    const int R = pass32n_tile(nc) / nc;
+    return sizeof(float) * (size_t)pass32n_stages(nc) * pass32n_tile(nc) + 16 * (size_t)nc +
            sizeof(double) * kP32Threads + sizeof(float2) * (size_t)R;
   }
   const int R = pass32g_rows(n);
@@ -501,7 +506,8 @@ __device__ __forceinline__ void pass32n_body(const float* __restrict__ A, int64_
                                              double* __restrict__ part, int cta, int nctas,
                                              unsigned char* smem) {
   constexpr int T = kP32Threads;
-  constexpr int R = kP32TileElems / NC, RB = R / 32;
+  constexpr int TE = pass32n_tile(NC), S = pass32n_stages(NC);
+  constexpr int R = TE / NC, RB = R / 32;
   constexpr int DR = RB >= 8 ? RB / 8 : 1;   // dot rows per thread
   constexpr int M = RB >= 8 ? 1 : 8 / RB;    // dot column groups per row block
   constexpr int DC = NC / M;                 // dot columns per thread
@@ -509,7 +515,7 @@ __device__ __forceinline__ void pass32n_body(const float* __restrict__ A, int64_
   constexpr int WPB = 8 / M;                 // warps per column group
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   float* tiles = reinterpret_cast<float*>(smem);
-  double* vd = reinterpret_cast<double*>(tiles + 2 * kP32TileElems);  // NC: x (RESID) or (ph, pl)
+  double* vd = reinterpret_cast<double*>(tiles + S * TE);  // NC: x (RESID) or (ph, pl)
   auto issue = [&](int64_t i0, float* buf) {
     if (cw == 4) p32n_issue<NC, R, 4>(A, lda, d, n, i0, buf);
     else if (cw == 2) p32n_issue<NC, R, 2>(A, lda, d, n, i0, buf);
@@ -538,20 +544,22 @@ __device__ __forceinline__ void pass32n_body(const float* __restrict__ A, int64_
   for (int c = 0; c < CC / 2; ++c) acc[c] = D2P{0ull, 0ull};
   double s1 = 0.0, s2 = 0.0;
   const int64_t ntiles = (d + R - 1) / R;
-  int64_t tile = cta;
-  if (tile < ntiles) issue(tile * R, tiles);
-  int buf = 0;
-  for (; tile < ntiles; tile += nctas, buf ^= 1) {
-    const int64_t next = tile + nctas;
-    __syncthreads();  // the other buffer and wv are free again
-    if (next < ntiles) {
-      issue(next * R, tiles + (buf ^ 1) * kP32TileElems);
-      p32_wait<1>();
-    } else {
-      p32_wait<0>();
-    }
+  // S-stage pipeline: tiles cta + m nctas, m = 0, 1, ...; stage m mod S
+  for (int m = 0; m < S - 1; ++m) {
+    const int64_t tm = cta + (int64_t)m * nctas;
+    if (tm < ntiles) issue(tm * R, tiles + m * TE);
+    else p32_commit();
+  }
+  for (int64_t m = 0;; ++m) {
+    const int64_t tile = cta + m * nctas;
+    if (tile >= ntiles) break;
+    __syncthreads();  // the stage refilled next and wv are free again
+    const int64_t next = tile + (int64_t)(S - 1) * nctas;
+    if (next < ntiles) issue(next * R, tiles + (int)((m + S - 1) % S) * TE);
+    else p32_commit();
+    p32_wait<S - 1>();
     __syncthreads();
-    const float* tl = tiles + buf * kP32TileElems;
+    const float* tl = tiles + (int)(m % S) * TE;
     const int64_t i0 = tile * R;
     // ---- dot phase
     const float* tdot = tl + cg * DC * R + rb0 * 32 + lane;
