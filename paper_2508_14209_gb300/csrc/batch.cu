@@ -14,11 +14,13 @@
 //                 memory);
 //   QR + solve    one launch, one thread-block cluster per problem;
 //   refinement    FP64 residual pass, reduction and CG start: one launch each;
-//                 the inner CG rounds (pass per width class, then the CG step
-//                 fused with the partials' reduction on one 8-CTA cluster per
-//                 problem) x kRound (knob "batch.round") are
-//                 captured once into a CUDA graph and replayed until every
-//                 problem has met its stopping rule.
+//                 the inner solve is one CUDA-graph launch whose while node
+//                 loops on the device — kRound (knob "batch.round") CG
+//                 iterations per trip (a pass per width class, then the CG
+//                 step fused with the partials' reduction on one 8-CTA
+//                 cluster per problem) — until every problem has met its
+//                 stopping rule.  Instantiated graphs are cached per host
+//                 thread by their launch arguments.
 // Problems that stop early are skipped by the later launches (device flags).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -258,8 +260,41 @@ __global__ void batch_arm_kernel(const BatchJob* __restrict__ jobs, int nprob,
     for (int q = 0; q < kScCount; ++q) J.sc[q] = 0.0;
     J.sc[2] = refining[j] ? 1.0 : 0.0;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) *active = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    active[0] = 0;  // problems still iterating (pcg_start counts them in)
+    active[1] = 0;  // CG iterations run by the device loop
+  }
 }
+
+// End of one device-loop iteration: continue while a problem is still
+// iterating, and never beyond kBatchMaxInner iterations in all (every problem
+// also stops itself at kBatchMaxInner steps).
+__global__ void batch_loop_cond_kernel(cudaGraphConditionalHandle h, int* __restrict__ active) {
+  const int it = ++active[1];
+  cudaGraphSetConditional(h, (active[0] > 0 && it < kBatchMaxInner) ? 1u : 0u);
+}
+
+// Instantiated refinement-loop graphs of this host thread, keyed by every
+// argument the capture baked in (the problems themselves are read from the
+// workspace at run time), so that a batch of a shape seen before skips
+// capture and instantiation.
+struct LoopKey {
+  const void* jobs;
+  const int* active;
+  const int* refining;
+  int nitems, round_len, ncls;
+  int nc[5], chunks[5], nmem[5];
+  const void* mem[5];
+  size_t smem[5];
+  bool operator==(const LoopKey& o) const { return std::memcmp(this, &o, sizeof(LoopKey)) == 0; }
+};
+struct LoopCache {
+  std::vector<std::pair<LoopKey, cudaGraphExec_t>> entries;  // most recent last
+  ~LoopCache() {
+    for (auto& e : entries) cudaGraphExecDestroy(e.second);
+  }
+};
+constexpr size_t kLoopCacheMax = 16;
 
 struct BatchPlan {
   std::vector<BatchJob> jobs;
@@ -559,37 +594,85 @@ int msk_batch_lstsq(const msk_batch_item* items, int nitems, int refine, double 
   if (refine) {
     batch_tri_inverse_kernel<<<dim3((P.max_n + 7) / 8, nitems), 256, 0, st>>>(jobs_dev);
     MSK_CHECK_LAUNCH("batch_tri_inverse_kernel");
-    // one captured round: `round` CG iterations over all problems
-    // Capture records work without running it, on a private stream (the
-    // legacy default stream cannot be captured); the graph is then launched on
-    // the caller's stream, in order with everything above.
+    // The inner solve as one graph launch: a while node whose body runs
+    // `round_len` CG iterations (passes per width class, then the fused step)
+    // and a condition kernel.  Capture records work without running it, on a
+    // private stream (the legacy default stream cannot be captured); the graph
+    // is launched on the caller's stream, in order with everything above.
     static thread_local cudaStream_t cap = nullptr;
+    static thread_local LoopCache cache;
     if (!cap) MSK_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    MSK_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
     const int round_len = (int)std::min<long long>(16, std::max<long long>(1, tune_get("batch.round", kRound)));
-    cudaLaunchConfig_t ucfg = {};
-    ucfg.gridDim = dim3(kUpdCL, nitems, 1);
-    ucfg.blockDim = dim3(kUpdThreads, 1, 1);
-    ucfg.stream = cap;
-    cudaLaunchAttribute uat[1];
-    uat[0].id = cudaLaunchAttributeClusterDimension;
-    uat[0].val.clusterDim.x = kUpdCL;
-    uat[0].val.clusterDim.y = 1;
-    uat[0].val.clusterDim.z = 1;
-    ucfg.attrs = uat;
-    ucfg.numAttrs = 1;
-    for (int r = 0; r < round_len; ++r) {
-      passes(false, nullptr, cap);
-      cudaLaunchKernelEx(&ucfg, batch_pcg_cluster_kernel, (const BatchJob*)jobs_dev, active, refining);
+    LoopKey key;
+    std::memset(&key, 0, sizeof(key));
+    key.jobs = jobs_dev;
+    key.active = active;
+    key.refining = refining;
+    key.nitems = nitems;
+    key.round_len = round_len;
+    key.ncls = (int)P.pass_nc.size();
+    for (int c = 0; c < key.ncls; ++c) {
+      key.nc[c] = P.pass_nc[c];
+      key.chunks[c] = P.pass_chunks[c];
+      key.nmem[c] = (int)P.pass_mem[c].size();
+      key.mem[c] = base + P.pass_mem_off[c];
+      key.smem[c] = pass32_smem(P.pass_nc[c]);
     }
-    cudaError_t ce = cudaStreamEndCapture(cap, &graph);
-    if (ce != cudaSuccess) return cuda_fail(ce, "capture of the refinement round");
-    ce = cudaGraphInstantiate(&exec, graph, 0);
-    if (ce != cudaSuccess) {
+    cudaGraphExec_t exec = nullptr;
+    for (size_t e = 0; e < cache.entries.size(); ++e)
+      if (cache.entries[e].first == key) {
+        exec = cache.entries[e].second;
+        auto hit = cache.entries[e];
+        cache.entries.erase(cache.entries.begin() + (long)e);
+        cache.entries.push_back(hit);
+        break;
+      }
+    cudaError_t ce = cudaSuccess;
+    if (!exec) {
+      cudaGraph_t graph = nullptr;
+      MSK_CUDA(cudaGraphCreate(&graph, 0));
+      cudaGraphConditionalHandle h;
+      ce = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
+      cudaGraphNodeParams cp = {};
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = h;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      cudaGraphNode_t wnode;
+      if (ce == cudaSuccess) ce = cudaGraphAddNode(&wnode, graph, nullptr, nullptr, 0, &cp);
+      if (ce == cudaSuccess)
+        ce = cudaStreamBeginCaptureToGraph(cap, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal);
+      if (ce != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return cuda_fail(ce, "refinement loop graph");
+      }
+      cudaLaunchConfig_t ucfg = {};
+      ucfg.gridDim = dim3(kUpdCL, nitems, 1);
+      ucfg.blockDim = dim3(kUpdThreads, 1, 1);
+      ucfg.stream = cap;
+      cudaLaunchAttribute uat[1];
+      uat[0].id = cudaLaunchAttributeClusterDimension;
+      uat[0].val.clusterDim.x = kUpdCL;
+      uat[0].val.clusterDim.y = 1;
+      uat[0].val.clusterDim.z = 1;
+      ucfg.attrs = uat;
+      ucfg.numAttrs = 1;
+      for (int r = 0; r < round_len; ++r) {
+        passes(false, nullptr, cap);
+        cudaLaunchKernelEx(&ucfg, batch_pcg_cluster_kernel, (const BatchJob*)jobs_dev, active, refining);
+      }
+      batch_loop_cond_kernel<<<1, 1, 0, cap>>>(h, active);
+      cudaGraph_t body = nullptr;
+      ce = cudaStreamEndCapture(cap, &body);
+      if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, graph, 0);
       cudaGraphDestroy(graph);
-      return cuda_fail(ce, "cudaGraphInstantiate");
+      if (ce != cudaSuccess) return cuda_fail(ce, "refinement loop graph");
+      if (cache.entries.size() >= kLoopCacheMax) {
+        cudaGraphExecDestroy(cache.entries.front().second);
+        cache.entries.erase(cache.entries.begin());
+      }
+      cache.entries.push_back({key, exec});
     }
     std::vector<int> ref(nitems, 0), recheck(nitems, 0);
     for (int outer = 0; outer < max_iter && !status; ++outer) {
@@ -606,17 +689,11 @@ int msk_batch_lstsq(const msk_batch_item* items, int nitems, int refine, double 
       }
       batch_arm_kernel<<<gblocks, 256, 0, st>>>(jobs_dev, nitems, refining, active);
       batch_pcg_start_kernel<<<nitems, 512, 0, st>>>(jobs_dev, tol, active);
-      int hact = nref;
-      for (int round = 0; round * round_len < kBatchMaxInner && hact > 0; ++round) {
-        ce = cudaGraphLaunch(exec, st);
-        if (ce == cudaSuccess) ce = cudaMemcpyAsync(&hact, active, sizeof(int), cudaMemcpyDeviceToHost, st);
-        if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
-        if (ce != cudaSuccess) {
-          status = cuda_fail(ce, "refinement round");
-          break;
-        }
+      ce = cudaGraphLaunch(exec, st);  // the whole inner solve, looping on the device
+      if (ce != cudaSuccess) {
+        status = cuda_fail(ce, "refinement loop");
+        break;
       }
-      if (status) break;
       // x += d for the problems still refining (those whose first step was
       // below the floor had their flag cleared: already converged)
       batch_axpy_kernel<<<nitems, 256, 0, st>>>(jobs_dev, refining);
@@ -651,8 +728,6 @@ int msk_batch_lstsq(const msk_batch_item* items, int nitems, int refine, double 
           conv[j] = 1;
       }
     }
-    cudaGraphExecDestroy(exec);
-    cudaGraphDestroy(graph);
     if (status) return status;
     for (int j = 0; j < nitems; ++j)
       if (!conv[j]) status = MSK_ENOCONV;
