@@ -2,7 +2,7 @@
 
     python -m paper_2508_14209_gb300.cases sketch  --d 1048576 --n 64 --dtype f64
     python -m paper_2508_14209_gb300.cases gemm    --p 1024 --k 32768 --ncol 257 --prec bf16x3
-    python -m paper_2508_14209_gb300.cases refined --d 1333142 --n 128 --log10-sigma -2.7
+    python -m paper_2508_14209_gb300.cases refined --d 1333142 --n 128 --log10-sigma -2.7 [--path single]
 
 Each case draws its seeded synthetic input once on the GPU (the generators of
 the `inputs` module), runs the library call `--reps` times and prints one JSON
@@ -35,6 +35,9 @@ def main(argv=None):
     ap.add_argument("--prec", default="bf16x3", choices=sorted(msk.GEMM_PRECS))
     ap.add_argument("--log10-sigma", type=float, default=-4.0)
     ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--path", choices=["batch", "single"], default="batch",
+                    help="refined: msk_batch_lstsq of one request (its inner loop runs inside a "
+                         "graph's while node) or ms_lstsq (the same kernels launched one by one)")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--seed", type=int, default=0x5EED0004)
     ap.add_argument("--tune", action="append", default=[], metavar="KNOB=VALUE",
@@ -66,14 +69,23 @@ def main(argv=None):
         out.update(p=a.p, k=a.k, ncol=a.ncol, prec=a.prec, flops_per_call=2 * a.p * a.k * a.ncol)
     else:
         A, b, _ = inputs.ls_problem(a.d, a.n, a.log10_sigma, seed=a.seed, dtype=torch.float32, device=dev)
-        prob = [(A, b, a.seed)]
-        ws = msk.workspace(msk.msk_batch_workspace(prob, True), dev)
         res = {}
+        if a.path == "batch":
+            prob = [(A, b, a.seed)]
+            ws = msk.workspace(msk.msk_batch_workspace(prob, True), dev)
 
-        def call():
-            res["r"] = msk.msk_batch_lstsq(prob, refine=True, tol=a.tol, max_iter=4, ws=ws)
+            def call():
+                r = msk.msk_batch_lstsq(prob, refine=True, tol=a.tol, max_iter=4, ws=ws)
+                res["r"] = r[1][0]
+        else:
+            k, p = 2 * a.n * a.n, 4 * a.n
+            ws = msk.workspace(msk.msk_lstsq_workspace(a.d, a.n, k, p, msk.MSK_F32, msk.GEMM_BF16X3, 1), dev)
 
-        out.update(d=a.d, n=a.n, tol=a.tol, bytes_per_pass=a.d * a.n * 4)
+            def call():
+                res["r"] = msk.ms_lstsq(A, b, k, p, a.seed, msk.GEMM_BF16X3, refine=True, tol=a.tol,
+                                        max_iter=4, ws=ws)[1]
+
+        out.update(d=a.d, n=a.n, tol=a.tol, path=a.path, bytes_per_pass=a.d * a.n * 4)
     call()
     torch.cuda.synchronize()
     ev[0].record()
@@ -83,7 +95,7 @@ def main(argv=None):
     torch.cuda.synchronize()
     out["ms_per_call"] = round(ev[0].elapsed_time(ev[1]) / a.reps, 5)
     if a.case == "refined":
-        out["info"] = res["r"][1][0]
+        out["info"] = res["r"]
     print(json.dumps(out), flush=True)
 
 

@@ -12,7 +12,8 @@
 //   Gaussian, split, GEMM, split-K reduction: one launch each, per-problem
 //                 descriptors (the GEMM reads its tensor maps from global
 //                 memory);
-//   QR + solve    one launch, one thread-block cluster per problem;
+//   QR (+ solve)  one launch, one thread-block cluster per problem; with
+//                 refinement, x0 = R^{-1} c after the explicit inverse;
 //   refinement    FP64 residual pass, reduction and CG start: one launch each;
 //                 the inner solve is one CUDA-graph launch whose while node
 //                 loops on the device — kRound (knob "batch.round") CG
@@ -134,19 +135,30 @@ __global__ void batch_gemm_reduce_kernel(const BatchJob* __restrict__ jobs) {
 
 // One cluster per problem: Householder QR of Z (p x (n+1)), then
 // x0 = R11^{-1} R[0:n, n] by the cluster's first CTA.
+// QR of every problem's sketch; with solve, also x0 = R11^{-1} R[0:n, n] by
+// the cluster's first CTA (the refined path forms x0 = R^{-1} c after the
+// explicit inverse instead).
 __global__ void __launch_bounds__(kQrThreads) batch_qr_kernel(const BatchJob* __restrict__ jobs,
-                                                             size_t smem_cap) {
+                                                             size_t smem_cap, int solve) {
   extern __shared__ __align__(16) double bqr_dyn[];
   const BatchJob& J = jobs[blockIdx.y];
   if (qr_smem_bytes(J.p, J.ncol, (int)cg::this_cluster().num_blocks()) <= smem_cap)
     qr_cluster_smem_body(J.Z, J.p, J.ncol, J.p, bqr_dyn);
   else
     qr_cluster_body(J.Z, J.p, J.ncol, J.p);
+  if (!solve) return;
   cg::this_cluster().sync();
   if (cg::this_cluster().block_rank() == 0) {
     __shared__ double xs[512];  // n <= 256 in a batch
     trsv_upper_body(J.Z, J.n, J.p, J.Z + (int64_t)J.n * J.p, J.x, nullptr, xs);
   }
+}
+
+// x0 = R^{-1} c from the explicit inverse (c = R[0:n, n]).
+__global__ void __launch_bounds__(512) batch_x0_kernel(const BatchJob* __restrict__ jobs) {
+  __shared__ double scr[512];
+  const BatchJob& J = jobs[blockIdx.x];
+  tri_matvec_body(J.Ri, J.n, J.Z + (int64_t)J.n * J.p, J.x, scr);
 }
 
 __global__ void batch_tri_inverse_kernel(const BatchJob* __restrict__ jobs) {
@@ -527,7 +539,7 @@ int msk_batch_lstsq(const msk_batch_item* items, int nitems, int refine, double 
       if (qr_smem_fits(J.p, J.ncol, 16)) qsm = std::max(qsm, qr_smem_bytes(J.p, J.ncol, 16));
     if (qsm) MSK_ALLOW_SMEM(batch_qr_kernel);
     cfg.dynamicSmemBytes = qsm;
-    MSK_CUDA(cudaLaunchKernelEx(&cfg, batch_qr_kernel, (const BatchJob*)jobs_dev, qsm));
+    MSK_CUDA(cudaLaunchKernelEx(&cfg, batch_qr_kernel, (const BatchJob*)jobs_dev, qsm, refine ? 0 : 1));
   }
   // 5. refinement
   std::vector<int> iters(nitems, 0), conv(nitems, refine ? 0 : 1);
@@ -586,14 +598,18 @@ int msk_batch_lstsq(const msk_batch_item* items, int nitems, int refine, double 
     return MSK_OK;
   };
   int status = MSK_OK;
+  if (refine) {  // R^{-1} (the preconditioner) and from it x0 = R^{-1} c
+    batch_tri_inverse_kernel<<<dim3((P.max_n + 7) / 8, nitems), 256, 0, st>>>(jobs_dev);
+    MSK_CHECK_LAUNCH("batch_tri_inverse_kernel");
+    batch_x0_kernel<<<nitems, 512, 0, st>>>(jobs_dev);
+    MSK_CHECK_LAUNCH("batch_x0_kernel");
+  }
   if (refine || infos) {
     rc = fp64_pass(nullptr, nullptr);
     if (rc) return rc;
     relres_sns = relres;
   }
   if (refine) {
-    batch_tri_inverse_kernel<<<dim3((P.max_n + 7) / 8, nitems), 256, 0, st>>>(jobs_dev);
-    MSK_CHECK_LAUNCH("batch_tri_inverse_kernel");
     // The inner solve as one graph launch: a while node whose body runs
     // `round_len` CG iterations (passes per width class, then the fused step)
     // and a condition kernel.  Capture records work without running it, on a

@@ -164,6 +164,11 @@ __global__ void __launch_bounds__(kP32Threads, pass32_ctas_per_sm(NC))
   else
     pass32n_body<NC, RESID>(A, lda, d, n, cw, b, vin, part, blockIdx.x, gridDim.x, p32_smem);
 }
+__global__ void __launch_bounds__(512) x0_kernel(const double* __restrict__ Ri, int n,
+                                                 const double* __restrict__ c, double* __restrict__ x) {
+  __shared__ double scr[512];
+  tri_matvec_body(Ri, n, c, x, scr);
+}
 __global__ void tri_inverse_kernel(const double* __restrict__ R, int n, int64_t ldr,
                                    double* __restrict__ Ri) {
   tri_inverse_body(R, n, ldr, Ri, blockIdx.x, gridDim.x);
@@ -348,9 +353,12 @@ int ms_lstsq(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, const 
   // 2. Householder QR of Z (in place): R = Z[0:n+1, 0:n+1]
   rc = launch_householder_qr(Z, p, n + 1, p, st);
   if (rc) return rc;
-  // 3. x0 = R11^{-1} R[0:n, n]
-  rc = launch_trsv_upper(Z, n, p, Z + n * p, x, nullptr, false, st);
-  if (rc) return rc;
+  // 3. x0 = R11^{-1} R[0:n, n]: a triangular solve, or with refinement the
+  //    product with the explicit inverse formed for the preconditioner
+  if (!refine) {
+    rc = launch_trsv_upper(Z, n, p, Z + n * p, x, nullptr, false, st);
+    if (rc) return rc;
+  }
   double relres_sns = -1.0, relres = -1.0, bnorm2 = 0.0;
   int iters = 0, converged = 1, inner_total = 0;
   int status = MSK_OK;
@@ -363,6 +371,8 @@ int ms_lstsq(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, const 
     double* gsave = vec + 4 * n;
     tri_inverse_kernel<<<(unsigned)std::max<int64_t>(1, (n + 7) / 8), 256, 0, st>>>(Z, (int)n, p, Ri);
     MSK_CHECK_LAUNCH("tri_inverse_kernel");
+    x0_kernel<<<1, 512, 0, st>>>(Ri, (int)n, Z + n * p, x);
+    MSK_CHECK_LAUNCH("x0_kernel");
     converged = 0;
     // FP64 true residual pass: pout = [A^T r, ||r||^2, ||b||^2]; rr = ||r||^2
     double rr = 0.0;

@@ -169,6 +169,29 @@ __device__ __forceinline__ void tri_inverse_body(const double* __restrict__ R, i
   }
 }
 
+// x = Ri c with Ri = R^{-1} upper triangular (n x n, column-major): the
+// sketch-and-solve start x0 = R11^{-1} R[0:n, n] when R^{-1} is formed anyway
+// (refinement).  One CTA: G = blockDim / n thread groups split the sum over
+// j >= i (reads of Ri[i + j n] contiguous across a group); partial sums added
+// in group order.  scratch: blockDim doubles of shared memory.
+__device__ __forceinline__ void tri_matvec_body(const double* __restrict__ Ri, int n,
+                                                const double* __restrict__ c, double* __restrict__ x,
+                                                double* scratch) {
+  const int G = (int)blockDim.x >= 2 * n ? (int)blockDim.x / n : 1;
+  for (int idx = threadIdx.x; idx < n * G; idx += blockDim.x) {
+    const int i = idx % n, g = idx / n;
+    double s = 0.0;
+    for (int j = i + g; j < n; j += G) s += Ri[i + (int64_t)j * n] * c[j];
+    scratch[idx] = s;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double s = 0.0;
+    for (int g = 0; g < G; ++g) s += scratch[g * n + i];
+    x[i] = s;
+  }
+}
+
 // State of the refinement, all device FP64 (n-vectors unless noted):
 //   x, dlt (correction), p (search dir), res (normal-eq. residual), z,
 //   sc[0] = rho.
