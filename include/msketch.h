@@ -124,6 +124,8 @@ const char *msk_last_error(void);
  *   "cs.f64.prefetch"     FP64-output CountSketch loads the next tile during the
  *                         current one's reductions: 1 on, 0 off (default: on
  *                         from 128 columns up)
+ *   "cs.f32.prefetch"     the same for the FP32 CountSketch (default: on at 128
+ *                         columns only)
  *   "tc.drain"            0 = split-BF16 GEMM without draining accumulators
  *   "batch.kt_per"        K tiles per CTA of the batched tensor-core GEMM (16)
  *   "batch.round"         CG iterations per captured graph round (4)

@@ -380,37 +380,49 @@ struct CsF32Tile {
     float tiles[2][kCsRows][PITCH];
     uint64_t hz[2][kCsRows];
   };
-  // One 32-row tile starting at row i0 of problem P into buffer `buf`.
-  __device__ __forceinline__ static void run(const CsParams<float>& P, int64_t i0, int buf,
-                                             Smem& sm) {
+  // A tile's loads into registers (v: this lane's row, the warp's column
+  // groups; vb: b by the last warp; zr: the row's hash draw by warp 0).
+  struct Regs {
+    float4 v[QG];
+    float vb;
+    uint64_t zr;
+  };
+  __device__ __forceinline__ static void load(const CsParams<float>& P, int64_t i0, Regs& g) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t i = i0 + lane;
     const bool row_ok = i < P.d;
-    float4 v[QG];
 #pragma unroll
     for (int q = 0; q < QG; ++q) {
-      const int g = warp + q * kCsWarps;
+      const int gi = warp + q * kCsWarps;
       float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (row_ok && g < NG) {
-        const float* a = P.A + i + (int64_t)(4 * g) * P.lda;
+      if (row_ok && gi < NG) {
+        const float* a = P.A + i + (int64_t)(4 * gi) * P.lda;
         x.x = __ldcs(a);
         x.y = __ldcs(a + P.lda);
         x.z = __ldcs(a + 2 * P.lda);
         x.w = __ldcs(a + 3 * P.lda);
       }
-      v[q] = x;
+      g.v[q] = x;
     }
-    float vb = 0.f;
-    if (HAS_B && warp == kCsWarps - 1) vb = row_ok ? (float)__ldcs(P.b + i) : 0.f;
-    if (warp == 0) sm.hz[buf][lane] = row_ok ? draw(P.key, (uint64_t)i) : 0ull;
+    g.vb = 0.f;
+    if (HAS_B && warp == kCsWarps - 1) g.vb = row_ok ? (float)__ldcs(P.b + i) : 0.f;
+    g.zr = 0ull;
+    if (warp == 0) g.zr = row_ok ? draw(P.key, (uint64_t)i) : 0ull;
+  }
+  __device__ __forceinline__ static void store(const Regs& g, int buf, Smem& sm) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
     for (int q = 0; q < QG; ++q) {
-      const int g = warp + q * kCsWarps;
-      if (g < NG) *reinterpret_cast<float4*>(&sm.tiles[buf][lane][4 * g]) = v[q];
+      const int gi = warp + q * kCsWarps;
+      if (gi < NG) *reinterpret_cast<float4*>(&sm.tiles[buf][lane][4 * gi]) = g.v[q];
     }
-    if (HAS_B && warp == kCsWarps - 1) sm.tiles[buf][lane][NCA] = vb;
-    __syncthreads();
-    // reduction phase: RPI rows per warp instruction, row groups spread over warps
+    if (HAS_B && warp == kCsWarps - 1) sm.tiles[buf][lane][NCA] = g.vb;
+    if (warp == 0) sm.hz[buf][lane] = g.zr;
+  }
+  // reduction phase: RPI rows per warp instruction, row groups spread over warps
+  __device__ __forceinline__ static void reduce(const CsParams<float>& P, int64_t i0, int buf,
+                                                Smem& sm) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
     for (int r0 = warp * RPI; r0 < kCsRows; r0 += kCsWarps * RPI) {
       const int r = r0 + lane / LPR;
@@ -429,15 +441,39 @@ struct CsF32Tile {
       }
     }
   }
+  // One 32-row tile starting at row i0 of problem P into buffer `buf`.
+  __device__ __forceinline__ static void run(const CsParams<float>& P, int64_t i0, int buf,
+                                             Smem& sm) {
+    Regs g;
+    load(P, i0, g);
+    store(g, buf, sm);
+    __syncthreads();
+    reduce(P, i0, buf, sm);
+  }
 };
 
-template <int NCA, bool HAS_B>
+// PF: the next tile's loads are issued right after the barrier (see
+// cs_fixed_f64_kernel).  Knob "cs.f32.prefetch": 1 on, 0 off, unset = on at
+// 128 columns only (measured +3% there, -2% at 256, -15% at 16).
+template <int NCA, bool HAS_B, bool PF>
 __global__ void __launch_bounds__(kCsThreads) cs_fixed_f32_kernel(const CsParams<float> P) {
-  __shared__ __align__(16) typename CsF32Tile<NCA, HAS_B>::Smem sm;
+  using Tl = CsF32Tile<NCA, HAS_B>;
+  __shared__ __align__(16) typename Tl::Smem sm;
   const int64_t ntiles = (P.d + kCsRows - 1) / kCsRows;
   int buf = 0;
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, buf ^= 1)
-    CsF32Tile<NCA, HAS_B>::run(P, t * kCsRows, buf, sm);
+  if (!PF) {
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, buf ^= 1)
+      Tl::run(P, t * kCsRows, buf, sm);
+    return;
+  }
+  typename Tl::Regs g;
+  if ((int64_t)blockIdx.x < ntiles) Tl::load(P, (int64_t)blockIdx.x * kCsRows, g);
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, buf ^= 1) {
+    Tl::store(g, buf, sm);
+    __syncthreads();
+    if (t + gridDim.x < ntiles) Tl::load(P, (t + gridDim.x) * kCsRows, g);
+    Tl::reduce(P, t * kCsRows, buf, sm);
+  }
 }
 
 // Batched form: many problems of the same width in one persistent launch.
@@ -526,11 +562,16 @@ static int cs_fixed_chunk(const CsParams<T>& P, cudaStream_t st, int* rc) {
   } else {
     // v4 reductions need 16-byte aligned Y rows
     if ((P.ldy % 4) != 0 || (reinterpret_cast<uintptr_t>(P.Y) & 15) != 0) return 0;
-#define MSK_FIX32(N)                                                          \
-  if (nca == N) {                                                             \
-    *rc = hb ? launch_fixed(cs_fixed_f32_kernel<N, true>, P, st)              \
-             : launch_fixed(cs_fixed_f32_kernel<N, false>, P, st);            \
-    return 1;                                                                 \
+    const long long pf32 = tune_get("cs.f32.prefetch", -1);
+#define MSK_FIX32(N)                                                                  \
+  if (nca == N) {                                                                     \
+    if (pf32 > 0 || (pf32 < 0 && N == 128))                                           \
+      *rc = hb ? launch_fixed(cs_fixed_f32_kernel<N, true, true>, P, st)              \
+               : launch_fixed(cs_fixed_f32_kernel<N, false, true>, P, st);            \
+    else                                                                              \
+      *rc = hb ? launch_fixed(cs_fixed_f32_kernel<N, true, false>, P, st)             \
+               : launch_fixed(cs_fixed_f32_kernel<N, false, false>, P, st);           \
+    return 1;                                                                         \
   }
     MSK_FIX32(16) MSK_FIX32(32) MSK_FIX32(64) MSK_FIX32(128) MSK_FIX32(256)
 #undef MSK_FIX32
