@@ -1,0 +1,79 @@
+"""Parity at the configurations' full sizes, in the launch configurations the
+benchmark and the served path use, on what the oracle computes in seconds:
+
+* A 4194304 x 64 FP32 (N(0,1)): the whole multisketch Z (CountSketch to
+  k = 8192, split-BF16 tensor-core Gaussian stage to p = 256) against the
+  oracle's sketch of the same A, within the precision bound of the tensor
+  path plus the FP32 CountSketch tolerance;
+* A 8388608 x 128 FP64, sigma 1 -> 1e-6: FP64 sketch-and-solve with the same
+  S and G as the oracle, relative residual within 1e-8 of the oracle's;
+* A 16777216 x 256 FP32, sigma 1 -> 1e-8: the refined mixed-precision solve
+  converges; the relative residual it reports is the one the oracle
+  recomputes (FP64, compensated) for the returned x; it is not above FP64
+  sketch-and-solve of the same request.  (The exact minimiser of a 16 GiB
+  problem is out of the oracle's reach; its two-sided check runs at the
+  smaller sizes of test_gpu_lstsq.py and test_gpu_batch.py.)
+"""
+import numpy as np
+import pytest
+import torch
+
+import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def msk():
+    import paper_2508_14209_gb300 as m
+    from paper_2508_14209_gb300 import build
+
+    assert torch.cuda.is_available()
+    build.build()
+    m.load()
+    return m
+
+
+def test_multisketch_f32_full_size_bf16x3(msk, orc):
+    d, n, k, p, seed = 1 << 22, 64, 8192, 256, 0x5EED0002
+    A = inputs.normal_matrix(d, n, seed, dtype=torch.float32, device="cuda")
+    Z = msk.ms_sketch(A, k, p, seed, gemm_prec=msk.GEMM_BF16X3).cpu().numpy()
+    An = A.cpu().numpy()
+    del A
+    Zo, Gu, Yu = orc.multisketch(An, k, p, seed, gemm_prec="bf16x3")
+    _, absY, cnt = orc.countsketch_buckets(An, k, seed, np.arange(k))
+    assert cnt.sum() == d
+    bound = (3 * k + 2) * 2.0 ** -24 * (np.abs(Gu) @ np.abs(Yu)) + np.abs(Gu) @ (2e-5 * absY)
+    assert np.all(np.abs(Z - Zo) <= bound)
+
+
+def test_sns_f64_full_size(msk, orc):
+    d, n, k, p, seed = 1 << 23, 128, 32768, 512, 0x5EED0003
+    A, b, _ = inputs.ls_problem(d, n, -6, seed=seed, dtype=torch.float64, device="cuda")
+    x, info, rc = msk.ms_lstsq(A, b, k, p, seed, msk.GEMM_F64)
+    assert rc == 0
+    An, bn = A.cpu().numpy(), b.cpu().numpy()
+    del A, b
+    torch.cuda.empty_cache()
+    xo, ro, _ = orc.sns_lstsq(An, bn, k, p, seed, "f64")
+    rg = orc.relres(An, bn, x.cpu().numpy())
+    assert abs(rg - ro) <= 1e-8 * ro
+    assert abs(info["relres"] - rg) <= 1e-10 * rg
+
+
+def test_refined_f32_full_size(msk, orc):
+    d, n, k, p, seed = 1 << 24, 256, 131072, 1024, 0x5EED0004
+    A, b, _ = inputs.ls_problem(d, n, -8, seed=seed, dtype=torch.float32, device="cuda")
+    x, info, rc = msk.ms_lstsq(A, b, k, p, seed, msk.GEMM_BF16X3, refine=True, tol=1e-10,
+                               max_iter=10)
+    assert rc == 0 and info["converged"] == 1, info
+    x64, info64, rc64 = msk.ms_lstsq(A, b, k, p, seed, msk.GEMM_F64)
+    assert rc64 == 0
+    An, bn = A.cpu().numpy(), b.cpu().numpy()
+    del A, b
+    torch.cuda.empty_cache()
+    rg = orc.relres(An, bn, x.cpu().numpy())
+    assert abs(info["relres"] - rg) <= 1e-10 * rg
+    r64 = orc.relres(An, bn, x64.cpu().numpy())
+    assert rg <= (1 + 1e-8) * r64
+    assert info["relres"] < info["relres_sns"]
