@@ -98,14 +98,14 @@ __device__ __forceinline__ void qr_cluster_body(double* __restrict__ W, int m, i
 // in its shared memory for the whole factorisation.
 //   step j: the owner of column j forms the reflector v = x + sign(x0)||x|| e0,
 //     tau = 2 / v^T v from ||x||^2, which the warp that last updated column j
-//     accumulated on the way (no block reduction); it publishes (v0, tau) and
-//     writes R_jj into row j of its column.  Rows > j of that column are v's
-//     tail and never change again.
-//   one cluster barrier; every CTA copies v's tail from the owner's column
-//     through distributed shared memory (the copies spread over all CTAs'
-//     threads) and applies the reflector to its owned columns > j, one warp
-//     per column; the warp that updates column j + 1 also sums its new
-//     squares below row j.
+//     accumulated on the way (no block reduction); it writes v into W's
+//     column j in global memory (that column is only a broadcast slot until
+//     the final write-back), publishes tau, and writes R_jj into row j of its
+//     own copy.
+//   one cluster barrier; every CTA reads v from L2 (an L1-bypassing copy is
+//     faster than a pull through distributed shared memory) and applies the
+//     reflector to its owned columns > j, one warp per column; the warp that
+//     updates column j + 1 also sums its new squares below row j.
 // (v0, tau) use two slots alternating by step: slot j & 1 is rewritten at step
 // j + 2, after every CTA has passed the barrier of step j + 1.  The factor
 // goes back to W at the end, zeros below the diagonal.
@@ -147,23 +147,27 @@ __device__ __forceinline__ void qr_cluster_smem_body(double* __restrict__ W, int
   for (int j = 0; j < steps; ++j) {
     const int owner = j % CL, slot = j & 1;
     __syncthreads();  // column j and its norm are final; vl is free
-    if (rank == owner && threadIdx.x == 0) {
+    if (rank == owner) {
       double* x = cols + (size_t)(j / CL) * m;
-      const double norm2 = cnorm[j / CL];
-      const double x0 = x[j];
-      const double alpha = sqrt(norm2);
-      const double sgn = x0 >= 0.0 ? 1.0 : -1.0;
-      const double v0 = x0 + sgn * alpha;
-      const double vtv = norm2 - x0 * x0 + v0 * v0;
-      vsc[slot][0] = v0;
-      vsc[slot][1] = vtv > 0.0 ? 2.0 / vtv : 0.0;
-      x[j] = -sgn * alpha;
+      double* gcol = W + (int64_t)j * ldw;  // W's column j: a broadcast slot until write-back
+      if (threadIdx.x == 0) {
+        const double norm2 = cnorm[j / CL];
+        const double x0 = x[j];
+        const double alpha = sqrt(norm2);
+        const double sgn = x0 >= 0.0 ? 1.0 : -1.0;
+        const double v0 = x0 + sgn * alpha;
+        const double vtv = norm2 - x0 * x0 + v0 * v0;
+        gcol[j] = v0;
+        vsc[slot][1] = vtv > 0.0 ? 2.0 / vtv : 0.0;
+        x[j] = -sgn * alpha;
+      }
+      for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) gcol[i] = x[i];
+      __threadfence();
     }
     cluster.sync();
-    const double* ox = cluster.map_shared_rank(cols + (size_t)(j / CL) * m, owner);
-    const double* osc = cluster.map_shared_rank(&vsc[slot][0], owner);
-    for (int i = j + threadIdx.x; i < m; i += blockDim.x) vl[i] = (i == j) ? osc[0] : ox[i];
-    const double tau = osc[1];
+    const double* gv = W + (int64_t)j * ldw;
+    for (int i = j + threadIdx.x; i < m; i += blockDim.x) vl[i] = __ldcg(gv + i);
+    const double tau = *cluster.map_shared_rank(&vsc[slot][1], owner);
     __syncthreads();
     // owned columns > j: local index from the first one after j
     const int lj0 = (j + CL - rank) / CL;
