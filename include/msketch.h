@@ -114,6 +114,19 @@ const char *msk_version(void);
  * storage, empty when none). */
 const char *msk_last_error(void);
 
+/* Synchronises `stream` (a cudaStream_t, NULL = legacy default stream) and
+ * reports whether a tensor-core Gaussian-stage kernel (the library's
+ * mbarrier-pipelined kernels) gave up a bounded wait since the previous
+ * call: MSK_ETIMEOUT (the results of that launch are not valid), else
+ * MSK_OK.  Clears the record.  MSK_ECUDA if synchronising fails. */
+int msk_take_timeout(void *stream);
+
+/* Test hook for the bounded waits: launches one CTA whose thread waits, with
+ * the pipelined kernels' bounded wait (1 s), on an mbarrier that nothing
+ * arrives on; the wait expires and records a timeout that msk_take_timeout
+ * then reports.  Returns the launch status (MSK_OK or MSK_ECUDA). */
+int msk_selftest_wait(void *stream);
+
 /* ---- Tuning registry (set by the autotuner, read by the launchers) ------- */
 
 /* Named integer knobs that the launchers read (unset = launcher default):

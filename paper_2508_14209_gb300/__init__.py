@@ -31,7 +31,7 @@ GEMM_PRECS = {"f64": GEMM_F64, "f32": GEMM_F32, "bf16": GEMM_BF16, "f16": GEMM_F
               "bf16x3": GEMM_BF16X3}
 
 # Names of every function include/msketch.h declares (checked by the tests).
-EXPORTS = ("msk_version", "msk_last_error", "cs_hash", "ms_gaussian", "msk_cs_workspace",
+EXPORTS = ("msk_version", "msk_last_error", "msk_take_timeout", "msk_selftest_wait", "cs_hash", "ms_gaussian", "msk_cs_workspace",
            "cs_sketch", "msk_ms_workspace", "ms_sketch", "msk_gemm_workspace", "msk_gemm",
            "msk_householder_qr", "msk_trsv_upper", "msk_lstsq_workspace", "ms_lstsq",
            "msk_ne_workspace", "ne_lstsq", "msk_gemm_noalloc", "msk_tune_set", "msk_tune_get",
@@ -83,6 +83,8 @@ def _declare(L):
     sig = {
         "msk_version": (ctypes.c_char_p, []),
         "msk_last_error": (ctypes.c_char_p, []),
+        "msk_take_timeout": (_int, [_p]),
+        "msk_selftest_wait": (_int, [_p]),
         "cs_hash": (_int, [_u64, _i64, _i64, _i64, _p, _p, _p]),
         "ms_gaussian": (_int, [_u64, _i64, _i64, _int, _p, _i64, _p]),
         "msk_cs_workspace": (_sz, [_i64, _i64, _i64, _int, _int]),
@@ -138,6 +140,17 @@ def tune_clear(name: str | None = None) -> None:
 
 def version() -> str:
     return load().msk_version().decode()
+
+
+def msk_take_timeout(stream=None) -> int:
+    """Synchronise the stream; MSK_ETIMEOUT if a pipelined kernel gave up a
+    bounded wait since the last call (the record is cleared), else MSK_OK."""
+    return int(load().msk_take_timeout(_stream(stream)))
+
+
+def msk_selftest_wait(stream=None) -> None:
+    """Launch the bounded-wait test kernel (its wait expires after 1 s)."""
+    _check("msk_selftest_wait", load().msk_selftest_wait(_stream(stream)))
 
 
 def _check(fn, rc, ok=(MSK_OK,)):

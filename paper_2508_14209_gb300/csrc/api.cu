@@ -102,6 +102,15 @@ const char* msk_version(void) { return "msketch 0.1 (sm_103a)"; }
 
 const char* msk_last_error(void) { return g_last_error; }
 
+int msk_take_timeout(void* stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return tc_take_timeout(st);
+}
+
+int msk_selftest_wait(void* stream) {
+  return launch_tc_wait_selftest(static_cast<cudaStream_t>(stream));
+}
+
 int cs_hash(uint64_t seed, int64_t i0, int64_t count, int64_t k, uint32_t* h, int8_t* s,
             void* stream) {
   if (count < 0) return -3;

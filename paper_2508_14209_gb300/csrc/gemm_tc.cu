@@ -457,18 +457,6 @@ size_t tc_gemm_workspace(int64_t p, int64_t k, int64_t ncol, int prec) {
   return nd.used;
 }
 
-static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
-    void* ptr = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
-                                         &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
-  }
-  return fn;
-}
 
 int launch_tc_gemm(uint64_t gkey, int64_t p, int64_t k, int64_t ncol, const float* Y, int64_t ldy,
                    int prec, double* Z, int64_t ldz, void* ws, size_t ws_bytes, cudaStream_t st) {
@@ -493,7 +481,7 @@ int launch_tc_gemm(uint64_t gkey, int64_t p, int64_t k, int64_t ncol, const floa
       split_transpose_kernel<1, false><<<grid, 256, 0, st>>>(Y, ldy, k, (int)ncol, t.npad, t.kpitch, Yt);
     MSK_CHECK_LAUNCH("split_transpose_kernel");
   }
-  auto enc = encode_fn();
+  auto enc = tensor_map_encoder();
   if (!enc) {
     set_error_text("cuTensorMapEncodeTiled entry point not available");
     return MSK_ECUDA;
@@ -583,7 +571,7 @@ void tc_ds_shape(int64_t p, int64_t k, int64_t ncol, int kt_per, TcShape* s) {
 // of npad x k bf16).
 int tc_ds_make_job(int64_t p, int64_t k, int64_t ncol, const TcShape& s, const void* G,
                    const void* Yt, double* part, int item_begin, TcJob* job) {
-  auto enc = encode_fn();
+  auto enc = tensor_map_encoder();
   if (!enc) {
     set_error_text("cuTensorMapEncodeTiled entry point not available");
     return MSK_ECUDA;
@@ -634,6 +622,24 @@ int launch_tc_ds_batch(const TcJob* jobs, int njobs, int total_items, int max_nt
   MSK_ALLOW_SMEM(tc_gemm_ds_batch_kernel);
   tc_gemm_ds_batch_kernel<<<total_items, kDsThreads, smem, st>>>(jobs, njobs, stages);
   MSK_CHECK_LAUNCH("tc_gemm_ds_batch_kernel");
+  return MSK_OK;
+}
+
+// Test hook: a wait on an mbarrier that nothing arrives on, through the same
+// bounded wait as the pipelined kernels; it expires and sets g_tc_timeout.
+__global__ void tc_wait_selftest_kernel() {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_wait(smem_u32(&bar), 0, &g_tc_timeout);
+}
+
+int launch_tc_wait_selftest(cudaStream_t st) {
+  tc_wait_selftest_kernel<<<1, 32, 0, st>>>();
+  MSK_CHECK_LAUNCH("tc_wait_selftest_kernel");
   return MSK_OK;
 }
 

@@ -138,6 +138,7 @@ int tc_ds_make_job(int64_t p, int64_t k, int64_t ncol, const TcShape& s, const v
                    const void* Yt, double* part, int item_begin, TcJob* job);
 int launch_tc_ds_batch(const TcJob* jobs, int njobs, int total_items, int max_nt, cudaStream_t st);
 int tc_take_timeout(cudaStream_t st);
+int launch_tc_wait_selftest(cudaStream_t st);
 // gemm_tc.cu (tcgen05 tensor-core Gaussian stage)
 size_t tc_gemm_workspace(int64_t p, int64_t k, int64_t ncol, int prec);
 int launch_tc_gemm(uint64_t gkey, int64_t p, int64_t k, int64_t ncol, const float* Y, int64_t ldy,

@@ -43,6 +43,7 @@ def test_tensor_gemm_matches_oracle(msk, orc, prec, p, k, ncol):
         Gu, Yu = orc.round_bf16(G), orc.split_bf16x3(Y.numpy())
     Gu, Yu = Gu.astype(np.float64), Yu.astype(np.float64)
     Zo = orc.gemm(Gu, Yu)
+    assert msk.msk_take_timeout() == msk.MSK_OK  # no bounded wait gave up
     parts = 3 if prec == "bf16x3" else 1
     bound = (parts * k + 2) * 2.0 ** -24 * (np.abs(Gu) @ np.abs(Yu))
     assert np.all(np.abs(Zg - Zo) <= bound)
@@ -85,3 +86,16 @@ def test_refined_bf16x3_reaches_minimiser(msk, orc, d, n, lsig):
     assert abs(rg - ro) <= 1e-8 * ro
     _, r_sns64, _ = orc.sns_lstsq(An.astype(np.float64), bn, k, p, seed, "f64")
     assert rg <= (1 + 1e-8) * r_sns64
+
+
+def test_bounded_wait_expires_and_is_reported(msk):
+    """An mbarrier wait that nothing completes gives up after its limit (1 s),
+    records a timeout that msk_take_timeout reports once, and leaves the
+    context usable."""
+    assert msk.msk_take_timeout() == msk.MSK_OK
+    msk.msk_selftest_wait()
+    assert msk.msk_take_timeout() == msk.MSK_ETIMEOUT
+    assert msk.msk_take_timeout() == msk.MSK_OK  # the record was cleared
+    Y = torch.randn(1024, 9, dtype=torch.float32, device="cuda")
+    Z = msk.msk_gemm(5, 32, Y, gemm_prec=msk.GEMM_BF16)
+    assert torch.isfinite(Z).all() and msk.msk_take_timeout() == msk.MSK_OK
