@@ -88,6 +88,13 @@ typedef enum {
  *            increasing row order: deterministic, bitwise reproducible. */
 typedef enum { MSK_CS_ATOMIC = 0, MSK_CS_SORTED = 1 } msk_cs_strategy;
 
+/* Sketch of a sketch-and-solve (Section 6.3 compares the three):
+ *   MULTI : S = G C, CountSketch C to k rows then Gaussian G to p rows;
+ *   COUNT : S = C alone (k rows; the QR is of a k x (n+1) matrix);
+ *   GAUSS : S = G alone, a p x d Gaussian with the entries of the
+ *           multisketch's G at k = d (generated inside the product). */
+typedef enum { MSK_SKETCH_MULTI = 0, MSK_SKETCH_COUNT = 1, MSK_SKETCH_GAUSS = 2 } msk_sketch_kind;
+
 #define MSK_OK 0
 #define MSK_ENOCONV 1001  /* refinement stopped at max_iter (x is returned) */
 #define MSK_ENOMEM 1002   /* ws too small, or a request over the memory budget */
@@ -228,8 +235,9 @@ int msk_gemm(uint64_t seed, int64_t p, int64_t k, int64_t ncol, const void *Y,
  * R[j][j] = -sign(x_0) ||x|| (sign(0) = +1), the GeQRF step of Section 6.1;
  * the strictly lower part is overwritten with zeros.  One thread-block
  * cluster of up to 16 CTAs factors the matrix with the columns split across
- * the CTAs' shared memory.  Limits: m <= 2048, c <= 512.
- * Errors: -2 m < c or m > 2048, -3 c < 1 or c > 512, -4 ldw < m. */
+ * the CTAs' shared memory (or, when they do not fit, in place in global
+ * memory).  Limits: m < 2^31, c <= 512.
+ * Errors: -2 m < c or m >= 2^31, -3 c < 1 or c > 512, -4 ldw < m. */
 int msk_householder_qr(double *W, int64_t m, int64_t c, int64_t ldw,
                        void *stream);
 
@@ -307,6 +315,64 @@ size_t msk_ne_workspace(int64_t d, int64_t n);
 int ne_lstsq(const double *A, int64_t d, int64_t n, int64_t lda,
              const double *b, double *x, void *ws, size_t ws_bytes,
              void *stream);
+
+/* ---- Sketch-and-solve with one of the three sketches (Section 6.3) ------- */
+
+/* Scratch bytes of sns_lstsq. */
+size_t msk_sns_workspace(int64_t d, int64_t n, int kind, int64_t k, int64_t p,
+                         int dtype);
+
+/* Sketch-and-solve least squares (Algorithm 1) in FP64 with the sketch
+ * `kind` (msk_sketch_kind): W = S [A b]; Householder QR of W; x = R11^{-1}
+ * R[0:n, n].  MULTI is ms_lstsq with MSK_GEMM_F64 and no refinement.
+ * COUNT uses k (>= n+1; p is ignored): the FP64 CountSketch of [A b] (FP32
+ * A widened exactly), transposed to column-major for the QR.  GAUSS uses p
+ * (n+1 <= p <= 2048; k is ignored).  A, b, x, info and the return codes as
+ * ms_lstsq (n <= 400); -7 unknown kind, -8 bad k (COUNT), -9 bad p (GAUSS).
+ * info (optional, host): relres of x; relres_sns = relres. */
+int sns_lstsq(const void *A, int dtype, int64_t d, int64_t n, int64_t lda,
+              const double *b, int kind, int64_t k, int64_t p, uint64_t seed,
+              double *x, msk_lstsq_info *info, void *ws, size_t ws_bytes,
+              void *stream);
+
+/* ---- Randomized Cholesky QR (Section 6.3, Algorithms 4 and 5) ----------- */
+
+/* Scratch bytes of rcq_lstsq (want_q = 0) or rcq_qr (want_q = 1). */
+size_t msk_rcq_workspace(int64_t d, int64_t n, int64_t k, int64_t p, int dtype,
+                         int gemm_prec, int want_q);
+
+/* rand_cholQR least squares (Algorithm 5) with the multisketch S = G C of
+ * ms_sketch (CountSketch to k rows, Gaussian to p rows, gemm_prec as there):
+ *   Y = S A;  R0 = R of the Householder QR of Y;  Q0 = A R0^{-1} (formed in
+ *   FP64 through the explicit R0^{-1});  G = Q0^T Q0, z = Q0^T b (one pass);
+ *   R1 = chol(G);  R = R1 R0;  y = R1^{-T} z;  x = R^{-1} y.
+ * x is the least-squares minimiser with no sketching distortion, for
+ * kappa(A) < 1/u.  Arguments and layouts as ms_lstsq (A FP64 or FP32 values,
+ * column-major d x n, lda >= d; b, x device double); n <= 400,
+ * n + 1 <= p <= min(k, 2048).  Needs d x n doubles of workspace for Q0.
+ * info (optional, host): relres of x (an FP64 residual pass), iters = 0,
+ * converged = 1, relres_sns = -1.  Synchronises `stream`.
+ * Returns MSK_OK; -i for argument i; j+1 when R0[j][j] is zero or pivot j of
+ * chol(G) is not positive (x is then NaN); MSK_ENOMEM / MSK_ENOTSUP / MSK_ECUDA
+ * as ms_lstsq. */
+int rcq_lstsq(const void *A, int dtype, int64_t d, int64_t n, int64_t lda,
+              const double *b, int64_t k, int64_t p, uint64_t seed, int gemm_prec,
+              double *x, msk_lstsq_info *info, void *ws, size_t ws_bytes,
+              void *stream);
+
+/* rand_cholQR (Algorithm 4): the QR factorisation A = Q R from the sketch's
+ * R0 and one Cholesky step: Q0 = A R0^{-1}, R1 = chol(Q0^T Q0),
+ * Q = Q0 R1^{-1}, R = R1 R0.
+ *   Q : device double column-major d x n (ldq >= d), written; it may be A
+ *       itself when A is FP64 with lda == ldq (factorisation in place);
+ *   R : device double column-major n x n (ldr >= n), upper triangular
+ *       (zeros below the diagonal); the signs of its diagonal are those of
+ *       the Householder R0 of the sketch.
+ * Other arguments as rcq_lstsq.  Synchronises `stream`.  Returns MSK_OK, -i,
+ * or j+1 when R0[j][j] is zero or pivot j of chol(Q0^T Q0) is not positive. */
+int rcq_qr(const void *A, int dtype, int64_t d, int64_t n, int64_t lda, int64_t k,
+           int64_t p, uint64_t seed, int gemm_prec, double *Q, int64_t ldq,
+           double *R, int64_t ldr, void *ws, size_t ws_bytes, void *stream);
 
 /* ---- Batched solves (many uneven problems per launch) -------------------- */
 

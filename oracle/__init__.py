@@ -23,6 +23,13 @@ Parity status of each function (what pins it, see tests/test_oracle_*.py):
   ne_lstsq             agrees with QR when well conditioned, fails for
                        kappa > 1e8 (Section 6.3)
   refine               converges to the exact LS minimiser
+  sns_lstsq_count/     exact recovery for b = A x, distortion bound, E||S y||^2
+    _gauss             = ||y||^2 (sketch scaling), same minimiser class as
+                       sns_lstsq
+  rand_cholqr          Q^T Q = I, Q R = A, |R| against LAPACK's QR of A
+                       (Algorithm 4)
+  rand_cholqr_lstsq    the exact LS minimiser (Algorithm 5), at kappa up to
+                       1e10 where the normal equations fail
 """
 from __future__ import annotations
 
@@ -376,6 +383,76 @@ def sns_lstsq(A, b, k: int, p: int, seed: int, gemm_prec: str = "f64"):
     (x, relres, R) with R the (n+1) x (n+1) factor of [SA Sb]."""
     Z, _, _ = multisketch(A, k, p, seed, b=b, gemm_prec=gemm_prec)
     x, R = lstsq_from_sketch(Z)
+    return x, relres(A, b, x), R
+
+
+# --------------------------------------------------------------------------
+# Randomized Cholesky QR (Section 6.3, Algorithms 4 and 5).
+
+def _right_solve_upper(X, U):
+    """X U^{-1} for upper-triangular U (a triangular solve per row of X)."""
+    import scipy.linalg
+
+    return scipy.linalg.solve_triangular(np.asarray(U, dtype=np.float64),
+                                         np.asarray(X, dtype=np.float64).T,
+                                         trans="T", lower=False).T
+
+
+def rand_cholqr(A, k: int, p: int, seed: int, gemm_prec: str = "f64"):
+    """Algorithm 4 with the multisketch S = G C: Y = S A; R0 = R of the
+    economy QR of Y (Householder, as householder_r); Q0 = A R0^{-1};
+    G = Q0^T Q0; R1 = chol(G); Q = Q0 R1^{-1}; R = R1 R0.
+    Returns (Q, R, info) with info = j+1 when pivot j of chol(G) is not
+    positive (Q and R are then None)."""
+    A64 = np.asarray(A, dtype=np.float64)
+    Y, _, _ = multisketch(A, k, p, seed, gemm_prec=gemm_prec)
+    R0 = householder_r(Y)
+    Q0 = _right_solve_upper(A64, R0)
+    R1, info = cholesky_upper(Q0.T @ Q0)
+    if info:
+        return None, None, info
+    Q = _right_solve_upper(Q0, R1)
+    return Q, np.triu(R1 @ R0), 0
+
+
+def rand_cholqr_lstsq(A, b, k: int, p: int, seed: int, gemm_prec: str = "f64"):
+    """Algorithm 5: Y = S A; R0 from qr(Y); Q0 = A R0^{-1}; G = Q0^T Q0 and
+    z = Q0^T b; R1 = chol(G); R = R1 R0; y = R1^{-T} z; x = R^{-1} y.
+    Returns (x, info); x is NaN when chol(G) fails (info = j+1)."""
+    A64 = np.asarray(A, dtype=np.float64)
+    bb = np.asarray(b, dtype=np.float64)
+    Y, _, _ = multisketch(A, k, p, seed, gemm_prec=gemm_prec)
+    R0 = householder_r(Y)
+    Q0 = _right_solve_upper(A64, R0)
+    R1, info = cholesky_upper(Q0.T @ Q0)
+    if info:
+        return np.full(A64.shape[1], np.nan), info
+    z = Q0.T @ bb
+    R = np.triu(R1 @ R0)
+    y = forward_substitution_transposed(R1, z)
+    return back_substitution(R, y), 0
+
+
+def sns_lstsq_count(A, b, k: int, seed: int):
+    """Algorithm 1 with S = C alone: the k x d CountSketch (Definition 3) of
+    [A b], then the Householder QR and triangular solve of the k x (n+1)
+    result.  Returns (x, relres, R)."""
+    W = countsketch(A, k, seed, b)
+    x, R = lstsq_from_sketch(W)
+    return x, relres(A, b, x), R
+
+
+def gaussian_sketch(A, p: int, seed: int, b=None) -> np.ndarray:
+    """G [A b] for the p x d Gaussian sketch (Section 1) whose entries are the
+    multisketch's Gaussian at k = d: gaussian(seed, p, d)."""
+    A64 = np.asarray(A, dtype=np.float64)
+    X = A64 if b is None else np.hstack([A64, np.asarray(b, dtype=np.float64).reshape(-1, 1)])
+    return gemm(gaussian(seed, p, A64.shape[0]).astype(np.float64), X)
+
+
+def sns_lstsq_gauss(A, b, p: int, seed: int):
+    """Algorithm 1 with S = G alone (p x d Gaussian).  Returns (x, relres, R)."""
+    x, R = lstsq_from_sketch(gaussian_sketch(A, p, seed, b))
     return x, relres(A, b, x), R
 
 

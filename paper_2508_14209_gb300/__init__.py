@@ -34,7 +34,9 @@ GEMM_PRECS = {"f64": GEMM_F64, "f32": GEMM_F32, "bf16": GEMM_BF16, "f16": GEMM_F
 EXPORTS = ("msk_version", "msk_last_error", "msk_take_timeout", "msk_selftest_wait", "cs_hash", "ms_gaussian", "msk_cs_workspace",
            "cs_sketch", "msk_ms_workspace", "ms_sketch", "msk_gemm_workspace", "msk_gemm",
            "msk_householder_qr", "msk_trsv_upper", "msk_lstsq_workspace", "ms_lstsq",
-           "msk_ne_workspace", "ne_lstsq", "msk_gemm_noalloc", "msk_tune_set", "msk_tune_get",
+           "msk_ne_workspace", "ne_lstsq", "msk_rcq_workspace", "rcq_lstsq", "rcq_qr",
+           "msk_sns_workspace", "sns_lstsq",
+           "msk_gemm_noalloc", "msk_tune_set", "msk_tune_get",
            "msk_tune_clear", "msk_batch_workspace", "msk_batch_lstsq", "ms_server_create",
            "ms_server_submit", "ms_server_poll", "ms_server_wait_all", "ms_server_stats",
            "ms_server_destroy", "ms_server_error", "msk_autotune_workspace", "msk_autotune")
@@ -105,6 +107,14 @@ def _declare(L):
                             _p, ctypes.POINTER(LstsqInfo), _p, _sz, _p]),
         "msk_ne_workspace": (_sz, [_i64, _i64]),
         "ne_lstsq": (_int, [_p, _i64, _i64, _i64, _p, _p, _p, _sz, _p]),
+        "msk_rcq_workspace": (_sz, [_i64, _i64, _i64, _i64, _int, _int, _int]),
+        "msk_sns_workspace": (_sz, [_i64, _i64, _int, _i64, _i64, _int]),
+        "sns_lstsq": (_int, [_p, _int, _i64, _i64, _i64, _p, _int, _i64, _i64, _u64, _p, _p, _p, _sz,
+                             _p]),
+        "rcq_lstsq": (_int, [_p, _int, _i64, _i64, _i64, _p, _i64, _i64, _u64, _int, _p, _p, _p, _sz,
+                             _p]),
+        "rcq_qr": (_int, [_p, _int, _i64, _i64, _i64, _i64, _i64, _u64, _int, _p, _i64, _p, _i64, _p,
+                          _sz, _p]),
         "msk_batch_workspace": (_sz, [ctypes.POINTER(BatchItem), _int, _int]),
         "ms_server_create": (_int, [_sz, _int, _int, _int, _dbl, _i32, ctypes.POINTER(_p)]),
         "ms_server_submit": (_int, [_p, ctypes.POINTER(BatchItem), ctypes.POINTER(_u64)]),
@@ -362,6 +372,78 @@ def ne_lstsq(A, b, x=None, ws=None, stream=None):
     if rc < 0 or rc >= 1000:
         _check("ne_lstsq", rc)
     return x, rc
+
+
+SKETCH_MULTI, SKETCH_COUNT, SKETCH_GAUSS = 0, 1, 2
+
+
+def msk_sns_workspace(d, n, kind, k, p, dtype):
+    return load().msk_sns_workspace(d, n, kind, k, p, dtype)
+
+
+def sns_lstsq(A, b, kind, k, p, seed, x=None, ws=None, stream=None):
+    """FP64 sketch-and-solve with S = G C (SKETCH_MULTI), C alone
+    (SKETCH_COUNT, k rows) or G alone (SKETCH_GAUSS, p rows); returns
+    (x, info dict, status)."""
+    _cuda(A, "A"), _cuda(b, "b")
+    d, n = A.shape
+    dt = _dtype_code(A)
+    if x is None:
+        x = torch.empty(n, dtype=torch.float64, device=A.device)
+    if ws is None:
+        ws = workspace(msk_sns_workspace(d, n, kind, k, p, dt), A.device)
+    info = LstsqInfo()
+    rc = load().sns_lstsq(_ptr(A), dt, d, n, _colmajor(A), _ptr(b), kind, k, p, seed & (2**64 - 1),
+                          _ptr(x), ctypes.byref(info), _ptr(ws), ws.numel(), _stream(stream))
+    if rc < 0 or rc >= 1000:
+        _check("sns_lstsq", rc)
+    return x, {"iters": info.iters, "converged": info.converged, "relres": info.relres,
+               "relres_sns": info.relres_sns}, rc
+
+
+def msk_rcq_workspace(d, n, k, p, dtype, gemm_prec, want_q=False):
+    return load().msk_rcq_workspace(d, n, k, p, dtype, gemm_prec, int(bool(want_q)))
+
+
+def rcq_lstsq(A, b, k, p, seed, gemm_prec=GEMM_F64, x=None, ws=None, stream=None):
+    """rand_cholQR least squares (Algorithm 5); returns (x, info dict, status).
+    status j+1 > 0: R0[j][j] == 0 or pivot j of chol(Q0^T Q0) not positive
+    (x is NaN)."""
+    _cuda(A, "A"), _cuda(b, "b")
+    d, n = A.shape
+    dt = _dtype_code(A)
+    if x is None:
+        x = torch.empty(n, dtype=torch.float64, device=A.device)
+    if ws is None:
+        ws = workspace(msk_rcq_workspace(d, n, k, p, dt, gemm_prec), A.device)
+    info = LstsqInfo()
+    rc = load().rcq_lstsq(_ptr(A), dt, d, n, _colmajor(A), _ptr(b), k, p, seed & (2**64 - 1),
+                          gemm_prec, _ptr(x), ctypes.byref(info), _ptr(ws), ws.numel(),
+                          _stream(stream))
+    if rc < 0 or rc >= 1000:
+        _check("rcq_lstsq", rc)
+    return x, {"iters": info.iters, "converged": info.converged, "relres": info.relres,
+               "relres_sns": info.relres_sns}, rc
+
+
+def rcq_qr(A, k, p, seed, gemm_prec=GEMM_F64, Q=None, R=None, ws=None, stream=None):
+    """rand_cholQR (Algorithm 4): A = Q R.  Q is d x n column-major FP64 (may
+    be A itself when A is FP64 column-major); R is n x n column-major upper
+    triangular.  Returns (Q, R, status)."""
+    _cuda(A, "A")
+    d, n = A.shape
+    dt = _dtype_code(A)
+    if Q is None:
+        Q = colmajor(d, n, torch.float64, A.device)
+    if R is None:
+        R = colmajor(n, n, torch.float64, A.device)
+    if ws is None:
+        ws = workspace(msk_rcq_workspace(d, n, k, p, dt, gemm_prec, True), A.device)
+    rc = load().rcq_qr(_ptr(A), dt, d, n, _colmajor(A), k, p, seed & (2**64 - 1), gemm_prec, _ptr(Q),
+                       _colmajor(Q), _ptr(R), _colmajor(R), _ptr(ws), ws.numel(), _stream(stream))
+    if rc < 0 or rc >= 1000:
+        _check("rcq_qr", rc)
+    return Q, R, rc
 
 
 def _batch_items(problems, xs):

@@ -3,6 +3,9 @@
     python -m paper_2508_14209_gb300.cases sketch  --d 1048576 --n 64 --dtype f64
     python -m paper_2508_14209_gb300.cases gemm    --p 1024 --k 32768 --ncol 257 --prec bf16x3
     python -m paper_2508_14209_gb300.cases refined --d 1333142 --n 128 --log10-sigma -2.7 [--path single]
+    python -m paper_2508_14209_gb300.cases ne      --d 8388608 --n 128 --log10-sigma -6
+    python -m paper_2508_14209_gb300.cases sns     --d 8388608 --n 128 --log10-sigma -6 [--kind count|gauss]
+    python -m paper_2508_14209_gb300.cases rcq     --d 8388608 --n 128 --log10-sigma -6
 
 Each case draws its seeded synthetic input once on the GPU (the generators of
 the `inputs` module), runs the library call `--reps` times and prints one JSON
@@ -25,7 +28,7 @@ def main(argv=None):
     import paper_2508_14209_gb300 as msk
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["sketch", "gemm", "refined"])
+    ap.add_argument("case", choices=["sketch", "gemm", "refined", "ne", "sns", "rcq"])
     ap.add_argument("--d", type=int, default=1 << 20)
     ap.add_argument("--n", type=int, default=64)
     ap.add_argument("--dtype", choices=["f64", "f32"], default="f64")
@@ -38,6 +41,8 @@ def main(argv=None):
     ap.add_argument("--path", choices=["batch", "single"], default="batch",
                     help="refined: msk_batch_lstsq of one request (its inner loop runs inside a "
                          "graph's while node) or ms_lstsq (the same kernels launched one by one)")
+    ap.add_argument("--kind", choices=["multi", "count", "gauss"], default="multi",
+                    help="sns: the sketch (multisketch G C, CountSketch C alone, Gaussian G alone)")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--seed", type=int, default=0x5EED0004)
     ap.add_argument("--tune", action="append", default=[], metavar="KNOB=VALUE",
@@ -67,6 +72,38 @@ def main(argv=None):
         ws = msk.workspace(msk.msk_gemm_workspace(a.p, a.k, a.ncol, prec), dev)
         call = lambda: msk.msk_gemm(a.seed, a.p, Yr, gemm_prec=prec, Z=Z, ws=ws)  # noqa: E731
         out.update(p=a.p, k=a.k, ncol=a.ncol, prec=a.prec, flops_per_call=2 * a.p * a.k * a.ncol)
+    elif a.case in ("ne", "sns", "rcq"):
+        # FP64 normal equations (Gram of [A b], Cholesky, two TRSV) or FP64
+        # multisketch sketch-and-solve (k = 2n^2, p = 4n) on the same request
+        A, b, _ = inputs.ls_problem(a.d, a.n, a.log10_sigma, seed=a.seed, dtype=torch.float64, device=dev)
+        res = {}
+        if a.case == "ne":
+            ws = msk.workspace(msk.msk_ne_workspace(a.d, a.n), dev)
+
+            def call():
+                res["r"] = {"status": msk.ne_lstsq(A, b, ws=ws)[1]}
+            out.update(flops_per_call=a.d * (a.n + 1) * (a.n + 2))  # upper triangle incl. diagonal
+        elif a.case == "rcq":
+            # rand_cholQR least squares (Algorithm 5): sketch, QR, Q0 = A R0^{-1},
+            # Gram of [Q0 b], Cholesky, two triangular solves
+            k, p = 2 * a.n * a.n, 4 * a.n
+            ws = msk.workspace(msk.msk_rcq_workspace(a.d, a.n, k, p, msk.MSK_F64, msk.GEMM_F64), dev)
+
+            def call():
+                x, info, rc = msk.rcq_lstsq(A, b, k, p, a.seed, msk.GEMM_F64, ws=ws)
+                res["r"] = dict(info, status=rc)
+            # Q0: n(n+1)/2 FMAs per row; Gram of [Q0 b]: (n+1)(n+2)/2 per row
+            out.update(flops_per_call=a.d * (a.n * (a.n + 1) + (a.n + 1) * (a.n + 2)))
+        else:
+            k, p = 2 * a.n * a.n, 4 * a.n
+            kind = {"multi": msk.SKETCH_MULTI, "count": msk.SKETCH_COUNT, "gauss": msk.SKETCH_GAUSS}[a.kind]
+            ws = msk.workspace(msk.msk_sns_workspace(a.d, a.n, kind, k, p, msk.MSK_F64), dev)
+
+            def call():
+                x, info, rc = msk.sns_lstsq(A, b, kind, k, p, a.seed, ws=ws)
+                res["r"] = dict(info, status=rc)
+            out.update(kind=a.kind)
+        out.update(d=a.d, n=a.n, log10_sigma=a.log10_sigma)
     else:
         A, b, _ = inputs.ls_problem(a.d, a.n, a.log10_sigma, seed=a.seed, dtype=torch.float32, device=dev)
         res = {}
@@ -94,7 +131,7 @@ def main(argv=None):
     ev[1].record()
     torch.cuda.synchronize()
     out["ms_per_call"] = round(ev[0].elapsed_time(ev[1]) / a.reps, 5)
-    if a.case == "refined":
+    if a.case in ("refined", "ne", "sns", "rcq"):
         out["info"] = res["r"]
     print(json.dumps(out), flush=True)
 

@@ -146,6 +146,21 @@ int cs_sketch(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, const
 
 }  // extern "C"
 
+int msk::count_sketch_f64y(const void* A, int dtype, int64_t d, int64_t n, int64_t lda,
+                           const double* b, int64_t k, uint64_t seed, double* Y, int64_t ldy,
+                           cudaStream_t st) {
+  if (dtype == MSK_F64)
+    return launch_cs_atomic(A, dtype, d, n, lda, b, (uint32_t)k, stream_key(seed, kTagHash), Y, ldy,
+                            false, st);
+  const int64_t ncol = n + (b ? 1 : 0);
+  MSK_CUDA(cudaMemset2DAsync(Y, (size_t)ldy * 8, 0, (size_t)ncol * 8, (size_t)k, st));
+  int64_t maxc = 256;
+  const int64_t fit = (int64_t)(tune_get("cs.l2_budget_bytes", 48ll << 20)) / (k * 8);
+  if (fit >= 64 && fit / 64 * 64 < maxc) maxc = fit / 64 * 64;
+  return launch_cs_f32a_f64y(static_cast<const float*>(A), d, n, lda, b, (uint32_t)k,
+                             stream_key(seed, kTagHash), Y, ldy, maxc, st);
+}
+
 int msk::cs_sketch_internal(const void* A, int dtype, int64_t d, int64_t n, int64_t lda,
                             const double* b, int64_t k, uint64_t seed, void* Y, int64_t ldy,
                             int strategy, void* ws, size_t ws_bytes, bool pad_ok,
@@ -240,12 +255,7 @@ int ms_sketch(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, const
   if (ydt == MSK_F64 && dtype == MSK_F32) {
     // FP64 sketch of the FP32-stored A
     if (strategy != MSK_CS_ATOMIC) return MSK_ENOTSUP;
-    MSK_CUDA(cudaMemset2DAsync(Y, (size_t)ldy * 8, 0, (size_t)ncol * 8, (size_t)k, st));
-    int64_t maxc = 256;
-    const int64_t fit = (int64_t)(tune_get("cs.l2_budget_bytes", 48ll << 20)) / (k * 8);
-    if (fit >= 64 && fit / 64 * 64 < maxc) maxc = fit / 64 * 64;
-    rc = launch_cs_f32a_f64y(static_cast<const float*>(A), d, n, lda, b, (uint32_t)k,
-                             stream_key(seed, kTagHash), static_cast<double*>(Y), ldy, maxc, st);
+    rc = count_sketch_f64y(A, dtype, d, n, lda, b, k, seed, static_cast<double*>(Y), ldy, st);
   } else {
     rc = cs_sketch_internal(A, dtype, d, n, lda, b, k, seed, Y, ldy, strategy, csw, cs_ws, true,
                             st);

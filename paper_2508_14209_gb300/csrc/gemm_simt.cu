@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cstdint>
 
+#include "msk_device.cuh"
 #include "msk_internal.h"
 
 namespace msk {
@@ -133,6 +134,105 @@ int launch_gemm_simt(const float* G, int64_t ldg, const void* Y, bool y_f64, int
     gemm_simt_kernel<float, float><<<grid, kGThreads, 0, st>>>(
         G, ldg, static_cast<const float*>(Y), ldy, p, k, ncol, g.kchunk, part);
   MSK_CHECK_LAUNCH("gemm_simt_kernel");
+  const int64_t total = p * ncol;
+  splitk_reduce_kernel<<<(unsigned)std::min<int64_t>((total + 255) / 256, num_sms() * 8), 256, 0,
+                         st>>>(part, g.s, p, ncol, Z, ldz);
+  MSK_CHECK_LAUNCH("splitk_reduce_kernel");
+  return MSK_OK;
+}
+
+// Gaussian-only sketch of a column-major [A b] (the Gaussian sketch-and-solve
+// of Section 6.3, S = G with no CountSketch): Z = G [A b] with G the p x d
+// matrix of the multisketch's Gaussian definition at k = d (entry (r, i) is
+// standard normal number r*d + i of stream tag 2, divided by sqrt(p) in
+// binary32).  G is generated tile by tile inside the product instead of being
+// stored (p*d entries: 17 GB at d = 2^23, p = 512); its binary32 arithmetic
+// is a few percent of the FP64 products it feeds.  Split over row slices of A
+// like gemm_simt_kernel, FP64 accumulation, partials reduced in order.
+template <typename TA>
+__global__ void __launch_bounds__(kGThreads) gauss_gemm_kernel(uint64_t gkey, float sqrt_p,
+                                                            const TA* __restrict__ A, int64_t lda,
+                                                            int64_t d, int64_t n,
+                                                            const double* __restrict__ b, int64_t p,
+                                                            int64_t kchunk,
+                                                            double* __restrict__ part) {
+  __shared__ double Gs[kGBK][kGBM + 1];
+  __shared__ double Ys[kGBK][kGBN + 1];
+  const int64_t ncol = n + 1;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int64_t m0 = (int64_t)blockIdx.x * kGBM, n0 = (int64_t)blockIdx.y * kGBN;
+  const int64_t kb = (int64_t)blockIdx.z * kchunk, ke = (kb + kchunk < d) ? kb + kchunk : d;
+  double acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[a][c] = 0.0;
+  for (int64_t k0 = kb; k0 < ke; k0 += kGBK) {
+#pragma unroll
+    for (int q = 0; q < (kGBM * kGBK) / kGThreads; ++q) {
+      const int e = threadIdx.x + q * kGThreads;
+      const int r = e / kGBK, kk = e % kGBK;
+      const int64_t gr = m0 + r, gk = k0 + kk;
+      Gs[kk][r] = (gr < p && gk < ke)
+                      ? (double)__fdiv_rn(gauss_std(gkey, (uint64_t)(gr * d + gk)), sqrt_p)
+                      : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < (kGBN * kGBK) / kGThreads; ++q) {
+      const int e = threadIdx.x + q * kGThreads;
+      const int kk = e % kGBK, c = e / kGBK;
+      const int64_t gk = k0 + kk, gc = n0 + c;
+      double v = 0.0;
+      if (gk < ke && gc < ncol) v = gc < n ? (double)A[gk + gc * lda] : b[gk];
+      Ys[kk][c] = v;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < kGBK; ++kk) {
+      double av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = Gs[kk][ty + 16 * a];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) bv[c] = Ys[kk][tx + 16 * c];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[a][c] = fma(av[a], bv[c], acc[a][c]);
+    }
+    __syncthreads();
+  }
+  double* out = part + (int64_t)blockIdx.z * p * ncol;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int64_t r = m0 + ty + 16 * a, cc = n0 + tx + 16 * c;
+      if (r < p && cc < ncol) out[cc * p + r] = acc[a][c];
+    }
+}
+
+size_t gauss_gemm_workspace(int64_t p, int64_t d, int64_t ncol) {
+  return gemm_simt_workspace(p, d, ncol, true);
+}
+
+int launch_gauss_gemm(uint64_t gkey, int64_t p, const void* A, int dtype, int64_t d, int64_t n,
+                      int64_t lda, const double* b, double* Z, int64_t ldz, void* ws,
+                      size_t ws_bytes, cudaStream_t st) {
+  const int64_t ncol = n + 1;
+  if (p == 0 || d == 0) return MSK_OK;
+  GemmSplit g = gemm_split(p, d, ncol);
+  Carve cv(ws, ws_bytes);
+  double* part = static_cast<double*>(cv.take((size_t)g.s * p * ncol * sizeof(double)));
+  if (!part) return MSK_ENOMEM;
+  const float sqrt_p = __builtin_sqrtf((float)p);  // exact rounding of sqrt(p), p < 2^24
+  dim3 grid(g.mt, g.nt, g.s);
+  if (dtype == MSK_F64)
+    gauss_gemm_kernel<double><<<grid, kGThreads, 0, st>>>(gkey, sqrt_p, static_cast<const double*>(A),
+                                                         lda, d, n, b, p, g.kchunk, part);
+  else
+    gauss_gemm_kernel<float><<<grid, kGThreads, 0, st>>>(gkey, sqrt_p, static_cast<const float*>(A),
+                                                        lda, d, n, b, p, g.kchunk, part);
+  MSK_CHECK_LAUNCH("gauss_gemm_kernel");
   const int64_t total = p * ncol;
   splitk_reduce_kernel<<<(unsigned)std::min<int64_t>((total + 255) / 256, num_sms() * 8), 256, 0,
                          st>>>(part, g.s, p, ncol, Z, ldz);

@@ -27,7 +27,6 @@
 #include "msk_device.cuh"
 #include "msk_internal.h"
 #include "msk_pass.cuh"
-#include "msk_pass.cuh"
 #include "msk_refine.cuh"
 
 namespace msk {
@@ -90,34 +89,184 @@ __global__ void __launch_bounds__(kGrThreads) gram_kernel(const TA* __restrict__
     }
 }
 
-// Sum the slices (fixed order) and mirror the upper triangle.
+// Sum the slices and mirror the upper triangle: one warp per entry, lane l
+// adds slices l, l+32, ... in order, then a fixed shuffle tree (the same
+// order on every run).
 __global__ void gram_reduce_kernel(const double* __restrict__ part, int S, int64_t ncol,
                                    double* __restrict__ C) {
   const int64_t total = ncol * ncol;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t e = w0; e < total; e += nw) {
     const int64_t c = e / ncol, a = e % ncol;
     const int64_t src = a <= c ? c * ncol + a : a * ncol + c;
     double s = 0.0;
-    for (int q = 0; q < S; ++q) s += part[(int64_t)q * total + src];
-    C[e] = s;
+    for (int q = lane; q < S; q += 32) s += part[(int64_t)q * total + src];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) C[e] = s;
+  }
+}
+
+static void launch_gram_reduce(const double* part, int S, int64_t ncol, double* C, cudaStream_t st) {
+  const int64_t warps = ncol * ncol;
+  gram_reduce_kernel<<<(unsigned)std::min<int64_t>((warps + 7) / 8, 4096), 256, 0, st>>>(part, S,
+                                                                                       ncol, C);
+}
+
+// Gram of [A b] by 2x2 blocks of the upper triangle (up to kGtMaxCol
+// columns).  GB300's FP64 pipe (about 1.75 DFMA per clock per SM) is the
+// bound, so what counts is how many products are computed: blocks of 2x2
+// cover the upper triangle with half of each diagonal block to spare (1.02x
+// the needed products at 129 columns, where 64x64 tiles computed 2.9x).  A
+// CTA "panel" owns a contiguous run of the blocks (row-major order over the
+// upper triangle), each thread kGtBpt of them with their four accumulators
+// in registers; K rows of its row slice of [A b] are staged in shared memory
+// (zero-padded to an even column count), and a block takes two 16-byte loads
+// per four DFMAs.  Partials per row slice, reduced in a fixed order.
+constexpr int kGtK = 32, kGtBpt = 8, kGtMaxThreads = 512, kGtMaxCol = 513;
+
+__device__ __forceinline__ void gt_cp8(double* dst, const double* src, int bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(bytes)
+               : "memory");
+}
+
+// nbuf = 2: the next K rows are copied (cp.async) while this K-row tile is
+// multiplied; nbuf = 1 when two tiles do not fit in shared memory.
+__global__ void __launch_bounds__(kGtMaxThreads) gram_tri_kernel(
+    const double* __restrict__ A, int64_t lda, int64_t d, int64_t n, const double* __restrict__ b,
+    int64_t rchunk, int nb, int per_panel, int nbuf, double* __restrict__ part) {
+  extern __shared__ __align__(16) double gt_x[];
+  const int64_t ncol = n + 1;
+  const int pitch = 2 * nb + 2;
+  const int64_t nblk = (int64_t)nb * (nb + 1) / 2;
+  const int64_t bfirst = (int64_t)blockIdx.x * per_panel;
+  const int64_t blast = min(nblk, bfirst + per_panel);
+  int ai[kGtBpt], cj[kGtBpt];
+#pragma unroll
+  for (int s = 0; s < kGtBpt; ++s) {
+    const int64_t q = bfirst + threadIdx.x + (int64_t)s * blockDim.x;
+    int i = 0, j = 0;
+    if (q < blast) {
+      int64_t r = q;
+      while (r >= nb - i) {
+        r -= nb - i;
+        ++i;
+      }
+      j = i + (int)r;
+    }
+    ai[s] = q < blast ? 2 * i : -1;  // -1: no block in this slot
+    cj[s] = 2 * j;
+  }
+  const int64_t r0 = (int64_t)blockIdx.y * rchunk, r1 = min(d, r0 + rchunk);
+  double acc[kGtBpt][4] = {};
+  const int width = 2 * nb;  // staged columns (ncol, or ncol + 1 zero column)
+  // rows k0 .. k0+K-1 of [A b] into buf (zero past r1 and in the pad column)
+  auto stage = [&](int64_t k0, double* buf) {
+    for (int e = threadIdx.x; e < kGtK * width; e += blockDim.x) {
+      const int kk = e % kGtK, cc = e / kGtK;
+      const int64_t i = k0 + kk;
+      const bool ok = i < r1 && cc < ncol;
+      const double* src = !ok ? A : (cc < n ? A + i + cc * lda : b + i);
+      gt_cp8(buf + kk * pitch + cc, src, ok ? 8 : 0);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  const int tsz = kGtK * pitch;  // doubles per staged tile
+  if (r0 < r1) stage(r0, gt_x);
+  int it = 0;
+  for (int64_t k0 = r0; k0 < r1; k0 += kGtK, ++it) {
+    double* cur = gt_x + (nbuf == 2 ? (it & 1) * tsz : 0);
+    if (nbuf == 2 && k0 + kGtK < r1) {
+      stage(k0 + kGtK, gt_x + ((it + 1) & 1) * tsz);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
+    __syncthreads();
+#pragma unroll 2
+    for (int kk = 0; kk < kGtK; ++kk) {
+      const double* row = cur + kk * pitch;
+#pragma unroll
+      for (int s = 0; s < kGtBpt; ++s) {
+        if (ai[s] < 0) continue;
+        const double2 av = *reinterpret_cast<const double2*>(row + ai[s]);
+        const double2 cv = *reinterpret_cast<const double2*>(row + cj[s]);
+        acc[s][0] = fma(av.x, cv.x, acc[s][0]);
+        acc[s][1] = fma(av.x, cv.y, acc[s][1]);
+        acc[s][2] = fma(av.y, cv.x, acc[s][2]);
+        acc[s][3] = fma(av.y, cv.y, acc[s][3]);
+      }
+    }
+    __syncthreads();  // cur is free for the copies issued next
+    if (nbuf == 1 && k0 + kGtK < r1) stage(k0 + kGtK, gt_x);
+  }
+  // part[slice][c * ncol + a] (column-major (n+1) x (n+1)); only a <= c kept
+  double* out = part + (int64_t)blockIdx.y * ncol * ncol;
+#pragma unroll
+  for (int s = 0; s < kGtBpt; ++s) {
+    if (ai[s] < 0) continue;
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+      for (int v = 0; v < 2; ++v) {
+        const int64_t a = ai[s] + u, c = cj[s] + v;
+        if (a < ncol && c < ncol && a <= c) out[c * ncol + a] = acc[s][2 * u + v];
+      }
   }
 }
 
 struct GramPlan {
-  int ntile, npairs, slices;
+  bool tri;              // gram_tri_kernel (else 64x64 tiles of gram_kernel)
+  int ntile, npairs;     // tiles: tiles per side, upper tile pairs
+  int nb, per_panel, npanels, threads, nbuf;  // tri: 2x2 blocks per side, blocks per CTA panel
+  int slices;
   int64_t rchunk;
+  size_t smem;
 };
 
 static GramPlan gram_plan(int64_t d, int64_t n) {
-  GramPlan g;
+  GramPlan g{};
   const int64_t ncol = n + 1;
-  g.ntile = (int)((ncol + kGrT - 1) / kGrT);
-  g.npairs = g.ntile * (g.ntile + 1) / 2;
-  int64_t s = std::max<int64_t>(1, (2LL * num_sms()) / g.npairs);
-  s = std::min<int64_t>(s, std::max<int64_t>(1, (d + kGrK - 1) / kGrK));
-  g.rchunk = ((d + s - 1) / s + kGrK - 1) / kGrK * kGrK;
-  if (g.rchunk < kGrK) g.rchunk = kGrK;
+  g.tri = ncol <= kGtMaxCol;
+  int64_t groups;  // CTAs per row slice
+  int64_t kstep;
+  int64_t target = 2LL * num_sms();  // CTAs in all
+  if (g.tri) {
+    g.nb = (int)((ncol + 1) / 2);
+    const int64_t nblk = (int64_t)g.nb * (g.nb + 1) / 2;
+    g.npanels = (int)((nblk + (int64_t)kGtMaxThreads * kGtBpt - 1) / ((int64_t)kGtMaxThreads * kGtBpt));
+    g.per_panel = (int)((nblk + g.npanels - 1) / g.npanels);
+    g.threads = (int)(((g.per_panel + kGtBpt - 1) / kGtBpt + 31) / 32 * 32);
+    const size_t tile = (size_t)kGtK * (2 * g.nb + 2) * sizeof(double);
+    g.nbuf = 2 * tile <= (size_t)160 * 1024 ? 2 : 1;
+    g.smem = g.nbuf * tile;
+    // The FP64 pipe needs many warps per SM (one warp's chain of dependent
+    // DFMAs issues far below the pipe's rate): about 16 warps per SM, as
+    // occupancy allows, by giving narrow panels more row slices.
+    int occ = 0;
+    if (allow_max_smem(reinterpret_cast<const void*>(gram_tri_kernel)) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gram_tri_kernel, g.threads, g.smem) !=
+            cudaSuccess)
+      occ = 1;
+    const int warps = g.threads / 32;
+    const int per_sm = std::max(1, std::min(occ, std::max(2, (16 + warps - 1) / warps)));
+    target = (int64_t)num_sms() * per_sm;
+    groups = g.npanels;
+    kstep = kGtK;
+  } else {
+    g.ntile = (int)((ncol + kGrT - 1) / kGrT);
+    g.npairs = g.ntile * (g.ntile + 1) / 2;
+    groups = g.npairs;
+    kstep = kGrK;
+  }
+  int64_t s = std::max<int64_t>(1, target / groups);
+  s = std::min<int64_t>(s, std::max<int64_t>(1, (d + kstep - 1) / kstep));
+  g.rchunk = ((d + s - 1) / s + kstep - 1) / kstep * kstep;
+  if (g.rchunk < kstep) g.rchunk = kstep;
   g.slices = (int)std::max<int64_t>(1, (d + g.rchunk - 1) / g.rchunk);
   return g;
 }
@@ -126,9 +275,31 @@ static size_t gram_workspace(int64_t d, int64_t n) {
   GramPlan g = gram_plan(d, n);
   const int64_t ncol = n + 1;
   Need nd;
-  nd.add((size_t)g.npairs * sizeof(int2));
+  nd.add((size_t)std::max(g.npairs, 1) * sizeof(int2));
   nd.add((size_t)g.slices * ncol * ncol * sizeof(double));
   return nd.used;
+}
+
+// Partials of the Gram of [A b] (FP64 A) into part[slices][ncol][ncol]
+// (upper entries a <= c); `tiles` is workspace for the 64x64-tile plan.
+static int launch_gram(const GramPlan& g, const double* A, int64_t lda, int64_t d, int64_t n,
+                       const double* b, int2* tiles, double* part, cudaStream_t st) {
+  if (g.tri) {
+    MSK_ALLOW_SMEM(gram_tri_kernel);
+    dim3 grid(g.npanels, g.slices);
+    gram_tri_kernel<<<grid, g.threads, g.smem, st>>>(A, lda, d, n, b, g.rchunk, g.nb, g.per_panel,
+                                                     g.nbuf, part);
+    MSK_CHECK_LAUNCH("gram_tri_kernel");
+    return MSK_OK;
+  }
+  std::vector<int2> hp;
+  for (int a = 0; a < g.ntile; ++a)
+    for (int c = a; c < g.ntile; ++c) hp.push_back(make_int2(a, c));
+  MSK_CUDA(cudaMemcpyAsync(tiles, hp.data(), hp.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
+  dim3 grid(g.npairs, g.slices);
+  gram_kernel<double><<<grid, kGrThreads, 0, st>>>(A, lda, d, n, b, g.rchunk, tiles, part);
+  MSK_CHECK_LAUNCH("gram_kernel");
+  return MSK_OK;
 }
 
 // Thin kernels over the bodies in msk_refine.cuh.
@@ -302,6 +473,112 @@ bool is_tensor_prec_l(int prec) {
   return prec == MSK_GEMM_BF16 || prec == MSK_GEMM_F16 || prec == MSK_GEMM_BF16X3;
 }
 
+
+
+// Column-major W (m x c, ldw) from row-major Y (m x c, ldy): 32 x 32 tiles
+// through shared memory (the CountSketch writes bucket rows; the QR reads
+// columns).
+__global__ void transpose_rm_to_cm_kernel(const double* __restrict__ Y, int64_t ldy, int64_t m,
+                                          int64_t c, double* __restrict__ W, int64_t ldw) {
+  __shared__ double t[32][33];
+  const int64_t r0 = (int64_t)blockIdx.x * 32, c0 = (int64_t)blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 256 threads: 8 rows per pass
+  for (int i = ty; i < 32; i += 8) {
+    const int64_t r = r0 + i, cc = c0 + tx;
+    t[i][tx] = (r < m && cc < c) ? Y[r * ldy + cc] : 0.0;
+  }
+  __syncthreads();
+  for (int j = ty; j < 32; j += 8) {
+    const int64_t cc = c0 + j, r = r0 + tx;
+    if (r < m && cc < c) W[r + cc * ldw] = t[tx][j];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Randomized Cholesky QR (Algorithms 4 and 5).  Shared front: Y = S A (the
+// multisketch of A alone), R0 from its Householder QR, the explicit R0^{-1}.
+struct RcqFront {
+  double* Z;    // p x n: R0 in its upper n x n
+  double* Ri0;  // n x n: R0^{-1}
+};
+
+static size_t rcq_front_workspace(int64_t d, int64_t n, int64_t k, int64_t p, int dtype,
+                                  int gemm_prec) {
+  Need nd;
+  nd.add(msk_ms_workspace(d, n, 0, k, p, dtype, gemm_prec, MSK_CS_ATOMIC));
+  nd.add((size_t)p * n * sizeof(double));  // Z
+  nd.add((size_t)n * n * sizeof(double));  // R0^{-1}
+  return nd.used;
+}
+
+// Returns MSK_OK, an error, or j+1 when R0[j][j] == 0 (synchronises then).
+static int rcq_front(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, int64_t k,
+                     int64_t p, uint64_t seed, int gemm_prec, Carve& cv, RcqFront* f,
+                     void* stream) {
+  cudaStream_t st = as_stream(stream);
+  const size_t ms_ws = msk_ms_workspace(d, n, 0, k, p, dtype, gemm_prec, MSK_CS_ATOMIC);
+  void* msw = cv.take(ms_ws);
+  f->Z = static_cast<double*>(cv.take((size_t)p * n * sizeof(double)));
+  f->Ri0 = static_cast<double*>(cv.take((size_t)n * n * sizeof(double)));
+  if (!f->Z || !f->Ri0) return MSK_ENOMEM;
+  // 1. Y = S A (Z = G C A)
+  int rc = ms_sketch(A, dtype, d, n, lda, nullptr, k, p, seed, gemm_prec, f->Z, p, MSK_CS_ATOMIC,
+                     msw, ms_ws, stream);
+  if (rc) return rc;
+  // 2. R0 = R of qr(Y, 0)
+  rc = launch_householder_qr(f->Z, p, n, p, st);
+  if (rc) return rc;
+  const int piv = first_zero_pivot(f->Z, n, p, st);
+  if (piv) return piv;
+  // 3. (Q0 = A R0^{-1} through) the explicit inverse
+  tri_inverse_kernel<<<(unsigned)std::max<int64_t>(1, (n + 7) / 8), 256, 0, st>>>(f->Z, (int)n, p,
+                                                                                 f->Ri0);
+  MSK_CHECK_LAUNCH("tri_inverse_kernel");
+  return MSK_OK;
+}
+
+// C (ncol x ncol, ld ncol) = X^T X for X = [Q0[:, 0:m] col] (m + 1 columns).
+static size_t rcq_gram_workspace(int64_t d, int64_t m) {
+  return gram_workspace(d, m) + (size_t)(m + 1) * (m + 1) * sizeof(double) + 256;
+}
+static int rcq_gram(const double* Q0, int64_t ldq, int64_t d, int64_t m, const double* col,
+                    Carve& cv, double** Cout, cudaStream_t st) {
+  GramPlan g = gram_plan(d, m);
+  const int64_t ncol = m + 1;
+  int2* tiles = static_cast<int2*>(cv.take((size_t)std::max(g.npairs, 1) * sizeof(int2)));
+  double* part = static_cast<double*>(cv.take((size_t)g.slices * ncol * ncol * sizeof(double)));
+  double* C = static_cast<double*>(cv.take((size_t)ncol * ncol * sizeof(double)));
+  if (!tiles || !part || !C) return MSK_ENOMEM;
+  int rc = launch_gram(g, Q0, ldq, d, m, col, tiles, part, st);
+  if (rc) return rc;
+  launch_gram_reduce(part, g.slices, ncol, C, st);
+  MSK_CHECK_LAUNCH("gram_reduce_kernel");
+  *Cout = C;
+  return MSK_OK;
+}
+
+static int rcq_args(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, int64_t k,
+                    int64_t p, int gemm_prec) {
+  if (!A) return -1;
+  if (dtype != MSK_F64 && dtype != MSK_F32) return -2;
+  if (d < n) return -3;
+  if (n < 1 || n > 400) return -4;
+  if (lda < d) return -5;
+  if (k < n + 1) return -7;
+  if (p < n + 1 || p > k || p > 2048) return -8;
+  if (gemm_prec < MSK_GEMM_F64 || gemm_prec > MSK_GEMM_BF16X3) return -10;
+  if (is_tensor_prec_l(gemm_prec) && dtype != MSK_F32) return MSK_ENOTSUP;
+  return MSK_OK;
+}
+
+// Fill x with NaN (a failed factorisation), then report status.
+static int rcq_fail(double* x, int64_t n, int status, cudaStream_t st) {
+  std::vector<double> nanv((size_t)n, std::nan(""));
+  MSK_CUDA(cudaMemcpyAsync(x, nanv.data(), (size_t)n * sizeof(double), cudaMemcpyHostToDevice, st));
+  MSK_CUDA(cudaStreamSynchronize(st));
+  return status;
+}
+
 }  // namespace
 
 extern "C" {
@@ -471,6 +748,217 @@ int ms_lstsq(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, const 
   return status;
 }
 
+size_t msk_sns_workspace(int64_t d, int64_t n, int kind, int64_t k, int64_t p, int dtype) {
+  if (kind == MSK_SKETCH_MULTI) return msk_lstsq_workspace(d, n, k, p, dtype, MSK_GEMM_F64, 0);
+  const int64_t ncol = n + 1;
+  Need nd;
+  if (kind == MSK_SKETCH_COUNT) {
+    nd.add((size_t)k * ((ncol + 1) / 2 * 2) * sizeof(double));  // Y, row-major
+    nd.add((size_t)k * ncol * sizeof(double));                  // W, column-major
+  } else {
+    nd.add((size_t)p * ncol * sizeof(double));  // Z
+    nd.add(gauss_gemm_workspace(p, d, ncol));
+  }
+  nd.add(pass_workspace(d, n));
+  nd.add((size_t)(n + 2) * sizeof(double));
+  return nd.used;
+}
+
+int sns_lstsq(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, const double* b,
+              int kind, int64_t k, int64_t p, uint64_t seed, double* x, msk_lstsq_info* info,
+              void* ws, size_t ws_bytes, void* stream) {
+  if (kind == MSK_SKETCH_MULTI)
+    return ms_lstsq(A, dtype, d, n, lda, b, k, p, seed, MSK_GEMM_F64, 0, 0.0, 0, x, info, ws,
+                    ws_bytes, stream);
+  if (!A) return -1;
+  if (dtype != MSK_F64 && dtype != MSK_F32) return -2;
+  if (d < n) return -3;
+  if (n < 1 || n > 400) return -4;
+  if (lda < d) return -5;
+  if (!b) return -6;
+  if (kind != MSK_SKETCH_COUNT && kind != MSK_SKETCH_GAUSS) return -7;
+  if (kind == MSK_SKETCH_COUNT && (k < n + 1 || k > 0xFFFFFFFFLL)) return -8;
+  if (kind == MSK_SKETCH_GAUSS && (p < n + 1 || p > 2048)) return -9;
+  if (!x) return -11;
+  if (ws_bytes < msk_sns_workspace(d, n, kind, k, p, dtype)) return MSK_ENOMEM;
+  cudaStream_t st = as_stream(stream);
+  Carve cv(ws, ws_bytes);
+  const int64_t ncol = n + 1;
+  double* W;  // the sketched [SA Sb], column-major m x ncol
+  int64_t m;
+  int rc;
+  if (kind == MSK_SKETCH_COUNT) {
+    // S = C: the k x (n+1) CountSketch itself (Definition 3), FP64
+    const int64_t ldy = (ncol + 1) / 2 * 2;
+    double* Y = static_cast<double*>(cv.take((size_t)k * ldy * sizeof(double)));
+    W = static_cast<double*>(cv.take((size_t)k * ncol * sizeof(double)));
+    if (!Y || !W) return MSK_ENOMEM;
+    rc = count_sketch_f64y(A, dtype, d, n, lda, b, k, seed, Y, ldy, st);
+    if (rc) return rc;
+    dim3 grid((unsigned)((k + 31) / 32), (unsigned)((ncol + 31) / 32));
+    transpose_rm_to_cm_kernel<<<grid, 256, 0, st>>>(Y, ldy, k, ncol, W, k);
+    MSK_CHECK_LAUNCH("transpose_rm_to_cm_kernel");
+    m = k;
+  } else {
+    // S = G: the p x d Gaussian sketch (Section 1), generated inside the product
+    W = static_cast<double*>(cv.take((size_t)p * ncol * sizeof(double)));
+    const size_t gws = gauss_gemm_workspace(p, d, ncol);
+    void* gw = cv.take(gws);
+    if (!W || !gw) return MSK_ENOMEM;
+    rc = launch_gauss_gemm(stream_key(seed, kTagGauss), p, A, dtype, d, n, lda, b, W, p, gw, gws,
+                           st);
+    if (rc) return rc;
+    m = p;
+  }
+  double* part = static_cast<double*>(cv.take(pass_workspace(d, n)));
+  double* pout = static_cast<double*>(cv.take((size_t)(n + 2) * sizeof(double)));
+  if (!part || !pout) return MSK_ENOMEM;
+  // Algorithm 1 steps 2-3: Householder QR of the sketched [A b], then TRSV
+  rc = launch_householder_qr(W, m, ncol, m, st);
+  if (rc) return rc;
+  rc = launch_trsv_upper(W, n, m, W + n * m, x, nullptr, false, st);
+  if (rc) return rc;
+  int status = MSK_OK;
+  if (info) {
+    rc = launch_pass(A, dtype, lda, d, (int)n, b, x, true, part, pout, nullptr, st);
+    if (rc) return rc;
+    double h[2];
+    MSK_CUDA(cudaMemcpyAsync(h, pout + n, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    MSK_CUDA(cudaStreamSynchronize(st));
+    info->iters = 0;
+    info->converged = 1;
+    info->relres = std::sqrt(std::max(h[0], 0.0) / (h[1] > 0.0 ? h[1] : 1.0));
+    info->relres_sns = info->relres;
+    const int piv = first_zero_pivot(W, n, m, st);
+    if (piv > 0) status = piv;
+  }
+  return status;
+}
+
+size_t msk_rcq_workspace(int64_t d, int64_t n, int64_t k, int64_t p, int dtype, int gemm_prec,
+                         int want_q) {
+  Need nd;
+  nd.add(rcq_front_workspace(d, n, k, p, dtype, gemm_prec));
+  nd.add((size_t)n * n * sizeof(double));  // R1
+  nd.add(64);                              // status
+  if (want_q) {
+    nd.add(rcq_gram_workspace(d, n - 1));    // Gram of Q0
+    nd.add((size_t)n * n * sizeof(double));  // R1^{-1}
+  } else {
+    nd.add((size_t)d * n * sizeof(double));  // Q0
+    nd.add(rcq_gram_workspace(d, n));        // Gram of [Q0 b]
+    nd.add((size_t)n * n * sizeof(double));  // R
+    nd.add((size_t)n * sizeof(double));      // y
+    nd.add(pass_workspace(d, n));            // residual pass partials
+    nd.add((size_t)(n + 2) * sizeof(double));
+  }
+  return nd.used;
+}
+
+int rcq_lstsq(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, const double* b,
+              int64_t k, int64_t p, uint64_t seed, int gemm_prec, double* x, msk_lstsq_info* info,
+              void* ws, size_t ws_bytes, void* stream) {
+  int rc = rcq_args(A, dtype, d, n, lda, k, p, gemm_prec);
+  if (rc) return rc;
+  if (!b) return -6;
+  if (!x) return -11;
+  if (ws_bytes < msk_rcq_workspace(d, n, k, p, dtype, gemm_prec, 0)) return MSK_ENOMEM;
+  cudaStream_t st = as_stream(stream);
+  Carve cv(ws, ws_bytes);
+  RcqFront f;
+  rc = rcq_front(A, dtype, d, n, lda, k, p, seed, gemm_prec, cv, &f, stream);
+  if (rc > 0 && rc < 1000) return rcq_fail(x, n, rc, st);
+  if (rc) return rc;
+  double* R1 = static_cast<double*>(cv.take((size_t)n * n * sizeof(double)));
+  int* status = static_cast<int*>(cv.take(64));
+  double* Q0 = static_cast<double*>(cv.take((size_t)d * n * sizeof(double)));
+  if (!R1 || !status || !Q0) return MSK_ENOMEM;
+  // Q0 = A R0^{-1}
+  rc = launch_trmm_upper(A, dtype, lda, d, n, f.Ri0, Q0, d, st);
+  if (rc) return rc;
+  // G = Q0^T Q0 and z = Q0^T b: the Gram of [Q0 b] (C[0:n, n] = z)
+  double* C = nullptr;
+  rc = rcq_gram(Q0, d, d, n, b, cv, &C, st);
+  if (rc) return rc;
+  double* R = static_cast<double*>(cv.take((size_t)n * n * sizeof(double)));
+  double* y = static_cast<double*>(cv.take((size_t)n * sizeof(double)));
+  double* part = static_cast<double*>(cv.take(pass_workspace(d, n)));
+  double* pout = static_cast<double*>(cv.take((size_t)(n + 2) * sizeof(double)));
+  if (!R || !y || !part || !pout) return MSK_ENOMEM;
+  const int64_t ncol = n + 1;
+  MSK_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
+  // R1 = chol(G); R = R1 R0; y = R1^{-T} z; x = R^{-1} y
+  rc = launch_cholesky(C, n, ncol, R1, n, status, st);
+  if (rc) return rc;
+  rc = launch_tri_mul_upper(R1, n, f.Z, p, n, R, n, st);
+  if (rc) return rc;
+  rc = launch_trsv_upper(R1, n, n, C + n * ncol, y, nullptr, true, st);
+  if (rc) return rc;
+  rc = launch_trsv_upper(R, n, n, y, x, nullptr, false, st);
+  if (rc) return rc;
+  int hs = 0;
+  MSK_CUDA(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  MSK_CUDA(cudaStreamSynchronize(st));
+  if (hs > 0) return rcq_fail(x, n, hs, st);
+  if (info) {
+    rc = launch_pass(A, dtype, lda, d, (int)n, b, x, true, part, pout, nullptr, st);
+    if (rc) return rc;
+    double h[2];
+    MSK_CUDA(cudaMemcpyAsync(h, pout + n, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    MSK_CUDA(cudaStreamSynchronize(st));
+    info->iters = 0;
+    info->converged = 1;
+    info->relres = std::sqrt(std::max(h[0], 0.0) / (h[1] > 0.0 ? h[1] : 1.0));
+    info->relres_sns = -1.0;
+  }
+  return MSK_OK;
+}
+
+int rcq_qr(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, int64_t k, int64_t p,
+           uint64_t seed, int gemm_prec, double* Q, int64_t ldq, double* R, int64_t ldr, void* ws,
+           size_t ws_bytes, void* stream) {
+  int rc = rcq_args(A, dtype, d, n, lda, k, p, gemm_prec);
+  if (rc) return rc;
+  if (!Q) return -10;
+  if (ldq < d) return -11;
+  if (!R) return -12;
+  if (ldr < n) return -13;
+  if (ws_bytes < msk_rcq_workspace(d, n, k, p, dtype, gemm_prec, 1)) return MSK_ENOMEM;
+  cudaStream_t st = as_stream(stream);
+  Carve cv(ws, ws_bytes);
+  RcqFront f;
+  rc = rcq_front(A, dtype, d, n, lda, k, p, seed, gemm_prec, cv, &f, stream);
+  if (rc) return rc;
+  double* R1 = static_cast<double*>(cv.take((size_t)n * n * sizeof(double)));
+  int* status = static_cast<int*>(cv.take(64));
+  if (!R1 || !status) return MSK_ENOMEM;
+  // Q0 = A R0^{-1}, into Q
+  rc = launch_trmm_upper(A, dtype, lda, d, n, f.Ri0, Q, ldq, st);
+  if (rc) return rc;
+  // G = Q0^T Q0: the Gram of [Q0[:, 0:n-1] Q0[:, n-1]]
+  double* C = nullptr;
+  rc = rcq_gram(Q, ldq, d, n - 1, Q + (n - 1) * ldq, cv, &C, st);
+  if (rc) return rc;
+  double* Ri1 = static_cast<double*>(cv.take((size_t)n * n * sizeof(double)));
+  if (!Ri1) return MSK_ENOMEM;
+  MSK_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
+  rc = launch_cholesky(C, n, n, R1, n, status, st);
+  if (rc) return rc;
+  int hs = 0;
+  MSK_CUDA(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  MSK_CUDA(cudaStreamSynchronize(st));
+  if (hs > 0) return hs;
+  // Q = Q0 R1^{-1} (in place), R = R1 R0
+  tri_inverse_kernel<<<(unsigned)std::max<int64_t>(1, (n + 7) / 8), 256, 0, st>>>(R1, (int)n, n, Ri1);
+  MSK_CHECK_LAUNCH("tri_inverse_kernel");
+  rc = launch_trmm_upper(Q, MSK_F64, ldq, d, n, Ri1, Q, ldq, st);
+  if (rc) return rc;
+  rc = launch_tri_mul_upper(R1, n, f.Z, p, n, R, ldr, st);
+  if (rc) return rc;
+  MSK_CUDA(cudaStreamSynchronize(st));
+  return MSK_OK;
+}
+
 size_t msk_ne_workspace(int64_t d, int64_t n) {
   Need nd;
   nd.add(gram_workspace(d, n));
@@ -494,24 +982,19 @@ int ne_lstsq(const double* A, int64_t d, int64_t n, int64_t lda, const double* b
   Carve cv(ws, ws_bytes);
   GramPlan g = gram_plan(d, n);
   const int64_t ncol = n + 1;
-  int2* tiles = static_cast<int2*>(cv.take((size_t)g.npairs * sizeof(int2)));
+  int2* tiles = static_cast<int2*>(cv.take((size_t)std::max(g.npairs, 1) * sizeof(int2)));
   double* part = static_cast<double*>(cv.take((size_t)g.slices * ncol * ncol * sizeof(double)));
   double* C = static_cast<double*>(cv.take((size_t)ncol * ncol * sizeof(double)));
   double* R = static_cast<double*>(cv.take((size_t)n * n * sizeof(double)));
   double* y = static_cast<double*>(cv.take((size_t)n * sizeof(double)));
   int* status = static_cast<int*>(cv.take(64));
   if (!tiles || !part || !C || !R || !y || !status) return MSK_ENOMEM;
-  std::vector<int2> hp;
-  for (int a = 0; a < g.ntile; ++a)
-    for (int c = a; c < g.ntile; ++c) hp.push_back(make_int2(a, c));
-  MSK_CUDA(cudaMemcpyAsync(tiles, hp.data(), hp.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
   MSK_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
-  dim3 grid(g.npairs, g.slices);
-  gram_kernel<double><<<grid, kGrThreads, 0, st>>>(A, lda, d, n, b, g.rchunk, tiles, part);
-  MSK_CHECK_LAUNCH("gram_kernel");
-  const int64_t tot = ncol * ncol;
-  gram_reduce_kernel<<<(unsigned)std::min<int64_t>((tot + 255) / 256, 1024), 256, 0, st>>>(
-      part, g.slices, ncol, C);
+  {
+    const int rc = launch_gram(g, A, lda, d, n, b, tiles, part, st);
+    if (rc) return rc;
+  }
+  launch_gram_reduce(part, g.slices, ncol, C, st);
   MSK_CHECK_LAUNCH("gram_reduce_kernel");
   // C[0:n,0:n] = A^T A, C[0:n, n] = A^T b.  Cholesky overwrites C's upper part.
   int rc = launch_cholesky(C, n, ncol, R, n, status, st);

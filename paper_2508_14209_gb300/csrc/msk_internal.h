@@ -150,7 +150,23 @@ int launch_trsv_upper(const double* R, int64_t n, int64_t ldr, const double* rhs
 int launch_cholesky(double* Gm, int64_t n, int64_t ldg, double* R, int64_t ldr, int* status,
                     cudaStream_t st);
 int first_zero_pivot(const double* R, int64_t n, int64_t ldr, cudaStream_t st);
+// rcq.cu (randomized Cholesky QR's tall product and small triangular product)
+size_t trmm_upper_smem(int64_t n);
+int launch_trmm_upper(const void* X, int dtype, int64_t ldx, int64_t d, int64_t n, const double* U,
+                      double* Y, int64_t ldy, cudaStream_t st);
+int launch_tri_mul_upper(const double* R1, int64_t ld1, const double* R0, int64_t ld0, int64_t n,
+                         double* R, int64_t ldr, cudaStream_t st);
+// gemm_simt.cu: Gaussian-only sketch Z = G [A b] (G p x d generated in place)
+size_t gauss_gemm_workspace(int64_t p, int64_t d, int64_t ncol);
+int launch_gauss_gemm(uint64_t gkey, int64_t p, const void* A, int dtype, int64_t d, int64_t n,
+                      int64_t lda, const double* b, double* Z, int64_t ldz, void* ws,
+                      size_t ws_bytes, cudaStream_t st);
 // api.cu
+// FP64 CountSketch of [A b] (FP64 A, or FP32 A widened exactly) into
+// row-major Y (k x ncol, ldy), atomic strategy; Y is zeroed first.
+int count_sketch_f64y(const void* A, int dtype, int64_t d, int64_t n, int64_t lda,
+                      const double* b, int64_t k, uint64_t seed, double* Y, int64_t ldy,
+                      cudaStream_t st);
 int gemm_stage(uint64_t seed, int64_t p, int64_t k, int64_t ncol, const void* Y, int y_dtype,
                int64_t ldy, int gemm_prec, double* Z, int64_t ldz, void* ws, size_t ws_bytes,
                cudaStream_t st);

@@ -70,7 +70,12 @@ __device__ __forceinline__ void qr_cluster_body(double* __restrict__ W, int m, i
     // stage v = (v0, W[j+1:m, j]) and apply the reflector to owned columns
     const double* opub = cluster.map_shared_rank(&pub[j & 1][0], owner);
     const double v0 = opub[0], tau = opub[1];
-    for (int i = j + threadIdx.x; i < m; i += blockDim.x) vbuf[i - j] = (i == j) ? v0 : __ldcg(colj + i);
+    // v = (v0, W[j+1:m, j]); staged in shared memory when it fits, else read
+    // from W's column j (L2) where it is needed (no CTA writes that column
+    // below the diagonal during the step)
+    const bool staged = m - j <= kQrMaxRows;
+    if (staged)
+      for (int i = j + threadIdx.x; i < m; i += blockDim.x) vbuf[i - j] = (i == j) ? v0 : __ldcg(colj + i);
     __syncthreads();
     if (tau != 0.0) {
       // owned columns > j: first owned column index >= j+1 with col % CL == rank
@@ -78,9 +83,15 @@ __device__ __forceinline__ void qr_cluster_body(double* __restrict__ W, int m, i
       for (int col = first + warp * CL; col < c; col += nwarps * CL) {
         double* w = W + (int64_t)col * ldw;
         double s = 0.0;
-        for (int i = j + lane; i < m; i += 32) s += vbuf[i - j] * w[i];
-        s = warp_sum(s) * tau;
-        for (int i = j + lane; i < m; i += 32) w[i] -= s * vbuf[i - j];
+        if (staged) {
+          for (int i = j + lane; i < m; i += 32) s += vbuf[i - j] * w[i];
+          s = warp_sum(s) * tau;
+          for (int i = j + lane; i < m; i += 32) w[i] -= s * vbuf[i - j];
+        } else {
+          for (int i = j + lane; i < m; i += 32) s += (i == j ? v0 : __ldcg(colj + i)) * w[i];
+          s = warp_sum(s) * tau;
+          for (int i = j + lane; i < m; i += 32) w[i] -= s * (i == j ? v0 : __ldcg(colj + i));
+        }
       }
     }
     __syncthreads();

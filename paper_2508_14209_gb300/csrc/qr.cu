@@ -193,7 +193,7 @@ extern "C" {
 
 int msk_householder_qr(double* W, int64_t m, int64_t c, int64_t ldw, void* stream) {
   if (!W) return -1;
-  if (m < c || m > kQrMaxRows) return -2;
+  if (m < c || m > 0x7fffffffLL) return -2;
   if (c < 1 || c > kQrMaxCols) return -3;
   if (ldw < m) return -4;
   return launch_householder_qr(W, m, c, ldw, as_stream(stream));

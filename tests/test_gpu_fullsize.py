@@ -7,6 +7,14 @@ benchmark and the served path use, on what the oracle computes in seconds:
   path plus the FP32 CountSketch tolerance;
 * A 8388608 x 128 FP64, sigma 1 -> 1e-6: FP64 sketch-and-solve with the same
   S and G as the oracle, relative residual within 1e-8 of the oracle's;
+* A 8388608 x 128 FP64, sigma 1 -> 1e-6 and 1 -> 1e-10: the normal equations
+  against FP64 sketch-and-solve of the same request (Section 6.3): at 1e-6
+  they succeed with a residual below sketch-and-solve's (no distortion); at
+  1e-10 they report the failed Cholesky (NaN x) or return a residual far
+  above sketch-and-solve's, which stays accurate;
+* the same requests by rand_cholQR least squares (Algorithm 5): a residual
+  not above the normal equations' (when they succeed) nor sketch-and-solve's;
+  the one the library reports is the oracle's recomputation;
 * A 16777216 x 256 FP32, sigma 1 -> 1e-8: the refined mixed-precision solve
   converges; the relative residual it reports is the one the oracle
   recomputes (FP64, compensated) for the returned x; it is not above FP64
@@ -59,6 +67,36 @@ def test_sns_f64_full_size(msk, orc):
     rg = orc.relres(An, bn, x.cpu().numpy())
     assert abs(rg - ro) <= 1e-8 * ro
     assert abs(info["relres"] - rg) <= 1e-10 * rg
+
+
+@pytest.mark.parametrize("lsig", [-6, -10])
+def test_ne_vs_sns_f64_full_size(msk, orc, lsig):
+    d, n, k, p, seed = 1 << 23, 128, 32768, 512, 0x5EED0003
+    A, b, _ = inputs.ls_problem(d, n, lsig, seed=seed, dtype=torch.float64, device="cuda")
+    xn, rcn = msk.ne_lstsq(A, b)
+    xs, info, rcs = msk.ms_lstsq(A, b, k, p, seed, msk.GEMM_F64)
+    assert rcs == 0
+    xq, infoq, rcq = msk.rcq_lstsq(A, b, k, p, seed, msk.GEMM_F64)
+    assert rcq == 0
+    An, bn = A.cpu().numpy(), b.cpu().numpy()
+    del A, b
+    torch.cuda.empty_cache()
+    rs = orc.relres(An, bn, xs.cpu().numpy())
+    assert abs(info["relres"] - rs) <= 1e-10 * rs
+    rq = orc.relres(An, bn, xq.cpu().numpy())
+    assert abs(infoq["relres"] - rq) <= 1e-10 * rq
+    assert rq < rs
+    if lsig == -6:
+        assert rcn == 0
+        rn = orc.relres(An, bn, xn.cpu().numpy())
+        assert rn < rs
+        assert rq <= (1 + 1e-8) * rn
+    else:
+        assert rs < 1e-5
+        if rcn == 0:
+            assert orc.relres(An, bn, xn.cpu().numpy()) > 10 * rs
+        else:
+            assert rcn > 0 and torch.isnan(xn).all()
 
 
 def test_refined_f32_full_size(msk, orc):

@@ -35,9 +35,10 @@ def dev_colmajor(M, msk):
 
 
 # Shapes whose owned columns fit in shared memory run the on-chip cluster QR;
-# (2048, 400) exceeds it and runs the global-memory form.
+# (2048, 400) exceeds it and runs the global-memory form; (8192, 65) and
+# (40000, 17) are taller than the global form's shared-memory staging of v.
 @pytest.mark.parametrize("m,c", [(8, 1), (9, 9), (64, 7), (129, 65), (512, 129), (1024, 257),
-                                 (2048, 100), (300, 17), (2048, 400)])
+                                 (2048, 100), (300, 17), (2048, 400), (8192, 65), (40000, 17)])
 def test_householder_r_matches_oracle(msk, orc, m, c):
     Z = np.random.default_rng(m * 7 + c).standard_normal((m, c))
     W = dev_colmajor(Z, msk)
@@ -146,6 +147,24 @@ def test_residual_pass_exact_with_subnormal_and_zero_entries(msk, orc, n):
     assert rc == 0
     r_orc = orc.relres(An, b.numpy(), x.cpu().numpy())
     assert abs(info["relres"] - r_orc) <= 1e-10 * r_orc
+
+
+@pytest.mark.parametrize("d,n", [(20000 + 3, 128), (9001, 255), (6000, 256), (3000, 520), (4000, 1)])
+def test_ne_shapes_match_oracle(msk, orc, d, n):
+    """Normal equations across the Gram kernels' layouts: one panel of 2x2
+    blocks (129 columns), several panels (256, 257 columns), an odd column
+    count with a zero pad column, the 64x64-tile form past 513 columns, and
+    a single column; kappa = 1e2, so both sides sit at the minimiser."""
+    A, b = _problem(d, n, -2, 300 + n, torch.float64)
+    x, rc = msk.ne_lstsq(dev_colmajor(A, msk), b.cuda())
+    assert rc == 0
+    xo, info = orc.ne_lstsq(A.numpy(), b.numpy())
+    assert info == 0
+    xg = x.cpu().numpy()
+    assert np.allclose(xg, xo, rtol=1e-8, atol=1e-8 * np.abs(xo).max())
+    rg = orc.relres(A.numpy(), b.numpy(), xg)
+    ro = orc.relres(A.numpy(), b.numpy(), xo)
+    assert abs(rg - ro) <= 1e-8 * ro
 
 
 def test_ne_matches_oracle_and_breaks_down(msk, orc):
