@@ -93,7 +93,12 @@ typedef enum { MSK_CS_ATOMIC = 0, MSK_CS_SORTED = 1 } msk_cs_strategy;
  *   COUNT : S = C alone (k rows; the QR is of a k x (n+1) matrix);
  *   GAUSS : S = G alone, a p x d Gaussian with the entries of the
  *           multisketch's G at k = d (generated inside the product). */
-typedef enum { MSK_SKETCH_MULTI = 0, MSK_SKETCH_COUNT = 1, MSK_SKETCH_GAUSS = 2 } msk_sketch_kind;
+typedef enum {
+  MSK_SKETCH_MULTI = 0,
+  MSK_SKETCH_COUNT = 1,
+  MSK_SKETCH_GAUSS = 2,
+  MSK_SKETCH_SRHT = 3 /* S = (1/sqrt(k)) P H D, k rows (d a power of two) */
+} msk_sketch_kind;
 
 #define MSK_OK 0
 #define MSK_ENOCONV 1001  /* refinement stopped at max_iter (x is returned) */
@@ -316,7 +321,31 @@ int ne_lstsq(const double *A, int64_t d, int64_t n, int64_t lda,
              const double *b, double *x, void *ws, size_t ws_bytes,
              void *stream);
 
-/* ---- Sketch-and-solve with one of the three sketches (Section 6.3) ------- */
+/* ---- SRHT (Section 5: Definition of the SRHT, Algorithm 3) -------------- */
+
+/* Scratch bytes of srht_sketch (d x ncol doubles when d > 8192, plus the
+ * sample lists). */
+size_t msk_srht_workspace(int64_t d, int64_t n, int with_b, int64_t k);
+
+/* Subsampled randomized Hadamard transform of [A b]:
+ *   Y = (1/sqrt(k)) P H_d D [A b],  d = 2^m (2 <= d <= 2^26),
+ *   D   diagonal, d_ii = -1 when bit 0 of draw i of stream tag 5 is set;
+ *   H_d the Hadamard matrix of the recursive definition
+ *       (H_d[i][j] = (-1)^popcount(i & j)), by the fast Walsh-Hadamard
+ *       transform with radix-4 butterflies (Algorithm 3);
+ *   P   k x d row sampling: row l picks row ((z >> 32) * d) >> 32 of H D [A b],
+ *       z = draw l of stream tag 6 (uniform, with replacement).
+ *   A: device FP64 or FP32 (widened exactly), column-major d x n (lda >= d);
+ *   b: device double[d] or NULL (then n >= 1);
+ *   Y: device double, row-major k x ncol (ldy >= ncol), every entry written.
+ * FP64 arithmetic.  Errors: -1 A NULL, -2 dtype, -3 d not a power of two in
+ * [2, 2^26], -4 bad n, -5 lda < d, -7 k < 1, -9 Y NULL, -10 ldy < ncol,
+ * MSK_ENOMEM ws too small. */
+int srht_sketch(const void *A, int dtype, int64_t d, int64_t n, int64_t lda,
+                const double *b, int64_t k, uint64_t seed, double *Y, int64_t ldy,
+                void *ws, size_t ws_bytes, void *stream);
+
+/* ---- Sketch-and-solve with one of the sketches (Section 6.3) ------------- */
 
 /* Scratch bytes of sns_lstsq. */
 size_t msk_sns_workspace(int64_t d, int64_t n, int kind, int64_t k, int64_t p,
@@ -327,7 +356,8 @@ size_t msk_sns_workspace(int64_t d, int64_t n, int kind, int64_t k, int64_t p,
  * R[0:n, n].  MULTI is ms_lstsq with MSK_GEMM_F64 and no refinement.
  * COUNT uses k (>= n+1; p is ignored): the FP64 CountSketch of [A b] (FP32
  * A widened exactly), transposed to column-major for the QR.  GAUSS uses p
- * (n+1 <= p <= 2048; k is ignored).  A, b, x, info and the return codes as
+ * (n+1 <= p <= 2048; k is ignored).  SRHT uses k (>= n+1) and needs d a
+ * power of two (srht_sketch).  A, b, x, info and the return codes as
  * ms_lstsq (n <= 400); -7 unknown kind, -8 bad k (COUNT), -9 bad p (GAUSS).
  * info (optional, host): relres of x; relres_sns = relres. */
 int sns_lstsq(const void *A, int dtype, int64_t d, int64_t n, int64_t lda,

@@ -23,6 +23,10 @@ Parity status of each function (what pins it, see tests/test_oracle_*.py):
   ne_lstsq             agrees with QR when well conditioned, fails for
                        kappa > 1e8 (Section 6.3)
   refine               converges to the exact LS minimiser
+  fwht / srht          the Hadamard matrix of the recursive definition
+                       (scipy.linalg.hadamard), brute force with the explicit
+                       dense S, E||S x||^2 = ||x||^2, uniform rows, balanced
+                       signs
   sns_lstsq_count/     exact recovery for b = A x, distortion bound, E||S y||^2
     _gauss             = ||y||^2 (sketch scaling), same minimiser class as
                        sns_lstsq
@@ -82,6 +86,10 @@ def _declare(L):
     L.or_draw.argtypes = [_u64, _u64]
     L.or_hash.restype = None
     L.or_hash.argtypes = [_u64, _i64, _i64, _i64, _p, _p]
+    L.or_srht_signs.restype = None
+    L.or_srht_signs.argtypes = [_u64, _i64, _p]
+    L.or_srht_rows.restype = None
+    L.or_srht_rows.argtypes = [_u64, _i64, _i64, _p]
     L.or_ln_f32.restype = ctypes.c_float
     L.or_ln_f32.argtypes = [ctypes.c_float]
     L.or_gauss_std.restype = ctypes.c_float
@@ -431,6 +439,61 @@ def rand_cholqr_lstsq(A, b, k: int, p: int, seed: int, gemm_prec: str = "f64"):
     R = np.triu(R1 @ R0)
     y = forward_substitution_transposed(R1, z)
     return back_substitution(R, y), 0
+
+
+# --------------------------------------------------------------------------
+# SRHT (Section 5): S = (1/sqrt(k)) P H_d D.
+
+def srht_signs(seed: int, d: int) -> np.ndarray:
+    """Diagonal of D (int8 +-1): -1 when bit 0 of draw i of stream tag 5 is set."""
+    s = np.empty(d, dtype=np.int8)
+    lib().or_srht_signs(seed & (2**64 - 1), d, _ptr(s))
+    return s
+
+
+def srht_rows(seed: int, k: int, d: int) -> np.ndarray:
+    """Rows of H D x that P samples (uint32, uniform in [0, d), with
+    replacement): multiply-shift of draw l of stream tag 6."""
+    j = np.empty(k, dtype=np.uint32)
+    lib().or_srht_rows(seed & (2**64 - 1), k, d, _ptr(j))
+    return j
+
+
+def fwht(X) -> np.ndarray:
+    """H_d X for the Hadamard matrix of the recursive definition
+    (H_2 = [[1, 1], [1, -1]], H_2l = [[H_l, H_l], [H_l, -H_l]]): the fast
+    Walsh-Hadamard transform, one radix-2 butterfly stage per power of two,
+    applied to every column of X (d x n, d a power of two)."""
+    X = np.array(X, dtype=np.float64, copy=True)
+    d = X.shape[0]
+    assert d >= 1 and d & (d - 1) == 0
+    rest = X.shape[1:]
+    h = 1
+    while h < d:
+        V = X.reshape((d // (2 * h), 2, h) + rest)
+        a = V[:, 0].copy()
+        V[:, 0] += V[:, 1]
+        V[:, 1] = a - V[:, 1]
+        X = V.reshape((d,) + rest)
+        h *= 2
+    return X
+
+
+def srht(A, k: int, seed: int, b=None) -> np.ndarray:
+    """Y = (1/sqrt(k)) P H_d D [A b] (Section 5), k x (n+1), FP64: D's signs
+    applied to the rows, the fast Walsh-Hadamard transform of every column,
+    the sampled rows divided by sqrt(k)."""
+    A64 = np.asarray(A, dtype=np.float64)
+    X = A64 if b is None else np.hstack([A64, np.asarray(b, dtype=np.float64).reshape(-1, 1)])
+    d = X.shape[0]
+    X = srht_signs(seed, d).astype(np.float64)[:, None] * X
+    return fwht(X)[srht_rows(seed, k, d).astype(np.int64)] / np.sqrt(np.float64(k))
+
+
+def sns_lstsq_srht(A, b, k: int, seed: int):
+    """Algorithm 1 with S the SRHT.  Returns (x, relres, R)."""
+    x, R = lstsq_from_sketch(srht(A, k, seed, b))
+    return x, relres(A, b, x), R
 
 
 def sns_lstsq_count(A, b, k: int, seed: int):

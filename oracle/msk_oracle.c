@@ -68,6 +68,23 @@ void or_hash(uint64_t seed, int64_t i0, int64_t count, int64_t k, uint32_t *h,
   }
 }
 
+/* SRHT randomness (Section 5): the diagonal D, d_ii = -1 when the lowest bit
+ * of draw i of stream tag 5 is set, else +1; the rows P samples, row l picks
+ * j_l = ((z >> 32) * d) >> 32 for draw l of stream tag 6 (uniform in [0,d),
+ * with replacement).                                                         */
+void or_srht_signs(uint64_t seed, int64_t d, int8_t *s) {
+  uint64_t key = or_stream_key(seed, 5);
+  for (int64_t i = 0; i < d; ++i) s[i] = (or_draw(key, (uint64_t)i) & 1ULL) ? (int8_t)-1 : (int8_t)1;
+}
+
+void or_srht_rows(uint64_t seed, int64_t k, int64_t d, uint32_t *j) {
+  uint64_t key = or_stream_key(seed, 6);
+  for (int64_t l = 0; l < k; ++l) {
+    uint64_t z = or_draw(key, (uint64_t)l);
+    j[l] = (uint32_t)(((z >> 32) * (uint64_t)d) >> 32);
+  }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Gaussian sampler in binary32 (the Gaussian sketch of Section 1, used as the
  * second stage of the multisketch).  Marsaglia & Bray's polar method:

@@ -35,7 +35,7 @@ EXPORTS = ("msk_version", "msk_last_error", "msk_take_timeout", "msk_selftest_wa
            "cs_sketch", "msk_ms_workspace", "ms_sketch", "msk_gemm_workspace", "msk_gemm",
            "msk_householder_qr", "msk_trsv_upper", "msk_lstsq_workspace", "ms_lstsq",
            "msk_ne_workspace", "ne_lstsq", "msk_rcq_workspace", "rcq_lstsq", "rcq_qr",
-           "msk_sns_workspace", "sns_lstsq",
+           "msk_sns_workspace", "sns_lstsq", "msk_srht_workspace", "srht_sketch",
            "msk_gemm_noalloc", "msk_tune_set", "msk_tune_get",
            "msk_tune_clear", "msk_batch_workspace", "msk_batch_lstsq", "ms_server_create",
            "ms_server_submit", "ms_server_poll", "ms_server_wait_all", "ms_server_stats",
@@ -109,6 +109,8 @@ def _declare(L):
         "ne_lstsq": (_int, [_p, _i64, _i64, _i64, _p, _p, _p, _sz, _p]),
         "msk_rcq_workspace": (_sz, [_i64, _i64, _i64, _i64, _int, _int, _int]),
         "msk_sns_workspace": (_sz, [_i64, _i64, _int, _i64, _i64, _int]),
+        "msk_srht_workspace": (_sz, [_i64, _i64, _int, _i64]),
+        "srht_sketch": (_int, [_p, _int, _i64, _i64, _i64, _p, _i64, _u64, _p, _i64, _p, _sz, _p]),
         "sns_lstsq": (_int, [_p, _int, _i64, _i64, _i64, _p, _int, _i64, _i64, _u64, _p, _p, _p, _sz,
                              _p]),
         "rcq_lstsq": (_int, [_p, _int, _i64, _i64, _i64, _p, _i64, _i64, _u64, _int, _p, _p, _p, _sz,
@@ -374,7 +376,27 @@ def ne_lstsq(A, b, x=None, ws=None, stream=None):
     return x, rc
 
 
-SKETCH_MULTI, SKETCH_COUNT, SKETCH_GAUSS = 0, 1, 2
+SKETCH_MULTI, SKETCH_COUNT, SKETCH_GAUSS, SKETCH_SRHT = 0, 1, 2, 3
+
+
+def msk_srht_workspace(d, n, with_b, k):
+    return load().msk_srht_workspace(d, n, int(bool(with_b)), k)
+
+
+def srht_sketch(A, k, seed, b=None, Y=None, ws=None, stream=None):
+    """Y = (1/sqrt(k)) P H D [A b] (Section 5), row-major k x (n+1) FP64
+    (d a power of two)."""
+    _cuda(A, "A")
+    d, n = A.shape
+    ncol = n + (0 if b is None else 1)
+    if Y is None:
+        Y = torch.empty((k, ncol), dtype=torch.float64, device=A.device)
+    if ws is None:
+        ws = workspace(msk_srht_workspace(d, n, b is not None, k), A.device)
+    rc = load().srht_sketch(_ptr(A), _dtype_code(A), d, n, _colmajor(A), _ptr(b), k, seed & (2**64 - 1),
+                            _ptr(Y), Y.stride(0), _ptr(ws), ws.numel(), _stream(stream))
+    _check("srht_sketch", rc)
+    return Y
 
 
 def msk_sns_workspace(d, n, kind, k, p, dtype):

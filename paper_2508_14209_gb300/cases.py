@@ -4,8 +4,9 @@
     python -m paper_2508_14209_gb300.cases gemm    --p 1024 --k 32768 --ncol 257 --prec bf16x3
     python -m paper_2508_14209_gb300.cases refined --d 1333142 --n 128 --log10-sigma -2.7 [--path single]
     python -m paper_2508_14209_gb300.cases ne      --d 8388608 --n 128 --log10-sigma -6
-    python -m paper_2508_14209_gb300.cases sns     --d 8388608 --n 128 --log10-sigma -6 [--kind count|gauss]
+    python -m paper_2508_14209_gb300.cases sns     --d 8388608 --n 128 --log10-sigma -6 [--kind count|gauss|srht]
     python -m paper_2508_14209_gb300.cases rcq     --d 8388608 --n 128 --log10-sigma -6
+    python -m paper_2508_14209_gb300.cases srht    --d 8388608 --n 128
 
 Each case draws its seeded synthetic input once on the GPU (the generators of
 the `inputs` module), runs the library call `--reps` times and prints one JSON
@@ -28,7 +29,7 @@ def main(argv=None):
     import paper_2508_14209_gb300 as msk
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["sketch", "gemm", "refined", "ne", "sns", "rcq"])
+    ap.add_argument("case", choices=["sketch", "gemm", "refined", "ne", "sns", "rcq", "srht"])
     ap.add_argument("--d", type=int, default=1 << 20)
     ap.add_argument("--n", type=int, default=64)
     ap.add_argument("--dtype", choices=["f64", "f32"], default="f64")
@@ -41,7 +42,7 @@ def main(argv=None):
     ap.add_argument("--path", choices=["batch", "single"], default="batch",
                     help="refined: msk_batch_lstsq of one request (its inner loop runs inside a "
                          "graph's while node) or ms_lstsq (the same kernels launched one by one)")
-    ap.add_argument("--kind", choices=["multi", "count", "gauss"], default="multi",
+    ap.add_argument("--kind", choices=["multi", "count", "gauss", "srht"], default="multi",
                     help="sns: the sketch (multisketch G C, CountSketch C alone, Gaussian G alone)")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--seed", type=int, default=0x5EED0004)
@@ -62,6 +63,15 @@ def main(argv=None):
         Y = torch.empty((k, a.n), dtype=dt, device=dev)
         call = lambda: msk.cs_sketch(A, k, a.seed, Y=Y)  # noqa: E731
         out.update(d=a.d, n=a.n, k=k, dtype=a.dtype, bytes_per_call=a.d * a.n * A.element_size())
+    elif a.case == "srht":
+        # SRHT of A (d a power of two) to k = 2 n^2 rows: FP64 adds, d n log2(d)
+        A = inputs.normal_matrix(a.d, a.n, a.seed, dtype=torch.float64, device=dev)
+        k = 2 * a.n * a.n
+        Y = torch.empty((k, a.n), dtype=torch.float64, device=dev)
+        ws = msk.workspace(msk.msk_srht_workspace(a.d, a.n, False, k), dev)
+        call = lambda: msk.srht_sketch(A, k, a.seed, Y=Y, ws=ws)  # noqa: E731
+        m = a.d.bit_length() - 1
+        out.update(d=a.d, n=a.n, k=k, adds_per_call=a.d * a.n * m)
     elif a.case == "gemm":
         prec = msk.GEMM_PRECS[a.prec]
         ydt = torch.float64 if prec == msk.GEMM_F64 else torch.float32
@@ -96,7 +106,8 @@ def main(argv=None):
             out.update(flops_per_call=a.d * (a.n * (a.n + 1) + (a.n + 1) * (a.n + 2)))
         else:
             k, p = 2 * a.n * a.n, 4 * a.n
-            kind = {"multi": msk.SKETCH_MULTI, "count": msk.SKETCH_COUNT, "gauss": msk.SKETCH_GAUSS}[a.kind]
+            kind = {"multi": msk.SKETCH_MULTI, "count": msk.SKETCH_COUNT, "gauss": msk.SKETCH_GAUSS,
+                    "srht": msk.SKETCH_SRHT}[a.kind]
             ws = msk.workspace(msk.msk_sns_workspace(a.d, a.n, kind, k, p, msk.MSK_F64), dev)
 
             def call():

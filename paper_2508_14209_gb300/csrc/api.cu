@@ -130,6 +130,25 @@ int ms_gaussian(uint64_t seed, int64_t p, int64_t k, int out_prec, void* G, int6
   return launch_gaussian(stream_key(seed, kTagGauss), p, k, out_prec, G, ldg, as_stream(stream));
 }
 
+size_t msk_srht_workspace(int64_t d, int64_t n, int with_b, int64_t k) {
+  return srht_workspace(d, n + (with_b ? 1 : 0), k);
+}
+
+int srht_sketch(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, const double* b,
+                int64_t k, uint64_t seed, double* Y, int64_t ldy, void* ws, size_t ws_bytes,
+                void* stream) {
+  if (!A) return -1;
+  if (dtype != MSK_F64 && dtype != MSK_F32) return -2;
+  if (d < 2 || (d & (d - 1)) != 0 || d > (int64_t(1) << 26)) return -3;
+  if (n < 0 || n + (b ? 1 : 0) < 1 || n + (b ? 1 : 0) > 65535) return -4;
+  if (lda < d) return -5;
+  if (k < 1 || k > 0xFFFFFFFFLL) return -7;
+  if (!Y) return -9;
+  if (ldy < n + (b ? 1 : 0)) return -10;
+  if (ws_bytes < msk_srht_workspace(d, n, b ? 1 : 0, k)) return MSK_ENOMEM;
+  return launch_srht(A, dtype, d, n, lda, b, k, seed, Y, ldy, ws, ws_bytes, as_stream(stream));
+}
+
 size_t msk_cs_workspace(int64_t d, int64_t n, int64_t k, int dtype, int strategy) {
   (void)n;
   (void)dtype;

@@ -838,6 +838,29 @@ __global__ void cs_bucket_sum_kernel(const T* __restrict__ A, int64_t lda, int64
   }
 }
 
+// Counting sort of the draws 0..count-1 of stream `key` by
+// bucket_of(draw, nb): offs[0..nb] the exclusive prefix of the bucket sizes,
+// perm[0..count) the draw indices grouped by bucket (in no fixed order within
+// a bucket).  cnt, cursor: nb words of scratch each.
+int launch_draw_bucket_sort(uint64_t key, int64_t count, uint32_t nb, uint32_t* offs,
+                            uint32_t* perm, uint32_t* cnt, uint32_t* cursor, cudaStream_t st) {
+  MSK_CUDA(cudaMemsetAsync(cnt, 0, (size_t)nb * 4, st));
+  MSK_CUDA(cudaMemsetAsync(cursor, 0, (size_t)nb * 4, st));
+  const unsigned gb =
+      (unsigned)std::max<int64_t>(1, std::min<int64_t>((count + 255) / 256, num_sms() * 16));
+  if (count > 0) {
+    cs_hist_kernel<<<gb, 256, 0, st>>>(key, count, nb, cnt);
+    MSK_CHECK_LAUNCH("cs_hist_kernel");
+  }
+  cs_scan_kernel<<<1, 1024, 0, st>>>(cnt, nb, offs);
+  MSK_CHECK_LAUNCH("cs_scan_kernel");
+  if (count > 0) {
+    cs_scatter_kernel<<<gb, 256, 0, st>>>(key, count, nb, offs, cursor, perm);
+    MSK_CHECK_LAUNCH("cs_scatter_kernel");
+  }
+  return MSK_OK;
+}
+
 int launch_cs_sorted(const void* A, int dtype, int64_t d, int64_t n, int64_t lda,
                      const double* b, uint32_t k, uint64_t key, void* Y, int64_t ldy,
                      void* ws, size_t ws_bytes, cudaStream_t st) {

@@ -752,9 +752,10 @@ size_t msk_sns_workspace(int64_t d, int64_t n, int kind, int64_t k, int64_t p, i
   if (kind == MSK_SKETCH_MULTI) return msk_lstsq_workspace(d, n, k, p, dtype, MSK_GEMM_F64, 0);
   const int64_t ncol = n + 1;
   Need nd;
-  if (kind == MSK_SKETCH_COUNT) {
+  if (kind == MSK_SKETCH_COUNT || kind == MSK_SKETCH_SRHT) {
     nd.add((size_t)k * ((ncol + 1) / 2 * 2) * sizeof(double));  // Y, row-major
     nd.add((size_t)k * ncol * sizeof(double));                  // W, column-major
+    if (kind == MSK_SKETCH_SRHT) nd.add(srht_workspace(d, ncol, k));
   } else {
     nd.add((size_t)p * ncol * sizeof(double));  // Z
     nd.add(gauss_gemm_workspace(p, d, ncol));
@@ -776,8 +777,11 @@ int sns_lstsq(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, const
   if (n < 1 || n > 400) return -4;
   if (lda < d) return -5;
   if (!b) return -6;
-  if (kind != MSK_SKETCH_COUNT && kind != MSK_SKETCH_GAUSS) return -7;
-  if (kind == MSK_SKETCH_COUNT && (k < n + 1 || k > 0xFFFFFFFFLL)) return -8;
+  if (kind != MSK_SKETCH_COUNT && kind != MSK_SKETCH_GAUSS && kind != MSK_SKETCH_SRHT) return -7;
+  if ((kind == MSK_SKETCH_COUNT || kind == MSK_SKETCH_SRHT) && (k < n + 1 || k > 0xFFFFFFFFLL))
+    return -8;
+  if (kind == MSK_SKETCH_SRHT && (d < 2 || (d & (d - 1)) != 0 || d > (int64_t(1) << 26)))
+    return MSK_ENOTSUP;
   if (kind == MSK_SKETCH_GAUSS && (p < n + 1 || p > 2048)) return -9;
   if (!x) return -11;
   if (ws_bytes < msk_sns_workspace(d, n, kind, k, p, dtype)) return MSK_ENOMEM;
@@ -787,13 +791,21 @@ int sns_lstsq(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, const
   double* W;  // the sketched [SA Sb], column-major m x ncol
   int64_t m;
   int rc;
-  if (kind == MSK_SKETCH_COUNT) {
-    // S = C: the k x (n+1) CountSketch itself (Definition 3), FP64
+  if (kind == MSK_SKETCH_COUNT || kind == MSK_SKETCH_SRHT) {
+    // S = C: the k x (n+1) CountSketch itself (Definition 3), FP64; or the
+    // SRHT (Section 5)
     const int64_t ldy = (ncol + 1) / 2 * 2;
     double* Y = static_cast<double*>(cv.take((size_t)k * ldy * sizeof(double)));
     W = static_cast<double*>(cv.take((size_t)k * ncol * sizeof(double)));
     if (!Y || !W) return MSK_ENOMEM;
-    rc = count_sketch_f64y(A, dtype, d, n, lda, b, k, seed, Y, ldy, st);
+    if (kind == MSK_SKETCH_COUNT) {
+      rc = count_sketch_f64y(A, dtype, d, n, lda, b, k, seed, Y, ldy, st);
+    } else {
+      const size_t sws = srht_workspace(d, ncol, k);
+      void* sw = cv.take(sws);
+      if (!sw) return MSK_ENOMEM;
+      rc = launch_srht(A, dtype, d, n, lda, b, k, seed, Y, ldy, sw, sws, st);
+    }
     if (rc) return rc;
     dim3 grid((unsigned)((k + 31) / 32), (unsigned)((ncol + 31) / 32));
     transpose_rm_to_cm_kernel<<<grid, 256, 0, st>>>(Y, ldy, k, ncol, W, k);

@@ -15,6 +15,8 @@ constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
 constexpr uint64_t kStreamMul = 0xD1B54A32D192ED03ull;
 constexpr uint64_t kTagHash = 0;
 constexpr uint64_t kTagGauss = 2;
+constexpr uint64_t kTagSrhtSign = 5;  // SRHT: the signs of D
+constexpr uint64_t kTagSrhtRow = 6;   // SRHT: the rows P samples
 
 __host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;

@@ -150,6 +150,14 @@ int launch_trsv_upper(const double* R, int64_t n, int64_t ldr, const double* rhs
 int launch_cholesky(double* Gm, int64_t n, int64_t ldg, double* R, int64_t ldr, int* status,
                     cudaStream_t st);
 int first_zero_pivot(const double* R, int64_t n, int64_t ldr, cudaStream_t st);
+// countsketch.cu: counting sort of counter draws by bucket
+int launch_draw_bucket_sort(uint64_t key, int64_t count, uint32_t nb, uint32_t* offs,
+                            uint32_t* perm, uint32_t* cnt, uint32_t* cursor, cudaStream_t st);
+// srht.cu (subsampled randomized Hadamard transform, Section 5)
+size_t srht_workspace(int64_t d, int64_t ncol, int64_t k);
+int launch_srht(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, const double* b,
+                int64_t k, uint64_t seed, double* Y, int64_t ldy, void* ws, size_t ws_bytes,
+                cudaStream_t st);
 // rcq.cu (randomized Cholesky QR's tall product and small triangular product)
 size_t trmm_upper_smem(int64_t n);
 int launch_trmm_upper(const void* X, int dtype, int64_t ldx, int64_t d, int64_t n, const double* U,
