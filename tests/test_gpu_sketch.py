@@ -151,9 +151,12 @@ def test_full_size_sampled_buckets_f64(msk, orc):
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
+# column counts 7, 32, 4, 64, 129, 65, 33: tiles of 32, 48 and 64 columns
 @pytest.mark.parametrize("d,n,k,p,with_b,dtype", [
     (5000, 6, 72, 24, True, torch.float64), (20000, 32, 2048, 128, False, torch.float64),
-    (3001, 3, 18, 12, True, torch.float32), (40000, 64, 8192, 256, False, torch.float32)])
+    (3001, 3, 18, 12, True, torch.float32), (40000, 64, 8192, 256, False, torch.float32),
+    (30000, 128, 4096, 200, True, torch.float64), (12000, 64, 2048, 130, True, torch.float64),
+    (9000, 32, 1024, 97, True, torch.float32)])
 def test_multisketch_simt(msk, orc, prec, d, n, k, p, with_b, dtype):
     seed = 0x5EED0003 + n
     A, b, Ad, bd = _inputs(d, n, with_b, dtype, seed, 0)
