@@ -39,9 +39,11 @@ def main(argv=None):
     ap.add_argument("--prec", default="bf16x3", choices=sorted(msk.GEMM_PRECS))
     ap.add_argument("--log10-sigma", type=float, default=-4.0)
     ap.add_argument("--tol", type=float, default=1e-6)
-    ap.add_argument("--path", choices=["batch", "single"], default="batch",
+    ap.add_argument("--path", choices=["batch", "single", "plain"], default="batch",
                     help="refined: msk_batch_lstsq of one request (its inner loop runs inside a "
-                         "graph's while node) or ms_lstsq (the same kernels launched one by one)")
+                         "graph's while node), ms_lstsq (the same kernels launched one by one), or "
+                         "plain: FP64 sketch-and-solve of the same stored FP32 A (ms_lstsq, MSK_GEMM_F64, "
+                         "no refinement), the served comparison's plain path")
     ap.add_argument("--kind", choices=["multi", "count", "gauss", "srht"], default="multi",
                     help="sns: the sketch (multisketch G C, CountSketch C alone, Gaussian G alone)")
     ap.add_argument("--reps", type=int, default=3)
@@ -125,6 +127,12 @@ def main(argv=None):
             def call():
                 r = msk.msk_batch_lstsq(prob, refine=True, tol=a.tol, max_iter=4, ws=ws)
                 res["r"] = r[1][0]
+        elif a.path == "plain":
+            k, p = 2 * a.n * a.n, 4 * a.n
+            ws = msk.workspace(msk.msk_lstsq_workspace(a.d, a.n, k, p, msk.MSK_F32, msk.GEMM_F64, 0), dev)
+
+            def call():
+                res["r"] = msk.ms_lstsq(A, b, k, p, a.seed, msk.GEMM_F64, ws=ws)[1]
         else:
             k, p = 2 * a.n * a.n, 4 * a.n
             ws = msk.workspace(msk.msk_lstsq_workspace(a.d, a.n, k, p, msk.MSK_F32, msk.GEMM_BF16X3, 1), dev)

@@ -47,3 +47,30 @@ def test_version_and_workspace_queries(lib):
     # pure host-side size queries
     assert msk.msk_cs_workspace(1000, 4, 64, msk.MSK_F64, msk.CS_ATOMIC) == 0
     assert msk.msk_cs_workspace(1000, 4, 64, msk.MSK_F64, msk.CS_SORTED) >= 1000 * 4
+
+
+def test_argument_checks_return_before_any_device_work(lib):
+    """Invalid arguments are refused with the documented negative codes
+    before any pointer is touched (the pointers below are never
+    dereferenced)."""
+    import paper_2508_14209_gb300 as msk
+
+    L = msk.load()
+    fake = ctypes.c_void_p(16)
+    # srht_sketch: d must be a power of two (-3); k >= 1 (-7)
+    assert L.srht_sketch(fake, msk.MSK_F64, 1000, 4, 1000, None, 10, 1, fake, 4, None, 0, None) == -3
+    assert L.srht_sketch(fake, msk.MSK_F64, 1024, 4, 1024, None, 0, 1, fake, 4, None, 0, None) == -7
+    # sns_lstsq: unknown sketch kind (-7); GAUSS needs n+1 <= p (-9)
+    assert L.sns_lstsq(fake, msk.MSK_F64, 100, 4, 100, fake, 9, 50, 8, 1, fake, None, None, 0, None) == -7
+    assert L.sns_lstsq(fake, msk.MSK_F64, 100, 4, 100, fake, msk.SKETCH_GAUSS, 0, 4, 1, fake, None, None,
+                       0, None) == -9
+    # rcq_lstsq / rcq_qr: n <= 400 (-4), p >= n + 1 (-8)
+    assert L.rcq_lstsq(fake, msk.MSK_F64, 10000, 401, 10000, fake, 400000, 1604, 1, msk.GEMM_F64, fake,
+                       None, None, 0, None) == -4
+    assert L.rcq_qr(fake, msk.MSK_F64, 10000, 20, 10000, 800, 20, 1, msk.GEMM_F64, fake, 10000, fake, 20,
+                    None, 0, None) == -8
+    # msk_householder_qr: c <= 512 (-3)
+    assert L.msk_householder_qr(fake, 1000, 513, 1000, None) == -3
+    # workspace queries are pure host arithmetic
+    assert msk.msk_srht_workspace(1 << 20, 7, True, 4096) >= (1 << 20) * 8 * 8
+    assert msk.msk_srht_workspace(1000, 7, True, 4096) == 0  # not a power of two
