@@ -52,10 +52,10 @@ DEFAULT = "multisketch_f64_4194304x64"
 # read + 3.06 MB written FP64; 270.55 + 3.13 MB FP32), scaled by the rows
 # processed (the kernel streams A once, so traffic grows in proportion).
 CS_TRAFFIC = {
-    "multisketch_f64_4194304x64": 4 * (541.097e6 + 3.062e6),
-    "multisketch_f32_4194304x64": 4 * (270.554e6 + 3.128e6),
-    "multisketch_f64_1048576x64": 541.097e6 + 3.062e6,
-    "multisketch_f32_1048576x64": 270.554e6 + 3.128e6,
+    "multisketch_f64_4194304x64": 4 * (541.098e6 + 3.041e6),
+    "multisketch_f32_4194304x64": 4 * (270.554e6 + 3.080e6),
+    "multisketch_f64_1048576x64": 541.098e6 + 3.041e6,
+    "multisketch_f32_1048576x64": 270.554e6 + 3.080e6,
 }
 
 
