@@ -31,6 +31,12 @@ int smem_optin_max() {
   return v;
 }
 
+cudaError_t zero_rows(void* Y, int64_t ldy, int64_t ncol, int64_t k, size_t esz, cudaStream_t st) {
+  if (k <= 0 || ncol <= 0) return cudaSuccess;
+  if (ldy == ncol) return cudaMemsetAsync(Y, 0, (size_t)k * (size_t)ncol * esz, st);
+  return cudaMemset2DAsync(Y, (size_t)ldy * esz, 0, (size_t)ncol * esz, (size_t)k, st);
+}
+
 cudaError_t allow_max_smem(const void* func) {
   cudaFuncAttributes fa;
   cudaError_t e = cudaFuncGetAttributes(&fa, func);
@@ -172,7 +178,7 @@ int msk::count_sketch_f64y(const void* A, int dtype, int64_t d, int64_t n, int64
     return launch_cs_atomic(A, dtype, d, n, lda, b, (uint32_t)k, stream_key(seed, kTagHash), Y, ldy,
                             false, st);
   const int64_t ncol = n + (b ? 1 : 0);
-  MSK_CUDA(cudaMemset2DAsync(Y, (size_t)ldy * 8, 0, (size_t)ncol * 8, (size_t)k, st));
+  MSK_CUDA(zero_rows(Y, ldy, ncol, k, 8, st));
   int64_t maxc = 256;
   const int64_t fit = (int64_t)(tune_get("cs.l2_budget_bytes", 48ll << 20)) / (k * 8);
   if (fit >= 64 && fit / 64 * 64 < maxc) maxc = fit / 64 * 64;

@@ -624,7 +624,7 @@ static int cs_atomic_typed(const T* A, int64_t d, int64_t n, int64_t lda, const 
                            uint32_t k, uint64_t key, T* Y, int64_t ldy, bool pad_ok,
                            cudaStream_t st) {
   const int64_t ncol = n + (b ? 1 : 0);
-  MSK_CUDA(cudaMemset2DAsync(Y, (size_t)ldy * sizeof(T), 0, (size_t)ncol * sizeof(T), (size_t)k, st));
+  MSK_CUDA(zero_rows(Y, ldy, ncol, k, sizeof(T), st));
   if (d == 0 || ncol == 0) return MSK_OK;
   // Column chunks of at most kCsMaxColsF64/F32; b rides with the last chunk.
   // Column chunks: at most the shared-memory limit, and narrow enough that the

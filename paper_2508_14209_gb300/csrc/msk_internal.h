@@ -54,6 +54,10 @@ struct Need {
 };
 
 int num_sms();
+// Zero the first `ncol` elements (esz bytes each) of k rows of pitch ldy
+// elements: one contiguous memset when the rows are packed (ldy == ncol),
+// a 2D memset otherwise.
+cudaError_t zero_rows(void* Y, int64_t ldy, int64_t ncol, int64_t k, size_t esz, cudaStream_t st);
 // Opt-in shared-memory limit per block of the current device (bytes).
 int smem_optin_max();
 // Allow `func` all the dynamic shared memory the device offers next to its
