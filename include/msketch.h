@@ -151,6 +151,9 @@ int msk_selftest_wait(void *stream);
  *                         from 128 columns up)
  *   "cs.f32.prefetch"     the same for the FP32 CountSketch (default: on at 128
  *                         columns only)
+ *   "cs.f64.narrow"       0 = no narrow FP64 kernel for <= 32 columns (default on)
+ *   "cs.f64.replicas"     0 = the narrow FP64 kernel adds into Y directly
+ *                         (default: replicas from ws where they apply)
  *   "tc.drain"            0 = split-BF16 GEMM without draining accumulators
  *   "batch.kt_per"        K tiles per CTA of the batched tensor-core GEMM (16)
  *   "batch.round"         CG iterations per captured graph round (4)
@@ -182,7 +185,10 @@ int ms_gaussian(uint64_t seed, int64_t p, int64_t k, int out_prec, void *G,
 
 /* ---- CountSketch (Definition 3; Algorithm 2) --------------------------- */
 
-/* Scratch bytes cs_sketch needs (0 for MSK_CS_ATOMIC). */
+/* Scratch bytes cs_sketch needs: for MSK_CS_SORTED the sort arrays; for
+ * MSK_CS_ATOMIC with FP64 A, room for 8 or 16 replicas of Y when the sketch
+ * has few 128-byte lines (k * ncol small, e.g. n = 16 at k = 512), else 0.
+ * A smaller ws is allowed for MSK_CS_ATOMIC: the replicas are then skipped. */
 size_t msk_cs_workspace(int64_t d, int64_t n, int64_t k, int dtype,
                         int strategy);
 

@@ -6,6 +6,7 @@
 
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 
 #include "msk_device.cuh"
 #include "msk_internal.h"
@@ -156,10 +157,10 @@ int srht_sketch(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, con
 }
 
 size_t msk_cs_workspace(int64_t d, int64_t n, int64_t k, int dtype, int strategy) {
-  (void)n;
-  (void)dtype;
   if (strategy == MSK_CS_SORTED) return cs_sorted_workspace(d, k);
-  return 0;
+  if (dtype != MSK_F64) return 0;
+  // replicas of Y for narrow FP64 sketches (with or without the b column)
+  return std::max(cs_replica_bytes(k, n), cs_replica_bytes(k, n + 1));
 }
 
 int cs_sketch(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, const double* b,
@@ -202,7 +203,8 @@ int msk::cs_sketch_internal(const void* A, int dtype, int64_t d, int64_t n, int6
   if (strategy != MSK_CS_ATOMIC && strategy != MSK_CS_SORTED) return -11;
   const uint64_t key = stream_key(seed, kTagHash);
   if (strategy == MSK_CS_ATOMIC)
-    return launch_cs_atomic(A, dtype, d, n, lda, b, (uint32_t)k, key, Y, ldy, pad_ok, st);
+    return launch_cs_atomic(A, dtype, d, n, lda, b, (uint32_t)k, key, Y, ldy, pad_ok, st, ws,
+                            ws_bytes);
   if (d >= (1LL << 31) || k >= (1LL << 31)) return MSK_ENOTSUP;
   if (ws_bytes < cs_sorted_workspace(d, k)) return MSK_ENOMEM;
   return launch_cs_sorted(A, dtype, d, n, lda, b, (uint32_t)k, key, Y, ldy, ws, ws_bytes, st);

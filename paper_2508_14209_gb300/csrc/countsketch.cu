@@ -369,6 +369,77 @@ __global__ void __launch_bounds__(kCsThreads) cs_fixed_f64_kernel(const CsParams
 
 
 
+// Narrow FP64 variant (at most 32 A columns): a 32-row tile of 16 or 32
+// columns carries too few elements for its barrier, hash and address work,
+// so a tile here is RB blocks of 32 rows (lane = row within a block in the
+// load phase; warp rb < RB hashes block rb), and in the reduction phase
+// NCA lanes cover a row, i.e. two rows per warp instruction at 16 columns.
+// nrep > 1: CTA c adds into replica c % nrep of Y (P.Y + (c % nrep) *
+// rep_stride): with k = 2n^2 the sketch of a narrow A has only a few hundred
+// to a few thousand 128-byte lines, and the L2 serialises reductions to the
+// same line; the replicas are summed into Y afterwards.
+template <int NCA, bool HAS_B, typename TA, int RB>
+__global__ void __launch_bounds__(kCsThreads) cs_narrow_f64_kernel(const CsParams<double> P,
+                                                                const TA* __restrict__ Aa,
+                                                                int nrep, int64_t rep_stride) {
+  static_assert(NCA == 16 || NCA == 32, "narrow widths");
+  static_assert(RB >= 1 && RB <= kCsWarps, "one hashing warp per row block");
+  constexpr int ROWS = 32 * RB;
+  constexpr int NCOL = NCA + (HAS_B ? 1 : 0);
+  constexpr int PITCH = NCOL | 1;
+  constexpr int Q = NCA / kCsWarps;  // columns per warp in the load phase
+  constexpr int RPI = 32 / NCA;      // rows per warp instruction in the reduction
+  __shared__ double tiles[2][ROWS][PITCH];
+  __shared__ uint64_t hz[2][ROWS];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nca = P.ncol_a;  // <= NCA
+  const int64_t ntiles = (P.d + ROWS - 1) / ROWS;
+  double* const ybase = P.Y + (nrep > 1 ? (int64_t)(blockIdx.x % nrep) * rep_stride : 0);
+  int buf = 0;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, buf ^= 1) {
+    const int64_t i0 = t * ROWS;
+    double v[RB][Q];
+    double vb[RB];
+    uint64_t zr = 0;
+#pragma unroll
+    for (int rb = 0; rb < RB; ++rb) {
+      const int64_t i = i0 + rb * 32 + lane;
+      const bool row_ok = i < P.d;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const int j = warp + q * kCsWarps;
+        v[rb][q] = (row_ok && j < nca) ? (double)__ldcs(Aa + i + (int64_t)j * P.lda) : 0.0;
+      }
+      vb[rb] = (HAS_B && warp == kCsWarps - 1 && row_ok) ? __ldcs(P.b + i) : 0.0;
+      if (warp == rb) zr = row_ok ? draw(P.key, (uint64_t)i) : 0ull;
+    }
+#pragma unroll
+    for (int rb = 0; rb < RB; ++rb) {
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const int j = warp + q * kCsWarps;
+        if (j < nca) tiles[buf][rb * 32 + lane][j] = v[rb][q];
+      }
+      if (HAS_B && warp == kCsWarps - 1) tiles[buf][rb * 32 + lane][nca] = vb[rb];
+    }
+    if (warp < RB) hz[buf][warp * 32 + lane] = zr;
+    __syncthreads();
+    const int c = lane % NCA;
+#pragma unroll
+    for (int r0 = warp * RPI; r0 < ROWS; r0 += kCsWarps * RPI) {
+      const int r = r0 + lane / NCA;
+      if (i0 + r < P.d) {
+        const uint64_t z = hz[buf][r];
+        double* yrow = ybase + (int64_t)bucket_of(z, P.k) * P.ldy;
+        const unsigned long long sg = negative_of(z) ? 0x8000000000000000ull : 0ull;
+        if (c < nca) red_add(yrow + c, flip(tiles[buf][r][c], sg));
+        if (HAS_B && c == 0) red_add(yrow + nca, flip(tiles[buf][r][nca], sg));
+      }
+    }
+  }
+}
+
+
 template <int NCA, bool HAS_B>
 struct CsF32Tile {
   static constexpr int NG = (NCA + 3) / 4;           // 4-column groups of A
@@ -499,16 +570,21 @@ __global__ void __launch_bounds__(kCsThreads) cs_batch_f32_kernel(const CsParams
 }
 
 template <typename KernT, typename ParT, typename... Extra>
-static int launch_fixed(KernT kern, const ParT& P, cudaStream_t st, Extra... extra) {
+static int launch_fixed_rows(KernT kern, int rows, const ParT& P, cudaStream_t st,
+                             Extra... extra) {
   int per_sm = 0;
   MSK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kCsThreads, 0));
   per_sm = std::max(per_sm, 1);
-  const int64_t ntiles = (P.d + kCsRows - 1) / kCsRows;
+  const int64_t ntiles = (P.d + rows - 1) / rows;
   const int64_t grid = std::min<int64_t>(ntiles, (int64_t)num_sms() * per_sm);
   if (grid <= 0) return MSK_OK;
   kern<<<(unsigned)grid, kCsThreads, 0, st>>>(P, extra...);
   MSK_CHECK_LAUNCH("cs_fixed_kernel");
   return MSK_OK;
+}
+template <typename KernT, typename ParT, typename... Extra>
+static int launch_fixed(KernT kern, const ParT& P, cudaStream_t st, Extra... extra) {
+  return launch_fixed_rows(kern, kCsRows, P, st, extra...);
 }
 
 // Batched FP32 CountSketch launch over `nprob` problems of A-width nca with a
@@ -535,9 +611,67 @@ int launch_cs_batch_f32(int nca, const CsParams<float>* Ps, const int64_t* tile_
   }
 }
 
+// Replicas of Y for the narrow FP64 kernel: doubled while the sketch has
+// fewer than 8192 distinct 128-byte lines in all, at most 16; used only when
+// that gives 8 or more (measured: 16 columns at k = 512, 1.7x; 32 columns at
+// k = 2048 with 4 replicas, no gain).
+static int cs_replicas(int64_t k, int64_t ncol) {
+  const int64_t lines = k * ((ncol * 8 + 127) / 128);
+  int r = 1;
+  while (r < 16 && lines * r * 2 <= 16384) r *= 2;
+  return r >= 8 ? r : 1;
+}
+size_t cs_replica_bytes(int64_t k, int64_t ncol) {
+  if (ncol < 1 || ncol > 33) return 0;
+  const int r = cs_replicas(k, ncol);
+  return r > 1 ? (size_t)r * (size_t)k * (size_t)ncol * sizeof(double) : 0;
+}
+
+// Y[r][c] = sum over the replicas (in replica order) of rep[q][r][c].
+__global__ void cs_replica_sum_kernel(const double* __restrict__ rep, int nrep, int64_t stride,
+                                      int64_t k, int ncol, double* __restrict__ Y, int64_t ldy) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < k * ncol;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int q = 0; q < nrep; ++q) s += rep[q * stride + e];
+    Y[(e / ncol) * ldy + e % ncol] = s;
+  }
+}
+
+// Narrow FP64 launch (<= 32 A columns), into replicas of Y when `ws` has room.
+template <int NCA, int RB, typename TA>
+static int launch_narrow_f64(const CsParams<double>& P0, const TA* Aa, void* ws, size_t ws_bytes,
+                             cudaStream_t st) {
+  const bool hb = P0.b != nullptr;
+  CsParams<double> P = P0;
+  int nrep = 1;
+  int64_t stride = 0;
+  const int r = cs_replicas(P0.k, P0.ncol);
+  if (r > 1 && ws && ws_bytes >= (size_t)r * P0.k * P0.ncol * sizeof(double) &&
+      tune_get("cs.f64.replicas", 1) != 0) {
+    nrep = r;
+    stride = (int64_t)P0.k * P0.ncol;
+    P.Y = static_cast<double*>(ws);
+    P.ldy = P0.ncol;
+    MSK_CUDA(cudaMemsetAsync(ws, 0, (size_t)nrep * stride * sizeof(double), st));
+  }
+  int rc = hb ? launch_fixed_rows(cs_narrow_f64_kernel<NCA, true, TA, RB>, 32 * RB, P, st, Aa, nrep,
+                                  stride)
+              : launch_fixed_rows(cs_narrow_f64_kernel<NCA, false, TA, RB>, 32 * RB, P, st, Aa, nrep,
+                                  stride);
+  if (rc || nrep == 1) return rc;
+  const int64_t total = (int64_t)P0.k * P0.ncol;
+  cs_replica_sum_kernel<<<(unsigned)std::min<int64_t>((total + 255) / 256, num_sms() * 8), 256, 0,
+                          st>>>(static_cast<const double*>(ws), nrep, stride, P0.k, P0.ncol, P0.Y,
+                                P0.ldy);
+  MSK_CHECK_LAUNCH("cs_replica_sum_kernel");
+  return MSK_OK;
+}
+
 // Returns 1 when a fixed-width kernel covered this chunk.
 template <typename T>
-static int cs_fixed_chunk(const CsParams<T>& P, cudaStream_t st, int* rc) {
+static int cs_fixed_chunk(const CsParams<T>& P, cudaStream_t st, int* rc, void* ws = nullptr,
+                          size_t ws_bytes = 0) {
   *rc = MSK_OK;
   if (tune_get("cs.fixed", 1) == 0) return 0;
   const bool hb = P.b != nullptr;
@@ -557,6 +691,14 @@ static int cs_fixed_chunk(const CsParams<T>& P, cudaStream_t st, int* rc) {
                : launch_fixed(cs_fixed_f64_kernel<N, false, double, false>, P, st, P.A);      \
     return 1;                                                                                 \
   }
+    if (nca <= 16 && tune_get("cs.f64.narrow", 1) != 0) {
+      *rc = launch_narrow_f64<16, 4>(P, P.A, ws, ws_bytes, st);
+      return 1;
+    }
+    if (nca <= 32 && tune_get("cs.f64.narrow", 1) != 0) {
+      *rc = launch_narrow_f64<32, 2>(P, P.A, ws, ws_bytes, st);
+      return 1;
+    }
     MSK_FIX64(16) MSK_FIX64(32) MSK_FIX64(64) MSK_FIX64(128) MSK_FIX64(256)
 #undef MSK_FIX64
   } else {
@@ -612,7 +754,17 @@ int launch_cs_f32a_f64y(const float* A, int64_t d, int64_t n, int64_t lda, const
       if (rc) return rc;                                                                \
       continue;                                                                         \
     }
-    MSK_FIXF(16) MSK_FIXF(32) MSK_FIXF(64) MSK_FIXF(128) MSK_FIXF(256)
+    if (w <= 16) {
+      rc = launch_narrow_f64<16, 4>(P, Ac, nullptr, 0, st);
+      if (rc) return rc;
+      continue;
+    }
+    if (w <= 32) {
+      rc = launch_narrow_f64<32, 2>(P, Ac, nullptr, 0, st);
+      if (rc) return rc;
+      continue;
+    }
+    MSK_FIXF(64) MSK_FIXF(128) MSK_FIXF(256)
 #undef MSK_FIXF
     return MSK_ENOTSUP;
   }
@@ -622,7 +774,7 @@ int launch_cs_f32a_f64y(const float* A, int64_t d, int64_t n, int64_t lda, const
 template <typename T>
 static int cs_atomic_typed(const T* A, int64_t d, int64_t n, int64_t lda, const double* b,
                            uint32_t k, uint64_t key, T* Y, int64_t ldy, bool pad_ok,
-                           cudaStream_t st) {
+                           void* ws, size_t ws_bytes, cudaStream_t st) {
   const int64_t ncol = n + (b ? 1 : 0);
   MSK_CUDA(zero_rows(Y, ldy, ncol, k, sizeof(T), st));
   if (d == 0 || ncol == 0) return MSK_OK;
@@ -665,7 +817,7 @@ static int cs_atomic_typed(const T* A, int64_t d, int64_t n, int64_t lda, const 
     P.Y = Y + c0;
     P.ldy = ldy;
     int rc = MSK_OK;
-    if (cs_fixed_chunk<T>(P, st, &rc)) {
+    if (cs_fixed_chunk<T>(P, st, &rc, ws, ws_bytes)) {
       if (rc) return rc;
       continue;
     }
@@ -683,12 +835,12 @@ static int cs_atomic_typed(const T* A, int64_t d, int64_t n, int64_t lda, const 
 
 int launch_cs_atomic(const void* A, int dtype, int64_t d, int64_t n, int64_t lda,
                      const double* b, uint32_t k, uint64_t key, void* Y, int64_t ldy,
-                     bool pad_ok, cudaStream_t st) {
+                     bool pad_ok, cudaStream_t st, void* ws, size_t ws_bytes) {
   if (dtype == MSK_F64)
     return cs_atomic_typed<double>(static_cast<const double*>(A), d, n, lda, b, k, key,
-                                   static_cast<double*>(Y), ldy, pad_ok, st);
+                                   static_cast<double*>(Y), ldy, pad_ok, ws, ws_bytes, st);
   return cs_atomic_typed<float>(static_cast<const float*>(A), d, n, lda, b, k, key,
-                                static_cast<float*>(Y), ldy, pad_ok, st);
+                                static_cast<float*>(Y), ldy, pad_ok, nullptr, 0, st);
 }
 
 // ---------------------------------------------------------------------------

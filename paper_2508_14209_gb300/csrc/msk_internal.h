@@ -94,9 +94,13 @@ int launch_cs_hash(uint64_t key, int64_t i0, int64_t count, uint32_t k, uint32_t
                    int8_t* s, cudaStream_t st);
 // pad_ok: the column after the last one of each Y row is scratch (ldy > ncol)
 // and may receive +0.0 from a padded bulk reduction.
+// ws (optional): room for the replicas of Y of the narrow FP64 kernels
+// (cs_replica_bytes); without it those kernels add into Y directly.
 int launch_cs_atomic(const void* A, int dtype, int64_t d, int64_t n, int64_t lda,
                      const double* b, uint32_t k, uint64_t key, void* Y, int64_t ldy,
-                     bool pad_ok, cudaStream_t st);
+                     bool pad_ok, cudaStream_t st, void* ws = nullptr, size_t ws_bytes = 0);
+// Bytes of the replicas of Y the FP64 CountSketch of `ncol` columns uses (0: none).
+size_t cs_replica_bytes(int64_t k, int64_t ncol);
 // Internal CountSketch launch used by the multisketch (same checks as cs_sketch).
 int cs_sketch_internal(const void* A, int dtype, int64_t d, int64_t n, int64_t lda,
                        const double* b, int64_t k, uint64_t seed, void* Y, int64_t ldy,

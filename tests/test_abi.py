@@ -45,7 +45,11 @@ def test_version_and_workspace_queries(lib):
 
     assert "sm_103a" in msk.version()
     # pure host-side size queries
-    assert msk.msk_cs_workspace(1000, 4, 64, msk.MSK_F64, msk.CS_ATOMIC) == 0
+    # FP64 atomic: replicas of Y while the sketch has few 128-byte lines
+    # (16 x 64 rows x 5 columns at k = 64), none at k = 8192, n = 64
+    assert msk.msk_cs_workspace(1000, 4, 64, msk.MSK_F64, msk.CS_ATOMIC) == 16 * 64 * 5 * 8
+    assert msk.msk_cs_workspace(1000, 64, 8192, msk.MSK_F64, msk.CS_ATOMIC) == 0
+    assert msk.msk_cs_workspace(1000, 4, 64, msk.MSK_F32, msk.CS_ATOMIC) == 0
     assert msk.msk_cs_workspace(1000, 4, 64, msk.MSK_F64, msk.CS_SORTED) >= 1000 * 4
 
 
