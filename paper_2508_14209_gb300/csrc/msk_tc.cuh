@@ -125,7 +125,7 @@ __device__ __forceinline__ void ds_accum(float& hi, float& lo, float v) {
 __device__ __forceinline__ void mbar_arrive(uint32_t a) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
 }
-// Host: the driver's cuTensorMapEncodeTiled, looked up once through the
+// Host: the CUDA driver API's cuTensorMapEncodeTiled, looked up once through the
 // runtime (no link against libcuda); null when unavailable.
 inline PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
