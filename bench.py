@@ -217,19 +217,18 @@ def run_ours(args):
     cs_alg_bytes = a_bytes + k * n * esz  # read A once, write Y once
     achieved = cs_alg_bytes / (cs_ms * 1e-3) / 1e9
 
-    # end to end: public ms_sketch call from pinned host A to host Z
+    # end to end: the public ms_sketch_host call, page-locked host A in, host
+    # Z out (row blocks copied to the device while the previous block is
+    # sketched)
     e2e = None
     if gp is not None and not args.no_e2e:
         Ah = torch.empty((n, d), dtype=dtype, pin_memory=True)
         Ah.copy_(A.t())
-        Zh = torch.empty((n, p), dtype=torch.float64, pin_memory=True)
-        Ad = msk.colmajor(d, n, dtype, dev)
-        mws = msk.workspace(msk.msk_ms_workspace(d, n, False, k, p, dt_code, gp), dev)
+        Zh = torch.empty((n, p), dtype=torch.float64, pin_memory=True).t()
+        mws = msk.workspace(msk.msk_ms_host_workspace(d, n, False, k, p, dt_code, gp), dev)
 
         def e2e_step():
-            Ad.copy_(Ah.t(), non_blocking=True)
-            Zd = msk.ms_sketch(Ad, k, p, seed, gemm_prec=gp, ws=mws)
-            Zh.copy_(Zd.t(), non_blocking=True)
+            msk.ms_sketch_host(Ah.t(), k, p, seed, gemm_prec=gp, Z=Zh, ws=mws)
 
         for _ in range(3):
             e2e_step()

@@ -228,6 +228,28 @@ int ms_sketch(const void *A, int dtype, int64_t d, int64_t n, int64_t lda,
               int gemm_prec, void *Z, int64_t ldz, int strategy, void *ws,
               size_t ws_bytes, void *stream);
 
+/* Scratch bytes (device) ms_sketch_host needs; chunk_rows as there. */
+size_t msk_ms_host_workspace(int64_t d, int64_t n, int with_b, int64_t k,
+                             int64_t p, int dtype, int gemm_prec,
+                             int64_t chunk_rows);
+
+/* ms_sketch from HOST memory, streamed: A (host, column-major d x n, lda),
+ * b (host double[d] or NULL) and Z (host double, column-major p x ncol,
+ * ldz >= p) live on the host; only Y, two staging blocks of chunk_rows rows
+ * and the Gaussian stage's scratch live on the device (ws), so d is not
+ * limited by device memory.  Block j of the rows is copied (a second stream,
+ * strided 2D copies) while block j-1 is CountSketched on `stream` with its
+ * global row indices, which the CountSketch is additive over; then Z = G Y
+ * and Z is copied back.  Same Z as ms_sketch (atomic strategy) up to the
+ * order of the reductions.  A and b should be page-locked for the copies to
+ * overlap the sketch.  chunk_rows = 0 picks blocks of about 256 MiB of A.
+ * Synchronises `stream` before returning.
+ * Errors as ms_sketch, plus -13 chunk_rows < 0. */
+int ms_sketch_host(const void *A, int dtype, int64_t d, int64_t n, int64_t lda,
+                   const double *b, int64_t k, int64_t p, uint64_t seed,
+                   int gemm_prec, double *Z, int64_t ldz, int64_t chunk_rows,
+                   void *ws, size_t ws_bytes, void *stream);
+
 /* ---- Dense building blocks (Algorithm 1 steps 2-3) ----------------------- */
 
 /* Scratch bytes msk_gemm needs. */

@@ -36,6 +36,7 @@ EXPORTS = ("msk_version", "msk_last_error", "msk_take_timeout", "msk_selftest_wa
            "msk_householder_qr", "msk_trsv_upper", "msk_lstsq_workspace", "ms_lstsq",
            "msk_ne_workspace", "ne_lstsq", "msk_rcq_workspace", "rcq_lstsq", "rcq_qr",
            "msk_sns_workspace", "sns_lstsq", "msk_srht_workspace", "srht_sketch",
+           "msk_ms_host_workspace", "ms_sketch_host",
            "msk_gemm_noalloc", "msk_tune_set", "msk_tune_get",
            "msk_tune_clear", "msk_batch_workspace", "msk_batch_lstsq", "ms_server_create",
            "ms_server_submit", "ms_server_poll", "ms_server_wait_all", "ms_server_stats",
@@ -110,6 +111,9 @@ def _declare(L):
         "msk_rcq_workspace": (_sz, [_i64, _i64, _i64, _i64, _int, _int, _int]),
         "msk_sns_workspace": (_sz, [_i64, _i64, _int, _i64, _i64, _int]),
         "msk_srht_workspace": (_sz, [_i64, _i64, _int, _i64]),
+        "msk_ms_host_workspace": (_sz, [_i64, _i64, _int, _i64, _i64, _int, _int, _i64]),
+        "ms_sketch_host": (_int, [_p, _int, _i64, _i64, _i64, _p, _i64, _i64, _u64, _int, _p, _i64, _i64,
+                                  _p, _sz, _p]),
         "srht_sketch": (_int, [_p, _int, _i64, _i64, _i64, _p, _i64, _u64, _p, _i64, _p, _sz, _p]),
         "sns_lstsq": (_int, [_p, _int, _i64, _i64, _i64, _p, _int, _i64, _i64, _u64, _p, _p, _p, _sz,
                              _p]),
@@ -263,6 +267,37 @@ def cs_sketch(A, k, seed, b=None, Y=None, strategy=CS_ATOMIC, ws=None, stream=No
                                          Y.stride(0), strategy, _ptr(ws),
                                          0 if ws is None else ws.numel(), _stream(stream)))
     return Y
+
+
+def msk_ms_host_workspace(d, n, with_b, k, p, dtype, gemm_prec, chunk_rows=0):
+    return load().msk_ms_host_workspace(d, n, int(with_b), k, p, dtype, gemm_prec, chunk_rows)
+
+
+def ms_sketch_host(A, k, p, seed, b=None, gemm_prec=GEMM_F64, Z=None, chunk_rows=0, ws=None,
+                   stream=None, device=None):
+    """Z = G S [A b] for a HOST column-major A (and host float64 b): row
+    blocks are copied to the device while the previous block is sketched;
+    returns Z on the host (column-major p x ncol float64).  Page-locked A
+    (and b) let the copies overlap the sketch."""
+    if A.is_cuda or (b is not None and b.is_cuda):
+        raise TypeError("ms_sketch_host takes host tensors")
+    d, n = A.shape
+    lda = _colmajor(A)
+    dt = _dtype_code(A)
+    ncol = n + (0 if b is None else 1)
+    if b is not None and (b.dtype != torch.float64 or b.numel() != d or not b.is_contiguous()):
+        raise ValueError("b must be contiguous float64 of length d")
+    if Z is None:
+        Z = colmajor(p, ncol, torch.float64, "cpu")
+    if Z.is_cuda or Z.dtype != torch.float64:
+        raise TypeError("Z must be a host float64 tensor")
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else device
+    if ws is None:
+        ws = workspace(msk_ms_host_workspace(d, n, b is not None, k, p, dt, gemm_prec, chunk_rows), dev)
+    _check("ms_sketch_host", load().ms_sketch_host(_ptr(A), dt, d, n, lda, _ptr(b), k, p,
+                                                   seed & (2**64 - 1), gemm_prec, _ptr(Z), _colmajor(Z),
+                                                   chunk_rows, _ptr(ws), ws.numel(), _stream(stream)))
+    return Z
 
 
 def msk_ms_workspace(d, n, with_b, k, p, dtype, gemm_prec, strategy=CS_ATOMIC):

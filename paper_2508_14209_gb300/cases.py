@@ -29,7 +29,7 @@ def main(argv=None):
     import paper_2508_14209_gb300 as msk
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["sketch", "gemm", "refined", "ne", "sns", "rcq", "srht"])
+    ap.add_argument("case", choices=["sketch", "gemm", "refined", "ne", "sns", "rcq", "srht", "host"])
     ap.add_argument("--d", type=int, default=1 << 20)
     ap.add_argument("--n", type=int, default=64)
     ap.add_argument("--dtype", choices=["f64", "f32"], default="f64")
@@ -46,6 +46,7 @@ def main(argv=None):
                          "no refinement), the served comparison's plain path")
     ap.add_argument("--kind", choices=["multi", "count", "gauss", "srht"], default="multi",
                     help="sns: the sketch (multisketch G C, CountSketch C alone, Gaussian G alone)")
+    ap.add_argument("--chunk-rows", type=int, default=0, help="host: rows per staged block (0: ~256 MiB)")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--seed", type=int, default=0x5EED0004)
     ap.add_argument("--tune", action="append", default=[], metavar="KNOB=VALUE",
@@ -65,6 +66,23 @@ def main(argv=None):
         Y = torch.empty((k, a.n), dtype=dt, device=dev)
         call = lambda: msk.cs_sketch(A, k, a.seed, Y=Y)  # noqa: E731
         out.update(d=a.d, n=a.n, k=k, dtype=a.dtype, bytes_per_call=a.d * a.n * A.element_size())
+    elif a.case == "host":
+        # multisketch of a page-locked HOST A (FP64 Gaussian stage), streamed
+        # in row blocks: host-to-device copies overlap the CountSketch
+        dt = torch.float64 if a.dtype == "f64" else torch.float32
+        Ad = inputs.normal_matrix(a.d, a.n, a.seed, dtype=dt, device=dev)
+        buf = torch.empty((a.n, a.d), dtype=dt, pin_memory=True)
+        buf.copy_(Ad.t())
+        A = buf.t()
+        del Ad
+        k, p = 2 * a.n * a.n, 4 * a.n
+        Zh = torch.empty((a.n, p), dtype=torch.float64, pin_memory=True).t()
+        ws = msk.workspace(msk.msk_ms_host_workspace(a.d, a.n, False, k, p, msk.MSK_F64 if a.dtype == "f64"
+                                                     else msk.MSK_F32, msk.GEMM_F64, a.chunk_rows), dev)
+        call = lambda: msk.ms_sketch_host(A, k, p, a.seed, gemm_prec=msk.GEMM_F64, Z=Zh,  # noqa: E731
+                                          chunk_rows=a.chunk_rows, ws=ws)
+        out.update(d=a.d, n=a.n, k=k, p=p, dtype=a.dtype, chunk_rows=a.chunk_rows,
+                   bytes_per_call=a.d * a.n * buf.element_size())
     elif a.case == "srht":
         # SRHT of A (d a power of two) to k = 2 n^2 rows: FP64 adds, d n log2(d)
         A = inputs.normal_matrix(a.d, a.n, a.seed, dtype=torch.float64, device=dev)

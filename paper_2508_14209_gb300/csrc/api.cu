@@ -174,17 +174,17 @@ int cs_sketch(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, const
 
 int msk::count_sketch_f64y(const void* A, int dtype, int64_t d, int64_t n, int64_t lda,
                            const double* b, int64_t k, uint64_t seed, double* Y, int64_t ldy,
-                           cudaStream_t st) {
+                           cudaStream_t st, bool zero, int64_t i0) {
   if (dtype == MSK_F64)
     return launch_cs_atomic(A, dtype, d, n, lda, b, (uint32_t)k, stream_key(seed, kTagHash), Y, ldy,
-                            false, st);
+                            false, st, nullptr, 0, zero, i0);
   const int64_t ncol = n + (b ? 1 : 0);
-  MSK_CUDA(zero_rows(Y, ldy, ncol, k, 8, st));
+  if (zero) MSK_CUDA(zero_rows(Y, ldy, ncol, k, 8, st));
   int64_t maxc = 256;
   const int64_t fit = (int64_t)(tune_get("cs.l2_budget_bytes", 48ll << 20)) / (k * 8);
   if (fit >= 64 && fit / 64 * 64 < maxc) maxc = fit / 64 * 64;
   return launch_cs_f32a_f64y(static_cast<const float*>(A), d, n, lda, b, (uint32_t)k,
-                             stream_key(seed, kTagHash), Y, ldy, maxc, st);
+                             stream_key(seed, kTagHash), Y, ldy, maxc, st, i0);
 }
 
 int msk::cs_sketch_internal(const void* A, int dtype, int64_t d, int64_t n, int64_t lda,
@@ -291,6 +291,119 @@ int ms_sketch(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, const
   const size_t rest_off = align_up(cv.used, 256);
   return gemm_stage(seed, p, k, ncol, Y, ydt, ldy, gemm_prec, static_cast<double*>(Z), ldz,
                     cv.base + rest_off, ws_bytes - rest_off, st);
+}
+
+// Rows per staged block of ms_sketch_host: the caller's value, else blocks of
+// about 256 MiB of A.
+static int64_t host_chunk_rows(int64_t d, int64_t n, int dtype, int64_t chunk_rows) {
+  if (chunk_rows > 0) return std::min<int64_t>(chunk_rows, std::max<int64_t>(d, 1));
+  const int64_t esz = dtype == MSK_F64 ? 8 : 4;
+  const int64_t rows = ((int64_t)256 << 20) / (std::max<int64_t>(n, 1) * esz);
+  return std::max<int64_t>(1, std::min<int64_t>(std::max<int64_t>(d, 1), rows / 256 * 256));
+}
+
+size_t msk_ms_host_workspace(int64_t d, int64_t n, int with_b, int64_t k, int64_t p, int dtype,
+                             int gemm_prec, int64_t chunk_rows) {
+  const int64_t ncol = n + (with_b ? 1 : 0);
+  const int64_t rows = host_chunk_rows(d, n, dtype, chunk_rows);
+  const int ydt = ms_y_dtype(dtype, gemm_prec);
+  Need nd;
+  nd.add((size_t)k * ws_ldy(ncol, ydt) * dtype_size(ydt));  // Y
+  nd.add(msk_cs_workspace(rows, n, k, ydt, MSK_CS_ATOMIC));  // replicas
+  for (int j = 0; j < 2; ++j) {
+    nd.add((size_t)rows * std::max<int64_t>(n, 1) * dtype_size(dtype));  // staged A rows
+    if (with_b) nd.add((size_t)rows * sizeof(double));                    // staged b rows
+  }
+  nd.add((size_t)p * ncol * sizeof(double));  // Z on the device
+  nd.add(msk_gemm_workspace(p, k, ncol, gemm_prec));
+  return nd.used;
+}
+
+int ms_sketch_host(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, const double* b,
+                   int64_t k, int64_t p, uint64_t seed, int gemm_prec, double* Z, int64_t ldz,
+                   int64_t chunk_rows, void* ws, size_t ws_bytes, void* stream) {
+  if (!A && d > 0 && n > 0) return -1;
+  if (dtype != MSK_F64 && dtype != MSK_F32) return -2;
+  if (d < 0) return -3;
+  if (n < 0) return -4;
+  if (lda < (d > 1 ? d : 1)) return -5;
+  if (k < 1 || k > 0xFFFFFFFFLL) return -7;
+  if (p < 1 || p >= (1LL << 24)) return -8;
+  if (gemm_prec < MSK_GEMM_F64 || gemm_prec > MSK_GEMM_BF16X3) return -10;
+  if (!Z) return -11;
+  if (ldz < p) return -12;
+  if (chunk_rows < 0) return -13;
+  const int64_t ncol = n + (b ? 1 : 0);
+  if (ncol < 1) return -4;
+  if (ws_bytes < msk_ms_host_workspace(d, n, b ? 1 : 0, k, p, dtype, gemm_prec, chunk_rows))
+    return MSK_ENOMEM;
+  if (is_tensor_prec(gemm_prec) && dtype != MSK_F32) return MSK_ENOTSUP;
+  cudaStream_t st = as_stream(stream);
+  const int64_t rows = host_chunk_rows(d, n, dtype, chunk_rows);
+  const int ydt = ms_y_dtype(dtype, gemm_prec);
+  const int64_t ldy = ws_ldy(ncol, ydt);
+  const size_t esz = dtype_size(dtype);
+  Carve cv(ws, ws_bytes);
+  void* Y = cv.take((size_t)k * ldy * dtype_size(ydt));
+  const size_t cs_ws = msk_cs_workspace(rows, n, k, ydt, MSK_CS_ATOMIC);
+  void* csw = cv.take(cs_ws);
+  void* sa[2];
+  double* sb[2] = {nullptr, nullptr};
+  for (int j = 0; j < 2; ++j) {
+    sa[j] = cv.take((size_t)rows * std::max<int64_t>(n, 1) * esz);
+    if (b) sb[j] = static_cast<double*>(cv.take((size_t)rows * sizeof(double)));
+  }
+  double* Zd = static_cast<double*>(cv.take((size_t)p * ncol * sizeof(double)));
+  if (!Y || !sa[0] || !sa[1] || (b && (!sb[0] || !sb[1])) || !Zd) return MSK_ENOMEM;
+  // a copy stream and five events per host thread: block j of the rows is
+  // copied into staging buffer j & 1 while block j - 1 is sketched on `st`
+  // (a second copy stream for alternate blocks measured no faster: the
+  // host link, ~200 GB/s, is the bound)
+  thread_local cudaStream_t cps = nullptr;
+  thread_local cudaEvent_t ev[5];
+  if (!cps) {
+    MSK_CUDA(cudaStreamCreateWithFlags(&cps, cudaStreamNonBlocking));
+    for (auto& e : ev) MSK_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
+  cudaEvent_t* ready = ev;      // ready[j]: block in buffer j copied
+  cudaEvent_t* done = ev + 2;   // done[j]: buffer j's block sketched
+  cudaEvent_t start = ev[4];    // earlier work on `st` (the caller's use of ws) finished
+  MSK_CUDA(cudaEventRecord(start, st));
+  MSK_CUDA(cudaStreamWaitEvent(cps, start, 0));
+  MSK_CUDA(zero_rows(Y, ldy, ncol, k, dtype_size(ydt), st));
+  const uint64_t key = stream_key(seed, kTagHash);
+  const int64_t nblk = d > 0 ? (d + rows - 1) / rows : 0;
+  for (int64_t j = 0; j < nblk; ++j) {
+    const int u = (int)(j & 1);
+    const int64_t r0 = j * rows, m = std::min<int64_t>(rows, d - r0);
+    if (j >= 2) MSK_CUDA(cudaStreamWaitEvent(cps, done[u], 0));
+    if (n > 0)
+      MSK_CUDA(cudaMemcpy2DAsync(sa[u], (size_t)rows * esz,
+                                 static_cast<const char*>(A) + (size_t)r0 * esz, (size_t)lda * esz,
+                                 (size_t)m * esz, (size_t)n, cudaMemcpyHostToDevice, cps));
+    if (b)
+      MSK_CUDA(cudaMemcpyAsync(sb[u], b + r0, (size_t)m * sizeof(double), cudaMemcpyHostToDevice,
+                               cps));
+    MSK_CUDA(cudaEventRecord(ready[u], cps));
+    MSK_CUDA(cudaStreamWaitEvent(st, ready[u], 0));
+    int rc;
+    if (ydt == MSK_F64 && dtype == MSK_F32)
+      rc = count_sketch_f64y(sa[u], dtype, m, n, rows, sb[u], k, seed, static_cast<double*>(Y), ldy,
+                             st, false, r0);
+    else
+      rc = launch_cs_atomic(sa[u], dtype, m, n, rows, sb[u], (uint32_t)k, key, Y, ldy, true, st, csw,
+                            cs_ws, false, r0);
+    if (rc) return rc;
+    MSK_CUDA(cudaEventRecord(done[u], st));
+  }
+  const size_t rest_off = align_up(cv.used, 256);
+  int rc = gemm_stage(seed, p, k, ncol, Y, ydt, ldy, gemm_prec, Zd, p, cv.base + rest_off,
+                      ws_bytes - rest_off, st);
+  if (rc) return rc;
+  MSK_CUDA(cudaMemcpy2DAsync(Z, (size_t)ldz * sizeof(double), Zd, (size_t)p * sizeof(double),
+                             (size_t)p * sizeof(double), (size_t)ncol, cudaMemcpyDeviceToHost, st));
+  MSK_CUDA(cudaStreamSynchronize(st));
+  return MSK_OK;
 }
 
 }  // extern "C"

@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(kCsThreads) cs_atomic_kernel(const CsParams<T>
         }
         v[q] = x;
       }
-      if (warp == 0) hz[buf * kCsRows + lane] = row_ok ? draw(P.key, (uint64_t)i) : 0ull;
+      if (warp == 0) hz[buf * kCsRows + lane] = row_ok ? draw(P.key, (uint64_t)(P.i0 + i)) : 0ull;
 #pragma unroll
       for (int q = 0; q < QMAX; ++q) {
         const int g = warp + q * kCsWarps;
@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(kCsThreads) cs_atomic_kernel(const CsParams<T>
         const int j = warp + q * kCsWarps;
         v[q] = (row_ok && j < P.ncol) ? load_col(P, i, j) : (T)0;
       }
-      if (warp == 0) hz[buf * kCsRows + lane] = row_ok ? draw(P.key, (uint64_t)i) : 0ull;
+      if (warp == 0) hz[buf * kCsRows + lane] = row_ok ? draw(P.key, (uint64_t)(P.i0 + i)) : 0ull;
 #pragma unroll
       for (int q = 0; q < QMAX; ++q) {
         const int j = warp + q * kCsWarps;
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(kCsThreads) cs_bulk_f64_kernel(const CsParams<
     const int64_t i0 = t * kCsRows;
     const int64_t i = i0 + lane;
     const bool row_ok = i < P.d;
-    const uint64_t z = row_ok ? draw(P.key, (uint64_t)i) : 0ull;
+    const uint64_t z = row_ok ? draw(P.key, (uint64_t)(P.i0 + i)) : 0ull;
     const unsigned long long sgn = negative_of(z) ? 0x8000000000000000ull : 0ull;
     double* tile = tiles + buf * kCsRows * P.pitch;
     double2 v[QMAX];
@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(kCsThreads) cs_fixed_f64_kernel(const CsParams
       v[q] = (row_ok && j < nca) ? (double)__ldcs(Aa + i + (int64_t)j * P.lda) : 0.0;
     }
     if (HAS_B && warp == kCsWarps - 1) vb = row_ok ? __ldcs(P.b + i) : 0.0;
-    if (warp == 0) zr = row_ok ? draw(P.key, (uint64_t)i) : 0ull;
+    if (warp == 0) zr = row_ok ? draw(P.key, (uint64_t)(P.i0 + i)) : 0ull;
   };
   int buf = 0;
   if (PF && (int64_t)blockIdx.x < ntiles) load(blockIdx.x);
@@ -411,7 +411,7 @@ __global__ void __launch_bounds__(kCsThreads) cs_narrow_f64_kernel(const CsParam
         v[rb][q] = (row_ok && j < nca) ? (double)__ldcs(Aa + i + (int64_t)j * P.lda) : 0.0;
       }
       vb[rb] = (HAS_B && warp == kCsWarps - 1 && row_ok) ? __ldcs(P.b + i) : 0.0;
-      if (warp == rb) zr = row_ok ? draw(P.key, (uint64_t)i) : 0ull;
+      if (warp == rb) zr = row_ok ? draw(P.key, (uint64_t)(P.i0 + i)) : 0ull;
     }
 #pragma unroll
     for (int rb = 0; rb < RB; ++rb) {
@@ -478,7 +478,7 @@ struct CsF32Tile {
     g.vb = 0.f;
     if (HAS_B && warp == kCsWarps - 1) g.vb = row_ok ? (float)__ldcs(P.b + i) : 0.f;
     g.zr = 0ull;
-    if (warp == 0) g.zr = row_ok ? draw(P.key, (uint64_t)i) : 0ull;
+    if (warp == 0) g.zr = row_ok ? draw(P.key, (uint64_t)(P.i0 + i)) : 0ull;
   }
   __device__ __forceinline__ static void store(const Regs& g, int buf, Smem& sm) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -627,14 +627,15 @@ size_t cs_replica_bytes(int64_t k, int64_t ncol) {
   return r > 1 ? (size_t)r * (size_t)k * (size_t)ncol * sizeof(double) : 0;
 }
 
-// Y[r][c] = sum over the replicas (in replica order) of rep[q][r][c].
+// Y[r][c] += sum over the replicas (in replica order) of rep[q][r][c] (Y
+// holds zeros, or the sketch of earlier row blocks).
 __global__ void cs_replica_sum_kernel(const double* __restrict__ rep, int nrep, int64_t stride,
                                       int64_t k, int ncol, double* __restrict__ Y, int64_t ldy) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < k * ncol;
        e += (int64_t)gridDim.x * blockDim.x) {
     double s = 0.0;
     for (int q = 0; q < nrep; ++q) s += rep[q * stride + e];
-    Y[(e / ncol) * ldy + e % ncol] = s;
+    Y[(e / ncol) * ldy + e % ncol] += s;
   }
 }
 
@@ -726,7 +727,7 @@ static int cs_fixed_chunk(const CsParams<T>& P, cudaStream_t st, int* rc, void* 
 // (and L2-resident Y slices).
 int launch_cs_f32a_f64y(const float* A, int64_t d, int64_t n, int64_t lda, const double* b,
                         uint32_t k, uint64_t key, double* Y, int64_t ldy, int64_t maxc,
-                        cudaStream_t st) {
+                        cudaStream_t st, int64_t i0) {
   const int64_t nchunks = n > 0 ? (n + maxc - 1) / maxc : 1;
   for (int64_t ch = 0; ch < nchunks; ++ch) {
     const int64_t c0 = ch * maxc, c1 = std::min<int64_t>(n, c0 + maxc);
@@ -743,6 +744,7 @@ int launch_cs_f32a_f64y(const float* A, int64_t d, int64_t n, int64_t lda, const
     P.key = key;
     P.Y = Y + c0;
     P.ldy = ldy;
+    P.i0 = i0;
     const float* Ac = A + c0 * lda;
     const bool hb = P.b != nullptr;
     const int w = P.ncol_a;
@@ -774,9 +776,9 @@ int launch_cs_f32a_f64y(const float* A, int64_t d, int64_t n, int64_t lda, const
 template <typename T>
 static int cs_atomic_typed(const T* A, int64_t d, int64_t n, int64_t lda, const double* b,
                            uint32_t k, uint64_t key, T* Y, int64_t ldy, bool pad_ok,
-                           void* ws, size_t ws_bytes, cudaStream_t st) {
+                           void* ws, size_t ws_bytes, bool zero, int64_t i0, cudaStream_t st) {
   const int64_t ncol = n + (b ? 1 : 0);
-  MSK_CUDA(zero_rows(Y, ldy, ncol, k, sizeof(T), st));
+  if (zero) MSK_CUDA(zero_rows(Y, ldy, ncol, k, sizeof(T), st));
   if (d == 0 || ncol == 0) return MSK_OK;
   // Column chunks of at most kCsMaxColsF64/F32; b rides with the last chunk.
   // Column chunks: at most the shared-memory limit, and narrow enough that the
@@ -816,6 +818,7 @@ static int cs_atomic_typed(const T* A, int64_t d, int64_t n, int64_t lda, const 
     P.key = key;
     P.Y = Y + c0;
     P.ldy = ldy;
+    P.i0 = i0;
     int rc = MSK_OK;
     if (cs_fixed_chunk<T>(P, st, &rc, ws, ws_bytes)) {
       if (rc) return rc;
@@ -835,12 +838,14 @@ static int cs_atomic_typed(const T* A, int64_t d, int64_t n, int64_t lda, const 
 
 int launch_cs_atomic(const void* A, int dtype, int64_t d, int64_t n, int64_t lda,
                      const double* b, uint32_t k, uint64_t key, void* Y, int64_t ldy,
-                     bool pad_ok, cudaStream_t st, void* ws, size_t ws_bytes) {
+                     bool pad_ok, cudaStream_t st, void* ws, size_t ws_bytes, bool zero,
+                     int64_t i0) {
   if (dtype == MSK_F64)
     return cs_atomic_typed<double>(static_cast<const double*>(A), d, n, lda, b, k, key,
-                                   static_cast<double*>(Y), ldy, pad_ok, ws, ws_bytes, st);
+                                   static_cast<double*>(Y), ldy, pad_ok, ws, ws_bytes, zero, i0,
+                                   st);
   return cs_atomic_typed<float>(static_cast<const float*>(A), d, n, lda, b, k, key,
-                                static_cast<float*>(Y), ldy, pad_ok, nullptr, 0, st);
+                                static_cast<float*>(Y), ldy, pad_ok, nullptr, 0, zero, i0, st);
 }
 
 // ---------------------------------------------------------------------------

@@ -83,6 +83,7 @@ struct CsParams {
   T* Y;
   int64_t ldy;
   int pitch;           // shared-memory row pitch (elements)
+  int64_t i0;          // hash index of row 0 (a row block of a taller A), 0 by default
 };
 
 // Tuning registry lookup (tune.cpp).
@@ -96,9 +97,12 @@ int launch_cs_hash(uint64_t key, int64_t i0, int64_t count, uint32_t k, uint32_t
 // and may receive +0.0 from a padded bulk reduction.
 // ws (optional): room for the replicas of Y of the narrow FP64 kernels
 // (cs_replica_bytes); without it those kernels add into Y directly.
+// zero = false: add into Y as it is (a further row block); i0: hash index of
+// A's row 0 (the row block's offset in the full matrix).
 int launch_cs_atomic(const void* A, int dtype, int64_t d, int64_t n, int64_t lda,
                      const double* b, uint32_t k, uint64_t key, void* Y, int64_t ldy,
-                     bool pad_ok, cudaStream_t st, void* ws = nullptr, size_t ws_bytes = 0);
+                     bool pad_ok, cudaStream_t st, void* ws = nullptr, size_t ws_bytes = 0,
+                     bool zero = true, int64_t i0 = 0);
 // Bytes of the replicas of Y the FP64 CountSketch of `ncol` columns uses (0: none).
 size_t cs_replica_bytes(int64_t k, int64_t ncol);
 // Internal CountSketch launch used by the multisketch (same checks as cs_sketch).
@@ -122,9 +126,10 @@ int launch_gemm_simt(const float* G, int64_t ldg, const void* Y, bool y_f64, int
 __global__ void splitk_reduce_kernel(const double* __restrict__ part, int S, int64_t p, int64_t ncol,
                                      double* __restrict__ Z, int64_t ldz);
 // countsketch.cu: FP64 CountSketch of FP32 A (column chunks of <= maxc <= 256)
+// (i0: hash index of A's row 0; Y is not zeroed here)
 int launch_cs_f32a_f64y(const float* A, int64_t d, int64_t n, int64_t lda, const double* b,
                         uint32_t k, uint64_t key, double* Y, int64_t ldy, int64_t maxc,
-                        cudaStream_t st);
+                        cudaStream_t st, int64_t i0 = 0);
 // countsketch.cu: batched FP32 CountSketch (problems of one A width + b)
 int launch_cs_batch_f32(int nca, const CsParams<float>* Ps, const int64_t* tile_begin, int nprob,
                         int64_t total_tiles, cudaStream_t st);
@@ -180,9 +185,10 @@ int launch_gauss_gemm(uint64_t gkey, int64_t p, const void* A, int dtype, int64_
 // api.cu
 // FP64 CountSketch of [A b] (FP64 A, or FP32 A widened exactly) into
 // row-major Y (k x ncol, ldy), atomic strategy; Y is zeroed first.
+// zero = false: add into Y as it is; i0: hash index of A's row 0.
 int count_sketch_f64y(const void* A, int dtype, int64_t d, int64_t n, int64_t lda,
                       const double* b, int64_t k, uint64_t seed, double* Y, int64_t ldy,
-                      cudaStream_t st);
+                      cudaStream_t st, bool zero = true, int64_t i0 = 0);
 int gemm_stage(uint64_t seed, int64_t p, int64_t k, int64_t ncol, const void* Y, int y_dtype,
                int64_t ldy, int gemm_prec, double* Z, int64_t ldz, void* ws, size_t ws_bytes,
                cudaStream_t st);
