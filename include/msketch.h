@@ -228,6 +228,19 @@ int ms_sketch(const void *A, int dtype, int64_t d, int64_t n, int64_t lda,
               int gemm_prec, void *Z, int64_t ldz, int strategy, void *ws,
               size_t ws_bytes, void *stream);
 
+/* ms_sketch of a row block of a taller [A b] (Section 7's block-row
+ * distribution): A, b hold rows row0 .. row0+d-1 of the full matrix, and
+ * the CountSketch hashes them with their global indices, so the Z of the
+ * blocks of a row partition add up to the Z of the whole matrix (up to the
+ * order of the reductions).  Atomic strategy; workspace msk_ms_workspace.
+ * Errors: -1 A NULL, -2 dtype, -3 d < 0, -4 n < 0, -5 lda < d, -7 row0 < 0,
+ * -8 k < 1, -9 p < 1, -11 gemm_prec, -12 Z NULL, -13 ldz < p, MSK_ENOMEM,
+ * MSK_ENOTSUP (tensor precisions need FP32 A). */
+int ms_sketch_rows(const void *A, int dtype, int64_t d, int64_t n, int64_t lda,
+                   const double *b, int64_t row0, int64_t k, int64_t p,
+                   uint64_t seed, int gemm_prec, double *Z, int64_t ldz, void *ws,
+                   size_t ws_bytes, void *stream);
+
 /* Scratch bytes (device) ms_sketch_host needs; chunk_rows as there. */
 size_t msk_ms_host_workspace(int64_t d, int64_t n, int with_b, int64_t k,
                              int64_t p, int dtype, int gemm_prec,

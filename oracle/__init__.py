@@ -17,6 +17,8 @@ Parity status of each function (what pins it, see tests/test_oracle_*.py):
   gaussian             moments, Kolmogorov-Smirnov against N(0,1/p), ln accuracy
   countsketch          brute force with the explicit dense S, sum invariant,
                        integer-exact sums
+  countsketch_rows     the blocks of a row partition add up to countsketch
+                       (integer-exact); row0 = 0 is countsketch itself
   gemm                 integer-exact products, bf16/fp16 rounding definition
   householder_r/solve  R^T R = Z^T Z, |R| against LAPACK's QR, numpy lstsq
   sns_lstsq            exact recovery for b = A x, distortion bound of Section 2
@@ -207,6 +209,18 @@ def countsketch(A, k: int, seed: int, b=None) -> np.ndarray:
     rc = lib().or_countsketch(_ptr(A), dt, d, n, lda, _ptr(bb), k, seed & (2**64 - 1), _ptr(Y), ncol)
     if rc != 0:
         raise MemoryError("oracle countsketch: out of memory")
+    return Y
+
+
+def countsketch_rows(A, k: int, seed: int, row0: int, b=None) -> np.ndarray:
+    """S_r [A b] for a block of rows row0 .. row0+d-1 of a taller matrix,
+    hashed with their global indices (Definition 3 restricted to the block;
+    the distribution of Section 7): k x ncol FP64, rows added in order."""
+    A64 = np.asarray(A, dtype=np.float64)
+    X = A64 if b is None else np.hstack([A64, np.asarray(b, dtype=np.float64).reshape(-1, 1)])
+    h, s = hash_rows(seed, row0, X.shape[0], k)
+    Y = np.zeros((k, X.shape[1]))
+    np.add.at(Y, h.astype(np.int64), s.astype(np.float64)[:, None] * X)
     return Y
 
 

@@ -36,7 +36,7 @@ EXPORTS = ("msk_version", "msk_last_error", "msk_take_timeout", "msk_selftest_wa
            "msk_householder_qr", "msk_trsv_upper", "msk_lstsq_workspace", "ms_lstsq",
            "msk_ne_workspace", "ne_lstsq", "msk_rcq_workspace", "rcq_lstsq", "rcq_qr",
            "msk_sns_workspace", "sns_lstsq", "msk_srht_workspace", "srht_sketch",
-           "msk_ms_host_workspace", "ms_sketch_host",
+           "msk_ms_host_workspace", "ms_sketch_host", "ms_sketch_rows",
            "msk_gemm_noalloc", "msk_tune_set", "msk_tune_get",
            "msk_tune_clear", "msk_batch_workspace", "msk_batch_lstsq", "ms_server_create",
            "ms_server_submit", "ms_server_poll", "ms_server_wait_all", "ms_server_stats",
@@ -112,6 +112,8 @@ def _declare(L):
         "msk_sns_workspace": (_sz, [_i64, _i64, _int, _i64, _i64, _int]),
         "msk_srht_workspace": (_sz, [_i64, _i64, _int, _i64]),
         "msk_ms_host_workspace": (_sz, [_i64, _i64, _int, _i64, _i64, _int, _int, _i64]),
+        "ms_sketch_rows": (_int, [_p, _int, _i64, _i64, _i64, _p, _i64, _i64, _i64, _u64, _int, _p, _i64, _p,
+                                  _sz, _p]),
         "ms_sketch_host": (_int, [_p, _int, _i64, _i64, _i64, _p, _i64, _i64, _u64, _int, _p, _i64, _i64,
                                   _p, _sz, _p]),
         "srht_sketch": (_int, [_p, _int, _i64, _i64, _i64, _p, _i64, _u64, _p, _i64, _p, _sz, _p]),
@@ -267,6 +269,24 @@ def cs_sketch(A, k, seed, b=None, Y=None, strategy=CS_ATOMIC, ws=None, stream=No
                                          Y.stride(0), strategy, _ptr(ws),
                                          0 if ws is None else ws.numel(), _stream(stream)))
     return Y
+
+
+def ms_sketch_rows(A, row0, k, p, seed, b=None, gemm_prec=GEMM_F64, Z=None, ws=None, stream=None):
+    """Z = G S [A b] for the row block A (device, column-major) holding rows
+    row0 .. row0+d-1 of a taller matrix: hashed with global row indices, so
+    the blocks' Z add up to the whole matrix's."""
+    _cuda(A, "A"), _cuda(b, "b")
+    d, n = A.shape
+    dt = _dtype_code(A)
+    ncol = n + (0 if b is None else 1)
+    if Z is None:
+        Z = colmajor(p, ncol, torch.float64, A.device)
+    if ws is None:
+        ws = workspace(msk_ms_workspace(d, n, b is not None, k, p, dt, gemm_prec), A.device)
+    _check("ms_sketch_rows", load().ms_sketch_rows(_ptr(A), dt, d, n, _colmajor(A), _ptr(b), row0, k, p,
+                                                   seed & (2**64 - 1), gemm_prec, _ptr(Z), _colmajor(Z),
+                                                   _ptr(ws), ws.numel(), _stream(stream)))
+    return Z
 
 
 def msk_ms_host_workspace(d, n, with_b, k, p, dtype, gemm_prec, chunk_rows=0):

@@ -293,6 +293,46 @@ int ms_sketch(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, const
                     cv.base + rest_off, ws_bytes - rest_off, st);
 }
 
+int ms_sketch_rows(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, const double* b,
+                   int64_t row0, int64_t k, int64_t p, uint64_t seed, int gemm_prec, double* Z,
+                   int64_t ldz, void* ws, size_t ws_bytes, void* stream) {
+  if (!A && d > 0 && n > 0) return -1;
+  if (dtype != MSK_F64 && dtype != MSK_F32) return -2;
+  if (d < 0) return -3;
+  if (n < 0) return -4;
+  if (lda < (d > 1 ? d : 1)) return -5;
+  if (row0 < 0) return -7;
+  if (k < 1 || k > 0xFFFFFFFFLL) return -8;
+  if (p < 1 || p >= (1LL << 24)) return -9;
+  if (gemm_prec < MSK_GEMM_F64 || gemm_prec > MSK_GEMM_BF16X3) return -11;
+  if (!Z) return -12;
+  if (ldz < p) return -13;
+  const int64_t ncol = n + (b ? 1 : 0);
+  if (ncol < 1) return -4;
+  if (ws_bytes < msk_ms_workspace(d, n, b ? 1 : 0, k, p, dtype, gemm_prec, MSK_CS_ATOMIC))
+    return MSK_ENOMEM;
+  if (is_tensor_prec(gemm_prec) && dtype != MSK_F32) return MSK_ENOTSUP;
+  cudaStream_t st = as_stream(stream);
+  Carve cv(ws, ws_bytes);
+  const int ydt = ms_y_dtype(dtype, gemm_prec);
+  const int64_t ldy = ws_ldy(ncol, ydt);
+  void* Y = cv.take((size_t)k * ldy * dtype_size(ydt));
+  const size_t cs_ws = msk_cs_workspace(d, n, k, ydt, MSK_CS_ATOMIC);
+  void* csw = cv.take(cs_ws);
+  if (!Y) return MSK_ENOMEM;
+  int rc;
+  if (ydt == MSK_F64 && dtype == MSK_F32)
+    rc = count_sketch_f64y(A, dtype, d, n, lda, b, k, seed, static_cast<double*>(Y), ldy, st, true,
+                           row0);
+  else
+    rc = launch_cs_atomic(A, dtype, d, n, lda, b, (uint32_t)k, stream_key(seed, kTagHash), Y, ldy,
+                          true, st, csw, cs_ws, true, row0);
+  if (rc) return rc;
+  const size_t rest_off = align_up(cv.used, 256);
+  return gemm_stage(seed, p, k, ncol, Y, ydt, ldy, gemm_prec, Z, ldz, cv.base + rest_off,
+                    ws_bytes - rest_off, st);
+}
+
 // Rows per staged block of ms_sketch_host: the caller's value, else blocks of
 // about 256 MiB of A.
 static int64_t host_chunk_rows(int64_t d, int64_t n, int dtype, int64_t chunk_rows) {
