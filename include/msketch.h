@@ -395,7 +395,7 @@ size_t msk_sns_workspace(int64_t d, int64_t n, int kind, int64_t k, int64_t p,
 /* Sketch-and-solve least squares (Algorithm 1) in FP64 with the sketch
  * `kind` (msk_sketch_kind): W = S [A b]; Householder QR of W; x = R11^{-1}
  * R[0:n, n].  MULTI is ms_lstsq with MSK_GEMM_F64 and no refinement.
- * COUNT uses k (>= n+1; p is ignored): the FP64 CountSketch of [A b] (FP32
+ * COUNT uses k (n+1 <= k < 2^31; p is ignored): the FP64 CountSketch of [A b] (FP32
  * A widened exactly), transposed to column-major for the QR.  GAUSS uses p
  * (n+1 <= p <= 2048; k is ignored).  SRHT uses k (>= n+1) and needs d a
  * power of two (srht_sketch).  A, b, x, info and the return codes as

@@ -399,12 +399,24 @@ int ms_sketch_host(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, 
   // copied into staging buffer j & 1 while block j - 1 is sketched on `st`
   // (a second copy stream for alternate blocks measured no faster: the
   // host link, ~200 GB/s, is the bound)
-  thread_local cudaStream_t cps = nullptr;
-  thread_local cudaEvent_t ev[5];
-  if (!cps) {
-    MSK_CUDA(cudaStreamCreateWithFlags(&cps, cudaStreamNonBlocking));
-    for (auto& e : ev) MSK_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  // (kept per device: streams and events belong to the device current when
+  // they were created)
+  struct HostStreamSet {
+    cudaStream_t cps = nullptr;
+    cudaEvent_t ev[5];
+  };
+  constexpr int kMaxDevices = 64;
+  thread_local HostStreamSet sets[kMaxDevices];
+  int dev = 0;
+  MSK_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return MSK_ENOTSUP;
+  HostStreamSet& hs = sets[dev];
+  if (!hs.cps) {
+    MSK_CUDA(cudaStreamCreateWithFlags(&hs.cps, cudaStreamNonBlocking));
+    for (auto& e : hs.ev) MSK_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   }
+  cudaStream_t cps = hs.cps;
+  cudaEvent_t* ev = hs.ev;
   cudaEvent_t* ready = ev;      // ready[j]: block in buffer j copied
   cudaEvent_t* done = ev + 2;   // done[j]: buffer j's block sketched
   cudaEvent_t start = ev[4];    // earlier work on `st` (the caller's use of ws) finished

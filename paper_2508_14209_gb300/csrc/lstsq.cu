@@ -778,7 +778,8 @@ int sns_lstsq(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, const
   if (lda < d) return -5;
   if (!b) return -6;
   if (kind != MSK_SKETCH_COUNT && kind != MSK_SKETCH_GAUSS && kind != MSK_SKETCH_SRHT) return -7;
-  if ((kind == MSK_SKETCH_COUNT || kind == MSK_SKETCH_SRHT) && (k < n + 1 || k > 0xFFFFFFFFLL))
+  // the QR of the k x (n+1) sketch indexes rows in 32 bits
+  if ((kind == MSK_SKETCH_COUNT || kind == MSK_SKETCH_SRHT) && (k < n + 1 || k > 0x7FFFFFFFLL))
     return -8;
   if (kind == MSK_SKETCH_SRHT && (d < 2 || (d & (d - 1)) != 0 || d > (int64_t(1) << 26)))
     return MSK_ENOTSUP;
