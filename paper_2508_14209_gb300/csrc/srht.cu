@@ -117,7 +117,8 @@ __global__ void __launch_bounds__(kSrThreads) srht_high_kernel(const TA* __restr
 // Last pass: CTA (q, c) transforms rows [q 2^tbits, (q+1) 2^tbits) of column
 // c along the low tbits bits — from the scratch T (two passes) or straight
 // from [A b] with D (one pass) — and stores the sampled rows of the tile:
-// samples perm[offs[q] .. offs[q+1]).
+// samples perm[offs[q] .. offs[q+1]).  The 8 lowest bits go in registers and
+// warp shuffles (their strides, 1 to 128 elements, conflict in shared memory).
 template <typename TA, bool FROM_A>
 __global__ void __launch_bounds__(kSrThreads) srht_low_kernel(
     const TA* __restrict__ A, int64_t lda, int64_t n, const double* __restrict__ b, int64_t d,
@@ -128,18 +129,57 @@ __global__ void __launch_bounds__(kSrThreads) srht_low_kernel(
   const int64_t q = blockIdx.x, c = blockIdx.y;
   const int nel = 1 << tbits;
   const int64_t g0 = q << tbits;
-  if (FROM_A) {
-    for (int e = threadIdx.x; e < nel; e += blockDim.x) {
+  const double* Tc = FROM_A ? nullptr : T + c * d + g0;
+  auto load = [&](int e) -> double {
+    if (FROM_A) {
       const int64_t g = g0 + e;
       const double x = sr_x(A, lda, n, b, g, c);
-      sr_s[e] = negative_of(draw(dkey, (uint64_t)g)) ? -x : x;
+      return negative_of(draw(dkey, (uint64_t)g)) ? -x : x;
     }
+    return Tc[e];
+  };
+  if (tbits >= 8) {
+    // the 8 low bits in registers: a warp takes 256 consecutive rows, lane =
+    // bits 0-4 (butterflies by shuffle), register j = bits 5-7 (butterflies
+    // within the thread); then the stages of the higher bits in shared
+    // memory on rows of 256 contiguous elements (conflict-free)
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nw = (int)(blockDim.x >> 5);
+    for (int w = warp; w < (nel >> 8); w += nw) {
+      const int base = w << 8;
+      double x[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) x[j] = load(base + j * 32 + lane);
+#pragma unroll
+      for (int t = 0; t < 3; ++t)
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (!(j & (1 << t))) {
+            const double a = x[j], v = x[j | (1 << t)];
+            x[j] = a + v;
+            x[j | (1 << t)] = a - v;
+          }
+#pragma unroll
+      for (int bt = 0; bt < 5; ++bt) {
+        // lo + hi on the lane whose bit is clear, lo - hi on its partner: one
+        // exact-product FMA either way (x * -1 + o is o - x exactly)
+        const double sg = (lane & (1 << bt)) ? -1.0 : 1.0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const double o = __shfl_xor_sync(0xffffffffu, x[j], 1 << bt);
+          x[j] = fma(x[j], sg, o);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) sr_s[base + j * 32 + lane] = x[j];
+    }
+    __syncthreads();
+    sr_fwht_smem(sr_s, tbits - 8, 256);
   } else {
-    const double* Tc = T + c * d + g0;
-    for (int e = threadIdx.x; e < nel; e += blockDim.x) sr_s[e] = Tc[e];
+    for (int e = threadIdx.x; e < nel; e += blockDim.x) sr_s[e] = load(e);
+    __syncthreads();
+    sr_fwht_smem(sr_s, tbits, 1);
   }
-  __syncthreads();
-  sr_fwht_smem(sr_s, tbits, 1);
   for (uint32_t u = offs[q] + threadIdx.x; u < offs[q + 1]; u += blockDim.x) {
     const uint32_t l = perm[u];
     const uint32_t j = bucket_of(draw(pkey, (uint64_t)l), (uint32_t)d);
