@@ -136,19 +136,27 @@ __device__ __forceinline__ void gt_cp8(double* dst, const double* src, int bytes
 
 // nbuf = 2: the next K rows are copied (cp.async) while this K-row tile is
 // multiplied; nbuf = 1 when two tiles do not fit in shared memory.
+// BPT: blocks (slots) per thread.  A CTA of blockDim = G * tpanel threads runs
+// G row groups over the same panel: group g takes rows kk = g, g + G, ... of
+// each staged tile with its own accumulators and writes its own partial slice
+// (blockIdx.y * G + g).  Narrow panels (few 2x2 blocks) use BPT = 2 and G > 1,
+// so that an SM holds enough independent FP64 accumulation chains.
+template <int BPT>
 __global__ void __launch_bounds__(kGtMaxThreads) gram_tri_kernel(
     const double* __restrict__ A, int64_t lda, int64_t d, int64_t n, const double* __restrict__ b,
-    int64_t rchunk, int nb, int per_panel, int nbuf, double* __restrict__ part) {
+    int64_t rchunk, int nb, int per_panel, int nbuf, int tpanel, double* __restrict__ part) {
   extern __shared__ __align__(16) double gt_x[];
   const int64_t ncol = n + 1;
   const int pitch = 2 * nb + 2;
   const int64_t nblk = (int64_t)nb * (nb + 1) / 2;
   const int64_t bfirst = (int64_t)blockIdx.x * per_panel;
   const int64_t blast = min(nblk, bfirst + per_panel);
-  int ai[kGtBpt], cj[kGtBpt];
+  const int G = (int)blockDim.x / tpanel;
+  const int grp = (int)threadIdx.x / tpanel, tl = (int)threadIdx.x % tpanel;
+  int ai[BPT], cj[BPT];
 #pragma unroll
-  for (int s = 0; s < kGtBpt; ++s) {
-    const int64_t q = bfirst + threadIdx.x + (int64_t)s * blockDim.x;
+  for (int s = 0; s < BPT; ++s) {
+    const int64_t q = bfirst + tl + (int64_t)s * tpanel;
     int i = 0, j = 0;
     if (q < blast) {
       int64_t r = q;
@@ -162,7 +170,7 @@ __global__ void __launch_bounds__(kGtMaxThreads) gram_tri_kernel(
     cj[s] = 2 * j;
   }
   const int64_t r0 = (int64_t)blockIdx.y * rchunk, r1 = min(d, r0 + rchunk);
-  double acc[kGtBpt][4] = {};
+  double acc[BPT][4] = {};
   const int width = 2 * nb;  // staged columns (ncol, or ncol + 1 zero column)
   // rows k0 .. k0+K-1 of [A b] into buf (zero past r1 and in the pad column)
   auto stage = [&](int64_t k0, double* buf) {
@@ -187,11 +195,13 @@ __global__ void __launch_bounds__(kGtMaxThreads) gram_tri_kernel(
       asm volatile("cp.async.wait_group 0;" ::: "memory");
     }
     __syncthreads();
+    // (8-slot panels have one row group: their loop keeps a unit stride)
+    const int kk0 = BPT == 2 ? grp : 0, kstep = BPT == 2 ? G : 1;
 #pragma unroll 2
-    for (int kk = 0; kk < kGtK; ++kk) {
+    for (int kk = kk0; kk < kGtK; kk += kstep) {
       const double* row = cur + kk * pitch;
 #pragma unroll
-      for (int s = 0; s < kGtBpt; ++s) {
+      for (int s = 0; s < BPT; ++s) {
         if (ai[s] < 0) continue;
         const double2 av = *reinterpret_cast<const double2*>(row + ai[s]);
         const double2 cv = *reinterpret_cast<const double2*>(row + cj[s]);
@@ -205,9 +215,9 @@ __global__ void __launch_bounds__(kGtMaxThreads) gram_tri_kernel(
     if (nbuf == 1 && k0 + kGtK < r1) stage(k0 + kGtK, gt_x);
   }
   // part[slice][c * ncol + a] (column-major (n+1) x (n+1)); only a <= c kept
-  double* out = part + (int64_t)blockIdx.y * ncol * ncol;
+  double* out = part + ((int64_t)blockIdx.y * G + grp) * ncol * ncol;
 #pragma unroll
-  for (int s = 0; s < kGtBpt; ++s) {
+  for (int s = 0; s < BPT; ++s) {
     if (ai[s] < 0) continue;
 #pragma unroll
     for (int u = 0; u < 2; ++u)
@@ -223,7 +233,9 @@ struct GramPlan {
   bool tri;              // gram_tri_kernel (else 64x64 tiles of gram_kernel)
   int ntile, npairs;     // tiles: tiles per side, upper tile pairs
   int nb, per_panel, npanels, threads, nbuf;  // tri: 2x2 blocks per side, blocks per CTA panel
+  int bpt, tpanel, groups;  // tri: slots per thread, threads per panel copy, row groups per CTA
   int slices;
+  int parts;                // partial slices written: slices * groups
   int64_t rchunk;
   size_t smem;
 };
@@ -238,22 +250,30 @@ static GramPlan gram_plan(int64_t d, int64_t n) {
   if (g.tri) {
     g.nb = (int)((ncol + 1) / 2);
     const int64_t nblk = (int64_t)g.nb * (g.nb + 1) / 2;
-    g.npanels = (int)((nblk + (int64_t)kGtMaxThreads * kGtBpt - 1) / ((int64_t)kGtMaxThreads * kGtBpt));
+    // narrow panels: 2 slots per thread and up to 8 row groups per CTA
+    g.bpt = nblk <= 512 ? 2 : kGtBpt;
+    const int64_t cap = (int64_t)(g.bpt == 2 ? 256 : kGtMaxThreads) * g.bpt;
+    g.npanels = (int)((nblk + cap - 1) / cap);
     g.per_panel = (int)((nblk + g.npanels - 1) / g.npanels);
-    g.threads = (int)(((g.per_panel + kGtBpt - 1) / kGtBpt + 31) / 32 * 32);
+    g.tpanel = (int)(((g.per_panel + g.bpt - 1) / g.bpt + 31) / 32 * 32);
+    g.groups = g.bpt == 2 ? std::max(1, std::min(8, 256 / g.tpanel)) : 1;
+    g.threads = g.tpanel * g.groups;
     const size_t tile = (size_t)kGtK * (2 * g.nb + 2) * sizeof(double);
     g.nbuf = 2 * tile <= (size_t)160 * 1024 ? 2 : 1;
     g.smem = g.nbuf * tile;
-    // The FP64 pipe needs many warps per SM (one warp's chain of dependent
-    // DFMAs issues far below the pipe's rate): about 16 warps per SM, as
-    // occupancy allows, by giving narrow panels more row slices.
+    // The FP64 pipe needs many independent accumulation chains per SM (one
+    // warp's chain of dependent DFMAs issues far below the pipe's rate):
+    // about 16 warps of 8-slot panels, or 48 of narrow 2-slot ones, as
+    // occupancy allows, by giving panels more row slices.
+    const void* kfn = g.bpt == 2 ? reinterpret_cast<const void*>(gram_tri_kernel<2>)
+                                 : reinterpret_cast<const void*>(gram_tri_kernel<kGtBpt>);
     int occ = 0;
-    if (allow_max_smem(reinterpret_cast<const void*>(gram_tri_kernel)) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gram_tri_kernel, g.threads, g.smem) !=
-            cudaSuccess)
+    if (allow_max_smem(kfn) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, g.threads, g.smem) != cudaSuccess)
       occ = 1;
     const int warps = g.threads / 32;
-    const int per_sm = std::max(1, std::min(occ, std::max(2, (16 + warps - 1) / warps)));
+    const int want = g.bpt == 2 ? 48 : 16;
+    const int per_sm = std::max(1, std::min(occ, std::max(2, (want + warps - 1) / warps)));
     target = (int64_t)num_sms() * per_sm;
     groups = g.npanels;
     kstep = kGtK;
@@ -268,6 +288,7 @@ static GramPlan gram_plan(int64_t d, int64_t n) {
   g.rchunk = ((d + s - 1) / s + kstep - 1) / kstep * kstep;
   if (g.rchunk < kstep) g.rchunk = kstep;
   g.slices = (int)std::max<int64_t>(1, (d + g.rchunk - 1) / g.rchunk);
+  g.parts = g.slices * (g.tri ? g.groups : 1);
   return g;
 }
 
@@ -276,7 +297,7 @@ static size_t gram_workspace(int64_t d, int64_t n) {
   const int64_t ncol = n + 1;
   Need nd;
   nd.add((size_t)std::max(g.npairs, 1) * sizeof(int2));
-  nd.add((size_t)g.slices * ncol * ncol * sizeof(double));
+  nd.add((size_t)g.parts * ncol * ncol * sizeof(double));
   return nd.used;
 }
 
@@ -285,10 +306,16 @@ static size_t gram_workspace(int64_t d, int64_t n) {
 static int launch_gram(const GramPlan& g, const double* A, int64_t lda, int64_t d, int64_t n,
                        const double* b, int2* tiles, double* part, cudaStream_t st) {
   if (g.tri) {
-    MSK_ALLOW_SMEM(gram_tri_kernel);
     dim3 grid(g.npanels, g.slices);
-    gram_tri_kernel<<<grid, g.threads, g.smem, st>>>(A, lda, d, n, b, g.rchunk, g.nb, g.per_panel,
-                                                     g.nbuf, part);
+    if (g.bpt == 2) {
+      MSK_ALLOW_SMEM(gram_tri_kernel<2>);
+      gram_tri_kernel<2><<<grid, g.threads, g.smem, st>>>(A, lda, d, n, b, g.rchunk, g.nb,
+                                                          g.per_panel, g.nbuf, g.tpanel, part);
+    } else {
+      MSK_ALLOW_SMEM(gram_tri_kernel<kGtBpt>);
+      gram_tri_kernel<kGtBpt><<<grid, g.threads, g.smem, st>>>(A, lda, d, n, b, g.rchunk, g.nb,
+                                                               g.per_panel, g.nbuf, g.tpanel, part);
+    }
     MSK_CHECK_LAUNCH("gram_tri_kernel");
     return MSK_OK;
   }
@@ -546,12 +573,12 @@ static int rcq_gram(const double* Q0, int64_t ldq, int64_t d, int64_t m, const d
   GramPlan g = gram_plan(d, m);
   const int64_t ncol = m + 1;
   int2* tiles = static_cast<int2*>(cv.take((size_t)std::max(g.npairs, 1) * sizeof(int2)));
-  double* part = static_cast<double*>(cv.take((size_t)g.slices * ncol * ncol * sizeof(double)));
+  double* part = static_cast<double*>(cv.take((size_t)g.parts * ncol * ncol * sizeof(double)));
   double* C = static_cast<double*>(cv.take((size_t)ncol * ncol * sizeof(double)));
   if (!tiles || !part || !C) return MSK_ENOMEM;
   int rc = launch_gram(g, Q0, ldq, d, m, col, tiles, part, st);
   if (rc) return rc;
-  launch_gram_reduce(part, g.slices, ncol, C, st);
+  launch_gram_reduce(part, g.parts, ncol, C, st);
   MSK_CHECK_LAUNCH("gram_reduce_kernel");
   *Cout = C;
   return MSK_OK;
@@ -996,7 +1023,7 @@ int ne_lstsq(const double* A, int64_t d, int64_t n, int64_t lda, const double* b
   GramPlan g = gram_plan(d, n);
   const int64_t ncol = n + 1;
   int2* tiles = static_cast<int2*>(cv.take((size_t)std::max(g.npairs, 1) * sizeof(int2)));
-  double* part = static_cast<double*>(cv.take((size_t)g.slices * ncol * ncol * sizeof(double)));
+  double* part = static_cast<double*>(cv.take((size_t)g.parts * ncol * ncol * sizeof(double)));
   double* C = static_cast<double*>(cv.take((size_t)ncol * ncol * sizeof(double)));
   double* R = static_cast<double*>(cv.take((size_t)n * n * sizeof(double)));
   double* y = static_cast<double*>(cv.take((size_t)n * sizeof(double)));
@@ -1007,7 +1034,7 @@ int ne_lstsq(const double* A, int64_t d, int64_t n, int64_t lda, const double* b
     const int rc = launch_gram(g, A, lda, d, n, b, tiles, part, st);
     if (rc) return rc;
   }
-  launch_gram_reduce(part, g.slices, ncol, C, st);
+  launch_gram_reduce(part, g.parts, ncol, C, st);
   MSK_CHECK_LAUNCH("gram_reduce_kernel");
   // C[0:n,0:n] = A^T A, C[0:n, n] = A^T b.  Cholesky overwrites C's upper part.
   int rc = launch_cholesky(C, n, ncol, R, n, status, st);
