@@ -219,10 +219,14 @@ size_t msk_ms_workspace(int64_t d, int64_t n, int with_b, int64_t k, int64_t p,
  * seed, strategy as in cs_sketch; the Gaussian uses the same seed (tag 2).
  *   gemm_prec : msk_gemm_prec, the arithmetic of Z = G Y.
  *   Z : device double, column-major p x ncol, leading dimension ldz >= p.
- * Errors as cs_sketch, plus -8 p < 1, -10 bad gemm_prec, -11 Z NULL,
- *   -12 ldz < p, MSK_ENOTSUP gemm_prec F64 with dtype F32 is allowed, every
- *   other combination too; MSK_ENOTSUP only for tensor paths on sizes over
- *   the documented limits (p <= 2^20, ncol <= 512). */
+ * Errors: -1 A NULL (with d, n > 0), -2 bad dtype, -3 d < 0, -4 n < 0 or
+ *   no column at all, -5 lda < d, -7 k < 1 or k >= 2^32, -8 p < 1 or
+ *   p >= 2^24, -10 bad gemm_prec, -11 Z NULL, -12 ldz < p, -13 bad strategy,
+ *   MSK_ENOMEM ws too small.  MSK_ENOTSUP in three cases only: a tensor-core
+ *   gemm_prec (BF16, F16, BF16X3) with dtype MSK_F64 (those paths take the
+ *   FP32 CountSketch); a tensor-core gemm_prec with ncol > 512; the sorted
+ *   strategy for the FP64 sketch of FP32 A (gemm_prec F64 with dtype F32).
+ *   Every other combination of dtype, gemm_prec and strategy is supported. */
 int ms_sketch(const void *A, int dtype, int64_t d, int64_t n, int64_t lda,
               const double *b, int64_t k, int64_t p, uint64_t seed,
               int gemm_prec, void *Z, int64_t ldz, int strategy, void *ws,
@@ -308,7 +312,9 @@ int msk_trsv_upper(const double *R, int64_t n, int64_t ldr, const double *rhs,
  *   loads it until the process exits.  No device memory is allocated.
  *   The first call made on a device looks up the array's device address (once
  *   per device, with that device current); make that first call before any
- *   stream capture starts on the device.
+ *   stream capture starts on the device.  A device reset (cudaDeviceReset)
+ *   ends the context the address belongs to: the first call after it looks
+ *   the address up again, and it too should come before any capture.
  *   All calls share the array and each call overwrites it: calls whose GPU
  *   work overlaps in time (e.g. on different streams) race and give wrong
  *   results; serialise them.  Nothing in the array needs to start at zero.

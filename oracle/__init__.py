@@ -21,6 +21,10 @@ Parity status of each function (what pins it, see tests/test_oracle_*.py):
                        (integer-exact); row0 = 0 is countsketch itself
   gemm                 integer-exact products, bf16/fp16 rounding definition
   householder_r/solve  R^T R = Z^T Z, |R| against LAPACK's QR, numpy lstsq
+  residual / relres /  integer problems whose residual is exact (r = e, norms
+    residual_and_g.    as exact integers), x = 0 and b = A x, numpy's FP64
+                       evaluation of r, A^T r and the norms, A^T r = 0 at
+                       LAPACK's least-squares minimiser
   sns_lstsq            exact recovery for b = A x, distortion bound of Section 2
   ne_lstsq             agrees with QR when well conditioned, fails for
                        kappa > 1e8 (Section 6.3)

@@ -347,10 +347,38 @@ def msk_gemm_workspace(p, k, ncol, gemm_prec):
     return load().msk_gemm_workspace(p, k, ncol, gemm_prec)
 
 
+def _gemm_operands(p, Y, Z, gemm_prec):
+    """Check the Gaussian-stage operands the C side cannot see through its
+    void pointers: Y row-major k x ncol on the GPU (unit column stride),
+    float64 for GEMM_F64 and float32 for every other precision; Z, when
+    given, a column-major p x ncol float64 GPU tensor."""
+    if gemm_prec not in _PREC_DTYPE and gemm_prec != GEMM_BF16X3:
+        raise ValueError(f"unknown gemm_prec {gemm_prec}")
+    if Y.dim() != 2:
+        raise ValueError("Y must be 2-D (k x ncol)")
+    k, ncol = Y.shape
+    want = torch.float64 if gemm_prec == GEMM_F64 else torch.float32
+    if Y.dtype != want:
+        raise ValueError(f"Y must be {want} for gemm_prec {gemm_prec}, got {Y.dtype}")
+    if ncol > 1 and Y.stride(1) != 1:
+        raise ValueError("Y must be row-major (stride(1) == 1)")
+    if k > 1 and Y.stride(0) < ncol:
+        raise ValueError("Y's row pitch stride(0) must be >= ncol")
+    if Z is not None:
+        if Z.dtype != torch.float64 or tuple(Z.shape) != (p, ncol):
+            raise ValueError(f"Z must be float64 of shape ({p}, {ncol})")
+        if p > 1 and Z.stride(0) != 1:
+            raise ValueError("Z must be column-major (stride(0) == 1)")
+        _cuda(Z, "Z")
+    _cuda(Y, "Y")
+    return k, ncol
+
+
 def msk_gemm(seed, p, Y, gemm_prec=GEMM_F64, Z=None, ws=None, stream=None):
     """Z = G Y with G the seed's p x k Gaussian; Y row-major k x ncol
     (float64 for GEMM_F64, float32 otherwise)."""
-    k, ncol = Y.shape
+    k, ncol = _gemm_operands(p, Y, Z, gemm_prec)
+    _cuda(ws, "ws")
     if Z is None:
         Z = colmajor(p, ncol, torch.float64, Y.device)
     if ws is None:
@@ -364,7 +392,7 @@ def msk_gemm_noalloc(seed, p, Y, gemm_prec=GEMM_F64, Z=None, stream=None):
     """msk_gemm with the library's fixed scratch array instead of a caller
     workspace (for callers that may not allocate device memory; Z is still the
     caller's).  Calls share the array: serialise them."""
-    k, ncol = Y.shape
+    k, ncol = _gemm_operands(p, Y, Z, gemm_prec)
     if Z is None:
         Z = colmajor(p, ncol, torch.float64, Y.device)
     _check("msk_gemm_noalloc", load().msk_gemm_noalloc(seed & (2**64 - 1), p, k, ncol, _ptr(Y), Y.stride(0),

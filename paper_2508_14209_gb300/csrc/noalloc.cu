@@ -23,7 +23,13 @@
 // name refers to a host-side stand-in).  The device address is therefore
 // looked up with cudaGetSymbolAddress once per device, with that device
 // current, on the first call made while that device is current; that first
-// call should come before any stream capture begins on that device.
+// call should come before any stream capture begins on that device.  The
+// address belongs to the device's current context: after cudaDeviceReset (or
+// any other teardown of that context) the module is loaded again, possibly
+// elsewhere, so the cached address is keyed by the context and looked up
+// afresh, by the next call, once the context has changed (make that call
+// before any capture too).
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -37,22 +43,54 @@ constexpr size_t kNoallocScratchBytes = MSK_NOALLOC_SCRATCH_BYTES;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
 namespace {
+// The driver API's cuCtxGetCurrent, looked up once through the runtime (no
+// link against libcuda, so the library still loads where no driver is
+// installed); null when unavailable.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+CtxGetCurrentFn ctx_get_current() {
+  static CtxGetCurrentFn fn = [] {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &ptr, 4000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      return reinterpret_cast<CtxGetCurrentFn>(ptr);
+    return static_cast<CtxGetCurrentFn>(nullptr);
+  }();
+  return fn;
+}
+
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 void* g_scratch_ptr[kMaxDevices] = {nullptr};
+CUcontext g_scratch_ctx[kMaxDevices] = {nullptr};
 }  // namespace
 
 // Device address of the scratch array on the current device (set up once per
-// device).  Returns MSK_OK or MSK_ECUDA.
+// device and context).  Returns MSK_OK or MSK_ECUDA.
 static int noalloc_scratch(void** out) {
   int dev = 0;
   MSK_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) return MSK_ENOTSUP;
+  // A thread on which the runtime has not yet made the device's context
+  // current sees none here; the look-up below makes it current.
+  CtxGetCurrentFn get_ctx = ctx_get_current();
+  if (!get_ctx) {
+    set_error_text("msk_gemm_noalloc: cuCtxGetCurrent entry point not available");
+    return MSK_ECUDA;
+  }
+  CUcontext ctx = nullptr;
+  if (get_ctx(&ctx) != CUDA_SUCCESS) ctx = nullptr;
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_ptr[dev]) {
+  if (!g_scratch_ptr[dev] || !ctx || g_scratch_ctx[dev] != ctx) {
     void* p = nullptr;
     MSK_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    if (get_ctx(&ctx) != CUDA_SUCCESS || !ctx) {
+      set_error_text("msk_gemm_noalloc: no current CUDA context");
+      return MSK_ECUDA;
+    }
     g_scratch_ptr[dev] = p;
+    g_scratch_ctx[dev] = ctx;
   }
   *out = g_scratch_ptr[dev];
   return MSK_OK;

@@ -78,3 +78,38 @@ def test_argument_checks_return_before_any_device_work(lib):
     # workspace queries are pure host arithmetic
     assert msk.msk_srht_workspace(1 << 20, 7, True, 4096) >= (1 << 20) * 8 * 8
     assert msk.msk_srht_workspace(1000, 7, True, 4096) == 0  # not a power of two
+
+
+def test_gemm_wrappers_refuse_operands_the_c_side_cannot_check():
+    """msk_gemm and msk_gemm_noalloc take Y and Z through void pointers whose
+    element type follows gemm_prec: the binding refuses a Y of the wrong
+    dtype (a float32 Y read as float64 would overrun it), a column-strided Y,
+    a Z of the wrong dtype, shape or layout, and host tensors — all before
+    any call into the library."""
+    import torch
+
+    import paper_2508_14209_gb300 as msk
+
+    k, ncol, p = 64, 5, 8
+    y64 = torch.zeros((k, ncol), dtype=torch.float64)
+    y32 = torch.zeros((k, ncol), dtype=torch.float32)
+    for fn in (msk.msk_gemm, msk.msk_gemm_noalloc):
+        with pytest.raises(ValueError, match="float64"):
+            fn(1, p, y32, gemm_prec=msk.GEMM_F64)
+        for prec in (msk.GEMM_F32, msk.GEMM_BF16, msk.GEMM_F16, msk.GEMM_BF16X3):
+            with pytest.raises(ValueError, match="float32"):
+                fn(1, p, y64, gemm_prec=prec)
+        with pytest.raises(ValueError, match="row-major"):
+            fn(1, p, torch.zeros((k, 2 * ncol), dtype=torch.float64)[:, ::2], gemm_prec=msk.GEMM_F64)
+        with pytest.raises(ValueError, match="2-D"):
+            fn(1, p, torch.zeros(k, dtype=torch.float64), gemm_prec=msk.GEMM_F64)
+        with pytest.raises(ValueError, match="Z must be float64"):
+            fn(1, p, y64, gemm_prec=msk.GEMM_F64, Z=torch.zeros((p, ncol), dtype=torch.float32))
+        with pytest.raises(ValueError, match="Z must be float64"):
+            fn(1, p, y64, gemm_prec=msk.GEMM_F64, Z=torch.zeros((p + 1, ncol), dtype=torch.float64))
+        with pytest.raises(ValueError, match="column-major"):
+            fn(1, p, y64, gemm_prec=msk.GEMM_F64, Z=torch.zeros((p, ncol), dtype=torch.float64))
+        with pytest.raises(ValueError, match="CUDA"):
+            fn(1, p, y64, gemm_prec=msk.GEMM_F64, Z=msk.colmajor(p, ncol, torch.float64, "cpu"))
+        with pytest.raises(ValueError, match="unknown gemm_prec"):
+            fn(1, p, y64, gemm_prec=9)

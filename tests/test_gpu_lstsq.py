@@ -149,12 +149,15 @@ def test_residual_pass_exact_with_subnormal_and_zero_entries(msk, orc, n):
     assert abs(info["relres"] - r_orc) <= 1e-10 * r_orc
 
 
-@pytest.mark.parametrize("d,n", [(20000 + 3, 128), (9001, 255), (6000, 256), (3000, 520), (4000, 1)])
+@pytest.mark.parametrize("d,n", [(20000 + 3, 128), (9001, 255), (6000, 256), (3000, 520), (4000, 1),
+                                 (9001, 24), (9001, 32), (9001, 10), (9001, 16)])
 def test_ne_shapes_match_oracle(msk, orc, d, n):
     """Normal equations across the Gram kernels' layouts: one panel of 2x2
     blocks (129 columns), several panels (256, 257 columns), an odd column
-    count with a zero pad column, the 64x64-tile form past 513 columns, and
-    a single column; kappa = 1e2, so both sides sit at the minimiser."""
+    count with a zero pad column, the 64x64-tile form past 513 columns, a
+    single column, and the narrow panels (two slots per thread) with 8, 4 and
+    2 row groups per CTA (11 and 17 columns: 8 groups; 25 columns: 4; 33
+    columns: 2); kappa = 1e2, so both sides sit at the minimiser."""
     A, b = _problem(d, n, -2, 300 + n, torch.float64)
     x, rc = msk.ne_lstsq(dev_colmajor(A, msk), b.cuda())
     assert rc == 0
@@ -189,3 +192,37 @@ def test_ne_matches_oracle_and_breaks_down(msk, orc):
         assert rn > 1e3 * rs
     else:
         assert rc > 0 and torch.isnan(xn).all()
+
+
+# The mixed-precision configuration's Gaussian-stage arms (FP32 A and FP32
+# CountSketch; the Gaussian stage in BF16, in FP16, or split-BF16 with
+# draining; FP64 QR and residuals), on its shape family scaled down
+# (k = 2n^2, p = 4n) at kappa = 1e4 and 1e8.  A single 16-bit rounding of the
+# sketch perturbs the preconditioner R by O(u16 kappa(A)), so the refinement
+# may run out of steps; each result must then be reported as MSK_ENOCONV and
+# still be no worse than FP64 sketch-and-solve of the same request.  A
+# converged result sits at the oracle's minimiser (two-sided, 1e-8).
+@pytest.mark.parametrize("prec", ["bf16", "f16", "bf16x3"])
+@pytest.mark.parametrize("lsig", [-4, -8])
+def test_refined_gaussian_stage_arms(msk, orc, prec, lsig):
+    d, n = 1 << 16, 64
+    A, b = _problem(d, n, lsig, 500 + n, torch.float32)
+    k, p, seed = 2 * n * n, 4 * n, 0x5EED0004
+    Ad = dev_colmajor(A, msk)
+    x, info, rc = msk.ms_lstsq(Ad, b.cuda(), k, p, seed, msk.GEMM_PRECS[prec], refine=True,
+                               tol=1e-12, max_iter=20)
+    An, bn = A.numpy(), b.numpy()
+    ro = orc.relres(An, bn, orc.lstsq_exact(An, bn))
+    rg = orc.relres(An, bn, x.cpu().numpy())
+    _, r_sns64, _ = orc.sns_lstsq(An.astype(np.float64), bn, k, p, seed, "f64")
+    print(f"arm {prec} kappa=1e{-lsig}: status {rc} inner iterations {info['iters']} "
+          f"|relres - relres*|/relres* = {abs(rg - ro) / ro:.3e} relres/relres_SnS64 = {rg / r_sns64:.6f}")
+    assert abs(info["relres"] - rg) <= 1e-10 * rg
+    assert rg <= (1 + 1e-8) * r_sns64
+    if rc == msk.MSK_OK:
+        assert info["converged"] == 1
+        assert abs(rg - ro) <= 1e-8 * ro
+    else:
+        assert rc == msk.MSK_ENOCONV and info["converged"] == 0, (rc, info)
+    if prec == "bf16x3":
+        assert rc == msk.MSK_OK   # the draining split-BF16 stage converges at both kappa
