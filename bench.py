@@ -382,13 +382,13 @@ def _relres_fp64(A, b, x):
     return float(torch.sqrt(rr) / torch.linalg.vector_norm(b))
 
 
-def _timed(call, reps):
-    """Median CUDA-event time (ms) of `call` over `reps` runs after one
-    untimed run; returns (ms, last result)."""
+def _timed(call, reps, warm=True):
+    """Median CUDA-event time (ms) of `call` over `reps` runs (after one
+    untimed run when `warm`); returns (ms, last result)."""
     import numpy as np
     import torch
 
-    out = call()
+    out = call() if warm else None
     torch.cuda.synchronize()
     ts = []
     for _ in range(reps):
@@ -449,11 +449,13 @@ def run_ls_configs(dev):
     r64 = _relres_fp64(A, b, x)
     del ws64
     cfg4 = {"fp64_sns": {"ms_per_solve": round(ms64, 3), "status": rc64, "relres": float(f"{r64:.6e}")}}
+    # the single-rounding arms may run out of steps (MSK_ENOCONV after
+    # max_iter outer steps of up to 200 CG iterations): timed once, cold
     for name, reps in (("bf16x3", 3), ("bf16", 1), ("f16", 1)):
         gp = msk.GEMM_PRECS[name]
         ws = msk.workspace(msk.msk_lstsq_workspace(d, n, k, p, msk.MSK_F32, gp, 1), dev)
         ms, (_, info, rc) = _timed(lambda: msk.ms_lstsq(A, b, k, p, 0x5EED0004, gp, refine=True, tol=1e-10,
-                                                        max_iter=10, x=x, ws=ws), reps)
+                                                        max_iter=10, x=x, ws=ws), reps, warm=name == "bf16x3")
         rg = _relres_fp64(A, b, x)
         cfg4[f"refined_{name}"] = {
             "ms_per_solve": round(ms, 3), "status": rc, "converged": info["converged"],
@@ -620,7 +622,7 @@ def main():
     ap.add_argument("--no-ls", action="store_true", help="skip the least-squares configurations")
     ap.add_argument("--serve-requests", type=int, default=4000)
     ap.add_argument("--serve-rate", type=float, default=400.0)
-    ap.add_argument("--serve-tol", type=float, default=1e-6)
+    ap.add_argument("--serve-tol", type=float, default=1e-7)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -298,16 +298,16 @@ int msk_householder_qr(double *W, int64_t m, int64_t c, int64_t ldw,
 int msk_trsv_upper(const double *R, int64_t n, int64_t ldr, const double *rhs,
                    double *x, void *stream);
 
-/* Size of the fixed scratch array behind msk_gemm_noalloc (24 MiB). */
-#define MSK_NOALLOC_SCRATCH_BYTES ((size_t)24 << 20)
+/* Size of the fixed scratch array behind msk_gemm_noalloc (64 MiB). */
+#define MSK_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
 
 /* msk_gemm without a caller workspace, for programs that may not allocate
  * device memory when they need the Gaussian stage (for instance a component
  * running under a host application whose allocator owns all device memory, or
  * a loop that cannot pay for the device-wide synchronisation an allocation can
  * cause).  The paper has no counterpart; this is a convenience of the library.
- *   Same arguments and result as msk_gemm, minus ws/ws_bytes.  The scratch (the
- *   binary32 G and the split-K partials) lives in one array of
+ *   Same arguments and result as msk_gemm, minus ws/ws_bytes.  The scratch (G
+ *   or its slices, the slices of Y and the split-K partials) lives in one array of
  *   MSK_NOALLOC_SCRATCH_BYTES inside the library, reserved on every GPU that
  *   loads it until the process exits.  No device memory is allocated.
  *   The first call made on a device looks up the array's device address (once

@@ -89,6 +89,12 @@ int gemm_stage(uint64_t seed, int64_t p, int64_t k, int64_t ncol, const void* Y,
     return launch_tc_gemm(gkey, p, k, ncol, static_cast<const float*>(Y), ldy, gemm_prec, Z, ldz,
                           ws, ws_bytes, st);
   }
+  // FP64 Y and FP64 arithmetic: the exact-slicing tensor-core stage where it
+  // applies and the workspace holds it, else the FP64 SIMT kernel
+  if (gemm_prec == MSK_GEMM_F64 && y_dtype == MSK_F64 && oz_applicable(p, k, ncol) &&
+      ws_bytes >= oz_gemm_workspace(p, k, ncol))
+    return launch_oz_gemm(gkey, p, k, ncol, static_cast<const double*>(Y), ldy, Z, ldz, ws, ws_bytes,
+                          st);
   Carve cv(ws, ws_bytes);
   float* G = static_cast<float*>(cv.take((size_t)p * k * sizeof(float)));
   if (!G) return MSK_ENOMEM;
@@ -219,6 +225,8 @@ size_t msk_gemm_workspace(int64_t p, int64_t k, int64_t ncol, int gemm_prec) {
   } else {
     nd.add((size_t)p * k * sizeof(float));  // G in binary32
     nd.add(gemm_simt_workspace(p, k, ncol, gemm_prec == MSK_GEMM_F64));
+    if (gemm_prec == MSK_GEMM_F64 && oz_applicable(p, k, ncol))
+      return std::max(nd.used, oz_gemm_workspace(p, k, ncol));
   }
   return nd.used;
 }

@@ -156,6 +156,11 @@ int launch_tc_wait_selftest(cudaStream_t st);
 size_t tc_gemm_workspace(int64_t p, int64_t k, int64_t ncol, int prec);
 int launch_tc_gemm(uint64_t gkey, int64_t p, int64_t k, int64_t ncol, const float* Y, int64_t ldy,
                    int prec, double* Z, int64_t ldz, void* ws, size_t ws_bytes, cudaStream_t st);
+// gemm_oz.cu (FP64 Gaussian stage on the tensor cores by exact 8-bit slicing)
+bool oz_applicable(int64_t p, int64_t k, int64_t ncol);
+size_t oz_gemm_workspace(int64_t p, int64_t k, int64_t ncol);
+int launch_oz_gemm(uint64_t gkey, int64_t p, int64_t k, int64_t ncol, const double* Y, int64_t ldy,
+                   double* Z, int64_t ldz, void* ws, size_t ws_bytes, cudaStream_t st);
 // qr.cu
 int launch_householder_qr(double* W, int64_t m, int64_t c, int64_t ldw, cudaStream_t st);
 int launch_trsv_upper(const double* R, int64_t n, int64_t ldr, const double* rhs, double* x,

@@ -7,8 +7,8 @@
 // application whose own allocator owns every byte of device memory, or a
 // latency-critical loop that cannot afford the implicit device-wide
 // synchronisation an allocation may cause.  Such callers still pass their own
-// Y and Z; only the scratch (the binary32 Gaussian G and the split-K partial
-// products) comes from here.
+// Y and Z; only the scratch (the Gaussian G or its slices, the slices of Y and
+// the split-K partial products) comes from here.
 //
 // The scratch is the file-scope array below, kNoallocScratchBytes long.  Every
 // GPU that loads this library reserves it for the life of the process.  All

@@ -1,5 +1,5 @@
 """The request server in the configuration the served benchmark runs
-(tolerance 1e-6, at most 4 outer refinement steps, 3 workers, batches of up
+(tolerance 1e-7, at most 4 outer refinement steps, 3 workers, batches of up
 to 32), on requests shaped like the served workload: n from {16, 32, 64, 128},
 d log-uniform, sigma log-spaced from 1 to 10^-U(2,8), FP32 A, k = 2n^2,
 p = 4n, fresh seeds.  Every result is checked against the oracle:
@@ -18,7 +18,7 @@ import inputs
 
 pytestmark = pytest.mark.gpu
 
-SERVED = dict(tol=1e-6, max_iter=4, workers=3, max_batch=32)
+SERVED = dict(tol=1e-7, max_iter=4, workers=3, max_batch=32)
 
 
 @pytest.fixture(scope="module")

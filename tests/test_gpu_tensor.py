@@ -99,3 +99,47 @@ def test_bounded_wait_expires_and_is_reported(msk):
     Y = torch.randn(1024, 9, dtype=torch.float32, device="cuda")
     Z = msk.msk_gemm(5, 32, Y, gemm_prec=msk.GEMM_BF16)
     assert torch.isfinite(Z).all() and msk.msk_take_timeout() == msk.MSK_OK
+
+
+def _f64_stage_inputs(k, ncol, seed):
+    """FP64 Y with N(0,1) columns and, where there is room, the awkward ones:
+    a zero column, a column of subnormal-scale entries (1e-310), one spanning
+    six decades, one of huge entries (1e300) and one with a single nonzero."""
+    g = torch.Generator().manual_seed(seed)
+    Y = torch.randn(k, ncol, generator=g, dtype=torch.float64)
+    if ncol >= 6:
+        Y[:, 1] = 0.0
+        Y[:, 2] *= 1e-310
+        Y[:, 3] = torch.sign(Y[:, 3]) * 10.0 ** (-6.0 * torch.rand(k, generator=g, dtype=torch.float64))
+        Y[:, 4] *= 1e300
+        Y[:, 5] = 0.0
+        Y[k // 3, 5] = -3.25
+    return Y
+
+
+# The FP64 Gaussian stage from k = 1024 up runs on the tensor cores by exact
+# 8-bit slicing of G and Y; below, and with the knob off, on the FP64 SIMT
+# kernel.  Both must stay within the FP64 dot-product bound of the oracle's
+# compensated product on the same binary32 G, and give the same Z to that
+# bound as each other; repeated calls are bitwise equal.
+@pytest.mark.parametrize("p,k,ncol", [(256, 8192, 64), (512, 32768, 129), (200, 1024, 1), (130, 5000, 65),
+                                      (1024, 2048, 257), (128, 1024, 16), (300, 3001, 7), (64, 1500, 33)])
+def test_f64_stage_sliced_matches_oracle(msk, orc, p, k, ncol):
+    seed = 0x5EED0007 + p + ncol
+    Y = _f64_stage_inputs(k, ncol, k + ncol)
+    Yd = Y.cuda()
+    Z = msk.msk_gemm(seed, p, Yd, gemm_prec=msk.GEMM_F64).cpu().numpy()
+    Z2 = msk.msk_gemm(seed, p, Yd, gemm_prec=msk.GEMM_F64).cpu().numpy()
+    assert msk.msk_take_timeout() == msk.MSK_OK
+    assert np.array_equal(Z, Z2)
+    G = orc.gaussian(seed, p, k).astype(np.float64)
+    Yh = Y.numpy()
+    Zo = orc.gemm(G, Yh)
+    bound = (k + 2) * np.finfo(np.float64).eps * (np.abs(G) @ np.abs(Yh))
+    assert np.all(np.abs(Z - Zo) <= bound)
+    msk.tune_set("gemm.f64_ozaki", 0)
+    try:
+        Zs = msk.msk_gemm(seed, p, Yd, gemm_prec=msk.GEMM_F64).cpu().numpy()
+    finally:
+        msk.tune_clear("gemm.f64_ozaki")
+    assert np.all(np.abs(Zs - Zo) <= bound)
