@@ -14,14 +14,19 @@
 //                 memory);
 //   QR (+ solve)  one launch, one thread-block cluster per problem; with
 //                 refinement, x0 = R^{-1} c after the explicit inverse;
-//   refinement    FP64 residual pass, reduction and CG start: one launch each;
-//                 the inner solve is one CUDA-graph launch whose while node
-//                 loops on the device — kRound (knob "batch.round") CG
+//   refinement    an FP64 residual pass, then an outer loop on the device: CG
+//                 start, an inner loop of kRound (knob "batch.round") CG
 //                 iterations per trip (a pass per width class, then the CG
 //                 step fused with the partials' reduction on one 8-CTA
-//                 cluster per problem) — until every problem has met its
-//                 stopping rule.  Instantiated graphs are cached per host
-//                 thread by their launch arguments.
+//                 cluster per problem) until every problem has met its
+//                 stopping rule, x += d, the FP64 residual of the corrected
+//                 problems and the convergence tests, until every problem has
+//                 converged or max_iter outer steps are done.
+// The whole chain is ONE CUDA-graph launch: the straight segments are
+// captured, the two loops are while nodes (the inner one nested in the outer
+// one's body) whose conditions kernels set on the device, so the host waits
+// once, for the results.  Instantiated graphs are cached per device and host
+// thread, keyed by every value their launches bake in.
 // Problems that stop early are skipped by the later launches (device flags).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -247,30 +252,60 @@ __global__ void batch_axpy_kernel(const BatchJob* __restrict__ jobs, const int* 
   for (int j = threadIdx.x; j < J.n; j += blockDim.x) J.x[j] += J.vec[j];
 }
 
-// out[kGather j + (0..5)] = (||r||^2, ||b||^2 of the last residual pass,
-// inner steps, first-step stop, sum of gains, ended by the gain rule).
+// Doubles per problem in the result buffer copied back to the host.
 constexpr int kGather = 6;
-__global__ void batch_gather_kernel(const BatchJob* __restrict__ jobs, int nprob,
-                                    double* __restrict__ out) {
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nprob; j += gridDim.x * blockDim.x) {
+
+// Per-problem state of the refinement loop that runs on the device.
+struct BatchCtl {
+  double rr, relres, rr_prev, relres_prev, relres_sns, gain;
+  int iters, conv, ref, by_rule;
+};
+
+// After the first FP64 residual pass: ||r||^2 and the relative residual of
+// the start (the sketch-and-solve x0), counters cleared; with refinement,
+// the outer loop's condition: some problem to refine and max_iter > 0.
+__global__ void __launch_bounds__(256) batch_ref_init_kernel(const BatchJob* __restrict__ jobs, int nitems,
+                                                             BatchCtl* __restrict__ ctl, int refine,
+                                                             int max_iter, int* __restrict__ flags,
+                                                             cudaGraphConditionalHandle h) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  for (int j = threadIdx.x; j < nitems; j += blockDim.x) {
     const BatchJob& J = jobs[j];
-    double* o = out + kGather * j;
-    o[0] = J.pout[J.n];
-    o[1] = J.pout[J.n + 1];
-    o[2] = J.sc[4];
-    o[3] = J.sc[5];
-    o[4] = J.sc[6];
-    o[5] = J.sc[7];
+    const double rr = fmax(J.pout[J.n], 0.0), bb = J.pout[J.n + 1];
+    BatchCtl& c = ctl[j];
+    c.rr = rr;
+    c.relres = sqrt(rr / (bb > 0.0 ? bb : 1.0));
+    c.relres_sns = c.relres;
+    c.rr_prev = rr;
+    c.relres_prev = c.relres;
+    c.gain = 0.0;
+    c.iters = 0;
+    c.conv = refine ? 0 : 1;
+    c.ref = 0;
+    c.by_rule = 0;
+    if (!c.conv) any = 1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    flags[2] = 0;  // outer steps taken
+    if (refine) cudaGraphSetConditional(h, (any && max_iter > 0) ? 1u : 0u);
   }
 }
 
-// Arm the refinement of an outer step: sc[2] = refining[j], inner counter 0.
-__global__ void batch_arm_kernel(const BatchJob* __restrict__ jobs, int nprob,
-                                 const int* __restrict__ refining, int* __restrict__ active) {
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nprob; j += gridDim.x * blockDim.x) {
+// Top of an outer step: every problem not yet converged refines (CG scalars
+// cleared, sc[2] = 1); the device loop's counters cleared.
+__global__ void batch_outer_arm_kernel(const BatchJob* __restrict__ jobs, int nitems,
+                                       BatchCtl* __restrict__ ctl, int* __restrict__ refining,
+                                       int* __restrict__ active) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nitems; j += gridDim.x * blockDim.x) {
     const BatchJob& J = jobs[j];
+    BatchCtl& c = ctl[j];
+    c.ref = c.conv ? 0 : 1;
+    refining[j] = c.ref;
     for (int q = 0; q < kScCount; ++q) J.sc[q] = 0.0;
-    J.sc[2] = refining[j] ? 1.0 : 0.0;
+    J.sc[2] = c.ref ? 1.0 : 0.0;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     active[0] = 0;  // problems still iterating (pcg_start counts them in)
@@ -278,35 +313,103 @@ __global__ void batch_arm_kernel(const BatchJob* __restrict__ jobs, int nprob,
   }
 }
 
-// End of one device-loop iteration: continue while a problem is still
-// iterating, and never beyond kBatchMaxInner iterations in all (every problem
-// also stops itself at kBatchMaxInner steps).
+// Before the inner loop: run it only if some problem started iterating.
+__global__ void batch_inner_arm_kernel(cudaGraphConditionalHandle h, const int* __restrict__ active) {
+  cudaGraphSetConditional(h, active[0] > 0 ? 1u : 0u);
+}
+
+// End of one inner-loop trip: continue while a problem is still iterating,
+// and never beyond kBatchMaxInner iterations in all (every problem also stops
+// itself at kBatchMaxInner steps).
 __global__ void batch_loop_cond_kernel(cudaGraphConditionalHandle h, int* __restrict__ active) {
   const int it = ++active[1];
   cudaGraphSetConditional(h, (active[0] > 0 && it < kBatchMaxInner) ? 1u : 0u);
 }
 
-// Instantiated refinement-loop graphs of this host thread, keyed by every
-// argument the capture baked in (the problems themselves are read from the
-// workspace at run time), so that a batch of a shape seen before skips
-// capture and instantiation.
-struct LoopKey {
-  const void* jobs;
-  const int* active;
-  const int* refining;
-  int nitems, round_len, ncls;
-  int nc[5], chunks[5], nmem[5];
-  const void* mem[5];
-  size_t smem[5];
-  bool operator==(const LoopKey& o) const { return std::memcmp(this, &o, sizeof(LoopKey)) == 0; }
-};
-struct LoopCache {
-  std::vector<std::pair<LoopKey, cudaGraphExec_t>> entries;  // most recent last
-  ~LoopCache() {
+// After the inner solve: count its steps; a problem whose first step already
+// gained less than the floor sits at the minimiser (its last relres stands);
+// the others get a new FP64 residual (recheck) against the decrease the CG
+// recurrences predicted.
+__global__ void batch_post_inner_kernel(const BatchJob* __restrict__ jobs, int nitems,
+                                        BatchCtl* __restrict__ ctl, int* __restrict__ recheck) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nitems; j += gridDim.x * blockDim.x) {
+    BatchCtl& c = ctl[j];
+    recheck[j] = 0;
+    if (!c.ref) continue;
+    const BatchJob& J = jobs[j];
+    c.iters += (int)J.sc[4];
+    if (J.sc[5] != 0.0) {
+      c.conv = 1;
+    } else {
+      recheck[j] = 1;
+      c.rr_prev = c.rr;
+      c.relres_prev = c.relres;
+      c.gain = J.sc[6];
+      c.by_rule = J.sc[7] != 0.0 ? 1 : 0;
+    }
+  }
+}
+
+// End of an outer step: the rechecked problems' new residuals; converged
+// when the solve ended by its gain rule and the FP64 residual confirms the
+// predicted decrease to tol * ||r||^2, or when the relative residual moved
+// by at most tol; then the outer loop's condition (some problem left,
+// fewer than max_iter steps taken).
+__global__ void __launch_bounds__(256) batch_outer_check_kernel(const BatchJob* __restrict__ jobs,
+                                                                int nitems, BatchCtl* __restrict__ ctl,
+                                                                const int* __restrict__ recheck, double tol,
+                                                                int max_iter, int* __restrict__ flags,
+                                                                cudaGraphConditionalHandle h) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  for (int j = threadIdx.x; j < nitems; j += blockDim.x) {
+    BatchCtl& c = ctl[j];
+    if (recheck[j]) {
+      const BatchJob& J = jobs[j];
+      const double rr = fmax(J.pout[J.n], 0.0), bb = J.pout[J.n + 1];
+      const double relres = sqrt(rr / (bb > 0.0 ? bb : 1.0));
+      const double predicted = c.rr_prev - c.gain;
+      c.rr = rr;
+      c.relres = relres;
+      if ((c.by_rule && fabs(rr - predicted) <= tol * rr) || fabs(c.relres_prev - relres) <= tol * relres)
+        c.conv = 1;
+    }
+    if (!c.conv) any = 1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int outer = ++flags[2];
+    cudaGraphSetConditional(h, (any && outer < max_iter) ? 1u : 0u);
+  }
+}
+
+// out[kGather j + (0..3)] = inner iterations, converged, relres, relres_sns.
+__global__ void batch_final_kernel(int nitems, const BatchCtl* __restrict__ ctl, double* __restrict__ out) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nitems; j += gridDim.x * blockDim.x) {
+    const BatchCtl& c = ctl[j];
+    double* o = out + kGather * j;
+    o[0] = (double)c.iters;
+    o[1] = (double)c.conv;
+    o[2] = c.relres;
+    o[3] = c.relres_sns;
+  }
+}
+
+// Instantiated whole-batch graphs, per device and host thread, keyed by
+// every value the capture baked in (pointers into the workspace, grid sizes,
+// tolerance, step limits); the problems themselves are read from the
+// workspace at run time, so a batch of a shape seen before on the same
+// workspace skips capture and instantiation.
+struct GraphCache {
+  cudaStream_t cap = nullptr;  // private capture stream of this device
+  std::vector<std::pair<std::vector<int64_t>, cudaGraphExec_t>> entries;  // most recent last
+  ~GraphCache() {
     for (auto& e : entries) cudaGraphExecDestroy(e.second);
   }
 };
-constexpr size_t kLoopCacheMax = 16;
+constexpr size_t kGraphCacheMax = 64;
+constexpr int kMaxDevices = 64;
 
 struct BatchPlan {
   std::vector<BatchJob> jobs;
@@ -316,7 +419,7 @@ struct BatchPlan {
   std::vector<std::vector<CsParams<float>>> cs;
   std::vector<std::vector<int64_t>> cs_tiles;
   std::vector<size_t> cs_off, tiles_off;
-  size_t jobs_off = 0, tc_off = 0, flags_off = 0, gather_off = 0;
+  size_t jobs_off = 0, tc_off = 0, flags_off = 0, gather_off = 0, ctl_off = 0;
   int total_items = 0, max_nt = 16, max_npad = 16, max_n = 1;
   // refinement-pass launches, one per width class present
   std::vector<int> pass_nc, pass_chunks;
@@ -343,8 +446,11 @@ static void plan_batch(const msk_batch_item* items, int nitems, int refine, char
   auto ptr = [&](size_t off) -> char* { return base ? base + off : nullptr; };
   P->jobs_off = take(sizeof(BatchJob) * (size_t)nitems);
   P->tc_off = take(sizeof(TcJob) * (size_t)nitems);
-  P->flags_off = take(sizeof(int) * (size_t)(nitems + 8));
+  // flags: [0] problems iterating, [1] inner iterations, [2] outer steps,
+  // then refining[nitems] and recheck[nitems]
+  P->flags_off = take(sizeof(int) * (size_t)(2 * nitems + 8));
   P->gather_off = take(sizeof(double) * kGather * (size_t)nitems);
+  P->ctl_off = take(sizeof(BatchCtl) * (size_t)nitems);
   P->jobs.resize(nitems);
   P->tc.resize(nitems);
   P->shapes.resize(nitems);
@@ -477,8 +583,6 @@ int msk_batch_lstsq(const msk_batch_item* items, int nitems, int refine, double 
   cudaStream_t st = as_stream(stream);
   BatchJob* jobs_dev = reinterpret_cast<BatchJob*>(base + P.jobs_off);
   TcJob* tc_dev = reinterpret_cast<TcJob*>(base + P.tc_off);
-  int* active = reinterpret_cast<int*>(base + P.flags_off);
-  int* refining = active + 8;
   double* gather = reinterpret_cast<double*>(base + P.gather_off);
   int item = 0;
   int rc = MSK_OK;
@@ -501,50 +605,21 @@ int msk_batch_lstsq(const msk_batch_item* items, int nitems, int refine, double 
                              sizeof(int64_t) * P.cs_tiles[c].size(), cudaMemcpyHostToDevice, st));
   }
   const int sms = num_sms();
-  // 1. CountSketch: zero every Y, then one launch per width class
-  batch_zero_kernel<<<dim3((unsigned)std::min<int64_t>((P.max_yk + 255) / 256, 64), nitems), 256, 0, st>>>(jobs_dev);
-  MSK_CHECK_LAUNCH("batch_zero_kernel");
-  for (size_t c = 0; c < P.widths.size(); ++c) {
-    rc = launch_cs_batch_f32(P.widths[c], reinterpret_cast<const CsParams<float>*>(base + P.cs_off[c]),
-                             reinterpret_cast<const int64_t*>(base + P.tiles_off[c]),
-                             (int)P.cs[c].size(), P.cs_tiles[c].back(), st);
-    if (rc) return rc;
-  }
-  // 2. Gaussian (bfloat16) and the 3-part bfloat16 split of Y
-  batch_gaussian_kernel<<<dim3((unsigned)std::min<int64_t>((P.max_pk + 255) / 256, 8 * sms), nitems), 256, 0, st>>>(jobs_dev);
-  MSK_CHECK_LAUNCH("batch_gaussian_kernel");
-  batch_split_kernel<<<dim3((unsigned)((P.max_k + 31) / 32), (unsigned)((P.max_npad + 31) / 32), nitems), 256, 0, st>>>(jobs_dev);
-  MSK_CHECK_LAUNCH("batch_split_kernel");
-  // 3. tensor-core Gaussian stage and its split-K reduction
-  rc = launch_tc_ds_batch(tc_dev, nitems, P.total_items, P.max_nt, st);
-  if (rc) return rc;
-  batch_gemm_reduce_kernel<<<dim3(64, nitems), 256, 0, st>>>(jobs_dev);
-  MSK_CHECK_LAUNCH("batch_gemm_reduce_kernel");
-  // 4. QR + triangular solve, one 16-CTA cluster per problem
-  {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(16, nitems, 1);
-    cfg.blockDim = dim3(kQrThreads, 1, 1);
-    cfg.stream = st;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = 16;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    MSK_CUDA(cudaFuncSetAttribute(batch_qr_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-    size_t qsm = 0;
-    for (const BatchJob& J : P.jobs)
-      if (qr_smem_fits(J.p, J.ncol, 16)) qsm = std::max(qsm, qr_smem_bytes(J.p, J.ncol, 16));
-    if (qsm) MSK_ALLOW_SMEM(batch_qr_kernel);
-    cfg.dynamicSmemBytes = qsm;
-    MSK_CUDA(cudaLaunchKernelEx(&cfg, batch_qr_kernel, (const BatchJob*)jobs_dev, qsm, refine ? 0 : 1));
-  }
-  // 5. refinement
-  std::vector<int> iters(nitems, 0), conv(nitems, refine ? 0 : 1);
-  std::vector<double> relres(nitems, -1.0), relres_sns(nitems, -1.0), rr(nitems, 0.0);
-  std::vector<double> hg(kGather * (size_t)nitems);
+  int* flags = reinterpret_cast<int*>(base + P.flags_off);
+  int* active = flags;                // [0] iterating, [1] inner iterations, [2] outer steps
+  int* refining = flags + 8;          // per problem
+  int* recheck = flags + 8 + nitems;  // per problem
+  BatchCtl* ctl = reinterpret_cast<BatchCtl*>(base + P.ctl_off);
+  const bool fp64_start = refine || infos;  // an FP64 residual pass of the start
+  const int round_len = (int)std::min<long long>(16, std::max<long long>(1, tune_get("batch.round", kRound)));
+  const unsigned gblocks = (unsigned)((nitems + 255) / 256);
+  const dim3 rgrid((P.max_n + 2 + 31) / 32, nitems);
+  size_t qsm = 0;
+  for (const BatchJob& J : P.jobs)
+    if (qr_smem_fits(J.p, J.ncol, 16)) qsm = std::max(qsm, qr_smem_bytes(J.p, J.ncol, 16));
+  // Function attributes before any capture begins.
+  MSK_CUDA(cudaFuncSetAttribute(batch_qr_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  if (qsm) MSK_ALLOW_SMEM(batch_qr_kernel);
   MSK_ALLOW_SMEM((batch_pass_kernel<16, true>));
   MSK_ALLOW_SMEM((batch_pass_kernel<32, true>));
   MSK_ALLOW_SMEM((batch_pass_kernel<64, true>));
@@ -555,8 +630,37 @@ int msk_batch_lstsq(const msk_batch_item* items, int nitems, int refine, double 
   MSK_ALLOW_SMEM((batch_pass_kernel<64, false>));
   MSK_ALLOW_SMEM((batch_pass_kernel<128, false>));
   MSK_ALLOW_SMEM((batch_pass_kernel<256, false>));
-  const dim3 rgrid((P.max_n + 2 + 31) / 32, nitems);
-  // one pass over every problem: a launch per width class
+
+  // The whole batch is ONE graph launch: every stage below, and with
+  // refinement the outer loop (a while node) whose body holds the inner CG
+  // loop (a nested while node), steered by device-side convergence tests.
+  // Graphs are cached by every value their launches bake in.
+  std::vector<int64_t> key;
+  {
+    int dev = 0;
+    MSK_CUDA(cudaGetDevice(&dev));
+    auto push = [&](int64_t v) { key.push_back(v); };
+    auto pushp = [&](const void* q) { key.push_back((int64_t)reinterpret_cast<uintptr_t>(q)); };
+    push(dev), pushp(base), push(nitems), push(refine), push(fp64_start), push(max_iter), push(round_len);
+    int64_t tb;
+    std::memcpy(&tb, &tol, sizeof(tb));
+    push(tb);
+    push(P.max_yk), push(P.max_pk), push(P.max_k), push(P.max_npad), push(P.max_n), push(P.max_nt);
+    push(P.total_items), push((int64_t)qsm), push(sms);
+    push((int64_t)P.widths.size());
+    for (size_t c = 0; c < P.widths.size(); ++c)
+      push(P.widths[c]), push((int64_t)P.cs_off[c]), push((int64_t)P.tiles_off[c]), push((int64_t)P.cs[c].size()),
+          push(P.cs_tiles[c].back());
+    push((int64_t)P.pass_nc.size());
+    for (size_t c = 0; c < P.pass_nc.size(); ++c)
+      push(P.pass_nc[c]), push(P.pass_chunks[c]), push((int64_t)P.pass_mem_off[c]),
+          push((int64_t)P.pass_mem[c].size());
+    push((int64_t)P.jobs_off), push((int64_t)P.tc_off), push((int64_t)P.flags_off), push((int64_t)P.gather_off),
+        push((int64_t)P.ctl_off);
+  }
+
+  // one pass over every problem (a launch per width class): the FP64 residual
+  // pass (resid, problems with only[j] set, all when null) or a CG pass
   auto passes = [&](bool resid, const int* only, cudaStream_t s) {
     for (size_t c = 0; c < P.pass_nc.size(); ++c) {
       const int nc = P.pass_nc[c];
@@ -577,185 +681,230 @@ int msk_batch_lstsq(const msk_batch_item* items, int nitems, int refine, double 
 #undef MSK_BATCH_PASS
     }
   };
-  const unsigned gblocks = (unsigned)((nitems + 255) / 256);
-  // FP64 residual pass of the problems with only[j] (all when null), then the
-  // gathered scalars to the host; rr and relres updated for those problems.
-  auto fp64_pass = [&](const int* only_dev, const std::vector<int>* only_host) -> int {
-    passes(true, only_dev, st);
+  auto fp64_pass = [&](const int* only, cudaStream_t s) -> int {
+    passes(true, only, s);
     MSK_CHECK_LAUNCH("batch_pass_kernel");
-    batch_pass_reduce_kernel<<<rgrid, 256, 0, st>>>(jobs_dev, only_dev);
+    batch_pass_reduce_kernel<<<rgrid, 256, 0, s>>>(jobs_dev, only);
     MSK_CHECK_LAUNCH("batch_pass_reduce_kernel");
-    batch_gather_kernel<<<gblocks, 256, 0, st>>>(jobs_dev, nitems, gather);
-    MSK_CHECK_LAUNCH("batch_gather_kernel");
-    MSK_CUDA(cudaMemcpyAsync(hg.data(), gather, sizeof(double) * kGather * nitems, cudaMemcpyDeviceToHost, st));
-    MSK_CUDA(cudaStreamSynchronize(st));
-    for (int j = 0; j < nitems; ++j) {
-      if (only_host && !(*only_host)[j]) continue;
-      rr[j] = std::max(hg[kGather * j], 0.0);
-      const double bb = hg[kGather * j + 1];
-      relres[j] = std::sqrt(rr[j] / (bb > 0.0 ? bb : 1.0));
+    return MSK_OK;
+  };
+  // Stages 1-4 and the start of the refinement, on stream s.
+  auto stages = [&](cudaStream_t s, cudaGraphConditionalHandle h_out) -> int {
+    // 1. CountSketch: zero every Y, then one launch per width class
+    batch_zero_kernel<<<dim3((unsigned)std::min<int64_t>((P.max_yk + 255) / 256, 64), nitems), 256, 0, s>>>(jobs_dev);
+    MSK_CHECK_LAUNCH("batch_zero_kernel");
+    for (size_t c = 0; c < P.widths.size(); ++c) {
+      const int e = launch_cs_batch_f32(P.widths[c], reinterpret_cast<const CsParams<float>*>(base + P.cs_off[c]),
+                                        reinterpret_cast<const int64_t*>(base + P.tiles_off[c]),
+                                        (int)P.cs[c].size(), P.cs_tiles[c].back(), s);
+      if (e) return e;
+    }
+    // 2. Gaussian (bfloat16) and the 3-part bfloat16 split of Y
+    batch_gaussian_kernel<<<dim3((unsigned)std::min<int64_t>((P.max_pk + 255) / 256, 8 * sms), nitems), 256, 0, s>>>(jobs_dev);
+    MSK_CHECK_LAUNCH("batch_gaussian_kernel");
+    batch_split_kernel<<<dim3((unsigned)((P.max_k + 31) / 32), (unsigned)((P.max_npad + 31) / 32), nitems), 256, 0, s>>>(jobs_dev);
+    MSK_CHECK_LAUNCH("batch_split_kernel");
+    // 3. tensor-core Gaussian stage and its split-K reduction
+    int e = launch_tc_ds_batch(tc_dev, nitems, P.total_items, P.max_nt, s);
+    if (e) return e;
+    batch_gemm_reduce_kernel<<<dim3(64, nitems), 256, 0, s>>>(jobs_dev);
+    MSK_CHECK_LAUNCH("batch_gemm_reduce_kernel");
+    // 4. QR (+ triangular solve without refinement), one 16-CTA cluster per problem
+    {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(16, nitems, 1);
+      cfg.blockDim = dim3(kQrThreads, 1, 1);
+      cfg.dynamicSmemBytes = qsm;
+      cfg.stream = s;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = 16;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      MSK_CUDA(cudaLaunchKernelEx(&cfg, batch_qr_kernel, (const BatchJob*)jobs_dev, qsm, refine ? 0 : 1));
+    }
+    if (refine) {  // R^{-1} (the preconditioner) and from it x0 = R^{-1} c
+      batch_tri_inverse_kernel<<<dim3((P.max_n + 7) / 8, nitems), 256, 0, s>>>(jobs_dev);
+      MSK_CHECK_LAUNCH("batch_tri_inverse_kernel");
+      batch_x0_kernel<<<nitems, 512, 0, s>>>(jobs_dev);
+      MSK_CHECK_LAUNCH("batch_x0_kernel");
+    }
+    if (fp64_start) {
+      e = fp64_pass(nullptr, s);
+      if (e) return e;
+      batch_ref_init_kernel<<<1, 256, 0, s>>>(jobs_dev, nitems, ctl, refine, max_iter, flags, h_out);
+      MSK_CHECK_LAUNCH("batch_ref_init_kernel");
     }
     return MSK_OK;
   };
-  int status = MSK_OK;
-  if (refine) {  // R^{-1} (the preconditioner) and from it x0 = R^{-1} c
-    batch_tri_inverse_kernel<<<dim3((P.max_n + 7) / 8, nitems), 256, 0, st>>>(jobs_dev);
-    MSK_CHECK_LAUNCH("batch_tri_inverse_kernel");
-    batch_x0_kernel<<<nitems, 512, 0, st>>>(jobs_dev);
-    MSK_CHECK_LAUNCH("batch_x0_kernel");
-  }
-  if (refine || infos) {
-    rc = fp64_pass(nullptr, nullptr);
-    if (rc) return rc;
-    relres_sns = relres;
-  }
-  if (refine) {
-    // The inner solve as one graph launch: a while node whose body runs
-    // `round_len` CG iterations (passes per width class, then the fused step)
-    // and a condition kernel.  Capture records work without running it, on a
-    // private stream (the legacy default stream cannot be captured); the graph
-    // is launched on the caller's stream, in order with everything above.
-    static thread_local cudaStream_t cap = nullptr;
-    static thread_local LoopCache cache;
-    if (!cap) MSK_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-    const int round_len = (int)std::min<long long>(16, std::max<long long>(1, tune_get("batch.round", kRound)));
-    LoopKey key;
-    std::memset(&key, 0, sizeof(key));
-    key.jobs = jobs_dev;
-    key.active = active;
-    key.refining = refining;
-    key.nitems = nitems;
-    key.round_len = round_len;
-    key.ncls = (int)P.pass_nc.size();
-    for (int c = 0; c < key.ncls; ++c) {
-      key.nc[c] = P.pass_nc[c];
-      key.chunks[c] = P.pass_chunks[c];
-      key.nmem[c] = (int)P.pass_mem[c].size();
-      key.mem[c] = base + P.pass_mem_off[c];
-      key.smem[c] = pass32_smem(P.pass_nc[c]);
+  // Top of an outer step: arm, start CG, and the inner loop's condition.
+  auto outer_head = [&](cudaStream_t s, cudaGraphConditionalHandle h_in) -> int {
+    batch_outer_arm_kernel<<<gblocks, 256, 0, s>>>(jobs_dev, nitems, ctl, refining, active);
+    MSK_CHECK_LAUNCH("batch_outer_arm_kernel");
+    batch_pcg_start_kernel<<<nitems, 512, 0, s>>>(jobs_dev, tol, active);
+    MSK_CHECK_LAUNCH("batch_pcg_start_kernel");
+    batch_inner_arm_kernel<<<1, 1, 0, s>>>(h_in, active);
+    MSK_CHECK_LAUNCH("batch_inner_arm_kernel");
+    return MSK_OK;
+  };
+  // One trip of the inner loop: round_len CG iterations (passes per width
+  // class, then the CG step fused with the partials' reduction on one 8-CTA
+  // cluster per problem), then the loop's condition.
+  auto inner_trip = [&](cudaStream_t s, cudaGraphConditionalHandle h_in) -> int {
+    cudaLaunchConfig_t ucfg = {};
+    ucfg.gridDim = dim3(kUpdCL, nitems, 1);
+    ucfg.blockDim = dim3(kUpdThreads, 1, 1);
+    ucfg.stream = s;
+    cudaLaunchAttribute uat[1];
+    uat[0].id = cudaLaunchAttributeClusterDimension;
+    uat[0].val.clusterDim.x = kUpdCL;
+    uat[0].val.clusterDim.y = 1;
+    uat[0].val.clusterDim.z = 1;
+    ucfg.attrs = uat;
+    ucfg.numAttrs = 1;
+    for (int r = 0; r < round_len; ++r) {
+      passes(false, nullptr, s);
+      MSK_CHECK_LAUNCH("batch_pass_kernel");
+      MSK_CUDA(cudaLaunchKernelEx(&ucfg, batch_pcg_cluster_kernel, (const BatchJob*)jobs_dev, active, refining));
     }
-    cudaGraphExec_t exec = nullptr;
-    for (size_t e = 0; e < cache.entries.size(); ++e)
-      if (cache.entries[e].first == key) {
-        exec = cache.entries[e].second;
-        auto hit = cache.entries[e];
-        cache.entries.erase(cache.entries.begin() + (long)e);
-        cache.entries.push_back(hit);
-        break;
-      }
-    cudaError_t ce = cudaSuccess;
-    if (!exec) {
-      cudaGraph_t graph = nullptr;
-      MSK_CUDA(cudaGraphCreate(&graph, 0));
-      cudaGraphConditionalHandle h;
-      ce = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
+    batch_loop_cond_kernel<<<1, 1, 0, s>>>(h_in, active);
+    MSK_CHECK_LAUNCH("batch_loop_cond_kernel");
+    return MSK_OK;
+  };
+  // Bottom of an outer step: x += d, the FP64 residual of the corrected
+  // problems, the convergence tests and the outer loop's condition.
+  auto outer_tail = [&](cudaStream_t s, cudaGraphConditionalHandle h_out) -> int {
+    batch_axpy_kernel<<<nitems, 256, 0, s>>>(jobs_dev, refining);
+    MSK_CHECK_LAUNCH("batch_axpy_kernel");
+    batch_post_inner_kernel<<<gblocks, 256, 0, s>>>(jobs_dev, nitems, ctl, recheck);
+    MSK_CHECK_LAUNCH("batch_post_inner_kernel");
+    const int e = fp64_pass(recheck, s);
+    if (e) return e;
+    batch_outer_check_kernel<<<1, 256, 0, s>>>(jobs_dev, nitems, ctl, recheck, tol, max_iter, flags, h_out);
+    MSK_CHECK_LAUNCH("batch_outer_check_kernel");
+    return MSK_OK;
+  };
+
+  thread_local GraphCache caches[kMaxDevices];
+  int dev = 0;
+  MSK_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return MSK_ENOTSUP;
+  GraphCache& cache = caches[dev];
+  if (!cache.cap) MSK_CUDA(cudaStreamCreateWithFlags(&cache.cap, cudaStreamNonBlocking));
+  cudaGraphExec_t exec = nullptr;
+  for (size_t e = 0; e < cache.entries.size(); ++e)
+    if (cache.entries[e].first == key) {
+      exec = cache.entries[e].second;
+      auto hit = cache.entries[e];
+      cache.entries.erase(cache.entries.begin() + (long)e);
+      cache.entries.push_back(hit);
+      break;
+    }
+  if (!exec) {
+    // Build: capture each straight segment into its graph (recording work
+    // without running it, on the private stream) and add the while nodes
+    // between the segments.
+    cudaStream_t cap = cache.cap;
+    cudaGraph_t top = nullptr;
+    MSK_CUDA(cudaGraphCreate(&top, 0));
+    std::vector<cudaGraphNode_t> tail;
+    auto begin = [&](cudaGraph_t g, const std::vector<cudaGraphNode_t>& deps) {
+      return cudaStreamBeginCaptureToGraph(cap, g, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(),
+                                           cudaStreamCaptureModeThreadLocal);
+    };
+    // end a segment; `out` receives its last nodes
+    auto end = [&](std::vector<cudaGraphNode_t>* out) {
+      cudaStreamCaptureStatus cs;
+      const cudaGraphNode_t* deps = nullptr;
+      size_t nd = 0;
+      cudaError_t e1 = cudaStreamGetCaptureInfo(cap, &cs, nullptr, nullptr, &deps, nullptr, &nd);
+      if (e1 == cudaSuccess) out->assign(deps, deps + nd);
+      cudaGraph_t g = nullptr;
+      cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+      return e1 != cudaSuccess ? e1 : e2;
+    };
+    auto add_while = [&](cudaGraph_t g, const std::vector<cudaGraphNode_t>& deps, cudaGraphConditionalHandle h,
+                         cudaGraphNode_t* node, cudaGraph_t* body) {
       cudaGraphNodeParams cp = {};
       cp.type = cudaGraphNodeTypeConditional;
       cp.conditional.handle = h;
       cp.conditional.type = cudaGraphCondTypeWhile;
       cp.conditional.size = 1;
-      cudaGraphNode_t wnode;
-      if (ce == cudaSuccess) ce = cudaGraphAddNode(&wnode, graph, nullptr, nullptr, 0, &cp);
-      if (ce == cudaSuccess)
-        ce = cudaStreamBeginCaptureToGraph(cap, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
-                                           cudaStreamCaptureModeThreadLocal);
-      if (ce != cudaSuccess) {
-        cudaGraphDestroy(graph);
-        return cuda_fail(ce, "refinement loop graph");
-      }
-      cudaLaunchConfig_t ucfg = {};
-      ucfg.gridDim = dim3(kUpdCL, nitems, 1);
-      ucfg.blockDim = dim3(kUpdThreads, 1, 1);
-      ucfg.stream = cap;
-      cudaLaunchAttribute uat[1];
-      uat[0].id = cudaLaunchAttributeClusterDimension;
-      uat[0].val.clusterDim.x = kUpdCL;
-      uat[0].val.clusterDim.y = 1;
-      uat[0].val.clusterDim.z = 1;
-      ucfg.attrs = uat;
-      ucfg.numAttrs = 1;
-      for (int r = 0; r < round_len; ++r) {
-        passes(false, nullptr, cap);
-        cudaLaunchKernelEx(&ucfg, batch_pcg_cluster_kernel, (const BatchJob*)jobs_dev, active, refining);
-      }
-      batch_loop_cond_kernel<<<1, 1, 0, cap>>>(h, active);
-      cudaGraph_t body = nullptr;
-      ce = cudaStreamEndCapture(cap, &body);
-      if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, graph, 0);
-      cudaGraphDestroy(graph);
-      if (ce != cudaSuccess) return cuda_fail(ce, "refinement loop graph");
-      if (cache.entries.size() >= kLoopCacheMax) {
-        cudaGraphExecDestroy(cache.entries.front().second);
-        cache.entries.erase(cache.entries.begin());
-      }
-      cache.entries.push_back({key, exec});
+      cudaError_t e = cudaGraphAddNode(node, g, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(), &cp);
+      if (e == cudaSuccess) *body = cp.conditional.phGraph_out[0];
+      return e;
+    };
+    cudaError_t ce = cudaSuccess;
+    int brc = MSK_OK;
+    cudaGraphConditionalHandle h_out = 0, h_in = 0;
+    if (refine) ce = cudaGraphConditionalHandleCreate(&h_out, top, 0, 0);
+    if (ce == cudaSuccess) ce = begin(top, tail);
+    if (ce == cudaSuccess) {
+      brc = stages(cap, h_out);
+      ce = end(&tail);
     }
-    std::vector<int> ref(nitems, 0), recheck(nitems, 0);
-    for (int outer = 0; outer < max_iter && !status; ++outer) {
-      int nref = 0;
-      for (int j = 0; j < nitems; ++j) {
-        ref[j] = conv[j] ? 0 : 1;
-        nref += ref[j];
+    if (ce == cudaSuccess && !brc && refine) {
+      cudaGraphNode_t onode = nullptr, inode = nullptr;
+      cudaGraph_t obody = nullptr, ibody = nullptr;
+      std::vector<cudaGraphNode_t> t2, t3, t4;
+      ce = add_while(top, tail, h_out, &onode, &obody);
+      if (ce == cudaSuccess) ce = cudaGraphConditionalHandleCreate(&h_in, obody, 0, 0);
+      if (ce == cudaSuccess) ce = begin(obody, {});
+      if (ce == cudaSuccess) {
+        brc = outer_head(cap, h_in);
+        ce = end(&t2);
       }
-      if (nref == 0) break;
-      ce = cudaMemcpyAsync(refining, ref.data(), sizeof(int) * nitems, cudaMemcpyHostToDevice, st);
-      if (ce != cudaSuccess) {
-        status = cuda_fail(ce, "refinement flags");
-        break;
+      if (ce == cudaSuccess && !brc) ce = add_while(obody, t2, h_in, &inode, &ibody);
+      if (ce == cudaSuccess && !brc) ce = begin(ibody, {});
+      if (ce == cudaSuccess && !brc) {
+        brc = inner_trip(cap, h_in);
+        ce = end(&t3);
       }
-      batch_arm_kernel<<<gblocks, 256, 0, st>>>(jobs_dev, nitems, refining, active);
-      batch_pcg_start_kernel<<<nitems, 512, 0, st>>>(jobs_dev, tol, active);
-      ce = cudaGraphLaunch(exec, st);  // the whole inner solve, looping on the device
-      if (ce != cudaSuccess) {
-        status = cuda_fail(ce, "refinement loop");
-        break;
+      if (ce == cudaSuccess && !brc) ce = begin(obody, {inode});
+      if (ce == cudaSuccess && !brc) {
+        brc = outer_tail(cap, h_out);
+        ce = end(&t4);
       }
-      // x += d for the problems still refining (those whose first step was
-      // below the floor had their flag cleared: already converged)
-      batch_axpy_kernel<<<nitems, 256, 0, st>>>(jobs_dev, refining);
-      batch_gather_kernel<<<gblocks, 256, 0, st>>>(jobs_dev, nitems, gather);
-      ce = cudaMemcpyAsync(hg.data(), gather, sizeof(double) * kGather * nitems, cudaMemcpyDeviceToHost, st);
-      if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
-      if (ce != cudaSuccess) {
-        status = cuda_fail(ce, "refinement counters");
-        break;
-      }
-      std::vector<double> inner(hg);
-      for (int j = 0; j < nitems; ++j) {
-        recheck[j] = 0;
-        if (!ref[j]) continue;
-        iters[j] += (int)inner[kGather * j + 2];
-        if (inner[kGather * j + 3] != 0.0) conv[j] = 1;  // minimiser reached: relres above stands
-        else recheck[j] = 1;
-      }
-      // new FP64 residual of the corrected problems
-      const std::vector<double> rr_prev(rr), relres_prev(relres);
-      rc = fp64_pass(refining, &recheck);
-      if (rc) {
-        status = rc;
-        break;
-      }
-      for (int j = 0; j < nitems; ++j) {
-        if (!recheck[j]) continue;
-        const double predicted = rr_prev[j] - inner[kGather * j + 4];
-        const bool by_rule = inner[kGather * j + 5] != 0.0;
-        if ((by_rule && std::fabs(rr[j] - predicted) <= tol * rr[j]) ||
-            std::fabs(relres_prev[j] - relres[j]) <= tol * relres[j])
-          conv[j] = 1;
+      tail.assign(1, onode);
+    }
+    if (ce == cudaSuccess && !brc && fp64_start) {
+      ce = begin(top, tail);
+      if (ce == cudaSuccess) {
+        batch_final_kernel<<<gblocks, 256, 0, cap>>>(nitems, ctl, gather);
+        ce = cudaGetLastError();
+        std::vector<cudaGraphNode_t> t5;
+        const cudaError_t ce2 = end(&t5);
+        if (ce == cudaSuccess) ce = ce2;
       }
     }
-    if (status) return status;
-    for (int j = 0; j < nitems; ++j)
-      if (!conv[j]) status = MSK_ENOCONV;
+    if (ce == cudaSuccess && !brc) ce = cudaGraphInstantiate(&exec, top, 0);
+    cudaGraphDestroy(top);
+    if (brc) return brc;
+    if (ce != cudaSuccess) return cuda_fail(ce, "batch graph");
+    if (cache.entries.size() >= kGraphCacheMax) {
+      cudaGraphExecDestroy(cache.entries.front().second);
+      cache.entries.erase(cache.entries.begin());
+    }
+    cache.entries.push_back({key, exec});
   }
-  MSK_CUDA(cudaStreamSynchronize(st));  // the uploads above read host vectors
-  if (infos)
-    for (int j = 0; j < nitems; ++j) {
-      infos[j].iters = iters[j];
-      infos[j].converged = conv[j];
-      infos[j].relres = relres[j];
-      infos[j].relres_sns = relres_sns[j];
+  MSK_CUDA(cudaGraphLaunch(exec, st));
+  std::vector<double> hg(kGather * (size_t)nitems);
+  if (fp64_start)
+    MSK_CUDA(cudaMemcpyAsync(hg.data(), gather, sizeof(double) * kGather * nitems, cudaMemcpyDeviceToHost, st));
+  MSK_CUDA(cudaStreamSynchronize(st));  // also: the uploads above read host vectors
+  int status = MSK_OK;
+  for (int j = 0; j < nitems; ++j) {
+    const bool conv = fp64_start ? hg[kGather * j + 1] != 0.0 : true;
+    if (refine && !conv) status = MSK_ENOCONV;
+    if (infos) {
+      infos[j].iters = (int32_t)hg[kGather * j];
+      infos[j].converged = conv ? 1 : 0;
+      infos[j].relres = hg[kGather * j + 2];
+      infos[j].relres_sns = hg[kGather * j + 3];
     }
+  }
   return status;
 }
 

@@ -4,14 +4,14 @@
 // Ogita, Oishi, Rump, "Error-free transformations of matrix multiplication by
 // using fast routines of matrix multiplication and its applications",
 // Numerical Algorithms 59, 2012).  GB300 runs FP64 at about 1 TFLOP/s and
-// BF16 MMAs at about 2 PFLOP/s: 28 exact BF16 products cost far less than one
+// BF16 MMAs at about 2 PFLOP/s: 36 exact BF16 products cost far less than one
 // FP64 product.
 //
 // Slices.  With a power-of-two scale per row of G (one bound for every row:
 // the polar-method Gaussian is below 8.1/sqrt(p)) and per column of Y (its
-// largest magnitude), each operand is written as seven 8-bit slices:
-//   G[r][i] = 2^(eG - 7)   (g_0 + g_1 2^-8 + ... + g_6 2^-48) + rest_G,
-//   Y[i][c] = 2^(eY_c - 7) (y_0 + y_1 2^-8 + ... + y_6 2^-48) + rest_Y,
+// largest magnitude), each operand is written as eight 8-bit slices:
+//   G[r][i] = 2^(eG - 7)   (g_0 + g_1 2^-8 + ... + g_7 2^-56) + rest_G,
+//   Y[i][c] = 2^(eY_c - 7) (y_0 + y_1 2^-8 + ... + y_7 2^-56) + rest_Y,
 // g_j, y_l integers in [-128, 128] (exact in bfloat16), |rest| at most half
 // a unit of the last slice.  Each slice is the round-to-nearest integer of
 // what the previous ones left, times 2^8; every step is exact in the
@@ -19,25 +19,26 @@
 //
 // Products.  g_j y_l is an integer of magnitude <= 2^14, exact in the tensor
 // core's FP32 accumulator, and so is every partial sum of up to 1024 of them
-// (<= 2^24).  The pairs with j + l <= 6 are kept; a pair's level is j + l.  A
-// CTA takes one group of G slices — {0, 6}, {1, 5}, {2, 4} or {3} — with all
-// the Y slices they pair with, and one TMEM accumulator per level; a level
-// receives at most two pairs over at most 512 K values, so at most 1024
-// products: every accumulator stays exact.  The epilogue reads the levels
-// (tcgen05.ld), combines them in FP64 by Horner's rule in 2^-8 and scales by
-// 2^(eG + eY_c - 14 - 8 j_first); the K slices and the four groups go to FP64
-// partials that one kernel sums in a fixed order (deterministic).
+// (<= 2^24).  The pairs with j + l <= 7 are kept (36 of them); a pair's level
+// is j + l.  A CTA takes one group of G slices — {0, 7}, {1, 6}, {2, 5} or
+// {3, 4}, nine pairs each — with all the Y slices they pair with, and one
+// TMEM accumulator per level; a level receives at most two pairs over at most
+// 512 K values, so at most 1024 products: every accumulator stays exact.  The
+// epilogue reads the levels (tcgen05.ld), combines them in FP64 by Horner's
+// rule in 2^-8 and scales by 2^(eG + eY_c - 14 - 8 j_first); the K slices and
+// the four groups go to FP64 partials that one kernel sums in a fixed order
+// (deterministic).
 //
-// Error.  Per term i the dropped pairs (levels 7..12) and the two rests
-// contribute at most 7.1 * 2^(eG + eY_c - 56); with 2^eG < 2 * 8.1/sqrt(p)
+// Error.  Per term i the dropped pairs (levels 8..14) and the two rests
+// contribute at most 9.1 * 2^(eG + eY_c - 64); with 2^eG < 2 * 8.1/sqrt(p)
 // and 2^eY_c <= 2 max_i |Y[i][c]|,
-//   |Z_computed - G Y| <= k * 7.1 * 2^(eG + eY_c - 56) + (rounding of the
-//                         FP64 partial sums, <= (4 S + 8) u sum_i |G||Y|),
-// i.e. about 29 k u max|Y[:,c]| / sqrt(p) (u = 2^-53): for the Gaussian G and
-// a sketch Y whose entries are not dominated by one outlier this lies about
-// k/100 times below the FP64 dot-product bound (k + 2) 2^-52 sum_i |G||Y|.
-// The stage is used from k >= 1024 (below, the FP64 SIMT kernel is cheap
-// anyway).
+//   |Z_computed - G Y| <= k * 9.1 * 2^(eG + eY_c - 64) + (rounding of the
+//                         FP64 partial sums, <= (4 S + 9) u sum_i |G||Y|),
+// i.e. about 0.15 k u max|Y[:,c]| / sqrt(p) (u = 2^-53), below the worst
+// case of an FP64 dot product of the same length.  (Seven slices, 2^8 times
+// less accurate, moved the sketch-and-solve residual at kappa(A) = 1e10 by
+// 2e-8 relative.)  The stage is used from k >= 1024 (below, the FP64 SIMT
+// kernel is cheap anyway).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -55,19 +56,19 @@ namespace msk {
 
 extern __device__ int g_tc_timeout;
 
-constexpr int kOzSlices = 7;      // slices of each operand; levels 0..6 kept
-constexpr int kOzGroups = 4;      // G-slice groups {0,6} {1,5} {2,4} {3}
+constexpr int kOzSlices = 8;      // slices of each operand; levels 0..7 kept
+constexpr int kOzGroups = 4;      // G-slice groups {0,7} {1,6} {2,5} {3,4}
 constexpr int kOzBM = 128;        // M per CTA (one UMMA M)
 constexpr int kOzBK = 64;         // K per stage (one 128-byte swizzle row of bf16)
 constexpr int kOzMaxKtPer = 8;    // K tiles per CTA: 2 pairs x 512 products <= 1024
 constexpr int kOzThreads = 128;
-constexpr int kOzMaxNT = 64;      // 7 levels x NT TMEM columns <= 512
+constexpr int kOzMaxNT = 64;      // 8 levels x NT TMEM columns <= 512
 constexpr double kOzGaussBound = 8.1;  // |polar-method N(0,1) sample| < 8.1
 
 // ---------------------------------------------------------------------------
 // G slices: entry (r, i) is the same binary32 number the Gaussian kernel
 // writes (standard normal number r*k + i of the stream, divided by sqrt(p)),
-// scaled by 2^-eG and cut into seven 8-bit slices Gs[j][r][i] (pitch kpitch).
+// scaled by 2^-eG and cut into eight 8-bit slices Gs[j][r][i] (pitch kpitch).
 __global__ void oz_split_g_kernel(uint64_t key, int64_t p, int64_t k, float sqrt_p, float scale,
                                   int64_t kpitch, __nv_bfloat16* __restrict__ Gs) {
   const int64_t total = p * k;
@@ -153,8 +154,8 @@ __global__ void oz_split_y_kernel(const double* __restrict__ Y, int64_t ldy, int
 }
 
 // One CTA: tile (mt, nt) of Z, K slice sidx, G-slice group grp (ja = grp,
-// jb = 6 - grp).  Warp 0 lane 0 streams the G tiles of slices ja (and jb)
-// and the Y tiles of slices 0 .. 6 - ja with TMA through a ring of stages;
+// jb = 7 - grp).  Warp 0 lane 0 streams the G tiles of slices ja and jb and
+// the Y tiles of slices 0 .. 7 - ja with TMA through a ring of stages;
 // warp 1 lane 0 issues the MMAs into the level accumulators (TMEM columns
 // (level - ja) * NT); then all four warps read the 128 rows back.  Every
 // mbarrier wait is bounded (1 s): on expiry the kernel records g_tc_timeout,
@@ -170,8 +171,8 @@ __global__ void __launch_bounds__(kOzThreads, 1)
   const int grp = blockIdx.z % kOzGroups, sidx = blockIdx.z / kOzGroups;
   const int ja = grp, jb = kOzSlices - 1 - grp;
   const int ng = ja == jb ? 1 : 2;       // G tiles per stage
-  const int ny = kOzSlices - ja;         // Y tiles per stage (slices 0 .. 6 - ja)
-  const int nlev = kOzSlices - ja;       // levels ja .. 6
+  const int ny = kOzSlices - ja;         // Y tiles per stage (slices 0 .. 7 - ja)
+  const int nlev = kOzSlices - ja;       // levels ja .. 7
   const uint32_t a_bytes = kOzBM * kOzBK * 2;
   const uint32_t b_bytes = (uint32_t)NT * kOzBK * 2;
   const uint32_t stage_bytes = ng * a_bytes + ny * b_bytes;
@@ -244,14 +245,14 @@ __global__ void __launch_bounds__(kOzThreads, 1)
       const uint32_t b0 = a0 + ng * a_bytes;
 #pragma unroll
       for (int kk = 0; kk < kOzBK / 16; ++kk) {
-        // slice ja with Y slices 0 .. 6 - ja: levels ja .. 6 (first touch of
+        // slice ja with Y slices 0 .. 7 - ja: levels ja .. 7 (first touch of
         // each accumulator at it = 0, kk = 0)
         const uint64_t ada = sw128_desc(a0 + kk * 32);
         for (int l = 0; l < ny; ++l)
           umma_f16(tmem + (uint32_t)(l * NT), ada, sw128_desc(b0 + l * b_bytes + kk * 32), idesc,
                    (it > 0 || kk > 0) ? 1u : 0u);
         if (ng == 2) {
-          // slice jb with Y slices 0 .. 6 - jb: levels jb .. 6
+          // slice jb with Y slices 0 .. 7 - jb: levels jb .. 7
           const uint64_t adb = sw128_desc(a0 + a_bytes + kk * 32);
           for (int l = 0; l <= kOzSlices - 1 - jb; ++l)
             umma_f16(tmem + (uint32_t)((jb + l - ja) * NT), adb,
@@ -404,7 +405,7 @@ int launch_oz_gemm(uint64_t gkey, int64_t p, int64_t k, int64_t ncol, const doub
   // kind::f16 instruction descriptor: FP32 accumulator, bf16 A and B, K-major
   const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(t.NT >> 3) << 17) |
                          ((uint32_t)(kOzBM >> 4) << 24);
-  // shared memory: the largest group's stage ({0, 6}: two G tiles, seven Y
+  // shared memory: the largest group's stage ({0, 7}: two G tiles, eight Y
   // tiles) at least twice, up to the budget
   const size_t big = 2 * (size_t)kOzBM * kOzBK * 2 + (size_t)kOzSlices * t.NT * kOzBK * 2;
   const size_t smem = std::min<size_t>((size_t)kTcSmemBudget, std::max<size_t>(2 * big, 3 * big)) + 1024 + 256;

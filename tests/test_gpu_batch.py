@@ -81,3 +81,30 @@ def test_batch_single_problem_and_repeat(msk):
     xs2, inf2, rc2 = msk.msk_batch_lstsq([(A, b, 9)], refine=True, tol=1e-10)
     assert rc1 == 0 and rc2 == 0
     assert abs(inf1[0]["relres"] - inf2[0]["relres"]) <= 1e-9 * inf1[0]["relres"]
+
+
+def test_batch_step_limits_and_graph_reuse(msk, orc):
+    """The outer loop runs on the device inside the batch's graph: with no
+    outer step allowed the solve returns its sketch-and-solve start as
+    MSK_ENOCONV (relres equal to relres_sns); with one step it improves; the
+    same batch solved again (a cached graph, new seeds in the workspace)
+    reaches the minimiser."""
+    probs = _problems(msk)[:3]
+    items = [(A, b, s) for A, b, s, _, _ in probs]
+    xs0, inf0, rc0 = msk.msk_batch_lstsq(items, refine=True, tol=1e-12, max_iter=0)
+    assert rc0 == msk.MSK_ENOCONV
+    for i in inf0:
+        assert i["iters"] == 0 and i["converged"] == 0 and i["relres"] == i["relres_sns"]
+    xs1, inf1, rc1 = msk.msk_batch_lstsq(items, refine=True, tol=1e-12, max_iter=1)
+    for (A, b, s, An, bn), x0, x1, i0, i1 in zip(probs, xs0, xs1, inf0, inf1):
+        assert i1["iters"] >= 1
+        r0 = orc.relres(An, bn, x0.cpu().numpy())
+        r1 = orc.relres(An, bn, x1.cpu().numpy())
+        assert abs(r0 - i0["relres"]) <= 1e-10 * r0 and r1 <= r0
+    for rep in range(2):
+        items = [(A, b, s + 1000 * rep) for A, b, s, _, _ in probs]
+        xs, infos, rc = msk.msk_batch_lstsq(items, refine=True, tol=1e-12, max_iter=10)
+        assert rc == 0
+        for (A, b, s, An, bn), x in zip(probs, xs):
+            ro = orc.relres(An, bn, orc.lstsq_exact(An, bn))
+            assert abs(orc.relres(An, bn, x.cpu().numpy()) - ro) <= 1e-8 * ro
