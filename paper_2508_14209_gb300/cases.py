@@ -7,6 +7,7 @@
     python -m paper_2508_14209_gb300.cases sns     --d 8388608 --n 128 --log10-sigma -6 [--kind count|gauss|srht]
     python -m paper_2508_14209_gb300.cases rcq     --d 8388608 --n 128 --log10-sigma -6
     python -m paper_2508_14209_gb300.cases srht    --d 8388608 --n 128
+    python -m paper_2508_14209_gb300.cases qr      --p 512 --ncol 129
 
 Each case draws its seeded synthetic input once on the GPU (the generators of
 the `inputs` module), runs the library call `--reps` times and prints one JSON
@@ -29,7 +30,7 @@ def main(argv=None):
     import paper_2508_14209_gb300 as msk
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["sketch", "gemm", "refined", "ne", "sns", "rcq", "srht", "host"])
+    ap.add_argument("case", choices=["sketch", "gemm", "refined", "ne", "sns", "rcq", "srht", "host", "qr"])
     ap.add_argument("--d", type=int, default=1 << 20)
     ap.add_argument("--n", type=int, default=64)
     ap.add_argument("--dtype", choices=["f64", "f32"], default="f64")
@@ -92,6 +93,16 @@ def main(argv=None):
         call = lambda: msk.srht_sketch(A, k, a.seed, Y=Y, ws=ws)  # noqa: E731
         m = a.d.bit_length() - 1
         out.update(d=a.d, n=a.n, k=k, adds_per_call=a.d * a.n * m)
+    elif a.case == "qr":
+        # Householder QR of a p x ncol FP64 matrix (the sketched [SA Sb]),
+        # restored from a saved copy before every call (copy included)
+        Z0 = inputs.normal_matrix(a.p, a.ncol, a.seed, dtype=torch.float64, device=dev)
+        W = msk.colmajor(a.p, a.ncol, torch.float64, dev)
+
+        def call():
+            W.copy_(Z0)
+            msk.msk_householder_qr(W)
+        out.update(p=a.p, ncol=a.ncol, flops_per_call=2 * a.p * a.ncol ** 2 - 2 * a.ncol ** 3 // 3)
     elif a.case == "gemm":
         prec = msk.GEMM_PRECS[a.prec]
         ydt = torch.float64 if prec == msk.GEMM_F64 else torch.float32

@@ -24,16 +24,16 @@
 // {3, 4}, nine pairs each — with all the Y slices they pair with, and one
 // TMEM accumulator per level; a level receives at most two pairs over at most
 // 512 K values, so at most 1024 products: every accumulator stays exact.  The
-// epilogue reads the levels (tcgen05.ld), combines them in FP64 by Horner's
-// rule in 2^-8 and scales by 2^(eG + eY_c - 14 - 8 j_first); the K slices and
-// the four groups go to FP64 partials that one kernel sums in a fixed order
-// (deterministic).
+// epilogue reads the levels (tcgen05.ld) and combines them exactly into two
+// 64-bit integers; one kernel sums the partials of all K slices and groups
+// exactly in 64-bit integers (so the result is the same in any order) and
+// rounds once to FP64.  Slicing, combining and summing use integer
+// arithmetic only: GB300's FP64 pipe would otherwise bound the stage.
 //
 // Error.  Per term i the dropped pairs (levels 8..14) and the two rests
 // contribute at most 9.1 * 2^(eG + eY_c - 64); with 2^eG < 2 * 8.1/sqrt(p)
 // and 2^eY_c <= 2 max_i |Y[i][c]|,
-//   |Z_computed - G Y| <= k * 9.1 * 2^(eG + eY_c - 64) + (rounding of the
-//                         FP64 partial sums, <= (4 S + 9) u sum_i |G||Y|),
+//   |Z_computed - G Y| <= k * 9.1 * 2^(eG + eY_c - 64) + 3 u |Z|,
 // i.e. about 0.15 k u max|Y[:,c]| / sqrt(p) (u = 2^-53), below the worst
 // case of an FP64 dot product of the same length.  (Seven slices, 2^8 times
 // less accurate, moved the sketch-and-solve residual at kappa(A) = 1e10 by
@@ -66,26 +66,64 @@ constexpr int kOzMaxNT = 64;      // 8 levels x NT TMEM columns <= 512
 constexpr double kOzGaussBound = 8.1;  // |polar-method N(0,1) sample| < 8.1
 
 // ---------------------------------------------------------------------------
+// Fixed-point forms, in integer arithmetic only (GB300's FP64 pipe is slow).
+// The integer nearest to m 2^sh (0 <= m < 2^53), ties upward, for shifts
+// that keep it below 2^63.
+__device__ __forceinline__ long long oz_shift_round(unsigned long long m, int sh) {
+  if (sh >= 0) return (long long)(m << sh);
+  const int s = -sh;
+  if (s >= 64) return 0;
+  return (long long)((m + (1ull << (s - 1))) >> s);
+}
+// X = round(y 2^(63 - e)) for a finite |y| < 2^e, so |X| < 2^63.
+__device__ __forceinline__ long long oz_fixed_f64(double y, int e) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(y);
+  const int E = (int)((bits >> 52) & 0x7FF);
+  const unsigned long long frac = bits & ((1ull << 52) - 1);
+  const unsigned long long m = E ? (frac | (1ull << 52)) : frac;
+  const long long X = oz_shift_round(m, (E ? E : 1) - 1075 + 63 - e);  // y = m 2^(E - 1075)
+  return (bits >> 63) ? -X : X;
+}
+__device__ __forceinline__ long long oz_fixed_f32(float g, int e) {
+  const unsigned bits = __float_as_uint(g);
+  const int E = (int)((bits >> 23) & 0xFF);
+  const unsigned long long m = E ? ((bits & 0x7FFFFFu) | 0x800000u) : (bits & 0x7FFFFFu);
+  const long long X = oz_shift_round(m, (E ? E : 1) - 150 + 63 - e);  // g = m 2^(E - 150)
+  return (bits >> 31) ? -X : X;
+}
+// The eight slices of X: X = sum_l s_l 2^(56 - 8 l), s_l the nearest integer
+// to what the previous slices left over 2^(56 - 8 l) (ties upward), in
+// [-128, 128]; the last one takes the remainder, in [-128, 127].
+__device__ __forceinline__ void oz_slices(long long X, float (&s)[kOzSlices]) {
+  unsigned long long r = (unsigned long long)X;
+#pragma unroll
+  for (int l = 0; l < kOzSlices - 1; ++l) {
+    const int sh = 56 - 8 * l;
+    const long long rs = (long long)r;
+    const long long q = (rs >> sh) + ((rs >> (sh - 1)) & 1);
+    s[l] = (float)q;
+    r -= (unsigned long long)q << sh;
+  }
+  s[kOzSlices - 1] = (float)(long long)r;
+}
+
 // G slices: entry (r, i) is the same binary32 number the Gaussian kernel
 // writes (standard normal number r*k + i of the stream, divided by sqrt(p)),
-// scaled by 2^-eG and cut into eight 8-bit slices Gs[j][r][i] (pitch kpitch).
-__global__ void oz_split_g_kernel(uint64_t key, int64_t p, int64_t k, float sqrt_p, float scale,
+// in fixed point at 2^(eG - 63) and cut into eight slices Gs[j][r][i]
+// (pitch kpitch).  Rows over gridDim.y, columns over gridDim.x.
+__global__ void oz_split_g_kernel(uint64_t key, int64_t p, int64_t k, float sqrt_p, int eG,
                                   int64_t kpitch, __nv_bfloat16* __restrict__ Gs) {
-  const int64_t total = p * k;
   const int64_t plane = p * kpitch;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = e / k, c = e - r * k;
-    const float g = __fdiv_rn(gauss_std(key, (uint64_t)e), sqrt_p);
-    float t = __fmul_rn(__fmul_rn(g, scale), 128.0f);  // |t| < 128, exact
-    __nv_bfloat16* out = Gs + r * kpitch + c;
+  for (int64_t r = blockIdx.y; r < p; r += gridDim.y)
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < k;
+         c += (int64_t)gridDim.x * blockDim.x) {
+      const float g = __fdiv_rn(gauss_std(key, (uint64_t)(r * k + c)), sqrt_p);
+      float sl[kOzSlices];
+      oz_slices(oz_fixed_f32(g, eG), sl);
+      __nv_bfloat16* out = Gs + r * kpitch + c;
 #pragma unroll
-    for (int j = 0; j < kOzSlices; ++j) {
-      const float s = rintf(t);
-      out[j * plane] = __float2bfloat16_rn(s);  // integer in [-128, 128]: exact
-      t = __fmul_rn(__fsub_rn(t, s), 256.0f);   // remainder in [-0.5, 0.5], exact
+      for (int j = 0; j < kOzSlices; ++j) out[j * plane] = __float2bfloat16_rn(sl[j]);  // exact
     }
-  }
 }
 
 // Largest |Y[i][c]| of every column, as the bit pattern of a non-negative
@@ -99,7 +137,8 @@ __global__ void oz_colmax_kernel(const double* __restrict__ Y, int64_t ldy, int6
   unsigned long long m = 0;
   if (c < ncol)
     for (int64_t i = (int64_t)blockIdx.y * 8 + ty; i < k; i += (int64_t)gridDim.y * 8) {
-      const unsigned long long b = (unsigned long long)__double_as_longlong(fabs(Y[i * ldy + c]));
+      const unsigned long long b =
+          (unsigned long long)__double_as_longlong(Y[i * ldy + c]) & 0x7FFFFFFFFFFFFFFFull;
       m = b > m ? b : m;
     }
   red[ty][tx] = m;
@@ -119,8 +158,9 @@ __device__ __forceinline__ int oz_exp_of(unsigned long long bits) {
 }
 
 // Y slices: Ys[l][c][i] (K-major, pitch kpitch, npad rows; rows >= ncol
-// zero) from the row-major FP64 Y, 32x32 tiles transposed in shared memory;
-// eY[c] the column exponents (0 for the padding columns).
+// zero) from the row-major FP64 Y, in fixed point at 2^(eY_c - 63); 32x32
+// tiles transposed in shared memory; eY[c] the column exponents (0 for the
+// padding columns).
 __global__ void oz_split_y_kernel(const double* __restrict__ Y, int64_t ldy, int64_t k, int ncol,
                                   int npad, int64_t kpitch, const unsigned long long* __restrict__ mx,
                                   int* __restrict__ eY, __nv_bfloat16* __restrict__ Ys) {
@@ -141,15 +181,12 @@ __global__ void oz_split_y_kernel(const double* __restrict__ Y, int64_t ldy, int
     const int n = n0 + r;
     const int64_t i = k0 + tx;
     if (n >= npad || i >= k) continue;
-    double t = 0.0;
-    if (n < ncol) t = scalbn(tile[tx][r], 7 - oz_exp_of(mx[n]));  // |t| < 128, exact
+    const long long X = n < ncol ? oz_fixed_f64(tile[tx][r], oz_exp_of(mx[n])) : 0;
+    float sl[kOzSlices];
+    oz_slices(X, sl);
     __nv_bfloat16* out = Ys + (int64_t)n * kpitch + i;
 #pragma unroll
-    for (int l = 0; l < kOzSlices; ++l) {
-      const double s = rint(t);
-      out[l * plane] = __float2bfloat16_rn((float)s);  // integer in [-128, 128]: exact
-      t = (t - s) * 256.0;                              // remainder in [-0.5, 0.5], exact
-    }
+    for (int l = 0; l < kOzSlices; ++l) out[l * plane] = __float2bfloat16_rn(sl[l]);  // exact
   }
 }
 
@@ -163,8 +200,8 @@ __global__ void oz_split_y_kernel(const double* __restrict__ Y, int64_t ldy, int
 // returns.
 __global__ void __launch_bounds__(kOzThreads, 1)
     oz_gemm_kernel(const __grid_constant__ CUtensorMap tmG, const __grid_constant__ CUtensorMap tmY,
-                   int p, int ncol, int NT, int KT, int kt_per, int eG, uint32_t idesc,
-                   const int* __restrict__ eY, double* __restrict__ part) {
+                   int p, int ncol, int NT, int KT, int kt_per, uint32_t idesc,
+                   longlong2* __restrict__ part) {
   extern __shared__ __align__(1024) unsigned char oz_smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(oz_smem_raw) + 1023) & ~uintptr_t(1023));
@@ -267,25 +304,34 @@ __global__ void __launch_bounds__(kOzThreads, 1)
   const bool done = mbar_wait(smem_u32(&bars[2 * stages]), 0, &g_tc_timeout);
   tc_fence_after();
   if (__all_sync(0xffffffffu, done && !*abort_flag && nk > 0)) {
+    // Level sums are exact integers below 2^24: combined exactly as
+    // H = sum_{s<4} V_s 2^(8(3-s)) and L = sum_{s>=4} V_s 2^(8(7-s)) (each
+    // below 2^49), so Z's entry is 2^(eG + eY - 70) (H 2^32 + L) summed over
+    // all CTAs — integer work only (GB300's FP64 pipe would make this epilogue
+    // the kernel's bottleneck).
     const int row = m0 + warp * 32 + lane;
-    double* out = part + (int64_t)blockIdx.z * p * ncol;
+    longlong2* out = part + (int64_t)blockIdx.z * p * ncol;
     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
     for (int c0 = 0; c0 < NT; c0 += 16) {
-      double h[16];
-      uint32_t v[16];
-      tmem_ld16(lane_base + (uint32_t)((nlev - 1) * NT + c0), v);
+      long long H[16], L[16];
 #pragma unroll
-      for (int q = 0; q < 16; ++q) h[q] = (double)__uint_as_float(v[q]);
-      for (int lev = nlev - 2; lev >= 0; --lev) {
+      for (int q = 0; q < 16; ++q) H[q] = L[q] = 0;
+      for (int lev = 0; lev < nlev; ++lev) {
+        const int s = ja + lev;  // this accumulator's level
+        uint32_t v[16];
         tmem_ld16(lane_base + (uint32_t)(lev * NT + c0), v);
 #pragma unroll
-        for (int q = 0; q < 16; ++q) h[q] = fma(h[q], 0x1p-8, (double)__uint_as_float(v[q]));
+        for (int q = 0; q < 16; ++q) {
+          const long long x = (long long)__float2int_rn(__uint_as_float(v[q]));  // exact
+          if (s < 4) H[q] += x * (1LL << (8 * (3 - s)));
+          else L[q] += x * (1LL << (8 * (7 - s)));
+        }
       }
       if (row < p) {
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
           const int col = n0 + c0 + q;
-          if (col < ncol) out[(int64_t)col * p + row] = scalbn(h[q], eG + eY[col] - 14 - 8 * ja);
+          if (col < ncol) out[(int64_t)col * p + row] = make_longlong2(H[q], L[q]);
         }
       }
     }
@@ -295,6 +341,37 @@ __global__ void __launch_bounds__(kOzThreads, 1)
   if (warp == 2)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols)
                  : "memory");
+}
+
+// Z[r + c ldz] = 2^(eG + eY_c - 70) (H 2^32 + L) with H, L the sums of the
+// S partials of entry e = c p + r.  Block 32 x 8: 32 consecutive entries, 8
+// lanes over the partials.  The partial sums are exact 64-bit integers (below
+// 2^49 S), so the result does not depend on the order of the sums; the one
+// rounding is the conversion to FP64 at the end.
+__global__ void oz_reduce_kernel(const longlong2* __restrict__ part, int S, int64_t p, int64_t ncol, int eG,
+                                 const int* __restrict__ eY, double* __restrict__ Z, int64_t ldz) {
+  __shared__ long long sh[8][32], sl[8][32];
+  const int64_t total = p * ncol;
+  const int64_t e = (int64_t)blockIdx.x * 32 + threadIdx.x;
+  long long H = 0, L = 0;
+  if (e < total)
+    for (int q = threadIdx.y; q < S; q += 8) {
+      const longlong2 v = part[(int64_t)q * total + e];
+      H += v.x;
+      L += v.y;
+    }
+  sh[threadIdx.y][threadIdx.x] = H;
+  sl[threadIdx.y][threadIdx.x] = L;
+  __syncthreads();
+  if (threadIdx.y == 0 && e < total) {
+#pragma unroll
+    for (int q = 1; q < 8; ++q) {
+      H += sh[q][threadIdx.x];
+      L += sl[q][threadIdx.x];
+    }
+    const int64_t c = e / p, r = e - c * p;
+    Z[r + c * ldz] = scalbn(fma((double)H, 0x1p32, (double)L), eG + eY[c] - 70);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -326,7 +403,7 @@ size_t oz_gemm_workspace(int64_t p, int64_t k, int64_t ncol) {
   Need nd;
   nd.add((size_t)kOzSlices * p * t.kpitch * 2);                // G slices
   nd.add((size_t)kOzSlices * t.npad * t.kpitch * 2);           // Y slices
-  nd.add((size_t)kOzGroups * t.S * p * ncol * sizeof(double));  // partials
+  nd.add((size_t)kOzGroups * t.S * p * ncol * sizeof(longlong2));  // partials
   nd.add((size_t)ncol * sizeof(unsigned long long));           // column maxima
   nd.add((size_t)t.npad * sizeof(int));                        // column exponents
   return nd.used;
@@ -348,7 +425,7 @@ int launch_oz_gemm(uint64_t gkey, int64_t p, int64_t k, int64_t ncol, const doub
   Carve cv(ws, ws_bytes);
   auto* Gs = static_cast<__nv_bfloat16*>(cv.take((size_t)kOzSlices * p * t.kpitch * 2));
   auto* Ys = static_cast<__nv_bfloat16*>(cv.take((size_t)kOzSlices * t.npad * t.kpitch * 2));
-  auto* part = static_cast<double*>(cv.take((size_t)kOzGroups * t.S * p * ncol * sizeof(double)));
+  auto* part = static_cast<longlong2*>(cv.take((size_t)kOzGroups * t.S * p * ncol * sizeof(longlong2)));
   auto* mx = static_cast<unsigned long long*>(cv.take((size_t)ncol * sizeof(unsigned long long)));
   auto* eY = static_cast<int*>(cv.take((size_t)t.npad * sizeof(int)));
   if (!Gs || !Ys || !part || !mx || !eY) return MSK_ENOMEM;
@@ -357,9 +434,8 @@ int launch_oz_gemm(uint64_t gkey, int64_t p, int64_t k, int64_t ncol, const doub
   const float sqrt_p = __builtin_sqrtf((float)p);
   const int eG = oz_g_exponent(sqrt_p);
   {
-    const int64_t total = p * k;
-    const unsigned grid = (unsigned)std::min<int64_t>((total + 255) / 256, (int64_t)sms * 32);
-    oz_split_g_kernel<<<grid, 256, 0, st>>>(gkey, p, k, sqrt_p, std::ldexp(1.0f, -eG), t.kpitch, Gs);
+    const dim3 grid((unsigned)std::min<int64_t>((k + 255) / 256, 64), (unsigned)std::min<int64_t>(p, 65535));
+    oz_split_g_kernel<<<grid, 256, 0, st>>>(gkey, p, k, sqrt_p, eG, t.kpitch, Gs);
     MSK_CHECK_LAUNCH("oz_split_g_kernel");
   }
   // column maxima of Y, then its slices
@@ -411,13 +487,13 @@ int launch_oz_gemm(uint64_t gkey, int64_t p, int64_t k, int64_t ncol, const doub
   const size_t smem = std::min<size_t>((size_t)kTcSmemBudget, std::max<size_t>(2 * big, 3 * big)) + 1024 + 256;
   MSK_ALLOW_SMEM(oz_gemm_kernel);
   dim3 grid((unsigned)t.Mt, (unsigned)t.Nt, (unsigned)(kOzGroups * t.S));
-  oz_gemm_kernel<<<grid, kOzThreads, smem, st>>>(tmG, tmY, (int)p, (int)ncol, t.NT, t.KT, t.kt_per, eG,
-                                                 idesc, eY, part);
+  oz_gemm_kernel<<<grid, kOzThreads, smem, st>>>(tmG, tmY, (int)p, (int)ncol, t.NT, t.KT, t.kt_per, idesc,
+                                                 part);
   MSK_CHECK_LAUNCH("oz_gemm_kernel");
   const int64_t total = p * ncol;
-  splitk_reduce_kernel<<<(unsigned)std::min<int64_t>((total + 255) / 256, (int64_t)sms * 8), 256, 0, st>>>(
-      part, kOzGroups * t.S, p, ncol, Z, ldz);
-  MSK_CHECK_LAUNCH("splitk_reduce_kernel");
+  oz_reduce_kernel<<<(unsigned)((total + 31) / 32), dim3(32, 8), 0, st>>>(part, kOzGroups * t.S, p, ncol, eG, eY,
+                                                                          Z, ldz);
+  MSK_CHECK_LAUNCH("oz_reduce_kernel");
   return MSK_OK;
 }
 

@@ -104,28 +104,43 @@ __device__ __forceinline__ void qr_cluster_body(double* __restrict__ W, int m, i
   }
 }
 
-// Shared-memory form of the cluster QR, for matrices whose owned columns fit
-// on chip (qr_smem_fits): CTA `rank` keeps columns rank, rank + CL, ... of W
-// in its shared memory for the whole factorisation.
-//   step j: the owner of column j forms the reflector v = x + sign(x0)||x|| e0,
-//     tau = 2 / v^T v from ||x||^2, which the warp that last updated column j
-//     accumulated on the way (no block reduction); it writes v into W's
-//     column j in global memory (that column is only a broadcast slot until
-//     the final write-back), publishes tau, and writes R_jj into row j of its
-//     own copy.
-//   one cluster barrier; every CTA reads v from L2 (an L1-bypassing copy is
-//     faster than a pull through distributed shared memory) and applies the
-//     reflector to its owned columns > j, one warp per column; the warp that
-//     updates column j + 1 also sums its new squares below row j.
-// (v0, tau) use two slots alternating by step: slot j & 1 is rewritten at step
-// j + 2, after every CTA has passed the barrier of step j + 1.  The factor
-// goes back to W at the end, zeros below the diagonal.
-// Dynamic shared memory: (ceil(c / CL) + 1) * m doubles + ceil(c / CL) norms.
-__host__ __device__ __forceinline__ size_t qr_smem_bytes(int m, int c, int CL) {
-  const size_t own = (size_t)((c + CL - 1) / CL);
-  return sizeof(double) * ((own + 1) * (size_t)m + own);
+// Shared-memory form of the cluster QR, blocked by panels of kQrPanel
+// columns, for matrices whose owned columns fit on chip (qr_smem_fits).
+// Panel P (columns P b .. P b + b - 1) belongs to CTA P mod CL, which keeps
+// its panels in shared memory for the whole factorisation.
+//   panel P: its owner factors the panel alone (b Householder steps: the
+//     reflector v = x + sign(x0)||x|| e0, tau = 2 / v^T v of each column from
+//     ||x||^2, which the warp that last updated the column accumulated on the
+//     way, then the panel's later columns updated one warp per column), writes
+//     the b reflectors into W's panel columns in global memory (those columns
+//     are broadcast slots until the final write-back) and publishes the taus;
+//   one cluster barrier per panel (not per column); every CTA reads the
+//     panel's reflectors from L2 and applies them, in order, to each of its
+//     columns after the panel, one warp per column; the warp that updates the
+//     first column of the next panel also sums its squares below the pivot.
+// Every column receives the same reflectors in the same order and the same
+// arithmetic as the unblocked algorithm, so R is the same.  The taus use two
+// slots alternating by panel: slot P & 1 is rewritten at panel P + 2, after
+// every CTA has passed the barrier of panel P + 1.  The factor goes back to W
+// at the end, zeros below the diagonal.
+constexpr int kQrPanel = 8;
+// Columns held by the CTA owning the most (panels cyclic over the cluster).
+__host__ __device__ __forceinline__ int qr_owned_cols(int c, int CL, int rank) {
+  const int npan = (c + kQrPanel - 1) / kQrPanel;
+  int n = 0;
+  for (int P = rank; P < npan; P += CL) n += min(kQrPanel, c - P * kQrPanel);
+  return n;
 }
-constexpr size_t kQrSmemMax = 160 * 1024;  // 1024 x 257 on a 16-CTA cluster: 148 KB
+// Dynamic shared memory: the owned columns of the busiest CTA (stored panel
+// after panel; only a CTA's last panel can be narrower than kQrPanel, so
+// panel q starts at local column q kQrPanel) and the current panel's
+// reflectors, m doubles per column, plus the owned columns' norms.
+__host__ __device__ __forceinline__ size_t qr_smem_bytes(int m, int c, int CL) {
+  int own = 0;
+  for (int r = 0; r < CL; ++r) own = max(own, qr_owned_cols(c, CL, r));
+  return sizeof(double) * ((size_t)(own + kQrPanel) * (size_t)m + (size_t)own);
+}
+constexpr size_t kQrSmemMax = 205 * 1024;  // 1024 x 257 on a 16-CTA cluster: 200 KB
 __host__ __device__ __forceinline__ bool qr_smem_fits(int m, int c, int CL) {
   return qr_smem_bytes(m, c, CL) <= kQrSmemMax;
 }
@@ -135,17 +150,25 @@ __device__ __forceinline__ void qr_cluster_smem_body(double* __restrict__ W, int
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   const int CL = (int)cluster.num_blocks();
-  const int own = (c + CL - 1) / CL;
-  const int nown = (c - rank + CL - 1) / CL;  // columns rank, rank + CL, ...
-  double* cols = sm;                           // own x m
-  double* vl = sm + (size_t)own * m;           // m: local copy of the step's v
-  double* cnorm = vl + m;                      // own: ||column below the pivot row||^2
-  __shared__ double vsc[2][2];
+  constexpr int b = kQrPanel;
+  const int npan = (c + b - 1) / b;
+  int own = 0;
+  for (int r = 0; r < CL; ++r) own = max(own, qr_owned_cols(c, CL, r));
+  const int myp = (npan - rank + CL - 1) / CL;  // panels rank, rank + CL, ...
+  double* cols = sm;                            // panel q, column t: cols[(q b + t) m + i]
+  double* vl = sm + (size_t)own * m;            // the current panel's reflectors, b x m
+  double* cnorm = vl + (size_t)b * m;           // per owned column: ||column below its pivot||^2
+  __shared__ double taus[2][kQrPanel];
+  __shared__ double rdiag[kQrPanel];
   __shared__ double red[32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  for (int lj = 0; lj < nown; ++lj) {
-    const double* src = W + (int64_t)(rank + lj * CL) * ldw;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) cols[(size_t)lj * m + i] = src[i];
+  auto width = [&](int P) { return min(b, c - P * b); };
+  for (int q = 0; q < myp; ++q) {
+    const int P = rank + q * CL;
+    for (int t = 0; t < width(P); ++t) {
+      const double* src = W + (int64_t)(P * b + t) * ldw;
+      for (int i = threadIdx.x; i < m; i += blockDim.x) cols[(size_t)(q * b + t) * m + i] = src[i];
+    }
   }
   __syncthreads();
   if (rank == 0) {  // ||column 0||^2
@@ -154,58 +177,105 @@ __device__ __forceinline__ void qr_cluster_smem_body(double* __restrict__ W, int
     s = block_sum(s, red);
     if (threadIdx.x == 0) cnorm[0] = s;
   }
-  const int steps = min(m, c);
-  for (int j = 0; j < steps; ++j) {
-    const int owner = j % CL, slot = j & 1;
-    __syncthreads();  // column j and its norm are final; vl is free
+  for (int P = 0; P < npan; ++P) {
+    const int owner = P % CL, slot = P & 1, c0 = P * b, wP = width(P);
+    __syncthreads();  // the panel's columns and first norm are final; vl is free
     if (rank == owner) {
-      double* x = cols + (size_t)(j / CL) * m;
-      double* gcol = W + (int64_t)j * ldw;  // W's column j: a broadcast slot until write-back
-      if (threadIdx.x == 0) {
-        const double norm2 = cnorm[j / CL];
-        const double x0 = x[j];
-        const double alpha = sqrt(norm2);
-        const double sgn = x0 >= 0.0 ? 1.0 : -1.0;
-        const double v0 = x0 + sgn * alpha;
-        const double vtv = norm2 - x0 * x0 + v0 * v0;
-        gcol[j] = v0;
-        vsc[slot][1] = vtv > 0.0 ? 2.0 / vtv : 0.0;
-        x[j] = -sgn * alpha;
+      double* pc = cols + (size_t)(P / CL) * b * m;
+      for (int t = 0; t < wP; ++t) {
+        const int j = c0 + t;
+        double* x = pc + (size_t)t * m;
+        if (threadIdx.x == 0) {
+          const double norm2 = cnorm[(P / CL) * b + t];
+          const double x0 = x[j];
+          const double alpha = sqrt(norm2);
+          const double sgn = x0 >= 0.0 ? 1.0 : -1.0;
+          const double v0 = x0 + sgn * alpha;
+          const double vtv = norm2 - x0 * x0 + v0 * v0;
+          taus[slot][t] = vtv > 0.0 ? 2.0 / vtv : 0.0;
+          rdiag[t] = -sgn * alpha;
+          x[j] = v0;  // column j holds v from row j down until the panel is published
+        }
+        __syncthreads();
+        const double tau = taus[slot][t];
+        for (int u = t + 1 + warp; u < wP; u += nwarps) {
+          double* w = pc + (size_t)u * m;
+          double s = 0.0;
+          for (int i = j + lane; i < m; i += 32) s += x[i] * w[i];
+          s = warp_sum(s) * tau;
+          if (u == t + 1) {  // the panel's next pivot column: update and sum squares
+            double s2 = 0.0;
+            for (int i = j + lane; i < m; i += 32) {
+              const double wi = w[i] - s * x[i];
+              w[i] = wi;
+              if (i > j) s2 += wi * wi;
+            }
+            s2 = warp_sum(s2);
+            if (lane == 0) cnorm[(P / CL) * b + u] = s2;
+          } else {
+            for (int i = j + lane; i < m; i += 32) w[i] -= s * x[i];
+          }
+        }
+        __syncthreads();
       }
-      for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) gcol[i] = x[i];
+      // publish the reflectors (zeros above each pivot), then R's diagonal
+      for (int t = 0; t < wP; ++t) {
+        double* g = W + (int64_t)(c0 + t) * ldw;
+        const double* x = pc + (size_t)t * m;
+        for (int i = threadIdx.x; i < m; i += blockDim.x) g[i] = i < c0 + t ? 0.0 : x[i];
+      }
+      __syncthreads();
+      if (threadIdx.x < wP) pc[(size_t)threadIdx.x * m + c0 + threadIdx.x] = rdiag[threadIdx.x];
       __threadfence();
     }
     cluster.sync();
-    const double* gv = W + (int64_t)j * ldw;
-    for (int i = j + threadIdx.x; i < m; i += blockDim.x) vl[i] = __ldcg(gv + i);
-    const double tau = *cluster.map_shared_rank(&vsc[slot][1], owner);
+    if (P + 1 == npan) break;  // no column after the last panel
+    // the panel's reflectors (rows from c0 down) and taus
+    for (int t = 0; t < wP; ++t) {
+      const double* g = W + (int64_t)(c0 + t) * ldw;
+      for (int i = c0 + threadIdx.x; i < m; i += blockDim.x) vl[(size_t)t * m + i] = __ldcg(g + i);
+    }
+    double tau[kQrPanel];
+    const double* otau = cluster.map_shared_rank(&taus[slot][0], owner);
+#pragma unroll
+    for (int t = 0; t < kQrPanel; ++t) tau[t] = t < wP ? otau[t] : 0.0;
     __syncthreads();
-    // owned columns > j: local index from the first one after j
-    const int lj0 = (j + CL - rank) / CL;
-    for (int lj = lj0 + warp; lj < nown; lj += nwarps) {
-      double* w = cols + (size_t)lj * m;
-      double t = 0.0;
-      for (int i = j + lane; i < m; i += 32) t += vl[i] * w[i];
-      t = warp_sum(t) * tau;
-      if (rank + lj * CL == j + 1) {  // the next pivot column: update and sum squares
+    // owned columns after the panel, one warp per column: the panel's
+    // reflectors in order
+    const int q0 = (P + 1 - rank + CL - 1) / CL;  // first owned panel after P
+    const int nfirst = (P + 1) * b;               // the next panel's first column
+    int lc = 0;
+    for (int q = q0; q < myp; ++q) lc += width(rank + q * CL);
+    for (int g = warp; g < lc; g += nwarps) {
+      int q = q0, t = g;
+      while (t >= width(rank + q * CL)) t -= width(rank + q * CL), ++q;
+      const int col = (rank + q * CL) * b + t;
+      double* w = cols + (size_t)(q * b + t) * m;
+      for (int r = 0; r < wP; ++r) {
+        const int j = c0 + r;
+        const double* v = vl + (size_t)r * m;
+        double s = 0.0;
+        for (int i = j + lane; i < m; i += 32) s += v[i] * w[i];
+        s = warp_sum(s) * tau[r];
+        for (int i = j + lane; i < m; i += 32) w[i] -= s * v[i];
+      }
+      if (col == nfirst) {  // the next pivot column: its squares below the pivot
         double s2 = 0.0;
-        for (int i = j + lane; i < m; i += 32) {
-          const double wi = w[i] - t * vl[i];
-          w[i] = wi;
-          if (i > j) s2 += wi * wi;
-        }
+        for (int i = nfirst + lane; i < m; i += 32) s2 += w[i] * w[i];
         s2 = warp_sum(s2);
-        if (lane == 0) cnorm[lj] = s2;
-      } else {
-        for (int i = j + lane; i < m; i += 32) w[i] -= t * vl[i];
+        if (lane == 0) cnorm[q * b + t] = s2;
       }
     }
   }
   __syncthreads();
-  for (int lj = 0; lj < nown; ++lj) {
-    const int col = rank + lj * CL;
-    double* dst = W + (int64_t)col * ldw;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) dst[i] = i <= col ? cols[(size_t)lj * m + i] : 0.0;
+  for (int q = 0; q < myp; ++q) {
+    const int P = rank + q * CL;
+    for (int t = 0; t < width(P); ++t) {
+      const int col = P * b + t;
+      double* dst = W + (int64_t)col * ldw;
+      const double* src = cols + (size_t)(q * b + t) * m;
+      for (int i = threadIdx.x; i < m; i += blockDim.x) dst[i] = i <= col ? src[i] : 0.0;
+    }
   }
   __threadfence();
   cluster.sync();

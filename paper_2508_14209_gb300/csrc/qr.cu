@@ -4,13 +4,15 @@
 //
 // Householder QR of the sketched m x c matrix (m = p rows, c = n+1 columns):
 // one thread-block cluster (up to 16 CTAs on 16 SMs) factors one matrix.
-// Column j belongs to CTA j mod CL (cyclic, so the shrinking trailing matrix
-// stays balanced).  Step j: the owner builds the reflector of column j
-// (v = x + sign(x0)||x|| e0, tau = 2 / v^T v, R[j][j] = -sign(x0)||x||) and
-// publishes v0 and tau; after one cluster barrier every CTA applies
-// I - tau v v^T to the columns it owns, one warp per column.  The matrix stays
-// in global memory (it is at most a few MB and lives in L2); v is staged in
-// each CTA's shared memory.  FP64 throughout.
+// Reflector of column j: v = x + sign(x0)||x|| e0, tau = 2 / v^T v,
+// R[j][j] = -sign(x0)||x||.  Two forms:
+//   on chip (qr_smem_fits): panels of kQrPanel columns, panel P owned by CTA
+//     P mod CL and kept in its shared memory; the owner factors a whole panel
+//     alone, then one cluster barrier per panel and every CTA applies the
+//     panel's reflectors to the columns it owns (msk_qr.cuh);
+//   in global memory (larger matrices): column j owned by CTA j mod CL, one
+//     cluster barrier per column; v staged in each CTA's shared memory.
+// FP64 throughout.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
