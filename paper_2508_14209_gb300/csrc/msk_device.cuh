@@ -70,20 +70,23 @@ __device__ __forceinline__ float ln_f32(float s) {
 
 // Standard normal number `elem` of the stream `key` (polar method; attempt a
 // uses draw index elem*2^16 + a; u, v are odd multiples of 2^-24 in (-1,1)).
+// The rejection loop only draws; the logarithm, division and square root
+// run once, after it, so that a warp whose lanes accept at different
+// attempts does not repeat them.
 __device__ __forceinline__ float gauss_std(uint64_t key, uint64_t elem) {
+  float u = 0.0f, s = 1.0f;
   for (uint32_t a = 0; a < 65536u; ++a) {
     const uint64_t z = draw(key, (elem << 16) | a);
     const int32_t U = (int32_t)(z >> 40);
     const int32_t V = (int32_t)((z >> 16) & 0xFFFFFFu);
-    const float u = __fmul_rn((float)(2 * U + 1 - (1 << 24)), 0x1p-24f);
+    u = __fmul_rn((float)(2 * U + 1 - (1 << 24)), 0x1p-24f);
     const float v = __fmul_rn((float)(2 * V + 1 - (1 << 24)), 0x1p-24f);
-    const float s = __fadd_rn(__fmul_rn(u, u), __fmul_rn(v, v));
-    if (s < 1.0f) {
-      const float q = __fdiv_rn(__fmul_rn(-2.0f, ln_f32(s)), s);
-      return __fmul_rn(u, __fsqrt_rn(q));
-    }
+    s = __fadd_rn(__fmul_rn(u, u), __fmul_rn(v, v));
+    if (s < 1.0f) break;
   }
-  return 0.0f;
+  if (!(s < 1.0f)) return 0.0f;
+  const float q = __fdiv_rn(__fmul_rn(-2.0f, ln_f32(s)), s);
+  return __fmul_rn(u, __fsqrt_rn(q));
 }
 
 // L2 reductions (the atomic adds of Algorithm 2, issued without a return value).

@@ -104,45 +104,62 @@ __device__ __forceinline__ void qr_cluster_body(double* __restrict__ W, int m, i
   }
 }
 
-// Shared-memory form of the cluster QR, blocked by panels of kQrPanel
-// columns, for matrices whose owned columns fit on chip (qr_smem_fits).
-// Panel P (columns P b .. P b + b - 1) belongs to CTA P mod CL, which keeps
-// its panels in shared memory for the whole factorisation.
-//   panel P: its owner factors the panel alone (b Householder steps: the
-//     reflector v = x + sign(x0)||x|| e0, tau = 2 / v^T v of each column from
-//     ||x||^2, which the warp that last updated the column accumulated on the
-//     way, then the panel's later columns updated one warp per column), writes
-//     the b reflectors into W's panel columns in global memory (those columns
-//     are broadcast slots until the final write-back) and publishes the taus;
-//   one cluster barrier per panel (not per column); every CTA reads the
-//     panel's reflectors from L2 and applies them, in order, to each of its
-//     columns after the panel, one warp per column; the warp that updates the
-//     first column of the next panel also sums its squares below the pivot.
-// Every column receives the same reflectors in the same order and the same
-// arithmetic as the unblocked algorithm, so R is the same.  The taus use two
-// slots alternating by panel: slot P & 1 is rewritten at panel P + 2, after
-// every CTA has passed the barrier of panel P + 1.  The factor goes back to W
-// at the end, zeros below the diagonal.
-constexpr int kQrPanel = 8;
-// Columns held by the CTA owning the most (panels cyclic over the cluster).
-__host__ __device__ __forceinline__ int qr_owned_cols(int c, int CL, int rank) {
-  const int npan = (c + kQrPanel - 1) / kQrPanel;
-  int n = 0;
-  for (int P = rank; P < npan; P += CL) n += min(kQrPanel, c - P * kQrPanel);
-  return n;
-}
-// Dynamic shared memory: the owned columns of the busiest CTA (stored panel
-// after panel; only a CTA's last panel can be narrower than kQrPanel, so
-// panel q starts at local column q kQrPanel) and the current panel's
-// reflectors, m doubles per column, plus the owned columns' norms.
+// Shared-memory form of the cluster QR, for matrices whose owned columns fit
+// on chip (qr_smem_fits): CTA `rank` keeps columns rank, rank + CL, ... of W
+// in its shared memory for the whole factorisation.
+//   step j: every CTA waits for reflector j (v = x + sign(x0)||x|| e0,
+//     tau = 2 / v^T v) to be published, copies v from W's column j in L2
+//     (that column is only a broadcast slot until the final write-back) and
+//     tau from the owner's shared memory, and applies I - tau v v^T to its
+//     owned columns > j, one warp per column;
+//   look-ahead: the owner of column j + 1 updates that column first (warp 0),
+//     summing its squares below the pivot on the way, and publishes
+//     reflector j + 1 before it updates its other columns.
+// The steps are chained by the split cluster barrier: a thread arrives at
+// phase j + 1 as soon as it has read reflector j (warp 0 of the next owner
+// only after publishing reflector j + 1) and waits for phase j + 1 when it
+// needs that reflector, so the publication of reflector j + 1 overlaps the
+// updates of step j.  v is copied into one of two buffers by step parity and
+// tau sits in one of two slots: both are rewritten two steps later, after
+// every thread of the cluster has arrived at the phase in between (and so has
+// finished with them).  The factor goes back to W at the end, zeros below the
+// diagonal.
+// Dynamic shared memory: (ceil(c / CL) + 2) * m doubles.
 __host__ __device__ __forceinline__ size_t qr_smem_bytes(int m, int c, int CL) {
-  int own = 0;
-  for (int r = 0; r < CL; ++r) own = max(own, qr_owned_cols(c, CL, r));
-  return sizeof(double) * ((size_t)(own + kQrPanel) * (size_t)m + (size_t)own);
+  const size_t own = (size_t)((c + CL - 1) / CL);
+  return sizeof(double) * ((own + 2) * (size_t)m);
 }
-constexpr size_t kQrSmemMax = 205 * 1024;  // 1024 x 257 on a 16-CTA cluster: 200 KB
+constexpr size_t kQrSmemMax = 160 * 1024;  // 1024 x 257 on a 16-CTA cluster: 152 KB
 __host__ __device__ __forceinline__ bool qr_smem_fits(int m, int c, int CL) {
   return qr_smem_bytes(m, c, CL) <= kQrSmemMax;
+}
+
+__device__ __forceinline__ void cluster_arrive_release() {
+  asm volatile("barrier.cluster.arrive.release;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait_acquire() {
+  asm volatile("barrier.cluster.wait.acquire;" ::: "memory");
+}
+
+// Reflector j from the owner's copy x of column j (norm2 = ||x[j:]||^2), by
+// one whole warp: tau into the slot of step j, v into W's column j (v0 at the
+// pivot, then x below it), R[j][j] into x[j].
+__device__ __forceinline__ void qr_publish_reflector(double* __restrict__ x, double* __restrict__ gcol,
+                                                     int j, int m, double norm2, double* tau_slot) {
+  const int lane = threadIdx.x & 31;
+  if (lane == 0) {
+    const double x0 = x[j];
+    const double alpha = sqrt(norm2);
+    const double sgn = x0 >= 0.0 ? 1.0 : -1.0;
+    const double v0 = x0 + sgn * alpha;
+    const double vtv = norm2 - x0 * x0 + v0 * v0;
+    *tau_slot = vtv > 0.0 ? 2.0 / vtv : 0.0;
+    gcol[j] = v0;
+    x[j] = -sgn * alpha;
+  }
+  for (int i = j + 1 + lane; i < m; i += 32) gcol[i] = x[i];
+  __threadfence();
+  __syncwarp();
 }
 
 __device__ __forceinline__ void qr_cluster_smem_body(double* __restrict__ W, int m, int c,
@@ -150,135 +167,66 @@ __device__ __forceinline__ void qr_cluster_smem_body(double* __restrict__ W, int
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   const int CL = (int)cluster.num_blocks();
-  constexpr int b = kQrPanel;
-  const int npan = (c + b - 1) / b;
-  int own = 0;
-  for (int r = 0; r < CL; ++r) own = max(own, qr_owned_cols(c, CL, r));
-  const int myp = (npan - rank + CL - 1) / CL;  // panels rank, rank + CL, ...
-  double* cols = sm;                            // panel q, column t: cols[(q b + t) m + i]
-  double* vl = sm + (size_t)own * m;            // the current panel's reflectors, b x m
-  double* cnorm = vl + (size_t)b * m;           // per owned column: ||column below its pivot||^2
-  __shared__ double taus[2][kQrPanel];
-  __shared__ double rdiag[kQrPanel];
+  const int own = (c + CL - 1) / CL;
+  const int nown = (c - rank + CL - 1) / CL;  // columns rank, rank + CL, ...
+  double* cols = sm;                           // own x m
+  double* vl = sm + (size_t)own * m;           // 2 x m: the step's v, by step parity
+  __shared__ double vsc[2];                    // tau, by step parity
   __shared__ double red[32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  auto width = [&](int P) { return min(b, c - P * b); };
-  for (int q = 0; q < myp; ++q) {
-    const int P = rank + q * CL;
-    for (int t = 0; t < width(P); ++t) {
-      const double* src = W + (int64_t)(P * b + t) * ldw;
-      for (int i = threadIdx.x; i < m; i += blockDim.x) cols[(size_t)(q * b + t) * m + i] = src[i];
-    }
+  for (int lj = 0; lj < nown; ++lj) {
+    const double* src = W + (int64_t)(rank + lj * CL) * ldw;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) cols[(size_t)lj * m + i] = src[i];
   }
   __syncthreads();
-  if (rank == 0) {  // ||column 0||^2
+  const int steps = min(m, c);
+  if (rank == 0 && steps > 0) {  // reflector 0
     double s = 0.0;
     for (int i = threadIdx.x; i < m; i += blockDim.x) s += cols[i] * cols[i];
     s = block_sum(s, red);
-    if (threadIdx.x == 0) cnorm[0] = s;
+    if (warp == 0) qr_publish_reflector(cols, W, 0, m, s, &vsc[0]);
   }
-  for (int P = 0; P < npan; ++P) {
-    const int owner = P % CL, slot = P & 1, c0 = P * b, wP = width(P);
-    __syncthreads();  // the panel's columns and first norm are final; vl is free
-    if (rank == owner) {
-      double* pc = cols + (size_t)(P / CL) * b * m;
-      for (int t = 0; t < wP; ++t) {
-        const int j = c0 + t;
-        double* x = pc + (size_t)t * m;
-        if (threadIdx.x == 0) {
-          const double norm2 = cnorm[(P / CL) * b + t];
-          const double x0 = x[j];
-          const double alpha = sqrt(norm2);
-          const double sgn = x0 >= 0.0 ? 1.0 : -1.0;
-          const double v0 = x0 + sgn * alpha;
-          const double vtv = norm2 - x0 * x0 + v0 * v0;
-          taus[slot][t] = vtv > 0.0 ? 2.0 / vtv : 0.0;
-          rdiag[t] = -sgn * alpha;
-          x[j] = v0;  // column j holds v from row j down until the panel is published
-        }
-        __syncthreads();
-        const double tau = taus[slot][t];
-        for (int u = t + 1 + warp; u < wP; u += nwarps) {
-          double* w = pc + (size_t)u * m;
-          double s = 0.0;
-          for (int i = j + lane; i < m; i += 32) s += x[i] * w[i];
-          s = warp_sum(s) * tau;
-          if (u == t + 1) {  // the panel's next pivot column: update and sum squares
-            double s2 = 0.0;
-            for (int i = j + lane; i < m; i += 32) {
-              const double wi = w[i] - s * x[i];
-              w[i] = wi;
-              if (i > j) s2 += wi * wi;
-            }
-            s2 = warp_sum(s2);
-            if (lane == 0) cnorm[(P / CL) * b + u] = s2;
-          } else {
-            for (int i = j + lane; i < m; i += 32) w[i] -= s * x[i];
-          }
-        }
-        __syncthreads();
-      }
-      // publish the reflectors (zeros above each pivot), then R's diagonal
-      for (int t = 0; t < wP; ++t) {
-        double* g = W + (int64_t)(c0 + t) * ldw;
-        const double* x = pc + (size_t)t * m;
-        for (int i = threadIdx.x; i < m; i += blockDim.x) g[i] = i < c0 + t ? 0.0 : x[i];
-      }
-      __syncthreads();
-      if (threadIdx.x < wP) pc[(size_t)threadIdx.x * m + c0 + threadIdx.x] = rdiag[threadIdx.x];
-      __threadfence();
-    }
-    cluster.sync();
-    if (P + 1 == npan) break;  // no column after the last panel
-    // the panel's reflectors (rows from c0 down) and taus
-    for (int t = 0; t < wP; ++t) {
-      const double* g = W + (int64_t)(c0 + t) * ldw;
-      for (int i = c0 + threadIdx.x; i < m; i += blockDim.x) vl[(size_t)t * m + i] = __ldcg(g + i);
-    }
-    double tau[kQrPanel];
-    const double* otau = cluster.map_shared_rank(&taus[slot][0], owner);
-#pragma unroll
-    for (int t = 0; t < kQrPanel; ++t) tau[t] = t < wP ? otau[t] : 0.0;
+  cluster_arrive_release();  // phase 0: reflector 0 published
+  for (int j = 0; j < steps; ++j) {
+    const int owner = j % CL, slot = j & 1;
+    cluster_wait_acquire();  // phase j: reflector j published, buffers of step j - 2 free
+    double* v = vl + (size_t)slot * m;
+    const double* gv = W + (int64_t)j * ldw;
+    for (int i = j + threadIdx.x; i < m; i += blockDim.x) v[i] = __ldcg(gv + i);
+    const double tau = *cluster.map_shared_rank(&vsc[slot], owner);
     __syncthreads();
-    // owned columns after the panel, one warp per column: the panel's
-    // reflectors in order
-    const int q0 = (P + 1 - rank + CL - 1) / CL;  // first owned panel after P
-    const int nfirst = (P + 1) * b;               // the next panel's first column
-    int lc = 0;
-    for (int q = q0; q < myp; ++q) lc += width(rank + q * CL);
-    for (int g = warp; g < lc; g += nwarps) {
-      int q = q0, t = g;
-      while (t >= width(rank + q * CL)) t -= width(rank + q * CL), ++q;
-      const int col = (rank + q * CL) * b + t;
-      double* w = cols + (size_t)(q * b + t) * m;
-      for (int r = 0; r < wP; ++r) {
-        const int j = c0 + r;
-        const double* v = vl + (size_t)r * m;
-        double s = 0.0;
-        for (int i = j + lane; i < m; i += 32) s += v[i] * w[i];
-        s = warp_sum(s) * tau[r];
-        for (int i = j + lane; i < m; i += 32) w[i] -= s * v[i];
+    const int lj0 = (j + CL - rank) / CL;  // first owned column after j
+    const bool pivot = j + 1 < steps && rank == (j + 1) % CL;  // then lj0 is column j + 1
+    if (pivot && warp == 0) {
+      double* w = cols + (size_t)lj0 * m;
+      double t = 0.0;
+      for (int i = j + lane; i < m; i += 32) t += v[i] * w[i];
+      t = warp_sum(t) * tau;
+      double s2 = 0.0;
+      for (int i = j + lane; i < m; i += 32) {
+        const double wi = w[i] - t * v[i];
+        w[i] = wi;
+        if (i > j) s2 += wi * wi;
       }
-      if (col == nfirst) {  // the next pivot column: its squares below the pivot
-        double s2 = 0.0;
-        for (int i = nfirst + lane; i < m; i += 32) s2 += w[i] * w[i];
-        s2 = warp_sum(s2);
-        if (lane == 0) cnorm[q * b + t] = s2;
-      }
+      s2 = warp_sum(s2);
+      qr_publish_reflector(w, W + (int64_t)(j + 1) * ldw, j + 1, m, s2, &vsc[slot ^ 1]);
+    }
+    cluster_arrive_release();  // phase j + 1
+    for (int lj = lj0 + (pivot ? 1 : 0) + warp; lj < nown; lj += nwarps) {
+      double* w = cols + (size_t)lj * m;
+      double t = 0.0;
+      for (int i = j + lane; i < m; i += 32) t += v[i] * w[i];
+      t = warp_sum(t) * tau;
+      for (int i = j + lane; i < m; i += 32) w[i] -= t * v[i];
     }
   }
+  cluster_wait_acquire();  // every CTA has read the last reflector
   __syncthreads();
-  for (int q = 0; q < myp; ++q) {
-    const int P = rank + q * CL;
-    for (int t = 0; t < width(P); ++t) {
-      const int col = P * b + t;
-      double* dst = W + (int64_t)col * ldw;
-      const double* src = cols + (size_t)(q * b + t) * m;
-      for (int i = threadIdx.x; i < m; i += blockDim.x) dst[i] = i <= col ? src[i] : 0.0;
-    }
+  for (int lj = 0; lj < nown; ++lj) {
+    const int col = rank + lj * CL;
+    double* dst = W + (int64_t)col * ldw;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) dst[i] = i <= col ? cols[(size_t)lj * m + i] : 0.0;
   }
-  __threadfence();
-  cluster.sync();
 }
 
 // R x = rhs, R upper (column-major, ldr).  x may alias rhs.

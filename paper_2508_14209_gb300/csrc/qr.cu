@@ -4,15 +4,16 @@
 //
 // Householder QR of the sketched m x c matrix (m = p rows, c = n+1 columns):
 // one thread-block cluster (up to 16 CTAs on 16 SMs) factors one matrix.
-// Reflector of column j: v = x + sign(x0)||x|| e0, tau = 2 / v^T v,
-// R[j][j] = -sign(x0)||x||.  Two forms:
-//   on chip (qr_smem_fits): panels of kQrPanel columns, panel P owned by CTA
-//     P mod CL and kept in its shared memory; the owner factors a whole panel
-//     alone, then one cluster barrier per panel and every CTA applies the
-//     panel's reflectors to the columns it owns (msk_qr.cuh);
-//   in global memory (larger matrices): column j owned by CTA j mod CL, one
-//     cluster barrier per column; v staged in each CTA's shared memory.
-// FP64 throughout.
+// Column j belongs to CTA j mod CL (cyclic, so the shrinking trailing matrix
+// stays balanced).  Step j: the owner builds the reflector of column j
+// (v = x + sign(x0)||x|| e0, tau = 2 / v^T v, R[j][j] = -sign(x0)||x||) and
+// publishes it; every CTA then applies I - tau v v^T to the columns it owns,
+// one warp per column.  On chip (qr_cluster_smem_body) the owned columns stay
+// in shared memory and the steps overlap through a split cluster barrier with
+// one column of look-ahead; in global memory (larger matrices) one full
+// cluster barrier per column, v staged in each CTA's shared memory.  FP64
+// throughout: GB300's FP64 rate (2 FMAs per clock per SM) over the cluster's
+// 16 SMs bounds the factorisation at 2 m c^2 flops.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
