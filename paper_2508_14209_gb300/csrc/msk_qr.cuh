@@ -112,7 +112,8 @@ __device__ __forceinline__ void qr_cluster_body(double* __restrict__ W, int m, i
 //     (that column is only a broadcast slot until the final write-back) and
 //     tau from the owner's shared memory, and applies I - tau v v^T to its
 //     owned columns > j, one warp per column;
-//   look-ahead: the owner of column j + 1 updates that column first (warp 0),
+//   look-ahead: the owner of column j + 1 updates that column first (warp 0,
+//     its other warps waiting so that the SM's FP64 pipe serves it alone),
 //     summing its squares below the pivot on the way, and publishes
 //     reflector j + 1 before it updates its other columns.
 // The steps are chained by the split cluster barrier: a thread arrives at
@@ -212,6 +213,9 @@ __device__ __forceinline__ void qr_cluster_smem_body(double* __restrict__ W, int
       qr_publish_reflector(w, W + (int64_t)(j + 1) * ldw, j + 1, m, s2, &vsc[slot ^ 1]);
     }
     cluster_arrive_release();  // phase j + 1
+    // the FP64 pipe is the SM's scarcest resource: in the pivot's CTA the
+    // other warps start their updates only once reflector j + 1 is out
+    if (pivot) __syncthreads();
     for (int lj = lj0 + (pivot ? 1 : 0) + warp; lj < nown; lj += nwarps) {
       double* w = cols + (size_t)lj * m;
       double t = 0.0;
