@@ -2,26 +2,35 @@
 
 Workload (default): a 4194304 x 64 FP64 matrix with N(0,1) entries, CountSketch
 to k = 2n^2 = 8192 rows, then the p = 4n = 256 row Gaussian sketch in FP64
-(the paper's multisketch, Section 6.2).  One step = one ms_sketch pass:
-zero Y, hashed CountSketch of A, Gaussian generation, Z = G Y (split-K FP64),
-split-K reduction.  The input (2 GiB) is larger than L2 (129 MB), so every step
+(the paper's multisketch, Section 6.2).  One step = the CountSketch (zero Y,
+hashed scatter-add of A) and the FP64 Gaussian stage Z = G Y (G sliced on the
+tensor cores).  The input (2 GiB) is larger than L2 (129 MB), so every step
 reads A from HBM.
 
 Prints ONE JSON line (rank 0).  value = CountSketch-input bytes per second over
 the whole step (GB/s); roofline = the CountSketch kernel against the measured
-HBM copy bandwidth; e2e = the same metric through the public ms_sketch call
-with pinned host buffers (host->device copy of A and device->host copy of Z
-inside the timed region); cpu_baseline = the CPU oracle on the machine's host.
+HBM copy bandwidth; e2e = the same metric through the public ms_sketch_host
+call with pinned host buffers (host->device copy of A and device->host copy of
+Z inside the timed region); cpu_baseline = the CPU oracle on the machine's host,
+the same program and sample as the reference arm's step.
 
-The same line carries the served least-squares comparison ("serving"): a pool
-of least-squares problems shaped like the served configuration (n uniform in
-{16, 32, 64, 128}, d log-uniform in [2^14, 2^21], sigma log-spaced from 1 to
-10^-U(2,8), FP32 A), a trace of requests drawn from the pool with fresh seeds
-and Poisson arrivals, solved (a) by the request server with the mixed-precision
-path (FP32 CountSketch, split-BF16 tensor-core Gaussian stage, FP64 QR,
-refinement) and (b) one at a time by plain FP64 sketch-and-solve on the same
-trace; solves/s and p50/p99 latency (arrival to completion) for both, at
-capacity (all requests at t = 0) and at a fixed Poisson rate.
+The line also carries:
+* "least_squares": the least-squares configurations, device-timed: FP64
+  multisketch sketch-and-solve against the normal equations at 8388608 x 128
+  (sigma to 1e-6 and to 1e-10), and the refined mixed-precision solve at
+  16777216 x 256 (split-BF16, BF16 and FP16 Gaussian stages) against FP64
+  sketch-and-solve; every relative residual recomputed in FP64 by torch;
+* "serving": a pool of least-squares problems shaped like the served
+  configuration (n uniform in {16, 32, 64, 128}, d log-uniform in
+  [2^14, 2^21], sigma log-spaced from 1 to 10^-U(2,8), FP32 A), a trace of
+  requests drawn from the pool with fresh seeds, at capacity (all at t = 0)
+  and with Poisson arrivals, solved (a) by the request server with the
+  mixed-precision path (FP32 CountSketch, split-BF16 tensor-core Gaussian
+  stage, FP64 QR, refinement to the minimiser), (b) one at a time by plain
+  FP64 sketch-and-solve, and (c) one at a time by the FP64 sketch refined to
+  the same tolerance as (a); solves/s and p50/p99 latency (arrival to
+  completion) for each, and the accuracy of a sample of (a)'s results against
+  the least-squares minimiser.
 """
 from __future__ import annotations
 
@@ -338,10 +347,14 @@ def _serve_mixed(msk, pool, pick, arrivals, dev, tol, keep=None):
             "converged": conv, "batches": stats["batches"]}
 
 
-def _serve_plain(msk, pool, pick, arrivals, dev, keep=None):
+def _serve_plain(msk, pool, pick, arrivals, dev, keep=None, refine_tol=None):
+    """One request at a time: FP64 sketch-and-solve (the plain path), or with
+    refine_tol the same FP64 sketch refined to that tolerance (the plain path
+    at the served path's accuracy)."""
     import numpy as np
     import torch
 
+    refine = refine_tol is not None
     ws = {}
     lat = []
     xs = []
@@ -353,9 +366,11 @@ def _serve_plain(msk, pool, pick, arrivals, dev, keep=None):
         A, b, d, n = pool[j]
         k, p = 2 * n * n, 4 * n
         if (d, n) not in ws:
-            ws[(d, n)] = msk.workspace(msk.msk_lstsq_workspace(d, n, k, p, msk.MSK_F32, msk.GEMM_F64, 0), dev)
+            ws[(d, n)] = msk.workspace(msk.msk_lstsq_workspace(d, n, k, p, msk.MSK_F32, msk.GEMM_F64, int(refine)),
+                                       dev)
         x = torch.empty(n, dtype=torch.float64, device=dev)
-        msk.ms_lstsq(A, b, k, p, 0x5EED0005 + i, msk.GEMM_F64, refine=False, x=x, ws=ws[(d, n)], want_info=False)
+        msk.ms_lstsq(A, b, k, p, 0x5EED0005 + i, msk.GEMM_F64, refine=refine, tol=refine_tol or 0.0,
+                     max_iter=SERVED["max_iter"], x=x, ws=ws[(d, n)], want_info=refine)
         torch.cuda.synchronize()
         lat.append(time.perf_counter() - t0 - arrivals[i])
         if keep is not None and len(xs) < 16:
@@ -512,15 +527,18 @@ def run_serving(args, dev, rank):
     # warm-up of both paths (module loads, graph machinery, workspace)
     _serve_mixed(msk, pool, pick[:16], np.zeros(16), dev, args.serve_tol)
     _serve_plain(msk, pool, pick[:16], np.zeros(16), dev)
+    _serve_plain(msk, pool, pick[:16], np.zeros(16), dev, refine_tol=args.serve_tol)
     zero = np.zeros(N)
     x_mixed, x_plain = [], []
     out["capacity"] = {"mixed": _serve_mixed(msk, pool, pick, zero, dev, args.serve_tol, keep=x_mixed),
-                       "plain_fp64": _serve_plain(msk, pool, pick, zero, dev, keep=x_plain)}
+                       "plain_fp64": _serve_plain(msk, pool, pick, zero, dev, keep=x_plain),
+                       "plain_fp64_refined": _serve_plain(msk, pool, pick, zero, dev, refine_tol=args.serve_tol)}
     rate = args.serve_rate
     arrivals = np.cumsum(rng.exponential(1.0 / rate, N))
     out["poisson"] = {"rate_per_s": rate,
                       "mixed": _serve_mixed(msk, pool, pick, arrivals, dev, args.serve_tol),
-                      "plain_fp64": _serve_plain(msk, pool, pick, arrivals, dev)}
+                      "plain_fp64": _serve_plain(msk, pool, pick, arrivals, dev),
+                      "plain_fp64_refined": _serve_plain(msk, pool, pick, arrivals, dev, refine_tol=args.serve_tol)}
     # accuracy of the first 16 served results (capacity run), recomputed in
     # FP64 outside the library: two-sided against the least-squares minimiser
     # of the stored A, and one-sided against plain FP64 sketch-and-solve of
