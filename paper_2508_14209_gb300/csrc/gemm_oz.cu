@@ -91,20 +91,39 @@ __device__ __forceinline__ long long oz_fixed_f32(float g, int e) {
   const long long X = oz_shift_round(m, (E ? E : 1) - 150 + 63 - e);  // g = m 2^(E - 150)
   return (bits >> 31) ? -X : X;
 }
-// The eight slices of X: X = sum_l s_l 2^(56 - 8 l), s_l the nearest integer
-// to what the previous slices left over 2^(56 - 8 l) (ties upward), in
-// [-128, 128]; the last one takes the remainder, in [-128, 127].
-__device__ __forceinline__ void oz_slices(long long X, float (&s)[kOzSlices]) {
+// The integer value of a binary32 holding an integer of magnitude < 2^31,
+// from its bits (integer operations only).
+__device__ __forceinline__ int oz_int_of_f32(uint32_t bits) {
+  const int e = (int)((bits >> 23) & 0xFF) - 127;  // |f| = 1.m 2^e
+  if (e < 0) return 0;
+  const int m = (int)((bits & 0x7FFFFFu) | 0x800000u);
+  const int v = e >= 23 ? (m << (e - 23)) : (m >> (23 - e));
+  return (bits >> 31) ? -v : v;
+}
+// bfloat16 bits of an integer q with |q| <= 128 (exact), by integer
+// operations (the integer-to-float conversions run on a slow pipe).
+__device__ __forceinline__ uint16_t oz_bf16_of_int(int q) {
+  if (q == 0) return 0;
+  const unsigned a = (unsigned)(q < 0 ? -q : q);
+  const int e = 31 - __clz(a);  // 0 .. 7
+  const unsigned mant = (a << (7 - e)) & 0x7Fu;
+  return (uint16_t)((q < 0 ? 0x8000u : 0u) | ((unsigned)(e + 127) << 7) | mant);
+}
+// The eight slices of X, as bfloat16 bits: X = sum_l s_l 2^(56 - 8 l), s_l
+// the nearest integer to what the previous slices left over 2^(56 - 8 l)
+// (ties upward), in [-128, 128]; the last one takes the remainder, in
+// [-128, 127].
+__device__ __forceinline__ void oz_slices(long long X, uint16_t (&s)[kOzSlices]) {
   unsigned long long r = (unsigned long long)X;
 #pragma unroll
   for (int l = 0; l < kOzSlices - 1; ++l) {
     const int sh = 56 - 8 * l;
     const long long rs = (long long)r;
     const long long q = (rs >> sh) + ((rs >> (sh - 1)) & 1);
-    s[l] = (float)q;
+    s[l] = oz_bf16_of_int((int)q);
     r -= (unsigned long long)q << sh;
   }
-  s[kOzSlices - 1] = (float)(long long)r;
+  s[kOzSlices - 1] = oz_bf16_of_int((int)(long long)r);
 }
 
 // G slices: entry (r, i) is the same binary32 number the Gaussian kernel
@@ -118,11 +137,11 @@ __global__ void oz_split_g_kernel(uint64_t key, int64_t p, int64_t k, float sqrt
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < k;
          c += (int64_t)gridDim.x * blockDim.x) {
       const float g = __fdiv_rn(gauss_std(key, (uint64_t)(r * k + c)), sqrt_p);
-      float sl[kOzSlices];
+      uint16_t sl[kOzSlices];
       oz_slices(oz_fixed_f32(g, eG), sl);
-      __nv_bfloat16* out = Gs + r * kpitch + c;
+      uint16_t* out = reinterpret_cast<uint16_t*>(Gs) + r * kpitch + c;
 #pragma unroll
-      for (int j = 0; j < kOzSlices; ++j) out[j * plane] = __float2bfloat16_rn(sl[j]);  // exact
+      for (int j = 0; j < kOzSlices; ++j) out[j * plane] = sl[j];
     }
 }
 
@@ -182,11 +201,11 @@ __global__ void oz_split_y_kernel(const double* __restrict__ Y, int64_t ldy, int
     const int64_t i = k0 + tx;
     if (n >= npad || i >= k) continue;
     const long long X = n < ncol ? oz_fixed_f64(tile[tx][r], oz_exp_of(mx[n])) : 0;
-    float sl[kOzSlices];
+    uint16_t sl[kOzSlices];
     oz_slices(X, sl);
-    __nv_bfloat16* out = Ys + (int64_t)n * kpitch + i;
+    uint16_t* out = reinterpret_cast<uint16_t*>(Ys) + (int64_t)n * kpitch + i;
 #pragma unroll
-    for (int l = 0; l < kOzSlices; ++l) out[l * plane] = __float2bfloat16_rn(sl[l]);  // exact
+    for (int l = 0; l < kOzSlices; ++l) out[l * plane] = sl[l];
   }
 }
 
@@ -322,7 +341,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
         tmem_ld16(lane_base + (uint32_t)(lev * NT + c0), v);
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
-          const long long x = (long long)__float2int_rn(__uint_as_float(v[q]));  // exact
+          const long long x = oz_int_of_f32(v[q]);  // exact
           if (s < 4) H[q] += x * (1LL << (8 * (3 - s)));
           else L[q] += x * (1LL << (8 * (7 - s)));
         }
