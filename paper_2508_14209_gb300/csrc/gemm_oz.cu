@@ -91,15 +91,6 @@ __device__ __forceinline__ long long oz_fixed_f32(float g, int e) {
   const long long X = oz_shift_round(m, (E ? E : 1) - 150 + 63 - e);  // g = m 2^(E - 150)
   return (bits >> 31) ? -X : X;
 }
-// The integer value of a binary32 holding an integer of magnitude < 2^31,
-// from its bits (integer operations only).
-__device__ __forceinline__ int oz_int_of_f32(uint32_t bits) {
-  const int e = (int)((bits >> 23) & 0xFF) - 127;  // |f| = 1.m 2^e
-  if (e < 0) return 0;
-  const int m = (int)((bits & 0x7FFFFFu) | 0x800000u);
-  const int v = e >= 23 ? (m << (e - 23)) : (m >> (23 - e));
-  return (bits >> 31) ? -v : v;
-}
 // bfloat16 bits of an integer q with |q| <= 128 (exact), by integer
 // operations (the integer-to-float conversions run on a slow pipe).
 __device__ __forceinline__ uint16_t oz_bf16_of_int(int q) {
@@ -341,7 +332,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
         tmem_ld16(lane_base + (uint32_t)(lev * NT + c0), v);
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
-          const long long x = oz_int_of_f32(v[q]);  // exact
+          const long long x = (long long)__float2int_rn(__uint_as_float(v[q]));  // exact
           if (s < 4) H[q] += x * (1LL << (8 * (3 - s)));
           else L[q] += x * (1LL << (8 * (7 - s)));
         }
