@@ -40,18 +40,6 @@ __device__ __forceinline__ uint32_t bucket_of(uint64_t z, uint32_t k) {
 }
 __device__ __forceinline__ bool negative_of(uint64_t z) { return (z & 1ull) != 0; }
 
-// The binary32 value of an integer v with |v| < 2^24 (exact), assembled
-// from its bits by integer operations: the same number an integer-to-float
-// conversion gives, without the conversion unit, whose throughput bounds the
-// Gaussian sampler.
-__device__ __forceinline__ float float_of_small_int(int v) {
-  if (v == 0) return 0.0f;
-  const unsigned a = (unsigned)(v < 0 ? -v : v);
-  const int e = 31 - __clz(a);  // 0 .. 23
-  const unsigned mant = (a << (23 - e)) & 0x7FFFFFu;
-  return __uint_as_float((v < 0 ? 0x80000000u : 0u) | ((unsigned)(e + 127) << 23) | mant);
-}
-
 // ln(s) for a normal positive binary32 s:
 //   s = m 2^e, m in [sqrt(1/2), sqrt(2)),  ln s = e ln2 + 2 atanh(t),
 //   t = (m-1)/(m+1),  atanh(t) ~ t (1 + t^2/3 + t^4/5 + t^6/7 + t^8/9).
@@ -77,7 +65,7 @@ __device__ __forceinline__ float ln_f32(float s) {
   p = __fadd_rn(__fmul_rn(p, w), c3);
   p = __fadd_rn(__fmul_rn(p, w), 1.0f);
   const float lnm = __fmul_rn(__fmul_rn(2.0f, t), p);
-  return __fadd_rn(__fmul_rn(float_of_small_int(e), kLn2), lnm);
+  return __fadd_rn(__fmul_rn((float)e, kLn2), lnm);
 }
 
 // Standard normal number `elem` of the stream `key` (polar method; attempt a
@@ -91,8 +79,8 @@ __device__ __forceinline__ float gauss_std(uint64_t key, uint64_t elem) {
     const uint64_t z = draw(key, (elem << 16) | a);
     const int32_t U = (int32_t)(z >> 40);
     const int32_t V = (int32_t)((z >> 16) & 0xFFFFFFu);
-    u = __fmul_rn(float_of_small_int(2 * U + 1 - (1 << 24)), 0x1p-24f);
-    const float v = __fmul_rn(float_of_small_int(2 * V + 1 - (1 << 24)), 0x1p-24f);
+    u = __fmul_rn((float)(2 * U + 1 - (1 << 24)), 0x1p-24f);
+    const float v = __fmul_rn((float)(2 * V + 1 - (1 << 24)), 0x1p-24f);
     s = __fadd_rn(__fmul_rn(u, u), __fmul_rn(v, v));
     if (s < 1.0f) break;
   }
