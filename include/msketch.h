@@ -469,14 +469,23 @@ typedef struct {
 /* Scratch bytes msk_batch_lstsq needs for these items. */
 size_t msk_batch_workspace(const msk_batch_item *items, int nitems, int refine);
 
+/* An upper bound of one item's part of msk_batch_workspace that adds up over
+ * a batch: the sum over any batch's items is at least msk_batch_workspace of
+ * that batch.  Host arithmetic only; the server admits requests by it in
+ * time linear in the batch.  0 for a NULL item or an unsupported n.  The
+ * paper has no counterpart. */
+size_t msk_batch_item_bound(const msk_batch_item *item, int refine);
+
 /* Solve every problem of the batch with the mixed-precision multisketch path:
  * FP32 CountSketch, split-BF16 tensor-core Gaussian stage with FP32
  * accumulators drained into double-single registers, FP64 Householder QR and
  * solve (Algorithm 1), and with refine = 1 the refinement of ms_lstsq (FP64
  * residual passes, double-single CG passes) until each problem's relative
  * residual changes by at most tol * relres, or max_iter outer steps.  Each
- * stage is one launch over all problems; the CG rounds are replayed from a
- * CUDA graph.  items: host array of nitems; infos: host array of nitems or
+ * stage is one launch over all problems, and the whole batch — the stages,
+ * the outer refinement loop and the inner CG loop — is one CUDA-graph launch
+ * whose loops are device-driven while nodes, so the host waits once, for the
+ * results.  items: host array of nitems; infos: host array of nitems or
  * NULL.  Synchronises `stream`.  ws: 256-byte aligned, msk_batch_workspace
  * bytes.  Returns MSK_OK, MSK_ENOCONV if some problem hit max_iter, or -1
  * (bad item), -2 (nitems < 1), -3 (bad refine), MSK_ENOMEM. */
@@ -513,11 +522,14 @@ int msk_autotune(const msk_batch_item *items, int nitems, int refine, double tol
 /* A server for msk_batch_item requests.  mem_budget bytes of device memory are
  * reserved once here and split evenly over `workers` worker threads (each
  * with its own stream); nothing else is allocated while serving.  A free
- * worker admits waiting requests in arrival order while their batched
- * workspace (msk_batch_workspace) fits its share of the budget, at most
- * max_batch per batch, and solves them with msk_batch_lstsq(refine, tol,
- * max_iter); batches of different workers overlap on the GPU.  The paper
- * serves single problems; this is the serving layer around its solver.
+ * worker admits waiting requests in arrival order while the sum of their
+ * msk_batch_item_bound fits its share of the budget, at most max_batch per
+ * batch, and solves them with msk_batch_lstsq(refine, tol, max_iter);
+ * batches of different workers overlap on the GPU.  A request larger than a
+ * share but not than the budget runs alone with the whole budget once the
+ * other workers' batches are done (workers start nothing new meanwhile).
+ * The paper serves single problems; this is the serving layer around its
+ * solver.
  * Errors: -1 budget < 1 MiB, -2 workers outside 1..16, -3 max_batch < 1,
  * -4 bad refine, -7 srv NULL, MSK_ENOMEM when the pool cannot be reserved. */
 int ms_server_create(size_t mem_budget, int workers, int max_batch, int refine,
@@ -525,8 +537,8 @@ int ms_server_create(size_t mem_budget, int workers, int max_batch, int refine,
 
 /* Queue one request (non-blocking).  The request's arrays must stay valid
  * until it is done; x is written in place.  *ticket identifies it.
- * MSK_ENOMEM when the request alone exceeds a worker's share of the budget,
- * MSK_EBUSY when the server is stopping or its queue is full. */
+ * MSK_ENOMEM when the request alone exceeds the whole budget, MSK_EBUSY when
+ * the server is stopping or its queue is full. */
 int ms_server_submit(void *srv, const msk_batch_item *req, uint64_t *ticket);
 
 /* *done = 1 once the request is solved; then info (host, may be NULL) and

@@ -38,7 +38,7 @@ EXPORTS = ("msk_version", "msk_last_error", "msk_take_timeout", "msk_selftest_wa
            "msk_sns_workspace", "sns_lstsq", "msk_srht_workspace", "srht_sketch",
            "msk_ms_host_workspace", "ms_sketch_host", "ms_sketch_rows",
            "msk_gemm_noalloc", "msk_tune_set", "msk_tune_get",
-           "msk_tune_clear", "msk_batch_workspace", "msk_batch_lstsq", "ms_server_create",
+           "msk_tune_clear", "msk_batch_workspace", "msk_batch_item_bound", "msk_batch_lstsq", "ms_server_create",
            "ms_server_submit", "ms_server_poll", "ms_server_wait_all", "ms_server_stats",
            "ms_server_destroy", "ms_server_error", "msk_autotune_workspace", "msk_autotune")
 
@@ -124,6 +124,7 @@ def _declare(L):
         "rcq_qr": (_int, [_p, _int, _i64, _i64, _i64, _i64, _i64, _u64, _int, _p, _i64, _p, _i64, _p,
                           _sz, _p]),
         "msk_batch_workspace": (_sz, [ctypes.POINTER(BatchItem), _int, _int]),
+        "msk_batch_item_bound": (_sz, [ctypes.POINTER(BatchItem), _int]),
         "ms_server_create": (_int, [_sz, _int, _int, _int, _dbl, _i32, ctypes.POINTER(_p)]),
         "ms_server_submit": (_int, [_p, ctypes.POINTER(BatchItem), ctypes.POINTER(_u64)]),
         "ms_server_poll": (_int, [_p, _u64, ctypes.POINTER(_int), ctypes.POINTER(LstsqInfo),
@@ -569,6 +570,14 @@ def msk_batch_workspace(problems, refine=True):
         d, n = A.shape
         arr[j] = BatchItem(A.data_ptr(), d, n, _colmajor(A), bb.data_ptr(), seed & (2**64 - 1), 0)
     return load().msk_batch_workspace(arr, len(problems), int(refine))
+
+
+def msk_batch_item_bound(problem, refine=True):
+    """Additive upper bound of one problem's part of msk_batch_workspace."""
+    A, bb, seed = problem
+    d, n = A.shape
+    item = BatchItem(A.data_ptr(), d, n, _colmajor(A), bb.data_ptr(), seed & (2**64 - 1), 0)
+    return load().msk_batch_item_bound(ctypes.byref(item), int(refine))
 
 
 def msk_batch_lstsq(problems, refine=True, tol=1e-10, max_iter=10, ws=None, stream=None):

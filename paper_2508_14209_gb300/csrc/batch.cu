@@ -565,6 +565,39 @@ size_t msk_batch_workspace(const msk_batch_item* items, int nitems, int refine) 
   return P.bytes;
 }
 
+// Every piece plan_batch takes for this item, each with its alignment slack,
+// its refinement pass at the most CTAs it can receive, its entries of the
+// batch-wide arrays, and 4 KiB towards the per-batch remainder (alignment of
+// the five batch arrays, 256 bytes each, and of a width class's three
+// tables, 776 bytes: a batch with c classes has at least c items).
+size_t msk_batch_item_bound(const msk_batch_item* item, int refine) {
+  if (!item || !width_ok(item->n)) return 0;
+  const int64_t n = item->n, k = 2 * n * n, p = 4 * n, ncol = n + 1;
+  const int kt_per = (int)std::min<long long>(64, std::max<long long>(1, tune_get("batch.kt_per", kBatchKtPer)));
+  TcShape sh;
+  tc_ds_shape(p, k, ncol, kt_per, &sh);
+  const int64_t ldy = (ncol + 3) / 4 * 4;
+  const int nc = pass32_class((int)n);
+  const int64_t tiles = (item->d + pass32_rows(nc) - 1) / pass32_rows(nc);
+  const int64_t cap = (int64_t)pass32_ctas_per_sm(nc) * num_sms();
+  const int64_t nchunks = std::max<int64_t>(1, std::min<int64_t>(cap, tiles));
+  size_t b = 4096;
+  auto piece = [&](size_t bytes) { b += bytes + 255; };
+  piece(sizeof(BatchJob) + sizeof(TcJob) + 2 * sizeof(int) + kGather * sizeof(double) + sizeof(BatchCtl));
+  piece((size_t)k * ldy * 4);                          // Y
+  piece((size_t)p * sh.kpitch * 2);                    // G
+  piece((size_t)3 * sh.npad * sh.kpitch * 2);          // Yt
+  piece((size_t)sh.S * p * ncol * 8);                  // GEMM partials
+  piece((size_t)p * ncol * 8);                         // Z
+  piece(refine ? (size_t)n * n * 8 : 0);               // R^{-1}
+  piece(refine ? (size_t)5 * n * 8 : 0);               // CG vectors
+  piece((size_t)kScCount * 8);                         // CG scalars
+  piece((size_t)(n + 2) * 8);                          // pass result
+  piece((size_t)nchunks * (n + 2) * 8);                // pass partials
+  piece(sizeof(int) + sizeof(CsParams<float>) + sizeof(int64_t));  // class tables
+  return b;
+}
+
 int msk_batch_lstsq(const msk_batch_item* items, int nitems, int refine, double tol,
                     int32_t max_iter, msk_lstsq_info* infos, void* ws, size_t ws_bytes,
                     void* stream) {

@@ -3,10 +3,13 @@
 // A server owns a device memory pool reserved once at creation (the budget)
 // and W worker threads, each with its own CUDA stream and an equal slice of the
 // pool.  Submitted requests wait in a FIFO queue.  A free worker admits, in
-// arrival order, the waiting requests whose batched workspace still fits its
-// slice (admission by device memory; a request larger than a slice is refused
-// at submission), solves them with one msk_batch_lstsq call and records, per
-// ticket, the result summary and the latency from submission to completion.
+// arrival order, the waiting requests whose additive workspace bounds
+// (msk_batch_item_bound) still fit its slice — admission by device memory, in
+// time linear in the batch — solves them with one msk_batch_lstsq call and
+// records, per ticket, the result summary and the latency from submission to
+// completion.  A request larger than a slice (but not than the pool; larger
+// ones are refused at submission) runs alone with the whole pool once the
+// other workers' batches are done; no worker starts a batch meanwhile.
 // While one worker's batch is on the GPU, requests that arrive meanwhile are
 // admitted by the next free worker, so batches overlap on the device.
 // Nothing is allocated on the device after creation.
@@ -47,7 +50,9 @@ struct Server {
   int max_iter = 10;
   int max_batch = 64;
   size_t slice = 0;
+  size_t pool_bytes = 0;
   char* pool = nullptr;
+  bool exclusive = false;  // a request larger than a slice holds (or awaits) the whole pool
   std::vector<std::thread> workers;
   std::vector<cudaStream_t> streams;
   std::mutex mu;
@@ -65,35 +70,54 @@ struct Server {
 
 void worker_loop(Server* S, int w) {
   cudaSetDevice(S->device);
-  char* arena = S->pool + (size_t)w * S->slice;
+  char* const own = S->pool + (size_t)w * S->slice;
   std::vector<uint64_t> ids;
   std::vector<msk_batch_item> items;
   std::vector<msk_lstsq_info> infos;
   for (;;) {
     ids.clear();
     items.clear();
+    char* arena = own;
+    size_t cap = S->slice;
+    bool whole = false;
     {
       std::unique_lock<std::mutex> lock(S->mu);
-      S->cv_work.wait(lock, [&] { return S->stopping || !S->queue.empty(); });
-      if (S->queue.empty() && S->stopping) return;
-      // admit in arrival order while the batch workspace fits this slice
-      while (!S->queue.empty() && (int)items.size() < S->max_batch) {
-        const uint64_t id = S->queue.front();
-        items.push_back(S->tickets[id].item);
-        const size_t need = msk_batch_workspace(items.data(), (int)items.size(), S->refine);
-        if (need > S->slice) {
-          items.pop_back();
-          break;
-        }
-        ids.push_back(id);
+      S->cv_work.wait(lock, [&] {
+        return (S->stopping && S->queue.empty()) || (!S->queue.empty() && !S->exclusive);
+      });
+      if (S->queue.empty()) return;  // stopping, nothing left
+      const uint64_t head = S->queue.front();
+      if (msk_batch_item_bound(&S->tickets[head].item, S->refine) > S->slice) {
+        // larger than a slice: alone, with the whole pool, once the other
+        // workers' batches are done (no worker starts a batch meanwhile)
+        S->exclusive = true;
+        S->cv_done.wait(lock, [&] { return S->in_flight == 0; });
+        items.push_back(S->tickets[head].item);
+        ids.push_back(head);
         S->queue.pop_front();
+        arena = S->pool;
+        cap = S->pool_bytes;
+        whole = true;
+      } else {
+        // admit in arrival order while the items' additive workspace bounds
+        // fit this slice (linear in the batch)
+        size_t used = 0;
+        while (!S->queue.empty() && (int)items.size() < S->max_batch) {
+          const uint64_t id = S->queue.front();
+          const size_t need = msk_batch_item_bound(&S->tickets[id].item, S->refine);
+          if (used + need > S->slice) break;
+          used += need;
+          items.push_back(S->tickets[id].item);
+          ids.push_back(id);
+          S->queue.pop_front();
+        }
       }
       if (items.empty()) continue;  // cannot happen: submit refuses oversized requests
       ++S->in_flight;
     }
     infos.assign(items.size(), msk_lstsq_info{});
     const int rc = msk_batch_lstsq(items.data(), (int)items.size(), S->refine, S->tol, S->max_iter,
-                                   infos.data(), arena, S->slice, S->streams[w]);
+                                   infos.data(), arena, cap, S->streams[w]);
     const auto now = Clock::now();
     {
       std::lock_guard<std::mutex> lock(S->mu);
@@ -108,6 +132,7 @@ void worker_loop(Server* S, int w) {
         std::snprintf(S->last_error, sizeof(S->last_error), "batch status %d: %s", rc,
                       msk_last_error());
       --S->in_flight;
+      if (whole) S->exclusive = false;
       S->batches += 1;
       S->solved += (int64_t)ids.size();
     }
@@ -133,8 +158,8 @@ int ms_server_create(size_t mem_budget, int workers, int max_batch, int refine, 
   S->max_iter = max_iter;
   S->max_batch = max_batch;
   S->slice = mem_budget / (size_t)workers / 256 * 256;
-  if (cudaGetDevice(&S->device) != cudaSuccess ||
-      cudaMalloc(&S->pool, S->slice * (size_t)workers) != cudaSuccess) {
+  S->pool_bytes = S->slice * (size_t)workers;
+  if (cudaGetDevice(&S->device) != cudaSuccess || cudaMalloc(&S->pool, S->pool_bytes) != cudaSuccess) {
     delete S;
     return MSK_ENOMEM;
   }
@@ -149,7 +174,7 @@ int ms_server_submit(void* srv, const msk_batch_item* req, uint64_t* ticket) {
   Server* S = static_cast<Server*>(srv);
   if (!S) return -1;
   if (!req || !ticket) return -2;
-  if (msk_batch_workspace(req, 1, S->refine) > S->slice) return MSK_ENOMEM;
+  if (msk_batch_item_bound(req, S->refine) > S->pool_bytes) return MSK_ENOMEM;
   {
     std::lock_guard<std::mutex> lock(S->mu);
     if (S->stopping) return MSK_EBUSY;

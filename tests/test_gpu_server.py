@@ -81,3 +81,27 @@ def test_server_admission_and_refusal(msk):
         assert srv.stats()["batches"] == 3
     finally:
         srv.close()
+
+
+def test_server_request_larger_than_a_worker_share(msk, orc):
+    """A request whose workspace exceeds one worker's share of the budget,
+    but not the budget, is solved alone with the whole pool (no worker starts
+    a batch meanwhile); the small requests around it are solved as usual."""
+    big_A, big_b, _ = inputs.ls_problem(300000, 128, -5, seed=41, dtype=torch.float32, device="cuda")
+    need = msk.msk_batch_item_bound((big_A, big_b, 1))
+    small = [inputs.ls_problem(6000, 16, -3, seed=50 + i, dtype=torch.float32, device="cuda") for i in range(4)]
+    # two workers, each with 3/4 of the big request's bound
+    srv = msk.Server(mem_budget=int(need * 1.5), workers=2, max_batch=4, refine=True, tol=1e-12, max_iter=10)
+    try:
+        reqs = [(A, b) for A, b, _ in small[:2]] + [(big_A, big_b)] + [(A, b) for A, b, _ in small[2:]]
+        xs = [torch.empty(A.shape[1], dtype=torch.float64, device="cuda") for A, _ in reqs]
+        ts = [srv.submit(A, b, 60 + i, x) for i, ((A, b), x) in enumerate(zip(reqs, xs))]
+        srv.wait_all()
+        for (A, b), x, t in zip(reqs, xs, ts):
+            done, info, lat, rc = srv.poll(t)
+            assert done and rc == 0, srv.error()
+            An, bn = A.cpu().numpy(), b.cpu().numpy()
+            ro = orc.relres(An, bn, orc.lstsq_exact(An, bn))
+            assert abs(orc.relres(An, bn, x.cpu().numpy()) - ro) <= 1e-8 * ro
+    finally:
+        srv.close()
