@@ -87,7 +87,7 @@ def test_server_request_larger_than_a_worker_share(msk, orc):
     """A request whose workspace exceeds one worker's share of the budget,
     but not the budget, is solved alone with the whole pool (no worker starts
     a batch meanwhile); the small requests around it are solved as usual."""
-    big_A, big_b, _ = inputs.ls_problem(300000, 128, -5, seed=41, dtype=torch.float32, device="cuda")
+    big_A, big_b, _ = inputs.ls_problem(40000, 128, -5, seed=41, dtype=torch.float32, device="cuda")
     need = msk.msk_batch_item_bound((big_A, big_b, 1))
     small = [inputs.ls_problem(6000, 16, -3, seed=50 + i, dtype=torch.float32, device="cuda") for i in range(4)]
     # two workers, each with 3/4 of the big request's bound
