@@ -83,6 +83,7 @@ size_t tc_gemm_workspace(int64_t p, int64_t k, int64_t ncol, int prec);
 int gemm_stage(uint64_t seed, int64_t p, int64_t k, int64_t ncol, const void* Y, int y_dtype,
                int64_t ldy, int gemm_prec, double* Z, int64_t ldz, void* ws, size_t ws_bytes,
                cudaStream_t st) {
+  StageRange nvtx_range_("gemm_stage");
   const uint64_t gkey = stream_key(seed, kTagGauss);
   if (is_tensor_prec(gemm_prec)) {
     if (y_dtype != MSK_F32) return MSK_ENOTSUP;
@@ -150,6 +151,7 @@ size_t msk_srht_workspace(int64_t d, int64_t n, int with_b, int64_t k) {
 int srht_sketch(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, const double* b,
                 int64_t k, uint64_t seed, double* Y, int64_t ldy, void* ws, size_t ws_bytes,
                 void* stream) {
+  StageRange nvtx_range_("srht_sketch");
   if (!A) return -1;
   if (dtype != MSK_F64 && dtype != MSK_F32) return -2;
   if (d < 2 || (d & (d - 1)) != 0 || d > (int64_t(1) << 26)) return -3;
@@ -172,6 +174,7 @@ size_t msk_cs_workspace(int64_t d, int64_t n, int64_t k, int dtype, int strategy
 int cs_sketch(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, const double* b,
               int64_t k, uint64_t seed, void* Y, int64_t ldy, int strategy, void* ws,
               size_t ws_bytes, void* stream) {
+  StageRange nvtx_range_("cs_sketch");
   return cs_sketch_internal(A, dtype, d, n, lda, b, k, seed, Y, ldy, strategy, ws, ws_bytes,
                             false, as_stream(stream));
 }
@@ -233,6 +236,7 @@ size_t msk_gemm_workspace(int64_t p, int64_t k, int64_t ncol, int gemm_prec) {
 
 int msk_gemm(uint64_t seed, int64_t p, int64_t k, int64_t ncol, const void* Y, int64_t ldy,
              int gemm_prec, double* Z, int64_t ldz, void* ws, size_t ws_bytes, void* stream) {
+  StageRange nvtx_range_("msk_gemm");
   if (p < 1 || p >= (1LL << 24)) return -2;
   if (k < 1) return -3;
   if (ncol < 1) return -4;
@@ -261,6 +265,7 @@ size_t msk_ms_workspace(int64_t d, int64_t n, int with_b, int64_t k, int64_t p, 
 int ms_sketch(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, const double* b,
               int64_t k, int64_t p, uint64_t seed, int gemm_prec, void* Z, int64_t ldz,
               int strategy, void* ws, size_t ws_bytes, void* stream) {
+  StageRange nvtx_range_("ms_sketch");
   if (!A && d > 0 && n > 0) return -1;
   if (dtype != MSK_F64 && dtype != MSK_F32) return -2;
   if (d < 0) return -3;
@@ -304,6 +309,7 @@ int ms_sketch(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, const
 int ms_sketch_rows(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, const double* b,
                    int64_t row0, int64_t k, int64_t p, uint64_t seed, int gemm_prec, double* Z,
                    int64_t ldz, void* ws, size_t ws_bytes, void* stream) {
+  StageRange nvtx_range_("ms_sketch_rows");
   if (!A && d > 0 && n > 0) return -1;
   if (dtype != MSK_F64 && dtype != MSK_F32) return -2;
   if (d < 0) return -3;
@@ -370,6 +376,7 @@ size_t msk_ms_host_workspace(int64_t d, int64_t n, int with_b, int64_t k, int64_
 int ms_sketch_host(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, const double* b,
                    int64_t k, int64_t p, uint64_t seed, int gemm_prec, double* Z, int64_t ldz,
                    int64_t chunk_rows, void* ws, size_t ws_bytes, void* stream) {
+  StageRange nvtx_range_("ms_sketch_host");
   if (!A && d > 0 && n > 0) return -1;
   if (dtype != MSK_F64 && dtype != MSK_F32) return -2;
   if (d < 0) return -3;

@@ -601,6 +601,7 @@ size_t msk_batch_item_bound(const msk_batch_item* item, int refine) {
 int msk_batch_lstsq(const msk_batch_item* items, int nitems, int refine, double tol,
                     int32_t max_iter, msk_lstsq_info* infos, void* ws, size_t ws_bytes,
                     void* stream) {
+  StageRange nvtx_range_("msk_batch_lstsq");
   if (!items) return -1;
   if (nitems < 1) return -2;
   if (refine != 0 && refine != 1) return -3;

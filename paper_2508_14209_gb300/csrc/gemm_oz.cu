@@ -54,8 +54,6 @@
 
 namespace msk {
 
-extern __device__ int g_tc_timeout;
-
 constexpr int kOzSlices = 8;      // slices of each operand; levels 0..7 kept
 constexpr int kOzGroups = 4;      // G-slice groups {0,7} {1,6} {2,5} {3,4}
 constexpr int kOzBM = 128;        // M per CTA (one UMMA M)
@@ -205,13 +203,14 @@ __global__ void oz_split_y_kernel(const double* __restrict__ Y, int64_t ldy, int
 // the Y tiles of slices 0 .. 7 - ja with TMA through a ring of stages;
 // warp 1 lane 0 issues the MMAs into the level accumulators (TMEM columns
 // (level - ja) * NT); then all four warps read the 128 rows back.  Every
-// mbarrier wait is bounded (1 s): on expiry the kernel records g_tc_timeout,
+// mbarrier wait is bounded (1 s): on expiry the kernel sets *timeout_flag
+// (the tensor-core kernels' flag, reported by msk_take_timeout),
 // waits (bounded) for its copies in flight, frees its tensor memory and
 // returns.
 __global__ void __launch_bounds__(kOzThreads, 1)
     oz_gemm_kernel(const __grid_constant__ CUtensorMap tmG, const __grid_constant__ CUtensorMap tmY,
                    int p, int ncol, int NT, int KT, int kt_per, uint32_t idesc,
-                   longlong2* __restrict__ part) {
+                   longlong2* __restrict__ part, int* timeout_flag) {
   extern __shared__ __align__(1024) unsigned char oz_smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(oz_smem_raw) + 1023) & ~uintptr_t(1023));
@@ -262,7 +261,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     for (int it = 0; it < nk; ++it) {
       const int s = it % stages;
       if (it >= stages &&
-          !mbar_wait(smem_u32(&bars[stages + s]), ((it / stages) & 1) ^ 1, &g_tc_timeout)) {
+          !mbar_wait(smem_u32(&bars[stages + s]), ((it / stages) & 1) ^ 1, timeout_flag)) {
         *abort_flag = 1;
         break;
       }
@@ -279,11 +278,11 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     }
     if (*abort_flag)
       for (int it = (issued > stages ? issued - stages : 0); it < issued; ++it)
-        mbar_wait(smem_u32(&bars[it % stages]), (it / stages) & 1, &g_tc_timeout);
+        mbar_wait(smem_u32(&bars[it % stages]), (it / stages) & 1, timeout_flag);
   } else if (warp == 1 && lane == 0) {
     for (int it = 0; it < nk; ++it) {
       const int s = it % stages;
-      if (!mbar_wait(smem_u32(&bars[s]), (it / stages) & 1, &g_tc_timeout)) {
+      if (!mbar_wait(smem_u32(&bars[s]), (it / stages) & 1, timeout_flag)) {
         *abort_flag = 1;
         break;
       }
@@ -311,7 +310,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     umma_commit(smem_u32(&bars[2 * stages]));
   }
   __syncwarp();
-  const bool done = mbar_wait(smem_u32(&bars[2 * stages]), 0, &g_tc_timeout);
+  const bool done = mbar_wait(smem_u32(&bars[2 * stages]), 0, timeout_flag);
   tc_fence_after();
   if (__all_sync(0xffffffffu, done && !*abort_flag && nk > 0)) {
     // Level sums are exact integers below 2^24: combined exactly as
@@ -496,9 +495,12 @@ int launch_oz_gemm(uint64_t gkey, int64_t p, int64_t k, int64_t ncol, const doub
   const size_t big = 2 * (size_t)kOzBM * kOzBK * 2 + (size_t)kOzSlices * t.NT * kOzBK * 2;
   const size_t smem = std::min<size_t>((size_t)kTcSmemBudget, std::max<size_t>(2 * big, 3 * big)) + 1024 + 256;
   MSK_ALLOW_SMEM(oz_gemm_kernel);
+  int* tflag = nullptr;
+  const int frc = tc_timeout_flag(&tflag);
+  if (frc) return frc;
   dim3 grid((unsigned)t.Mt, (unsigned)t.Nt, (unsigned)(kOzGroups * t.S));
   oz_gemm_kernel<<<grid, kOzThreads, smem, st>>>(tmG, tmY, (int)p, (int)ncol, t.NT, t.KT, t.kt_per, idesc,
-                                                 part);
+                                                 part, tflag);
   MSK_CHECK_LAUNCH("oz_gemm_kernel");
   const int64_t total = p * ncol;
   oz_reduce_kernel<<<(unsigned)((total + 31) / 32), dim3(32, 8), 0, st>>>(part, kOzGroups * t.S, p, ncol, eG, eY,

@@ -643,6 +643,23 @@ int launch_tc_wait_selftest(cudaStream_t st) {
   return MSK_OK;
 }
 
+// Device address of the timeout flag, for kernels of other files (looked up
+// once per device and context with that device current).
+int tc_timeout_flag(int** out) {
+  constexpr int kMaxDev = 64;
+  static int* addr[kMaxDev] = {nullptr};
+  int dev = 0;
+  MSK_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDev) return MSK_ENOTSUP;
+  if (!addr[dev]) {
+    void* p = nullptr;
+    MSK_CUDA(cudaGetSymbolAddress(&p, g_tc_timeout));
+    addr[dev] = static_cast<int*>(p);
+  }
+  *out = addr[dev];
+  return MSK_OK;
+}
+
 // Reads and clears the timeout flag of the tensor-core kernel (synchronises).
 int tc_take_timeout(cudaStream_t st) {
   int h = 0, zero = 0;

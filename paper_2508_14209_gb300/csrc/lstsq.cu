@@ -629,6 +629,7 @@ int ms_lstsq(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, const 
              int64_t k, int64_t p, uint64_t seed, int gemm_prec, int refine, double tol,
              int32_t max_iter, double* x, msk_lstsq_info* info, void* ws, size_t ws_bytes,
              void* stream) {
+  StageRange nvtx_range_("ms_lstsq");
   if (!A) return -1;
   if (dtype != MSK_F64 && dtype != MSK_F32) return -2;
   if (d < n) return -3;
@@ -795,6 +796,7 @@ size_t msk_sns_workspace(int64_t d, int64_t n, int kind, int64_t k, int64_t p, i
 int sns_lstsq(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, const double* b,
               int kind, int64_t k, int64_t p, uint64_t seed, double* x, msk_lstsq_info* info,
               void* ws, size_t ws_bytes, void* stream) {
+  StageRange nvtx_range_("sns_lstsq");
   if (kind == MSK_SKETCH_MULTI)
     return ms_lstsq(A, dtype, d, n, lda, b, k, p, seed, MSK_GEMM_F64, 0, 0.0, 0, x, info, ws,
                     ws_bytes, stream);
@@ -898,6 +900,7 @@ size_t msk_rcq_workspace(int64_t d, int64_t n, int64_t k, int64_t p, int dtype, 
 int rcq_lstsq(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, const double* b,
               int64_t k, int64_t p, uint64_t seed, int gemm_prec, double* x, msk_lstsq_info* info,
               void* ws, size_t ws_bytes, void* stream) {
+  StageRange nvtx_range_("rcq_lstsq");
   int rc = rcq_args(A, dtype, d, n, lda, k, p, gemm_prec);
   if (rc) return rc;
   if (!b) return -6;
@@ -957,6 +960,7 @@ int rcq_lstsq(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, const
 int rcq_qr(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, int64_t k, int64_t p,
            uint64_t seed, int gemm_prec, double* Q, int64_t ldq, double* R, int64_t ldr, void* ws,
            size_t ws_bytes, void* stream) {
+  StageRange nvtx_range_("rcq_qr");
   int rc = rcq_args(A, dtype, d, n, lda, k, p, gemm_prec);
   if (rc) return rc;
   if (!Q) return -10;
@@ -1011,6 +1015,7 @@ size_t msk_ne_workspace(int64_t d, int64_t n) {
 
 int ne_lstsq(const double* A, int64_t d, int64_t n, int64_t lda, const double* b, double* x,
              void* ws, size_t ws_bytes, void* stream) {
+  StageRange nvtx_range_("ne_lstsq");
   if (!A) return -1;
   if (d < n) return -2;
   if (n < 1 || n > 4096) return -3;

@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstddef>
 #include <cstdint>
@@ -29,6 +30,15 @@ void set_error_text(const char* msg);
   } while (0)
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Named host range around an entry point or stage, for profilers that read
+// NVTX (header-only; nothing happens unless such a tool is attached).
+struct StageRange {
+  explicit StageRange(const char* name) { nvtxRangePushA(name); }
+  ~StageRange() { nvtxRangePop(); }
+  StageRange(const StageRange&) = delete;
+  StageRange& operator=(const StageRange&) = delete;
+};
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -151,6 +161,8 @@ int tc_ds_make_job(int64_t p, int64_t k, int64_t ncol, const TcShape& s, const v
                    const void* Yt, double* part, int item_begin, TcJob* job);
 int launch_tc_ds_batch(const TcJob* jobs, int njobs, int total_items, int max_nt, cudaStream_t st);
 int tc_take_timeout(cudaStream_t st);
+// Device address of that flag (for the tensor-core kernels of other files).
+int tc_timeout_flag(int** out);
 int launch_tc_wait_selftest(cudaStream_t st);
 // gemm_tc.cu (tcgen05 tensor-core Gaussian stage)
 size_t tc_gemm_workspace(int64_t p, int64_t k, int64_t ncol, int prec);

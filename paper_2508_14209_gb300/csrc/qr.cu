@@ -195,6 +195,7 @@ using namespace msk;
 extern "C" {
 
 int msk_householder_qr(double* W, int64_t m, int64_t c, int64_t ldw, void* stream) {
+  StageRange nvtx_range_("msk_householder_qr");
   if (!W) return -1;
   if (m < c || m > 0x7fffffffLL) return -2;
   if (c < 1 || c > kQrMaxCols) return -3;
