@@ -298,6 +298,20 @@ int msk_householder_qr(double *W, int64_t m, int64_t c, int64_t ldw,
 int msk_trsv_upper(const double *R, int64_t n, int64_t ldr, const double *rhs,
                    double *x, void *stream);
 
+/* ---- Checked builds ------------------------------------------------------ */
+
+/* 1 when this library was built with device-side index checks (MSK_CHECKED:
+ * CountSketch buckets, the sliced FP64 stage's fixed-point ranges, the batch
+ * tables; a failed check skips the access and records its site), else 0.
+ * The paper has no counterpart: this stands in for a memory checker. */
+int msk_checked_build(void);
+
+/* Synchronise `stream`; return and clear the site of the first failed index
+ * check since the last call (1 CountSketch bucket, 2 fixed-point range of the
+ * sliced FP64 stage, 3 batch tables), 0 when none failed (always 0 in builds
+ * without checks), or MSK_ECUDA. */
+int msk_check_status(void *stream);
+
 /* Size of the fixed scratch array behind msk_gemm_noalloc (64 MiB). */
 #define MSK_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
 

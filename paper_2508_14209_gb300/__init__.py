@@ -19,7 +19,9 @@ import os
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libmsketch.so")
+# The library the binding loads: libmsketch.so, or another build of it (the
+# checked build, libmsketch_checked.so) named by MSK_LIB.
+LIB_PATH = os.environ.get("MSK_LIB") or os.path.join(_HERE, "libmsketch.so")
 
 MSK_F64, MSK_F32 = 0, 1
 GEMM_F64, GEMM_F32, GEMM_BF16, GEMM_F16, GEMM_BF16X3 = 0, 1, 2, 3, 4
@@ -31,7 +33,7 @@ GEMM_PRECS = {"f64": GEMM_F64, "f32": GEMM_F32, "bf16": GEMM_BF16, "f16": GEMM_F
               "bf16x3": GEMM_BF16X3}
 
 # Names of every function include/msketch.h declares (checked by the tests).
-EXPORTS = ("msk_version", "msk_last_error", "msk_take_timeout", "msk_selftest_wait", "cs_hash", "ms_gaussian", "msk_cs_workspace",
+EXPORTS = ("msk_version", "msk_last_error", "msk_checked_build", "msk_check_status", "msk_take_timeout", "msk_selftest_wait", "cs_hash", "ms_gaussian", "msk_cs_workspace",
            "cs_sketch", "msk_ms_workspace", "ms_sketch", "msk_gemm_workspace", "msk_gemm",
            "msk_householder_qr", "msk_trsv_upper", "msk_lstsq_workspace", "ms_lstsq",
            "msk_ne_workspace", "ne_lstsq", "msk_rcq_workspace", "rcq_lstsq", "rcq_qr",
@@ -87,6 +89,8 @@ def _declare(L):
         "msk_version": (ctypes.c_char_p, []),
         "msk_last_error": (ctypes.c_char_p, []),
         "msk_take_timeout": (_int, [_p]),
+        "msk_checked_build": (_int, []),
+        "msk_check_status": (_int, [_p]),
         "msk_selftest_wait": (_int, [_p]),
         "cs_hash": (_int, [_u64, _i64, _i64, _i64, _p, _p, _p]),
         "ms_gaussian": (_int, [_u64, _i64, _i64, _int, _p, _i64, _p]),
@@ -165,6 +169,19 @@ def msk_take_timeout(stream=None) -> int:
     """Synchronise the stream; MSK_ETIMEOUT if a pipelined kernel gave up a
     bounded wait since the last call (the record is cleared), else MSK_OK."""
     return int(load().msk_take_timeout(_stream(stream)))
+
+
+def msk_checked_build() -> bool:
+    """True when the loaded library was built with device-side index checks."""
+    return bool(load().msk_checked_build())
+
+
+def msk_check_status(stream=None) -> int:
+    """Site of the first failed index check since the last call (0: none)."""
+    rc = load().msk_check_status(_stream(stream))
+    if rc < 0 or rc == MSK_ECUDA:
+        _check("msk_check_status", rc)
+    return rc
 
 
 def msk_selftest_wait(stream=None) -> None:

@@ -1,5 +1,10 @@
 """Build libmsketch.so in-tree: every csrc/*.cu compiled for sm_103a by nvcc
-(in parallel), linked into one shared library next to this file."""
+(in parallel), linked into one shared library next to this file.
+
+build(checked=True) builds libmsketch_checked.so instead: the same sources
+with MSK_CHECKED defined (device-side index checks that record a failed
+check's site, read by msk_check_status) and relocatable device code, so that
+every file's kernels reach the one check flag."""
 from __future__ import annotations
 
 import glob
@@ -13,6 +18,9 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 BUILD_DIR = os.path.join(ROOT, "_build", "msketch")
 LIB = os.path.join(HERE, "libmsketch.so")
+CHECKED_DIR = os.path.join(ROOT, "_build", "msketch_checked")
+CHECKED_LIB = os.path.join(HERE, "libmsketch_checked.so")
+CHECKED_FLAGS = ["-DMSK_CHECKED", "-rdc=true"]
 
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -36,12 +44,12 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def _compile(src, verbose):
-    obj = os.path.join(BUILD_DIR, os.path.basename(src) + ".o")
+def _compile(src, verbose, out_dir=BUILD_DIR, extra=()):
+    obj = os.path.join(out_dir, os.path.basename(src) + ".o")
     if not _stale(obj, [src] + _headers()):
         return obj
     if src.endswith(".cu"):
-        cmd = [NVCC, *ARCH, *FLAGS, "-c", src, "-o", obj]
+        cmd = [NVCC, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
     else:
         cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-I", "/usr/local/cuda/include",
                "-I", os.path.join(ROOT, "include"), "-c", src, "-o", obj]
@@ -53,23 +61,25 @@ def _compile(src, verbose):
     return obj
 
 
-def build(verbose: bool = False, jobs: int | None = None) -> str:
-    os.makedirs(BUILD_DIR, exist_ok=True)
+def build(verbose: bool = False, jobs: int | None = None, checked: bool = False) -> str:
+    out_dir, lib = (CHECKED_DIR, CHECKED_LIB) if checked else (BUILD_DIR, LIB)
+    extra = CHECKED_FLAGS if checked else []
+    os.makedirs(out_dir, exist_ok=True)
     srcs = _sources()
     jobs = jobs or min(len(srcs), os.cpu_count() or 4)
     with ThreadPoolExecutor(max_workers=jobs) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose), srcs))
-    if _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-lcuda"]
+        objs = list(ex.map(lambda s: _compile(s, verbose, out_dir, extra), srcs))
+    if _stale(lib, objs):
+        tmp = lib + f".tmp{os.getpid()}"
+        cmd = [NVCC, *ARCH, *extra, "-shared", "-o", tmp, *objs, "-lcuda"]
         if verbose:
             print(" ".join(cmd), flush=True)
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed\n{r.stdout}\n{r.stderr}")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(verbose="-v" in sys.argv))
+    print(build(verbose="-v" in sys.argv, checked="--checked" in sys.argv))

@@ -77,6 +77,10 @@ static int ms_y_dtype(int dtype, int gemm_prec) {
 }  // namespace msk
 
 namespace msk {
+// First failed index check of a checked build (its site), 0 otherwise; the
+// kernels of other files reach it only in checked builds (relocatable device
+// code).
+__device__ int g_msk_check = 0;
 size_t tc_gemm_workspace(int64_t p, int64_t k, int64_t ncol, int prec);
 // Z = G Y for a Y of element type y_dtype (FP64 or FP32); the tensor-core
 // precisions take FP32 Y only.
@@ -113,6 +117,22 @@ using namespace msk;
 extern "C" {
 
 const char* msk_version(void) { return "msketch 0.1 (sm_103a)"; }
+
+int msk_checked_build(void) {
+#ifdef MSK_CHECKED
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+int msk_check_status(void* stream) {
+  MSK_CUDA(cudaStreamSynchronize(as_stream(stream)));
+  int h = 0, zero = 0;
+  MSK_CUDA(cudaMemcpyFromSymbol(&h, g_msk_check, sizeof(int)));
+  if (h) MSK_CUDA(cudaMemcpyToSymbol(g_msk_check, &zero, sizeof(int)));
+  return h;
+}
 
 const char* msk_last_error(void) { return g_last_error; }
 

@@ -190,6 +190,7 @@ __global__ void __launch_bounds__(kP32Threads, pass32_ctas_per_sm(NC))
   }
   const int j = mem[lo];
   const BatchJob& J = jobs[j];
+  MSK_CHECK_OR(lo >= 0 && lo < nmem && J.chunk_begin <= c, kCheckBatch, return);
   const int lc = c - J.chunk_begin;
   if (lc >= J.nchunks) return;
   if (RESID) {

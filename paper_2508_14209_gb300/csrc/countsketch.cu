@@ -131,6 +131,7 @@ __global__ void __launch_bounds__(kCsThreads) cs_atomic_kernel(const CsParams<T>
       const int r = warp + rr * kCsWarps;
       if (i0 + r >= P.d) break;
       const uint64_t z = hz[buf * kCsRows + r];
+      MSK_CHECK_OR(bucket_of(z, P.k) < P.k, kCheckBucket, continue);
       T* yrow = P.Y + (int64_t)bucket_of(z, P.k) * P.ldy;
       const bool neg = negative_of(z);
       const T* trow = tile + r * P.pitch;
@@ -250,7 +251,9 @@ __global__ void __launch_bounds__(kCsThreads) cs_bulk_f64_kernel(const CsParams<
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
-      if (row_ok) {
+      bool bucket_ok = true;
+      MSK_CHECK_OR(bucket_of(z, P.k) < P.k, kCheckBucket, bucket_ok = false);
+      if (row_ok && bucket_ok) {
         double* yrow = P.Y + (int64_t)bucket_of(z, P.k) * P.ldy;
         const uint32_t src = (uint32_t)__cvta_generic_to_shared(tile + lane * P.pitch);
         if (nbulk > 0)
@@ -357,6 +360,7 @@ __global__ void __launch_bounds__(kCsThreads) cs_fixed_f64_kernel(const CsParams
       const int r = warp + rr * kCsWarps;
       if (i0 + r >= P.d) break;
       const uint64_t z = hz[buf][r];
+      MSK_CHECK_OR(bucket_of(z, P.k) < P.k, kCheckBucket, continue);
       double* yrow = P.Y + (int64_t)bucket_of(z, P.k) * P.ldy;
       const unsigned long long sg = negative_of(z) ? 0x8000000000000000ull : 0ull;
 #pragma unroll
@@ -430,6 +434,7 @@ __global__ void __launch_bounds__(kCsThreads) cs_narrow_f64_kernel(const CsParam
       const int r = r0 + lane / NCA;
       if (i0 + r < P.d) {
         const uint64_t z = hz[buf][r];
+        MSK_CHECK_OR(bucket_of(z, P.k) < P.k, kCheckBucket, continue);
         double* yrow = ybase + (int64_t)bucket_of(z, P.k) * P.ldy;
         const unsigned long long sg = negative_of(z) ? 0x8000000000000000ull : 0ull;
         if (c < nca) red_add(yrow + c, flip(tiles[buf][r][c], sg));
@@ -500,6 +505,7 @@ struct CsF32Tile {
       const int cl = lane % LPR;
       const bool ok = i0 + r < P.d;
       const uint64_t z = sm.hz[buf][r];
+      MSK_CHECK_OR(bucket_of(z, P.k) < P.k, kCheckBucket, continue);
       float* yrow = P.Y + (int64_t)bucket_of(z, P.k) * P.ldy;
       const unsigned sg = negative_of(z) ? 0x80000000u : 0u;
       if (ok) {

@@ -13,9 +13,8 @@
 //   G[r][i] = 2^(eG - 7)   (g_0 + g_1 2^-8 + ... + g_7 2^-56) + rest_G,
 //   Y[i][c] = 2^(eY_c - 7) (y_0 + y_1 2^-8 + ... + y_7 2^-56) + rest_Y,
 // g_j, y_l integers in [-128, 128] (exact in bfloat16), |rest| at most half
-// a unit of the last slice.  Each slice is the round-to-nearest integer of
-// what the previous ones left, times 2^8; every step is exact in the
-// operand's own precision (binary32 for G, binary64 for Y).
+// a unit of the last slice: each operand is rounded once to 64-bit fixed
+// point, whose balanced base-256 digits are the slices (exact).
 //
 // Products.  g_j y_l is an integer of magnitude <= 2^14, exact in the tensor
 // core's FP32 accumulator, and so is every partial sum of up to 1024 of them
@@ -89,30 +88,29 @@ __device__ __forceinline__ long long oz_fixed_f32(float g, int e) {
   const long long X = oz_shift_round(m, (E ? E : 1) - 150 + 63 - e);  // g = m 2^(E - 150)
   return (bits >> 31) ? -X : X;
 }
-// bfloat16 bits of an integer q with |q| <= 128 (exact), by integer
-// operations (the integer-to-float conversions run on a slow pipe).
-__device__ __forceinline__ uint16_t oz_bf16_of_int(int q) {
-  if (q == 0) return 0;
-  const unsigned a = (unsigned)(q < 0 ? -q : q);
-  const int e = 31 - __clz(a);  // 0 .. 7
-  const unsigned mant = (a << (7 - e)) & 0x7Fu;
-  return (uint16_t)((q < 0 ? 0x8000u : 0u) | ((unsigned)(e + 127) << 7) | mant);
+// bfloat16 bits of the integer e - 128 (0 <= e <= 256): 2^23 + 2^22 + e - 128
+// assembled as binary32 bits, less 1.5 2^23 (exact, FP32 add), whose top 16
+// bits are the bfloat16 (the value has at most 8 significant bits).  One
+// integer add, one FP32 add and one shift: no conversion instruction.
+__device__ __forceinline__ uint16_t oz_bf16_of_biased(unsigned e) {
+  return (uint16_t)(__float_as_uint(__uint_as_float(0x4B3FFF80u + e) - 12582912.0f) >> 16);
 }
-// The eight slices of X, as bfloat16 bits: X = sum_l s_l 2^(56 - 8 l), s_l
-// the nearest integer to what the previous slices left over 2^(56 - 8 l)
-// (ties upward), in [-128, 128]; the last one takes the remainder, in
-// [-128, 127].
+// The eight slices of X as bfloat16 bits: X = sum_l s_l 2^(56 - 8 l) exactly,
+// with balanced base-256 digits.  Adding 128 to each of the low seven bytes
+// (0x0080808080808080, carries included) turns them into the digits s_1..s_7
+// plus 128, in [0, 255]; the carry out of byte 6 goes to s_0 = (X >> 56) +
+// carry, in [-128, 128].
 __device__ __forceinline__ void oz_slices(long long X, uint16_t (&s)[kOzSlices]) {
-  unsigned long long r = (unsigned long long)X;
-#pragma unroll
-  for (int l = 0; l < kOzSlices - 1; ++l) {
-    const int sh = 56 - 8 * l;
-    const long long rs = (long long)r;
-    const long long q = (rs >> sh) + ((rs >> (sh - 1)) & 1);
-    s[l] = oz_bf16_of_int((int)q);
-    r -= (unsigned long long)q << sh;
-  }
-  s[kOzSlices - 1] = oz_bf16_of_int((int)(long long)r);
+  const unsigned long long L = ((unsigned long long)X & 0x00FFFFFFFFFFFFFFull) + 0x0080808080808080ull;
+  const unsigned lo = (unsigned)L, hi = (unsigned)(L >> 32);
+  s[0] = oz_bf16_of_biased((unsigned)((int)(X >> 56) + (int)(hi >> 24) + 128));
+  s[1] = oz_bf16_of_biased((hi >> 16) & 0xFFu);
+  s[2] = oz_bf16_of_biased((hi >> 8) & 0xFFu);
+  s[3] = oz_bf16_of_biased(hi & 0xFFu);
+  s[4] = oz_bf16_of_biased(lo >> 24);
+  s[5] = oz_bf16_of_biased((lo >> 16) & 0xFFu);
+  s[6] = oz_bf16_of_biased((lo >> 8) & 0xFFu);
+  s[7] = oz_bf16_of_biased(lo & 0xFFu);
 }
 
 // G slices: entry (r, i) is the same binary32 number the Gaussian kernel
@@ -126,6 +124,7 @@ __global__ void oz_split_g_kernel(uint64_t key, int64_t p, int64_t k, float sqrt
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < k;
          c += (int64_t)gridDim.x * blockDim.x) {
       const float g = __fdiv_rn(gauss_std(key, (uint64_t)(r * k + c)), sqrt_p);
+      MSK_CHECK_OR(fabsf(g) < ldexpf(1.0f, eG), kCheckSlice, continue);
       uint16_t sl[kOzSlices];
       oz_slices(oz_fixed_f32(g, eG), sl);
       uint16_t* out = reinterpret_cast<uint16_t*>(Gs) + r * kpitch + c;
@@ -189,6 +188,7 @@ __global__ void oz_split_y_kernel(const double* __restrict__ Y, int64_t ldy, int
     const int n = n0 + r;
     const int64_t i = k0 + tx;
     if (n >= npad || i >= k) continue;
+    MSK_CHECK_OR(n >= ncol || fabs(tile[tx][r]) < ldexp(1.0, oz_exp_of(mx[n])), kCheckSlice, continue);
     const long long X = n < ncol ? oz_fixed_f64(tile[tx][r], oz_exp_of(mx[n])) : 0;
     uint16_t sl[kOzSlices];
     oz_slices(X, sl);

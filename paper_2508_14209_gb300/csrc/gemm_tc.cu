@@ -30,6 +30,7 @@
 #include <algorithm>
 #include <cstdint>
 
+#include "msk_device.cuh"
 #include "msk_internal.h"
 #include "msk_tc.cuh"
 
@@ -355,6 +356,7 @@ __global__ void __launch_bounds__(kDsThreads, 1)
     if (jobs[mid].item_begin <= b) lo = mid; else hi = mid - 1;
   }
   const TcJob& J = jobs[lo];
+  MSK_CHECK_OR(J.item_begin <= b, kCheckBatch, return);
   const int local = b - J.item_begin;
   const int mt = local % J.Mt, nt = (local / J.Mt) % J.Nt, sidx = local / (J.Mt * J.Nt);
   if (threadIdx.x == 0) {

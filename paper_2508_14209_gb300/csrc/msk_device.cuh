@@ -34,6 +34,25 @@ __host__ __device__ __forceinline__ uint64_t draw(uint64_t key, uint64_t i) {
   return mix64(key + (i + 1) * kGamma);
 }
 
+// Checked builds (compiled with MSK_CHECKED): a failed index check records
+// its site in g_msk_check (the first one stays) and the guarded access is
+// skipped; msk_check_status reports and clears it.  Other builds evaluate
+// nothing.  Sites:
+constexpr int kCheckBucket = 1;  // CountSketch bucket h(i) < k
+constexpr int kCheckSlice = 2;   // sliced FP64 stage: |G| < 2^eG, |Y[:,c]| < 2^eY_c
+constexpr int kCheckBatch = 3;   // batch tables: problem and chunk indices
+#ifdef MSK_CHECKED
+extern __device__ int g_msk_check;
+__device__ __forceinline__ bool msk_index_ok(bool cond, int site) {
+  if (!cond) atomicCAS(&g_msk_check, 0, site);
+  return cond;
+}
+#define MSK_CHECK_OR(cond, site, action) \
+  if (!::msk::msk_index_ok((cond), (site))) action
+#else
+#define MSK_CHECK_OR(cond, site, action)
+#endif
+
 // Bucket in [0,k) from the top 32 bits (multiply-shift), sign from bit 0.
 __device__ __forceinline__ uint32_t bucket_of(uint64_t z, uint32_t k) {
   return (uint32_t)(((z >> 32) * (uint64_t)k) >> 32);
