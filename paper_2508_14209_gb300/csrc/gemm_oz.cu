@@ -321,24 +321,30 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     const int row = m0 + warp * 32 + lane;
     longlong2* out = part + (int64_t)blockIdx.z * p * ncol;
     const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-    for (int c0 = 0; c0 < NT; c0 += 16) {
-      long long H[16], L[16];
+    // 8 columns at a time: every level's load issued before one wait
+    for (int c0 = 0; c0 < NT; c0 += 8) {
+      uint32_t v[kOzSlices][8];
 #pragma unroll
-      for (int q = 0; q < 16; ++q) H[q] = L[q] = 0;
-      for (int lev = 0; lev < nlev; ++lev) {
+      for (int lev = 0; lev < kOzSlices; ++lev)
+        if (lev < nlev) tmem_ld8_nowait(lane_base + (uint32_t)(lev * NT + c0), v[lev]);
+      tmem_wait_ld();
+      long long H[8], L[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) H[q] = L[q] = 0;
+#pragma unroll
+      for (int lev = 0; lev < kOzSlices; ++lev) {
+        if (lev >= nlev) break;
         const int s = ja + lev;  // this accumulator's level
-        uint32_t v[16];
-        tmem_ld16(lane_base + (uint32_t)(lev * NT + c0), v);
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const long long x = (long long)__float2int_rn(__uint_as_float(v[q]));  // exact
+        for (int q = 0; q < 8; ++q) {
+          const long long x = (long long)__float2int_rn(__uint_as_float(v[lev][q]));  // exact
           if (s < 4) H[q] += x * (1LL << (8 * (3 - s)));
           else L[q] += x * (1LL << (8 * (7 - s)));
         }
       }
       if (row < p) {
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
+        for (int q = 0; q < 8; ++q) {
           const int col = n0 + c0 + q;
           if (col < ncol) out[(int64_t)col * p + row] = make_longlong2(H[q], L[q]);
         }
