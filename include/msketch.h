@@ -217,6 +217,10 @@ size_t msk_ms_workspace(int64_t d, int64_t n, int with_b, int64_t k, int64_t p,
 /* Z = G (S [A b]): CountSketch to k rows, then the p x k Gaussian G
  * (Section 1 "Count-Gauss"; Section 6.2 uses k = 2n^2).  A, b, dtype, k,
  * seed, strategy as in cs_sketch; the Gaussian uses the same seed (tag 2).
+ * With the FP64 Gaussian stage on the tensor cores (gemm_prec F64, k >=
+ * 1024), G's slices are sampled on a library side stream while the
+ * CountSketch runs on `stream`, which waits for them before the stage (the
+ * call stays ordered on `stream`, and can be captured).
  *   gemm_prec : msk_gemm_prec, the arithmetic of Z = G Y.
  *   Z : device double, column-major p x ncol, leading dimension ldz >= p.
  * Errors: -1 A NULL (with d, n > 0), -2 bad dtype, -3 d < 0, -4 n < 0 or
@@ -231,6 +235,13 @@ int ms_sketch(const void *A, int dtype, int64_t d, int64_t n, int64_t lda,
               const double *b, int64_t k, int64_t p, uint64_t seed,
               int gemm_prec, void *Z, int64_t ldz, int strategy, void *ws,
               size_t ws_bytes, void *stream);
+
+/* Profiling hook: the next ms_sketch call of the calling thread records
+ * before_cs and after_cs (cudaEvent_t handles, or NULL) on its stream right
+ * before and right after its CountSketch, so that the CountSketch's own time
+ * can be read inside a timed loop of whole multisketch calls; the hook is
+ * then cleared.  Always returns MSK_OK.  The paper has no counterpart. */
+int msk_stage_events(void *before_cs, void *after_cs);
 
 /* ms_sketch of a row block of a taller [A b] (Section 7's block-row
  * distribution): A, b hold rows row0 .. row0+d-1 of the full matrix, and

@@ -33,7 +33,7 @@ GEMM_PRECS = {"f64": GEMM_F64, "f32": GEMM_F32, "bf16": GEMM_BF16, "f16": GEMM_F
               "bf16x3": GEMM_BF16X3}
 
 # Names of every function include/msketch.h declares (checked by the tests).
-EXPORTS = ("msk_version", "msk_last_error", "msk_checked_build", "msk_check_status", "msk_take_timeout", "msk_selftest_wait", "cs_hash", "ms_gaussian", "msk_cs_workspace",
+EXPORTS = ("msk_version", "msk_last_error", "msk_checked_build", "msk_check_status", "msk_stage_events", "msk_take_timeout", "msk_selftest_wait", "cs_hash", "ms_gaussian", "msk_cs_workspace",
            "cs_sketch", "msk_ms_workspace", "ms_sketch", "msk_gemm_workspace", "msk_gemm",
            "msk_householder_qr", "msk_trsv_upper", "msk_lstsq_workspace", "ms_lstsq",
            "msk_ne_workspace", "ne_lstsq", "msk_rcq_workspace", "rcq_lstsq", "rcq_qr",
@@ -90,6 +90,7 @@ def _declare(L):
         "msk_last_error": (ctypes.c_char_p, []),
         "msk_take_timeout": (_int, [_p]),
         "msk_checked_build": (_int, []),
+        "msk_stage_events": (_int, [_p, _p]),
         "msk_check_status": (_int, [_p]),
         "msk_selftest_wait": (_int, [_p]),
         "cs_hash": (_int, [_u64, _i64, _i64, _i64, _p, _p, _p]),
@@ -342,9 +343,17 @@ def msk_ms_workspace(d, n, with_b, k, p, dtype, gemm_prec, strategy=CS_ATOMIC):
     return load().msk_ms_workspace(d, n, int(with_b), k, p, dtype, gemm_prec, strategy)
 
 
+def _event_handle(ev, stream):
+    """The cudaEvent_t of a torch.cuda.Event (created by one record if new)."""
+    if not ev.cuda_event:
+        ev.record(stream)
+    return ctypes.c_void_p(ev.cuda_event)
+
+
 def ms_sketch(A, k, p, seed, b=None, gemm_prec=GEMM_F64, Z=None, strategy=CS_ATOMIC, ws=None,
-              stream=None):
-    """Z = G S [A b] (p x ncol, column-major FP64)."""
+              stream=None, cs_events=None):
+    """Z = G S [A b] (p x ncol, column-major FP64).  cs_events: optional pair
+    of torch.cuda.Event recorded around the call's CountSketch."""
     _cuda(A, "A"), _cuda(b, "b")
     d, n = A.shape
     lda = _colmajor(A)
@@ -355,6 +364,9 @@ def ms_sketch(A, k, p, seed, b=None, gemm_prec=GEMM_F64, Z=None, strategy=CS_ATO
     need = msk_ms_workspace(d, n, b is not None, k, p, dt, gemm_prec, strategy)
     if ws is None:
         ws = workspace(need, A.device)
+    if cs_events is not None:
+        s = torch.cuda.current_stream() if stream is None else stream
+        load().msk_stage_events(_event_handle(cs_events[0], s), _event_handle(cs_events[1], s))
     _check("ms_sketch", load().ms_sketch(_ptr(A), dt, d, n, lda, _ptr(b), k, p, seed & (2**64 - 1),
                                          gemm_prec, _ptr(Z), _colmajor(Z), strategy, _ptr(ws), ws.numel(),
                                          _stream(stream)))

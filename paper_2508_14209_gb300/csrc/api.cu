@@ -84,9 +84,45 @@ __device__ int g_msk_check = 0;
 size_t tc_gemm_workspace(int64_t p, int64_t k, int64_t ncol, int prec);
 // Z = G Y for a Y of element type y_dtype (FP64 or FP32); the tensor-core
 // precisions take FP32 Y only.
+// A side stream (and its fork/join events) per device and host thread.
+struct SideStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+static int side_stream(SideStream** out) {
+  constexpr int kMaxDev = 64;
+  thread_local SideStream sides[kMaxDev];
+  int dev = 0;
+  MSK_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDev) return MSK_ENOTSUP;
+  SideStream& sd = sides[dev];
+  if (!sd.s) {
+    MSK_CUDA(cudaStreamCreateWithFlags(&sd.s, cudaStreamNonBlocking));
+    MSK_CUDA(cudaEventCreateWithFlags(&sd.fork, cudaEventDisableTiming));
+    MSK_CUDA(cudaEventCreateWithFlags(&sd.join, cudaEventDisableTiming));
+  }
+  *out = &sd;
+  return MSK_OK;
+}
+
+// Events the next ms_sketch call of this thread records around its
+// CountSketch (msk_stage_events), then forgets.
+struct StageEvents {
+  cudaEvent_t before_cs = nullptr, after_cs = nullptr;
+};
+static StageEvents& stage_events() {
+  thread_local StageEvents ev;
+  return ev;
+}
+
+bool gemm_stage_sliced(int64_t p, int64_t k, int64_t ncol, int y_dtype, int gemm_prec, size_t ws_bytes) {
+  return gemm_prec == MSK_GEMM_F64 && y_dtype == MSK_F64 && oz_applicable(p, k, ncol) &&
+         ws_bytes >= oz_gemm_workspace(p, k, ncol);
+}
+
 int gemm_stage(uint64_t seed, int64_t p, int64_t k, int64_t ncol, const void* Y, int y_dtype,
                int64_t ldy, int gemm_prec, double* Z, int64_t ldz, void* ws, size_t ws_bytes,
-               cudaStream_t st) {
+               cudaStream_t st, bool g_ready) {
   StageRange nvtx_range_("gemm_stage");
   const uint64_t gkey = stream_key(seed, kTagGauss);
   if (is_tensor_prec(gemm_prec)) {
@@ -96,10 +132,9 @@ int gemm_stage(uint64_t seed, int64_t p, int64_t k, int64_t ncol, const void* Y,
   }
   // FP64 Y and FP64 arithmetic: the exact-slicing tensor-core stage where it
   // applies and the workspace holds it, else the FP64 SIMT kernel
-  if (gemm_prec == MSK_GEMM_F64 && y_dtype == MSK_F64 && oz_applicable(p, k, ncol) &&
-      ws_bytes >= oz_gemm_workspace(p, k, ncol))
+  if (gemm_stage_sliced(p, k, ncol, y_dtype, gemm_prec, ws_bytes))
     return launch_oz_gemm(gkey, p, k, ncol, static_cast<const double*>(Y), ldy, Z, ldz, ws, ws_bytes,
-                          st);
+                          st, g_ready);
   Carve cv(ws, ws_bytes);
   float* G = static_cast<float*>(cv.take((size_t)p * k * sizeof(float)));
   if (!G) return MSK_ENOMEM;
@@ -117,6 +152,13 @@ using namespace msk;
 extern "C" {
 
 const char* msk_version(void) { return "msketch 0.1 (sm_103a)"; }
+
+int msk_stage_events(void* before_cs, void* after_cs) {
+  StageEvents& ev = stage_events();
+  ev.before_cs = static_cast<cudaEvent_t>(before_cs);
+  ev.after_cs = static_cast<cudaEvent_t>(after_cs);
+  return MSK_OK;
+}
 
 int msk_checked_build(void) {
 #ifdef MSK_CHECKED
@@ -311,19 +353,39 @@ int ms_sketch(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, const
   const size_t cs_ws = msk_cs_workspace(d, n, k, ydt, strategy);
   void* csw = cv.take(cs_ws);
   if (!Y) return MSK_ENOMEM;
+  if (ydt == MSK_F64 && dtype == MSK_F32 && strategy != MSK_CS_ATOMIC) return MSK_ENOTSUP;
+  const size_t rest_off = align_up(cv.used, 256);
+  // The sliced FP64 stage's G slices depend on the seed only: they are
+  // sampled on a side stream while the CountSketch runs (the CountSketch is
+  // bound by L2 reductions, the sampler by the SMs' issue slots).
+  const bool fork = gemm_stage_sliced(p, k, ncol, ydt, gemm_prec, ws_bytes - rest_off) && d > 0;
+  SideStream* side = nullptr;
+  if (fork) {
+    int rc = side_stream(&side);
+    if (rc) return rc;
+    MSK_CUDA(cudaEventRecord(side->fork, st));
+    MSK_CUDA(cudaStreamWaitEvent(side->s, side->fork, 0));
+    rc = launch_oz_prepare_g(stream_key(seed, kTagGauss), p, k, ncol, cv.base + rest_off, ws_bytes - rest_off,
+                             side->s);
+    if (rc) return rc;
+    MSK_CUDA(cudaEventRecord(side->join, side->s));
+  }
+  StageEvents& sev = stage_events();
+  if (sev.before_cs) MSK_CUDA(cudaEventRecord(sev.before_cs, st));
   int rc = MSK_OK;
   if (ydt == MSK_F64 && dtype == MSK_F32) {
     // FP64 sketch of the FP32-stored A
-    if (strategy != MSK_CS_ATOMIC) return MSK_ENOTSUP;
     rc = count_sketch_f64y(A, dtype, d, n, lda, b, k, seed, static_cast<double*>(Y), ldy, st);
   } else {
     rc = cs_sketch_internal(A, dtype, d, n, lda, b, k, seed, Y, ldy, strategy, csw, cs_ws, true,
                             st);
   }
+  if (sev.after_cs) MSK_CUDA(cudaEventRecord(sev.after_cs, st));
+  sev = StageEvents{};
+  if (fork) MSK_CUDA(cudaStreamWaitEvent(st, side->join, 0));  // joined before any return
   if (rc) return rc;
-  const size_t rest_off = align_up(cv.used, 256);
   return gemm_stage(seed, p, k, ncol, Y, ydt, ldy, gemm_prec, static_cast<double*>(Z), ldz,
-                    cv.base + rest_off, ws_bytes - rest_off, st);
+                    cv.base + rest_off, ws_bytes - rest_off, st, fork);
 }
 
 int ms_sketch_rows(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, const double* b,

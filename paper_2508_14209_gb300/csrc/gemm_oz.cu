@@ -433,25 +433,54 @@ static int oz_g_exponent(float sqrt_p) {
   return e;
 }
 
-int launch_oz_gemm(uint64_t gkey, int64_t p, int64_t k, int64_t ncol, const double* Y, int64_t ldy,
-                   double* Z, int64_t ldz, void* ws, size_t ws_bytes, cudaStream_t st) {
+// The stage's pieces in the caller's workspace (the same for every call with
+// these sizes, so that the G slices a preparing call leaves are found).
+struct OzBufs {
+  __nv_bfloat16 *Gs, *Ys;
+  longlong2* part;
+  unsigned long long* mx;
+  int* eY;
+};
+static bool oz_carve(void* ws, size_t ws_bytes, const OzPlan& t, int64_t p, int64_t ncol, OzBufs* b) {
+  Carve cv(ws, ws_bytes);
+  b->Gs = static_cast<__nv_bfloat16*>(cv.take((size_t)kOzSlices * p * t.kpitch * 2));
+  b->Ys = static_cast<__nv_bfloat16*>(cv.take((size_t)kOzSlices * t.npad * t.kpitch * 2));
+  b->part = static_cast<longlong2*>(cv.take((size_t)kOzGroups * t.S * p * ncol * sizeof(longlong2)));
+  b->mx = static_cast<unsigned long long*>(cv.take((size_t)ncol * sizeof(unsigned long long)));
+  b->eY = static_cast<int*>(cv.take((size_t)t.npad * sizeof(int)));
+  return b->Gs && b->Ys && b->part && b->mx && b->eY;
+}
+
+int launch_oz_prepare_g(uint64_t gkey, int64_t p, int64_t k, int64_t ncol, void* ws, size_t ws_bytes,
+                        cudaStream_t st) {
   if (p < 1 || ncol < 1 || k < 1) return MSK_OK;
   const OzPlan t = oz_plan(p, k, ncol);
-  Carve cv(ws, ws_bytes);
-  auto* Gs = static_cast<__nv_bfloat16*>(cv.take((size_t)kOzSlices * p * t.kpitch * 2));
-  auto* Ys = static_cast<__nv_bfloat16*>(cv.take((size_t)kOzSlices * t.npad * t.kpitch * 2));
-  auto* part = static_cast<longlong2*>(cv.take((size_t)kOzGroups * t.S * p * ncol * sizeof(longlong2)));
-  auto* mx = static_cast<unsigned long long*>(cv.take((size_t)ncol * sizeof(unsigned long long)));
-  auto* eY = static_cast<int*>(cv.take((size_t)t.npad * sizeof(int)));
-  if (!Gs || !Ys || !part || !mx || !eY) return MSK_ENOMEM;
+  OzBufs bf;
+  if (!oz_carve(ws, ws_bytes, t, p, ncol, &bf)) return MSK_ENOMEM;
+  const float sqrt_p = __builtin_sqrtf((float)p);
+  const dim3 grid((unsigned)std::min<int64_t>((k + 255) / 256, 64), (unsigned)std::min<int64_t>(p, 65535));
+  oz_split_g_kernel<<<grid, 256, 0, st>>>(gkey, p, k, sqrt_p, oz_g_exponent(sqrt_p), t.kpitch, bf.Gs);
+  MSK_CHECK_LAUNCH("oz_split_g_kernel");
+  return MSK_OK;
+}
+
+int launch_oz_gemm(uint64_t gkey, int64_t p, int64_t k, int64_t ncol, const double* Y, int64_t ldy,
+                   double* Z, int64_t ldz, void* ws, size_t ws_bytes, cudaStream_t st, bool g_ready) {
+  if (p < 1 || ncol < 1 || k < 1) return MSK_OK;
+  const OzPlan t = oz_plan(p, k, ncol);
+  OzBufs bf;
+  if (!oz_carve(ws, ws_bytes, t, p, ncol, &bf)) return MSK_ENOMEM;
+  __nv_bfloat16 *Gs = bf.Gs, *Ys = bf.Ys;
+  longlong2* part = bf.part;
+  unsigned long long* mx = bf.mx;
+  int* eY = bf.eY;
   const int sms = num_sms();
-  // G slices (independent of Y)
+  // G slices (independent of Y), unless a preparing call already wrote them
   const float sqrt_p = __builtin_sqrtf((float)p);
   const int eG = oz_g_exponent(sqrt_p);
-  {
-    const dim3 grid((unsigned)std::min<int64_t>((k + 255) / 256, 64), (unsigned)std::min<int64_t>(p, 65535));
-    oz_split_g_kernel<<<grid, 256, 0, st>>>(gkey, p, k, sqrt_p, eG, t.kpitch, Gs);
-    MSK_CHECK_LAUNCH("oz_split_g_kernel");
+  if (!g_ready) {
+    const int rc = launch_oz_prepare_g(gkey, p, k, ncol, ws, ws_bytes, st);
+    if (rc) return rc;
   }
   // column maxima of Y, then its slices
   MSK_CUDA(cudaMemsetAsync(mx, 0, (size_t)ncol * sizeof(unsigned long long), st));

@@ -171,8 +171,14 @@ int launch_tc_gemm(uint64_t gkey, int64_t p, int64_t k, int64_t ncol, const floa
 // gemm_oz.cu (FP64 Gaussian stage on the tensor cores by exact 8-bit slicing)
 bool oz_applicable(int64_t p, int64_t k, int64_t ncol);
 size_t oz_gemm_workspace(int64_t p, int64_t k, int64_t ncol);
+// g_ready: a launch_oz_prepare_g with the same sizes and workspace already
+// wrote G's slices (ordered before this call's kernels).
 int launch_oz_gemm(uint64_t gkey, int64_t p, int64_t k, int64_t ncol, const double* Y, int64_t ldy,
-                   double* Z, int64_t ldz, void* ws, size_t ws_bytes, cudaStream_t st);
+                   double* Z, int64_t ldz, void* ws, size_t ws_bytes, cudaStream_t st,
+                   bool g_ready = false);
+// G's slices alone: the part of the sliced stage that depends on the seed only.
+int launch_oz_prepare_g(uint64_t gkey, int64_t p, int64_t k, int64_t ncol, void* ws, size_t ws_bytes,
+                        cudaStream_t st);
 // qr.cu
 int launch_householder_qr(double* W, int64_t m, int64_t c, int64_t ldw, cudaStream_t st);
 int launch_trsv_upper(const double* R, int64_t n, int64_t ldr, const double* rhs, double* x,
@@ -208,6 +214,8 @@ int count_sketch_f64y(const void* A, int dtype, int64_t d, int64_t n, int64_t ld
                       cudaStream_t st, bool zero = true, int64_t i0 = 0);
 int gemm_stage(uint64_t seed, int64_t p, int64_t k, int64_t ncol, const void* Y, int y_dtype,
                int64_t ldy, int gemm_prec, double* Z, int64_t ldz, void* ws, size_t ws_bytes,
-               cudaStream_t st);
+               cudaStream_t st, bool g_ready = false);
+// Whether gemm_stage takes the sliced FP64 path for these arguments.
+bool gemm_stage_sliced(int64_t p, int64_t k, int64_t ncol, int y_dtype, int gemm_prec, size_t ws_bytes);
 
 }  // namespace msk

@@ -171,3 +171,27 @@ def test_multisketch_simt(msk, orc, prec, d, n, k, p, with_b, dtype):
     absY = orc.bucket_abs_sums(An, k, seed, b=bn)
     bound = (k + 2) * u_mm * (np.abs(Gu) @ np.abs(Yu)) + np.abs(Gu) @ (u_cs * absY)
     assert np.all(np.abs(Z - Zo) <= bound)
+
+
+def test_multisketch_stage_events_and_side_stream(msk, orc):
+    """The FP64 multisketch samples G's slices on a side stream beside its
+    CountSketch; the result is the oracle's within the FP64 bound whether or
+    not the stage-event hook is set, and the hook's events bracket the
+    CountSketch inside the call's span."""
+    d, n, k, p, seed = 70001, 64, 8192, 256, 0x5EED0009
+    A = inputs.normal_matrix(d, n, seed, dtype=torch.float64)
+    Ad = msk.colmajor(d, n, torch.float64, "cuda")
+    Ad.copy_(A)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record()
+    Z = msk.ms_sketch(Ad, k, p, seed, gemm_prec=msk.GEMM_F64, cs_events=(ev[1], ev[2]))
+    ev[3].record()
+    torch.cuda.synchronize()
+    Z2 = msk.ms_sketch(Ad, k, p, seed, gemm_prec=msk.GEMM_F64).cpu().numpy()
+    cs_ms, all_ms = ev[1].elapsed_time(ev[2]), ev[0].elapsed_time(ev[3])
+    assert 0.0 < cs_ms <= all_ms
+    Zo, Gu, Yu = orc.multisketch(A.numpy(), k, p, seed, gemm_prec="f64")
+    absY = orc.bucket_abs_sums(A.numpy(), k, seed)
+    bound = (k + 2) * EPS64 * (np.abs(Gu) @ np.abs(Yu)) + np.abs(Gu) @ (64 * EPS64 * absY)
+    for Zg in (Z.cpu().numpy(), Z2):
+        assert np.all(np.abs(Zg - Zo) <= bound)
