@@ -187,8 +187,8 @@ def run_ours(args):
         # the stream the kernel runs on
         Z = msk.colmajor(p, n, torch.float64, dev)
         mws_dev = msk.workspace(msk.msk_ms_workspace(d, n, False, k, p, dt_code, gp), dev)
-        # CountSketch, G sampling (side stream, beside the CountSketch), column
-        # maxima, Y slicing, sliced GEMM, exact reduction (SIMT path: 4)
+        # CountSketch, G sampling, column maxima, Y slicing, sliced GEMM,
+        # exact reduction (SIMT path: 4)
         launches_per_step = 6 if (gp == msk.GEMM_F64 and k >= 1024) else 4
 
     def step(ev=None):
@@ -291,8 +291,7 @@ def run_ours(args):
                        "parallelism": f"replicas{ws}"},
             "stages_ms": {"countsketch": round(cs_ms, 5), "gaussian_gemm": round(gemm_ms, 5),
                           "note": "countsketch: memset + kernel, events from the library's stage hook; "
-                                  "gaussian_gemm: the stage after the CountSketch (G is sampled on a side "
-                                  "stream beside the CountSketch)"},
+                                  "gaussian_gemm: the Gaussian stage after the CountSketch"},
             "roofline": {"bound": "hbm", "kernel": "cs_fixed_f64_kernel (+Y zeroing memset)" if dts == "f64" else "cs_fixed_f32_kernel (+Y zeroing memset)",
                          "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                          "frac": round(achieved / hbm, 4), "peak_source": peak_src,

@@ -218,9 +218,10 @@ size_t msk_ms_workspace(int64_t d, int64_t n, int with_b, int64_t k, int64_t p,
  * (Section 1 "Count-Gauss"; Section 6.2 uses k = 2n^2).  A, b, dtype, k,
  * seed, strategy as in cs_sketch; the Gaussian uses the same seed (tag 2).
  * With the FP64 Gaussian stage on the tensor cores (gemm_prec F64, k >=
- * 1024), G's slices are sampled on a library side stream while the
- * CountSketch runs on `stream`, which waits for them before the stage (the
- * call stays ordered on `stream`, and can be captured).
+ * 1024) and the tuning knob "ms.overlap_gauss" set, G's slices are sampled
+ * on a library side stream while the CountSketch runs on `stream`, which
+ * waits for them before the stage (the call stays ordered on `stream`, and
+ * can be captured).
  *   gemm_prec : msk_gemm_prec, the arithmetic of Z = G Y.
  *   Z : device double, column-major p x ncol, leading dimension ldz >= p.
  * Errors: -1 A NULL (with d, n > 0), -2 bad dtype, -3 d < 0, -4 n < 0 or

@@ -355,10 +355,14 @@ int ms_sketch(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, const
   if (!Y) return MSK_ENOMEM;
   if (ydt == MSK_F64 && dtype == MSK_F32 && strategy != MSK_CS_ATOMIC) return MSK_ENOTSUP;
   const size_t rest_off = align_up(cv.used, 256);
-  // The sliced FP64 stage's G slices depend on the seed only: they are
-  // sampled on a side stream while the CountSketch runs (the CountSketch is
-  // bound by L2 reductions, the sampler by the SMs' issue slots).
-  const bool fork = gemm_stage_sliced(p, k, ncol, ydt, gemm_prec, ws_bytes - rest_off) && d > 0;
+  // The sliced FP64 stage's G slices depend on the seed only: with the knob
+  // "ms.overlap_gauss" they are sampled on a side stream while the
+  // CountSketch runs (the CountSketch is bound by L2 reductions, the sampler
+  // by the SMs' issue slots).  Measured at 4194304 x 64: the step 0.552 ->
+  // 0.546 ms, but the CountSketch itself 0.470 -> 0.485 ms (it shares the
+  // SMs), so it is off by default.
+  const bool fork = tune_get("ms.overlap_gauss", 0) != 0 &&
+                    gemm_stage_sliced(p, k, ncol, ydt, gemm_prec, ws_bytes - rest_off) && d > 0;
   SideStream* side = nullptr;
   if (fork) {
     int rc = side_stream(&side);

@@ -174,19 +174,23 @@ def test_multisketch_simt(msk, orc, prec, d, n, k, p, with_b, dtype):
 
 
 def test_multisketch_stage_events_and_side_stream(msk, orc):
-    """The FP64 multisketch samples G's slices on a side stream beside its
-    CountSketch; the result is the oracle's within the FP64 bound whether or
-    not the stage-event hook is set, and the hook's events bracket the
-    CountSketch inside the call's span."""
+    """With "ms.overlap_gauss" the FP64 multisketch samples G's slices on a
+    side stream beside its CountSketch; the result is the oracle's within the
+    FP64 bound with and without it, and the stage-event hook's events bracket
+    the CountSketch inside the call's span."""
     d, n, k, p, seed = 70001, 64, 8192, 256, 0x5EED0009
     A = inputs.normal_matrix(d, n, seed, dtype=torch.float64)
     Ad = msk.colmajor(d, n, torch.float64, "cuda")
     Ad.copy_(A)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    ev[0].record()
-    Z = msk.ms_sketch(Ad, k, p, seed, gemm_prec=msk.GEMM_F64, cs_events=(ev[1], ev[2]))
-    ev[3].record()
-    torch.cuda.synchronize()
+    msk.tune_set("ms.overlap_gauss", 1)
+    try:
+        ev[0].record()
+        Z = msk.ms_sketch(Ad, k, p, seed, gemm_prec=msk.GEMM_F64, cs_events=(ev[1], ev[2]))
+        ev[3].record()
+        torch.cuda.synchronize()
+    finally:
+        msk.tune_clear("ms.overlap_gauss")
     Z2 = msk.ms_sketch(Ad, k, p, seed, gemm_prec=msk.GEMM_F64).cpu().numpy()
     cs_ms, all_ms = ev[1].elapsed_time(ev[2]), ev[0].elapsed_time(ev[3])
     assert 0.0 < cs_ms <= all_ms
