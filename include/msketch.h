@@ -394,6 +394,28 @@ int ne_lstsq(const double *A, int64_t d, int64_t n, int64_t lda,
              const double *b, double *x, void *ws, size_t ws_bytes,
              void *stream);
 
+/* ---- The refinement's operator (Section 6.3, preconditioned normal
+ * equations): v = A^T (A p) for an FP32 A, as the conjugate-gradient steps of
+ * ms_lstsq(refine = 1) and msk_batch_lstsq apply it. ------------------------ */
+
+/* Scratch bytes of msk_normal_apply (0 for bad sizes). */
+size_t msk_normal_apply_workspace(int64_t d, int64_t n);
+
+/* v = A^T (A p) in double-single arithmetic.
+ *   A : device float column-major d x n (lda >= d), 1 <= n <= 512;
+ *   p : device double[n] (read as the pair fl32(p), fl32(p - fl32(p)));
+ *   v : device double[n] (written).
+ * Runs the refinement's FP64 residual pass first (with x = 0: it records the
+ * column maxima of |A| that bound the terms of the operator pass), then one
+ * operator pass: w = A p and v = A^T w, each product sum carried to about
+ * 2^-44 of its terms' magnitude (n <= 256: an exact integer part on a grid
+ * plus a binary32 rest; wider: compensated Dot2 sums).  Asynchronous on
+ * `stream`.  Returns MSK_OK; -1 null pointer, -2 d < 1, -3 n outside
+ * [1, 512], -4 lda < d, MSK_ENOMEM ws too small. */
+int msk_normal_apply(const float *A, int64_t d, int64_t n, int64_t lda,
+                     const double *p, double *v, void *ws, size_t ws_bytes,
+                     void *stream);
+
 /* ---- SRHT (Section 5: Definition of the SRHT, Algorithm 3) -------------- */
 
 /* Scratch bytes of srht_sketch (d x ncol doubles when d > 8192, plus the

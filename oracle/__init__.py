@@ -25,6 +25,8 @@ Parity status of each function (what pins it, see tests/test_oracle_*.py):
     residual_and_g.    as exact integers), x = 0 and b = A x, numpy's FP64
                        evaluation of r, A^T r and the norms, A^T r = 0 at
                        LAPACK's least-squares minimiser
+  normal_apply         brute force in exact rational arithmetic (each w_i
+                       rounded once), a cancellation case plain FP64 loses
   sns_lstsq            exact recovery for b = A x, distortion bound of Section 2
   ne_lstsq             agrees with QR when well conditioned, fails for
                        kappa > 1e8 (Section 6.3)
@@ -401,6 +403,35 @@ def residual_and_gradient(A, b, x):
     out = np.zeros(2)
     lib().or_residual(_ptr(A), dt, d, n, lda, _ptr(bb), _ptr(xx), _ptr(r), _ptr(g), _ptr(out))
     return r, g, float(np.sqrt(out[0])), float(np.sqrt(out[1]))
+
+
+def _split26(x):
+    """x = hi + lo exactly, each part with at most 26 significant bits
+    (Veltkamp's splitting with the factor 2^27 + 1), so that a binary32
+    times either part is exact in FP64."""
+    x = np.asarray(x, dtype=np.float64)
+    c = (2.0 ** 27 + 1.0) * x
+    hi = c - (c - x)
+    return hi, x - hi
+
+
+def normal_apply(A, p):
+    """v = A^T (A p) for a binary32 A: the operator of the preconditioned
+    normal equations the refinement iterates on (Section 6.3).  w_i = sum_j
+    a_ij p_j and then v_j = sum_i a_ij w_i, each sum the correctly rounded
+    FP64 value of its exact terms: a times the two 26-bit parts of the FP64
+    factor are exact products, and math.fsum rounds their exact sum once.
+    The only error left is the rounding of each w_i."""
+    import math
+
+    A64 = np.asarray(A, dtype=np.float32).astype(np.float64)
+    d, n = A64.shape
+    ph, pl = _split26(p)
+    P = np.concatenate((A64 * ph, A64 * pl), axis=1)
+    w = np.array([math.fsum(row) for row in P.tolist()])
+    wh, wl = _split26(w)
+    Q = np.concatenate((A64 * wh[:, None], A64 * wl[:, None]), axis=0)
+    return np.array([math.fsum(col) for col in Q.T.tolist()])
 
 
 def sns_lstsq(A, b, k: int, p: int, seed: int, gemm_prec: str = "f64"):

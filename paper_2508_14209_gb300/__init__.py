@@ -36,7 +36,7 @@ GEMM_PRECS = {"f64": GEMM_F64, "f32": GEMM_F32, "bf16": GEMM_BF16, "f16": GEMM_F
 EXPORTS = ("msk_version", "msk_last_error", "msk_checked_build", "msk_check_status", "msk_stage_events", "msk_take_timeout", "msk_selftest_wait", "cs_hash", "ms_gaussian", "msk_cs_workspace",
            "cs_sketch", "msk_ms_workspace", "ms_sketch", "msk_gemm_workspace", "msk_gemm",
            "msk_householder_qr", "msk_trsv_upper", "msk_lstsq_workspace", "ms_lstsq",
-           "msk_ne_workspace", "ne_lstsq", "msk_rcq_workspace", "rcq_lstsq", "rcq_qr",
+           "msk_ne_workspace", "ne_lstsq", "msk_normal_apply_workspace", "msk_normal_apply", "msk_rcq_workspace", "rcq_lstsq", "rcq_qr",
            "msk_sns_workspace", "sns_lstsq", "msk_srht_workspace", "srht_sketch",
            "msk_ms_host_workspace", "ms_sketch_host", "ms_sketch_rows",
            "msk_gemm_noalloc", "msk_tune_set", "msk_tune_get",
@@ -44,7 +44,7 @@ EXPORTS = ("msk_version", "msk_last_error", "msk_checked_build", "msk_check_stat
            "ms_server_submit", "ms_server_poll", "ms_server_wait_all", "ms_server_stats",
            "ms_server_destroy", "ms_server_error", "msk_autotune_workspace", "msk_autotune")
 
-NOALLOC_SCRATCH_BYTES = 24 << 20
+NOALLOC_SCRATCH_BYTES = 64 << 20
 
 
 class MskError(RuntimeError):
@@ -113,6 +113,8 @@ def _declare(L):
                             _p, ctypes.POINTER(LstsqInfo), _p, _sz, _p]),
         "msk_ne_workspace": (_sz, [_i64, _i64]),
         "ne_lstsq": (_int, [_p, _i64, _i64, _i64, _p, _p, _p, _sz, _p]),
+        "msk_normal_apply_workspace": (_sz, [_i64, _i64]),
+        "msk_normal_apply": (_int, [_p, _i64, _i64, _i64, _p, _p, _p, _sz, _p]),
         "msk_rcq_workspace": (_sz, [_i64, _i64, _i64, _i64, _int, _int, _int]),
         "msk_sns_workspace": (_sz, [_i64, _i64, _int, _i64, _i64, _int]),
         "msk_srht_workspace": (_sz, [_i64, _i64, _int, _i64]),
@@ -487,6 +489,25 @@ def ne_lstsq(A, b, x=None, ws=None, stream=None):
     if rc < 0 or rc >= 1000:
         _check("ne_lstsq", rc)
     return x, rc
+
+
+def msk_normal_apply_workspace(d, n):
+    return load().msk_normal_apply_workspace(d, n)
+
+
+def msk_normal_apply(A, p, v=None, ws=None, stream=None):
+    """v = A^T (A p) for FP32 A in double-single arithmetic: the refinement's
+    operator pass (after the residual pass that bounds its terms)."""
+    _cuda(A, "A")
+    d, n = A.shape
+    if v is None:
+        v = torch.empty(n, dtype=torch.float64, device=A.device)
+    if ws is None:
+        ws = workspace(msk_normal_apply_workspace(d, n), A.device)
+    rc = load().msk_normal_apply(_ptr(A), d, n, _colmajor(A), _ptr(p), _ptr(v), _ptr(ws), ws.numel(),
+                                 _stream(stream))
+    _check("msk_normal_apply", rc)
+    return v
 
 
 SKETCH_MULTI, SKETCH_COUNT, SKETCH_GAUSS, SKETCH_SRHT = 0, 1, 2, 3

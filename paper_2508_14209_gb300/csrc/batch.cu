@@ -71,8 +71,8 @@ struct BatchJob {
   double* Ri;
   double* vec;   // dlt, p, res, z, g: 5n
   double* sc;    // [0] rho, [1] gain, [2] active, [3] floor, [4] inner iters, [5] bb, [6] rr0
-  double* ppart; // pass partials: nchunks x (n + 2)
-  double* pout;  // reduced pass result: n + 2
+  double* ppart; // pass partials: nchunks x pass_out_len(n) (inner passes: stride n + 2)
+  double* pout;  // reduced pass result: pass_out_len(n) (A^T r, ||r||^2, ||b||^2, column maxima of |A|)
   int nchunks;      // CTAs of this problem in the refinement passes
   int chunk_begin;  // its first CTA in the batch-wide pass grid
   int cw;           // floats per tile copy (pass32_copy_width: 4, 2 or 1)
@@ -195,10 +195,11 @@ __global__ void __launch_bounds__(kP32Threads, pass32_ctas_per_sm(NC))
   if (lc >= J.nchunks) return;
   if (RESID) {
     if (only && !only[j]) return;
-    pass32n_body<NC, true>(J.A, J.lda, J.d, J.n, J.cw, J.b, J.x, J.ppart, lc, J.nchunks, bp_smem);
+    pass32n_body<NC, true>(J.A, J.lda, J.d, J.n, J.cw, J.b, J.x, nullptr, J.ppart, lc, J.nchunks,
+                           bp_smem);
   } else {
     if (J.sc[2] == 0.0) return;  // problem already stopped
-    pass32n_body<NC, false>(J.A, J.lda, J.d, J.n, J.cw, nullptr, J.vec + J.n, J.ppart, lc,
+    pass32n_body<NC, false>(J.A, J.lda, J.d, J.n, J.cw, nullptr, J.vec + J.n, J.pout + J.n + 2, J.ppart, lc,
                             J.nchunks, bp_smem);
   }
 }
@@ -208,8 +209,8 @@ __global__ void __launch_bounds__(256) batch_pass_reduce_kernel(const BatchJob* 
                                                                 const int* __restrict__ only) {
   const BatchJob& J = jobs[blockIdx.y];
   if (only && !only[blockIdx.y]) return;
-  if ((int)blockIdx.x * 32 >= J.n + 2) return;
-  pass_reduce_body(J.ppart, J.nchunks, J.n + 2, J.pout, blockIdx.x);
+  if ((int64_t)blockIdx.x * 32 >= pass_out_len(J.n)) return;
+  pass_reduce_body(J.ppart, J.nchunks, (int)pass_out_len(J.n), J.n + 2, J.pout, blockIdx.x);
 }
 
 __device__ __forceinline__ RefState ref_state(const BatchJob& J) {
@@ -483,7 +484,7 @@ static void plan_batch(const msk_batch_item* items, int nitems, int refine, char
     J.Ri = reinterpret_cast<double*>(ptr(take(refine ? (size_t)J.n * J.n * 8 : 0)));
     J.vec = reinterpret_cast<double*>(ptr(take(refine ? (size_t)5 * J.n * 8 : 0)));
     J.sc = reinterpret_cast<double*>(ptr(take(kScCount * 8)));
-    J.pout = reinterpret_cast<double*>(ptr(take((size_t)(J.n + 2) * 8)));
+    J.pout = reinterpret_cast<double*>(ptr(take((size_t)pass_out_len(J.n) * 8)));
     P->max_nt = std::max(P->max_nt, sh.NT);
     P->max_npad = std::max(P->max_npad, sh.npad);
     P->max_n = std::max(P->max_n, J.n);
@@ -516,7 +517,7 @@ static void plan_batch(const msk_batch_item* items, int nitems, int refine, char
       J.chunk_begin = begin;
       begin += J.nchunks;
       J.cw = pass32_copy_width(J.A, J.lda);
-      J.ppart = reinterpret_cast<double*>(ptr(take((size_t)J.nchunks * (J.n + 2) * 8)));
+      J.ppart = reinterpret_cast<double*>(ptr(take((size_t)J.nchunks * pass_out_len(J.n) * 8)));
     }
     P->pass_nc.push_back(nc);
     P->pass_chunks.push_back(begin);
@@ -593,8 +594,8 @@ size_t msk_batch_item_bound(const msk_batch_item* item, int refine) {
   piece(refine ? (size_t)n * n * 8 : 0);               // R^{-1}
   piece(refine ? (size_t)5 * n * 8 : 0);               // CG vectors
   piece((size_t)kScCount * 8);                         // CG scalars
-  piece((size_t)(n + 2) * 8);                          // pass result
-  piece((size_t)nchunks * (n + 2) * 8);                // pass partials
+  piece((size_t)pass_out_len(n) * 8);                  // pass result
+  piece((size_t)nchunks * pass_out_len(n) * 8);        // pass partials
   piece(sizeof(int) + sizeof(CsParams<float>) + sizeof(int64_t));  // class tables
   return b;
 }
@@ -648,7 +649,7 @@ int msk_batch_lstsq(const msk_batch_item* items, int nitems, int refine, double 
   const bool fp64_start = refine || infos;  // an FP64 residual pass of the start
   const int round_len = (int)std::min<long long>(16, std::max<long long>(1, tune_get("batch.round", kRound)));
   const unsigned gblocks = (unsigned)((nitems + 255) / 256);
-  const dim3 rgrid((P.max_n + 2 + 31) / 32, nitems);
+  const dim3 rgrid((unsigned)((pass_out_len(P.max_n) + 31) / 32), nitems);
   size_t qsm = 0;
   for (const BatchJob& J : P.jobs)
     if (qr_smem_fits(J.p, J.ncol, 16)) qsm = std::max(qsm, qr_smem_bytes(J.p, J.ncol, 16));

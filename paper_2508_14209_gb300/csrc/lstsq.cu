@@ -345,22 +345,23 @@ __global__ void __launch_bounds__(kPThreads) pass_kernel(const TA* __restrict__ 
   pass_body<TA, RESID>(A, lda, d, n, pitch, b, vin, part, blockIdx.x, gridDim.x, pk_smem);
 }
 __global__ void __launch_bounds__(256) pass_reduce_kernel(const double* __restrict__ part, int nctas,
-                                                          int len, double* __restrict__ out,
+                                                          int len, int nsum, double* __restrict__ out,
                                                           const double* __restrict__ active) {
   if (active && *active == 0.0) return;
-  pass_reduce_body(part, nctas, len, out, blockIdx.x);
+  pass_reduce_body(part, nctas, len, nsum, out, blockIdx.x);
 }
 template <int NC, bool RESID>
 __global__ void __launch_bounds__(kP32Threads, pass32_ctas_per_sm(NC))
     pass32_kernel(const float* __restrict__ A, int64_t lda, int64_t d, int n, int cw,
                   const double* __restrict__ b, const double* __restrict__ vin,
-                  double* __restrict__ part, const double* __restrict__ active) {
+                  const double* __restrict__ cmax, double* __restrict__ part,
+                  const double* __restrict__ active) {
   if (active && *active == 0.0) return;
   extern __shared__ __align__(16) unsigned char p32_smem[];
   if constexpr (NC == 0)
     pass32g_body<RESID>(A, lda, d, n, cw == 4, b, vin, part, blockIdx.x, gridDim.x, p32_smem);
   else
-    pass32n_body<NC, RESID>(A, lda, d, n, cw, b, vin, part, blockIdx.x, gridDim.x, p32_smem);
+    pass32n_body<NC, RESID>(A, lda, d, n, cw, b, vin, cmax, part, blockIdx.x, gridDim.x, p32_smem);
 }
 __global__ void __launch_bounds__(512) x0_kernel(const double* __restrict__ Ri, int n,
                                                  const double* __restrict__ c, double* __restrict__ x) {
@@ -410,7 +411,7 @@ static int launch_pass_t(const TA* A, int64_t lda, int64_t d, int n, const doubl
   MSK_CHECK_LAUNCH("pass_kernel");
   if (grid_out) *grid_out = grid;
   if (!out) return MSK_OK;
-  pass_reduce_kernel<<<(n + 2 + 31) / 32, 256, 0, st>>>(part, grid, n + 2, out, active);
+  pass_reduce_kernel<<<(n + 2 + 31) / 32, 256, 0, st>>>(part, grid, n + 2, n + 2, out, active);
   MSK_CHECK_LAUNCH("pass_reduce_kernel");
   return MSK_OK;
 }
@@ -426,10 +427,12 @@ static int pass32_grid(int64_t d, int n) {
   return (int)std::max<int64_t>(1, std::min<int64_t>((d + R - 1) / R, (int64_t)kPassCtasPerSm * num_sms()));
 }
 
+// cmax: the column maxima of |A| from an earlier residual pass (inner passes
+// of the specialised bodies).
 template <int NC, bool RESID>
 static int launch_pass32_nc(const float* A, int64_t lda, int64_t d, int n, const double* b,
-                            const double* vin, double* part, double* out, const double* active,
-                            cudaStream_t st, int* grid_out) {
+                            const double* vin, const double* cmax, double* part, double* out,
+                            const double* active, cudaStream_t st, int* grid_out) {
   const size_t smem = pass32_smem(n);
   auto kern = pass32_kernel<NC, RESID>;
   MSK_ALLOW_SMEM(kern);
@@ -438,36 +441,45 @@ static int launch_pass32_nc(const float* A, int64_t lda, int64_t d, int n, const
   per_sm = std::max(1, std::min<int>(per_sm, (int)std::min<long long>(kPassCtasPerSm, tune_get("pass.ctas_per_sm", kPassCtasPerSm))));
   const int R = pass32_rows(n);
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((d + R - 1) / R, (int64_t)per_sm * num_sms()));
-  kern<<<grid, kP32Threads, smem, st>>>(A, lda, d, n, pass32_copy_width(A, lda), b, vin, part, active);
+  if (!RESID && NC != 0 && !cmax) return MSK_ENOTSUP;  // no residual pass before
+  kern<<<grid, kP32Threads, smem, st>>>(A, lda, d, n, pass32_copy_width(A, lda), b, vin, cmax, part,
+                                        active);
   MSK_CHECK_LAUNCH("pass32_kernel");
   if (grid_out) *grid_out = grid;
   if (!out) return MSK_OK;
-  pass_reduce_kernel<<<(n + 2 + 31) / 32, 256, 0, st>>>(part, grid, n + 2, out, active);
+  const int len = RESID && NC != 0 ? (int)pass_out_len(n) : n + 2;
+  pass_reduce_kernel<<<(len + 31) / 32, 256, 0, st>>>(part, grid, len, n + 2, out, active);
   MSK_CHECK_LAUNCH("pass_reduce_kernel");
   return MSK_OK;
 }
 
 template <bool RESID>
 static int launch_pass32(const float* A, int64_t lda, int64_t d, int n, const double* b,
-                         const double* vin, double* part, double* out, const double* active,
-                         cudaStream_t st, int* grid_out) {
+                         const double* vin, const double* cmax, double* part, double* out,
+                         const double* active, cudaStream_t st, int* grid_out) {
   if (n > 2 * kP32Threads) return MSK_ENOTSUP;
+#define MSK_PASS32_NC(NCV) \
+  launch_pass32_nc<NCV, RESID>(A, lda, d, n, b, vin, cmax, part, out, active, st, grid_out)
   switch (pass32_class(n)) {
-    case 16: return launch_pass32_nc<16, RESID>(A, lda, d, n, b, vin, part, out, active, st, grid_out);
-    case 32: return launch_pass32_nc<32, RESID>(A, lda, d, n, b, vin, part, out, active, st, grid_out);
-    case 64: return launch_pass32_nc<64, RESID>(A, lda, d, n, b, vin, part, out, active, st, grid_out);
-    case 128: return launch_pass32_nc<128, RESID>(A, lda, d, n, b, vin, part, out, active, st, grid_out);
-    case 256: return launch_pass32_nc<256, RESID>(A, lda, d, n, b, vin, part, out, active, st, grid_out);
-    default: return launch_pass32_nc<0, RESID>(A, lda, d, n, b, vin, part, out, active, st, grid_out);
+    case 16: return MSK_PASS32_NC(16);
+    case 32: return MSK_PASS32_NC(32);
+    case 64: return MSK_PASS32_NC(64);
+    case 128: return MSK_PASS32_NC(128);
+    case 256: return MSK_PASS32_NC(256);
+    default: return MSK_PASS32_NC(0);
   }
+#undef MSK_PASS32_NC
 }
 
-// RESID: out = [A^T r (n), ||r||^2, ||b||^2] with r = b - A x (FP64; for FP32 A
-// the sum A^T r in double-single).
-// else : out = [A^T A p (n), ., .] (FP64 for FP64 A, double-single for FP32 A).
+// RESID: out = [A^T r (n), ||r||^2, ||b||^2, column maxima of |A| (n; FP32 A,
+// n <= 256)] with r = b - A x (FP64; for FP32 A the sum A^T r in
+// double-single): out holds pass_out_len(n) doubles.
+// else : out = [A^T A p (n), ., .] (FP64 for FP64 A, double-single for FP32 A,
+// which reads the column maxima at cmax = the residual pass's out + n + 2).
 static int launch_pass(const void* A, int dtype, int64_t lda, int64_t d, int n, const double* b,
                        const double* vin, bool resid, double* part, double* out,
-                       const double* active, cudaStream_t st, int* grid_out = nullptr) {
+                       const double* active, cudaStream_t st, int* grid_out = nullptr,
+                       const double* cmax = nullptr) {
   if (dtype == MSK_F64) {
     if (resid)
       return launch_pass_t<double, true>(static_cast<const double*>(A), lda, d, n, b, vin, part,
@@ -476,14 +488,14 @@ static int launch_pass(const void* A, int dtype, int64_t lda, int64_t d, int n, 
                                         active, st, grid_out);
   }
   if (resid)
-    return launch_pass32<true>(static_cast<const float*>(A), lda, d, n, b, vin, part, out, nullptr,
-                               st, grid_out);
-  return launch_pass32<false>(static_cast<const float*>(A), lda, d, n, nullptr, vin, part, out,
+    return launch_pass32<true>(static_cast<const float*>(A), lda, d, n, b, vin, nullptr, part, out,
+                               nullptr, st, grid_out);
+  return launch_pass32<false>(static_cast<const float*>(A), lda, d, n, nullptr, vin, cmax, part, out,
                               active, st, grid_out);
 }
 
 static size_t pass_workspace(int64_t d, int64_t n) {
-  return (size_t)std::max(pass_grid(d), pass32_grid(d, (int)n)) * (n + 2) * sizeof(double);
+  return (size_t)std::max(pass_grid(d), pass32_grid(d, (int)n)) * pass_out_len(n) * sizeof(double);
 }
 
 constexpr int kMaxInner = 200;
@@ -616,7 +628,7 @@ size_t msk_lstsq_workspace(int64_t d, int64_t n, int64_t k, int64_t p, int dtype
   nd.add(msk_ms_workspace(d, n, 1, k, p, dtype, gemm_prec, MSK_CS_ATOMIC));
   nd.add((size_t)p * (n + 1) * sizeof(double));  // Z
   nd.add(pass_workspace(d, n));                     // pass partials
-  nd.add((size_t)(n + 2) * sizeof(double));         // pass result
+  nd.add((size_t)pass_out_len(n) * sizeof(double));         // pass result
   if (refine) {
     nd.add((size_t)n * n * sizeof(double));  // R^{-1}
     nd.add((size_t)5 * n * sizeof(double));  // dlt, p, res, z, g copy
@@ -649,7 +661,7 @@ int ms_lstsq(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, const 
   void* msw = cv.take(ms_ws);
   double* Z = static_cast<double*>(cv.take((size_t)p * (n + 1) * sizeof(double)));
   double* part = static_cast<double*>(cv.take(pass_workspace(d, n)));
-  double* pout = static_cast<double*>(cv.take((size_t)(n + 2) * sizeof(double)));
+  double* pout = static_cast<double*>(cv.take((size_t)pass_out_len(n) * sizeof(double)));
   if (!Z || !part || !pout) return MSK_ENOMEM;
   // 1. Z = G S [A b]
   int rc = ms_sketch(A, dtype, d, n, lda, b, k, p, seed, gemm_prec, Z, p, MSK_CS_ATOMIC, msw, ms_ws,
@@ -720,7 +732,7 @@ int ms_lstsq(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, const 
         for (int r = 0; r < kInnerRound; ++r) {
           int nparts = 0;
           rc = launch_pass(A, dtype, lda, d, (int)n, nullptr, s.p, false, part, nullptr, sc + 2, st,
-                           &nparts);
+                           &nparts, pout + n + 2);
           if (rc) return rc;
           MSK_CUDA(cudaLaunchKernelEx(&ucfg, pcg_cluster_kernel, (const double*)part, nparts,
                                       (int)n + 2, (const double*)Ri, (int)n, s, (int)kMaxInner));
@@ -789,7 +801,7 @@ size_t msk_sns_workspace(int64_t d, int64_t n, int kind, int64_t k, int64_t p, i
     nd.add(gauss_gemm_workspace(p, d, ncol));
   }
   nd.add(pass_workspace(d, n));
-  nd.add((size_t)(n + 2) * sizeof(double));
+  nd.add((size_t)pass_out_len(n) * sizeof(double));
   return nd.used;
 }
 
@@ -853,7 +865,7 @@ int sns_lstsq(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, const
     m = p;
   }
   double* part = static_cast<double*>(cv.take(pass_workspace(d, n)));
-  double* pout = static_cast<double*>(cv.take((size_t)(n + 2) * sizeof(double)));
+  double* pout = static_cast<double*>(cv.take((size_t)pass_out_len(n) * sizeof(double)));
   if (!part || !pout) return MSK_ENOMEM;
   // Algorithm 1 steps 2-3: Householder QR of the sketched [A b], then TRSV
   rc = launch_householder_qr(W, m, ncol, m, st);
@@ -892,7 +904,7 @@ size_t msk_rcq_workspace(int64_t d, int64_t n, int64_t k, int64_t p, int dtype, 
     nd.add((size_t)n * n * sizeof(double));  // R
     nd.add((size_t)n * sizeof(double));      // y
     nd.add(pass_workspace(d, n));            // residual pass partials
-    nd.add((size_t)(n + 2) * sizeof(double));
+    nd.add((size_t)pass_out_len(n) * sizeof(double));
   }
   return nd.used;
 }
@@ -926,7 +938,7 @@ int rcq_lstsq(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, const
   double* R = static_cast<double*>(cv.take((size_t)n * n * sizeof(double)));
   double* y = static_cast<double*>(cv.take((size_t)n * sizeof(double)));
   double* part = static_cast<double*>(cv.take(pass_workspace(d, n)));
-  double* pout = static_cast<double*>(cv.take((size_t)(n + 2) * sizeof(double)));
+  double* pout = static_cast<double*>(cv.take((size_t)pass_out_len(n) * sizeof(double)));
   if (!R || !y || !part || !pout) return MSK_ENOMEM;
   const int64_t ncol = n + 1;
   MSK_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
@@ -1061,4 +1073,43 @@ int ne_lstsq(const double* A, int64_t d, int64_t n, int64_t lda, const double* b
   return MSK_OK;
 }
 
+size_t msk_normal_apply_workspace(int64_t d, int64_t n) {
+  if (d < 1 || n < 1 || n > 2 * kP32Threads) return 0;
+  Need nd;
+  nd.add((size_t)d * sizeof(double));                  // b = 0 of the residual pass
+  nd.add((size_t)n * sizeof(double));                  // x = 0
+  nd.add(pass_workspace(d, n));                        // pass partials
+  nd.add((size_t)pass_out_len(n) * sizeof(double));    // residual-pass result (column maxima)
+  nd.add((size_t)(n + 2) * sizeof(double));            // operator-pass result
+  return nd.used;
+}
+
+int msk_normal_apply(const float* A, int64_t d, int64_t n, int64_t lda, const double* p, double* v,
+                     void* ws, size_t ws_bytes, void* stream) {
+  StageRange nvtx_range_("msk_normal_apply");
+  if (!A || !p || !v) return -1;
+  if (d < 1) return -2;
+  if (n < 1 || n > 2 * kP32Threads) return -3;
+  if (lda < d) return -4;
+  if (ws_bytes < msk_normal_apply_workspace(d, n)) return MSK_ENOMEM;
+  cudaStream_t st = as_stream(stream);
+  Carve cv(ws, ws_bytes);
+  double* b0 = static_cast<double*>(cv.take((size_t)d * sizeof(double)));
+  double* x0 = static_cast<double*>(cv.take((size_t)n * sizeof(double)));
+  double* part = static_cast<double*>(cv.take(pass_workspace(d, n)));
+  double* pout = static_cast<double*>(cv.take((size_t)pass_out_len(n) * sizeof(double)));
+  double* vout = static_cast<double*>(cv.take((size_t)(n + 2) * sizeof(double)));
+  if (!b0 || !x0 || !part || !pout || !vout) return MSK_ENOMEM;
+  MSK_CUDA(cudaMemsetAsync(b0, 0, (size_t)d * sizeof(double), st));
+  MSK_CUDA(cudaMemsetAsync(x0, 0, (size_t)n * sizeof(double), st));
+  int rc = launch_pass(A, MSK_F32, lda, d, (int)n, b0, x0, true, part, pout, nullptr, st);
+  if (rc) return rc;
+  rc = launch_pass(A, MSK_F32, lda, d, (int)n, nullptr, p, false, part, vout, nullptr, st, nullptr,
+                   pout + n + 2);
+  if (rc) return rc;
+  MSK_CUDA(cudaMemcpyAsync(v, vout, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  return MSK_OK;
+}
+
 }  // extern "C"
+

@@ -61,6 +61,13 @@ __host__ __device__ __forceinline__ int pass32g_rows(int n) {
 // tile's load latency), 32 KiB tiles two deep at 256 (a tile keeps >= 32 rows).
 __host__ __device__ constexpr int pass32n_tile(int nc) { return nc <= 128 ? 4096 : 8192; }
 __host__ __device__ constexpr int pass32n_stages(int nc) { return nc <= 128 ? 3 : 2; }
+// Column pitch (floats) of a staged tile: R + 4, which is 4 mod 32, so that
+// 16-byte reads of eight consecutive columns at one row fall in eight
+// different quads of shared-memory banks.
+__host__ __device__ constexpr int pass32n_pitch(int nc) { return pass32n_tile(nc) / nc + 4; }
+// Length of a pass result (and of a residual pass's per-CTA partial in the
+// specialised bodies): [A^T v (n), two scalars, column maxima of |A| (n)].
+__host__ __device__ constexpr int64_t pass_out_len(int64_t n) { return 2 * n + 2; }
 // Rows per tile of the body that runs for n.
 __host__ __device__ __forceinline__ int pass32_rows(int n) {
   const int nc = pass32_class(n);
@@ -72,7 +79,7 @@ __host__ __device__ __forceinline__ size_t pass32_smem(int n) {
   const int nc = pass32_class(n);
   if (nc) {
     const int R = pass32n_tile(nc) / nc;
-    return sizeof(float) * (size_t)pass32n_stages(nc) * pass32n_tile(nc) + 16 * (size_t)nc +
+    return sizeof(float) * (size_t)pass32n_stages(nc) * nc * pass32n_pitch(nc) + 8 * (size_t)nc +
            sizeof(double) * kP32Threads + sizeof(float2) * (size_t)R;
   }
   const int R = pass32g_rows(n);
@@ -158,6 +165,79 @@ __device__ __forceinline__ void d2p_lanes(const D2P& a, D2& lo, D2& hi) {
   hi = D2{s.y, c.y};
 }
 
+// Extraction of a sum of products into an exact integer part and a small
+// rest: the error-free transformation of Rump, Ogita and Oishi ("Accurate
+// floating-point summation", SIAM J. Sci. Comput. 2008) with each product
+// put on the grid by one FMA.  For terms x = a xh with |x| < 2^(k-1) and
+// sigma = 1.5 2^k, t = fl(a xh + sigma) lies in [2^k, 2^(k+1)], so t - sigma is
+// x rounded to a multiple of u = 2^(k-23), exactly (Sterbenz), and equals
+// (bits(t) - bits(sigma)) u: the binary32 encodings of one binade and of its
+// upper end are consecutive integers.  Those integers are summed exactly; the
+// part below the grid, a xh - (t - sigma), is less than u/2 and comes from a
+// second FMA, rounded once, and goes with a xl (xh + xl a double-single
+// factor) into a binary32 rest.  Five binary32 operations per term, in packed
+// f32x2 pairs, and one integer add, against eleven for a Dot2 step, at about
+// the same accuracy (the rest carries the terms' bits below 2^(k-24)).
+struct XSig {
+  f2p s2;       // (sigma, sigma)
+  unsigned sb;  // binary32 bits of sigma
+  float u;      // the grid 2^(k-23)
+  float u12;    // 2^(k-11)
+};
+// sigma for 2^(k-1) above every term, k clamped to [-100, 126] (the grid
+// stays normal; terms of 2^125 and above are outside the method's range).
+__device__ __forceinline__ XSig xsig_make(int k) {
+  k = min(max(k, -100), 126);
+  XSig x;
+  x.sb = ((unsigned)(k + 127) << 23) | 0x00400000u;
+  const float s = __uint_as_float(x.sb);
+  x.s2 = f2p_make(s, s);
+  x.u = __uint_as_float((unsigned)(k + 104) << 23);
+  x.u12 = __uint_as_float((unsigned)(k + 116) << 23);
+  return x;
+}
+// e with |v| < 2^(e+1), from the bits of |v| (zero and subnormals give -126;
+// infinities and NaNs 128, which the clamp of xsig_make absorbs: the NaN then
+// reaches the rest through the second FMA).
+__device__ __forceinline__ int p32_exp_bound(unsigned abs_bits) {
+  return (int)max(abs_bits >> 23, 1u) - 127;
+}
+// S += the grid parts of a xh (two lanes; S starts at -(terms) bits(sigma),
+// modulo 2^32), lo += the parts below the grid and a xl.
+__device__ __forceinline__ void xs_step(unsigned& S, f2p& lo, f2p a, f2p xh, f2p xl, f2p s2) {
+  const f2p t = f2p_fma(a, xh, s2);
+  const f2p nq = f2p_sub(s2, t);
+  lo = f2p_add(lo, f2p_fma(a, xh, nq));
+  lo = f2p_fma(a, xl, lo);
+  const float2 tt = f2p_split(t);
+  S += __float_as_uint(tt.x) + __float_as_uint(tt.y);
+}
+// u S + lo as a normalised double-single pair, for S a two's-complement
+// integer below 2^31 in magnitude: S = H 2^12 + L (0 <= L < 2^12) gives two
+// exactly representable parts, combined with lo by two TwoSums (Knuth).
+__device__ __forceinline__ float2 xs_value(unsigned S, float lo, const XSig& x) {
+  const int Si = (int)S;
+  const float xh = __fmul_rn(__int2float_rn(Si >> 12), x.u12);
+  const float xl = __fmul_rn(__int2float_rn(Si & 4095), x.u);
+  const float s = __fadd_rn(xh, xl);
+  float v = __fsub_rn(s, xh);
+  const float e = __fadd_rn(__fsub_rn(xh, __fsub_rn(s, v)), __fsub_rn(xl, v));
+  const float c = __fadd_rn(e, lo);
+  const float h = __fadd_rn(s, c);
+  v = __fsub_rn(h, s);
+  return make_float2(h, __fadd_rn(__fsub_rn(s, __fsub_rn(h, v)), __fsub_rn(c, v)));
+}
+// acc += u S + lo for |S| <= 2^24 (one exact conversion, one TwoSum).
+__device__ __forceinline__ void xs_flush(D2& acc, unsigned S, f2p lo, const XSig& x) {
+  const float xv = __fmul_rn(__int2float_rn((int)S), x.u);
+  const float2 l = f2p_split(lo);
+  const float s = __fadd_rn(acc.s, xv);
+  const float v = __fsub_rn(s, acc.s);
+  const float e = __fadd_rn(__fsub_rn(acc.s, __fsub_rn(s, v)), __fsub_rn(xv, v));
+  acc.s = s;
+  acc.c = __fadd_rn(acc.c, __fadd_rn(e, __fadd_rn(l.x, l.y)));
+}
+
 __device__ __forceinline__ unsigned p32_smem_addr(const void* p) {
   return (unsigned)__cvta_generic_to_shared(p);
 }
@@ -225,11 +305,11 @@ __host__ __device__ __forceinline__ int pass32_copy_width(const float* A, int64_
 }
 
 // Staging of one tile for the specialised bodies: rows [i0, i0 + R) of the NC
-// columns, W floats per copy.  Chunk c = t + 256 k of the tile is column
+// columns at pitch P, W floats per copy.  Chunk c = t + 256 k of the tile is column
 // c / (R/W), rows (c mod (R/W)) * W ..; with R/W a power of two each thread's
 // chunks advance by a fixed column step and (when R/W > 256) a fixed row
 // step, so the unrolled loop needs one pointer add per copy.
-template <int NC, int R, int W>
+template <int NC, int R, int W, int P>
 __device__ __forceinline__ void p32n_issue(const float* __restrict__ A, int64_t lda, int64_t d, int n,
                                            int64_t i0, float* buf) {
   constexpr int CPC = R / W;               // chunks per column
@@ -243,7 +323,7 @@ __device__ __forceinline__ void p32n_issue(const float* __restrict__ A, int64_t 
     const int rbytes = left >= W ? 4 * W : (left > 0 ? (int)left * 4 : 0);
     const float* src = A + i + (int64_t)j0 * lda;
     const int64_t step = (int64_t)JS * lda;
-    float* dst = buf + j0 * R + r;
+    float* dst = buf + j0 * P + r;
     int j = j0;
 #pragma unroll 8
     for (int k = 0; k < KT; ++k) {
@@ -252,7 +332,7 @@ __device__ __forceinline__ void p32n_issue(const float* __restrict__ A, int64_t 
       else if constexpr (W == 2) p32_cp8(dst, bytes > 0 ? src : A, bytes);
       else p32_cp4(dst, bytes > 0 ? src : A, bytes > 0);
       src += step;
-      dst += JS * R;
+      dst += JS * P;
       j += JS;
     }
   } else {
@@ -264,9 +344,9 @@ __device__ __forceinline__ void p32n_issue(const float* __restrict__ A, int64_t 
       const int64_t left = j < n ? d - i : 0;
       const int bytes = left >= W ? 4 * W : (left > 0 ? (int)left * 4 : 0);
       const float* s = bytes > 0 ? A + i + (int64_t)j * lda : A;
-      if constexpr (W == 4) p32_cp16(buf + j * R + r, s, bytes);
-      else if constexpr (W == 2) p32_cp8(buf + j * R + r, s, bytes);
-      else p32_cp4(buf + j * R + r, s, bytes > 0);
+      if constexpr (W == 4) p32_cp16(buf + j * P + r, s, bytes);
+      else if constexpr (W == 2) p32_cp8(buf + j * P + r, s, bytes);
+      else p32_cp4(buf + j * P + r, s, bytes > 0);
     }
   }
   p32_commit();
@@ -488,161 +568,209 @@ __device__ __forceinline__ void pass32g_body(const float* __restrict__ A, int64_
 }
 
 // Specialised body for NC = pass32_class(n) staged columns (n <= NC real).
-// Tile: R = 8192 / NC rows (RB = R / 32 row blocks of 32 rows).
+// Tile: R = TE / NC rows (RB = R / 32 row blocks of 32 rows), columns at
+// pitch P = pass32n_pitch(NC) in shared memory.
 //   dot phase   : warp w takes row blocks rb0 .. rb0 + DR - 1 and the DC
 //                 columns of column group cg (M = 8 / min(RB, 8) groups share a
 //                 row block; their partials are merged through shared memory);
 //                 lane = row, so a warp reads 32 consecutive rows of a column.
-//   column phase: warp w owns columns w*CC .. w*CC + CC - 1 (CC = NC / 8), lane
-//                 = row within each of the RB row blocks; the CC compensated
-//                 accumulators stay in registers across tiles and are summed
-//                 over the 32 lanes by shuffles once per CTA.
-// Both phases touch 32 elements per thread per tile, fully unrolled with
-// compile-time shared-memory offsets.
+//                 RESID: FP64, one DFMA per element.  Else the extraction
+//                 (xs_step) with one sigma for the pass, from the column
+//                 maxima of |A| that the residual pass recorded (cmax) and
+//                 the largest |ph_j| of each column.
+//   column phase: thread (jc, g) = (t mod NC, t / NC) takes column jc over
+//                 the RPT rows g RPT .. of the tile (G = T / NC row groups),
+//                 by the extraction with sigma from the column's maximum of
+//                 |A| (cmax; the residual pass takes the tile's own and keeps
+//                 the running maximum for its output) and the tile's largest
+//                 |w_i|, and flushes the tile's sum into a compensated pair.
+//                 A margin of 2^MG in sigma keeps that integer sum within 2^24
+//                 (an exact conversion).  16-byte reads of the column, and
+//                 of w_i (one address per row group: a broadcast).
+// Output: part[cta][0..n) the CTA's vector partial, [n], [n+1] the scalars
+// (RESID) or zeros, and for RESID [n+2, 2n+2) its column maxima of |A|
+// (stride pass_out_len(n) for RESID, n + 2 otherwise).
 template <int NC, bool RESID>
 __device__ __forceinline__ void pass32n_body(const float* __restrict__ A, int64_t lda, int64_t d, int n,
                                              int cw, const double* __restrict__ b,
                                              const double* __restrict__ vin,
+                                             const double* __restrict__ cmax,
                                              double* __restrict__ part, int cta, int nctas,
                                              unsigned char* smem) {
   constexpr int T = kP32Threads;
   constexpr int TE = pass32n_tile(NC), S = pass32n_stages(NC);
-  constexpr int R = TE / NC, RB = R / 32;
+  constexpr int R = TE / NC, RB = R / 32, P = pass32n_pitch(NC), TP = NC * P;
   constexpr int DR = RB >= 8 ? RB / 8 : 1;   // dot rows per thread
   constexpr int M = RB >= 8 ? 1 : 8 / RB;    // dot column groups per row block
   constexpr int DC = NC / M;                 // dot columns per thread
-  constexpr int CC = NC / 8;                 // column-phase columns per thread
   constexpr int WPB = 8 / M;                 // warps per column group
+  constexpr int G = T / NC, RPT = R / G;     // column phase: row groups, rows per thread
+  constexpr int MG = RPT <= 16 ? 2 : 3;      // RPT 2^(22 - MG) <= 2^24
+  static_assert(RPT % 4 == 0 && RPT <= 32 && G * NC == T, "column-phase shape");
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   float* tiles = reinterpret_cast<float*>(smem);
-  double* vd = reinterpret_cast<double*>(tiles + S * TE);  // NC: x (RESID) or (ph, pl)
+  unsigned char* vreg = reinterpret_cast<unsigned char*>(tiles + S * TP);  // 8 NC bytes
+  double* vd = reinterpret_cast<double*>(vreg);   // RESID: x
+  float4* pvx = reinterpret_cast<float4*>(vreg);  // else (ph0, ph1, pl0, pl1) per column pair
+  double* wpd = reinterpret_cast<double*>(vreg + 8 * NC);  // T: merge space
+  uint2* wpx = reinterpret_cast<uint2*>(wpd);
+  float* qhs = reinterpret_cast<float*>(wpd + T);  // R: w_i = qhs[i] + qls[i]
+  float* qls = qhs + R;
+  __shared__ unsigned s_wmax[2];  // by tile parity: bits of the largest |qh_i|
+  __shared__ int s_e;             // dot phase: max_j of the exponent bounds of cmax_j |ph_j|
   auto issue = [&](int64_t i0, float* buf) {
-    if (cw == 4) p32n_issue<NC, R, 4>(A, lda, d, n, i0, buf);
-    else if (cw == 2) p32n_issue<NC, R, 2>(A, lda, d, n, i0, buf);
-    else p32n_issue<NC, R, 1>(A, lda, d, n, i0, buf);
+    if (cw == 4) p32n_issue<NC, R, 4, P>(A, lda, d, n, i0, buf);
+    else if (cw == 2) p32n_issue<NC, R, 2, P>(A, lda, d, n, i0, buf);
+    else p32n_issue<NC, R, 1, P>(A, lda, d, n, i0, buf);
   };
-  // vector region (16 NC bytes): x as FP64 (RESID), or for column pairs
-  // (2h, 2h+1) pvx[h] = (xh0, xh1, -xh0, -xh1) and pvl[h] = (xl0, xl1)
-  float4* pvx = reinterpret_cast<float4*>(vd);
-  float2* pvl = reinterpret_cast<float2*>(pvx + NC / 2);
-  double* wpd = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(vd) + 16 * NC);  // T
-  float2* wv = reinterpret_cast<float2*>(wpd + T);                    // R: (hi, lo) per row
-  float2* wpf = reinterpret_cast<float2*>(wpd);
+  if (t == 0) {
+    s_wmax[0] = 0u;
+    s_wmax[1] = 0u;
+    s_e = -1000;
+  }
+  __syncthreads();
   if (RESID) {
     for (int j = t; j < NC; j += T) vd[j] = j < n ? vin[j] : 0.0;
   } else {
     for (int h = t; h < NC / 2; h += T) {
       const double x0 = 2 * h < n ? vin[2 * h] : 0.0, x1 = 2 * h + 1 < n ? vin[2 * h + 1] : 0.0;
       const float h0 = __double2float_rn(x0), h1 = __double2float_rn(x1);
-      pvx[h] = make_float4(h0, h1, -h0, -h1);
-      pvl[h] = make_float2(__double2float_rn(x0 - (double)h0), __double2float_rn(x1 - (double)h1));
+      pvx[h] = make_float4(h0, h1, __double2float_rn(x0 - (double)h0), __double2float_rn(x1 - (double)h1));
+      int e = -1000;
+      if (2 * h < n)
+        e = p32_exp_bound(__float_as_uint(__double2float_ru(cmax[2 * h]))) +
+            p32_exp_bound(__float_as_uint(fabsf(h0)));
+      if (2 * h + 1 < n)
+        e = max(e, p32_exp_bound(__float_as_uint(__double2float_ru(cmax[2 * h + 1]))) +
+                       p32_exp_bound(__float_as_uint(fabsf(h1))));
+      atomicMax(&s_e, e);
     }
   }
+  // column phase: this thread's column, row group and (not RESID) the
+  // exponent part of sigma from the column's maximum
+  const int jc = t % NC, g = t / NC;
+  int kc = -1000;
+  if (!RESID && jc < n) kc = p32_exp_bound(__float_as_uint(__double2float_ru(cmax[jc]))) + 3 + MG;
+  __syncthreads();
+  // |a_ij ph_j| < 2^(s_e + 2) = 2^(k - 1)
+  const XSig xd = xsig_make(RESID ? 0 : s_e + 3);
   const int rb0 = (w % WPB) * DR, cg = w / WPB;
-  D2P acc[CC / 2];  // columns (2c, 2c + 1) of this warp's column block
-#pragma unroll
-  for (int c = 0; c < CC / 2; ++c) acc[c] = D2P{0ull, 0ull};
+  D2 acc{0.f, 0.f};  // column jc over this thread's rows of every tile
+  float cm = 0.f;    // RESID: running maximum of |A| in column jc
   double s1 = 0.0, s2 = 0.0;
   const int64_t ntiles = (d + R - 1) / R;
   // S-stage pipeline: tiles cta + m nctas, m = 0, 1, ...; stage m mod S
   for (int m = 0; m < S - 1; ++m) {
     const int64_t tm = cta + (int64_t)m * nctas;
-    if (tm < ntiles) issue(tm * R, tiles + m * TE);
+    if (tm < ntiles) issue(tm * R, tiles + m * TP);
     else p32_commit();
   }
   for (int64_t m = 0;; ++m) {
     const int64_t tile = cta + m * nctas;
     if (tile >= ntiles) break;
-    __syncthreads();  // the stage refilled next and wv are free again
+    __syncthreads();  // the stage refilled next, qhs/qls and s_wmax[(m + 1) & 1] are free again
+    if (t == 0) s_wmax[(m + 1) & 1] = 0u;
     const int64_t next = tile + (int64_t)(S - 1) * nctas;
-    if (next < ntiles) issue(next * R, tiles + (int)((m + S - 1) % S) * TE);
+    if (next < ntiles) issue(next * R, tiles + (int)((m + S - 1) % S) * TP);
     else p32_commit();
     p32_wait<S - 1>();
     __syncthreads();
-    const float* tl = tiles + (int)(m % S) * TE;
+    const float* tl = tiles + (int)(m % S) * TP;
     const int64_t i0 = tile * R;
+    unsigned* wmax = &s_wmax[m & 1];
     // ---- dot phase
-    const float* tdot = tl + cg * DC * R + rb0 * 32 + lane;
+    const float* tdot = tl + cg * DC * P + rb0 * 32 + lane;
     if (RESID) {
       // four independent DFMA chains per row (FP64 latency), summed in order
       constexpr int KS = DC >= 4 ? 4 : DC;
       double wd[DR], wk[DR][KS];
 #pragma unroll
-      for (int m = 0; m < DR; ++m)
+      for (int q = 0; q < DR; ++q)
 #pragma unroll
-        for (int q = 0; q < KS; ++q) wk[m][q] = 0.0;
+        for (int kk = 0; kk < KS; ++kk) wk[q][kk] = 0.0;
 #pragma unroll
       for (int jj = 0; jj < DC; ++jj) {
         const double xj = vd[cg * DC + jj];
 #pragma unroll
-        for (int m = 0; m < DR; ++m)
-          wk[m][jj % KS] = fma(f2d_exact(tdot[jj * R + m * 32]), xj, wk[m][jj % KS]);
+        for (int q = 0; q < DR; ++q)
+          wk[q][jj % KS] = fma(f2d_exact(tdot[jj * P + q * 32]), xj, wk[q][jj % KS]);
       }
 #pragma unroll
-      for (int m = 0; m < DR; ++m) {
-        wd[m] = wk[m][0];
+      for (int q = 0; q < DR; ++q) {
+        wd[q] = wk[q][0];
 #pragma unroll
-        for (int q = 1; q < KS; ++q) wd[m] += wk[m][q];
+        for (int kk = 1; kk < KS; ++kk) wd[q] += wk[q][kk];
       }
       if (M == 1) {
+        unsigned mx = 0u;
 #pragma unroll
-        for (int m = 0; m < DR; ++m) {
-          const int r = (rb0 + m) * 32 + lane;
+        for (int q = 0; q < DR; ++q) {
+          const int r = (rb0 + q) * 32 + lane;
           const int64_t i = i0 + r;
           float h = 0.f, l = 0.f;
           if (i < d) {
             const double bi = b[i];
-            const double ri = bi - wd[m];
+            const double ri = bi - wd[q];
             s1 = fma(ri, ri, s1);
             s2 = fma(bi, bi, s2);
             h = __double2float_rn(ri);
             l = __double2float_rn(ri - (double)h);
           }
-          wv[r] = make_float2(h, l);
+          qhs[r] = h;
+          qls[r] = l;
+          mx = max(mx, __float_as_uint(fabsf(h)));
         }
+        mx = __reduce_max_sync(0xffffffffu, mx);
+        if (lane == 0) atomicMax(wmax, mx);
       } else {
         wpd[cg * R + rb0 * 32 + lane] = wd[0];
       }
     } else {
-      // column pairs (jj, jj + 1): lane 0 sums the even columns, lane 1 the odd
-      D2P wq[DR];
+      // column pairs (jj, jj + 1) as the two lanes; two rests per row
+      unsigned sx[DR];
+      f2p lo[DR][2];
 #pragma unroll
-      for (int m = 0; m < DR; ++m) wq[m] = D2P{0ull, 0ull};
+      for (int q = 0; q < DR; ++q) {
+        sx[q] = 0u - (unsigned)DC * xd.sb;
+        lo[q][0] = 0ull;
+        lo[q][1] = 0ull;
+      }
 #pragma unroll
       for (int jj = 0; jj < DC; jj += 2) {
         const float4 xv = pvx[(cg * DC + jj) / 2];
-        const float2 xl = pvl[(cg * DC + jj) / 2];
-        const f2p xh = f2p_make(xv.x, xv.y), nxh = f2p_make(xv.z, xv.w), xlp = f2p_make(xl.x, xl.y);
+        const f2p xh = f2p_make(xv.x, xv.y), xl = f2p_make(xv.z, xv.w);
 #pragma unroll
-        for (int m = 0; m < DR; ++m)
-          d2p_fma(wq[m], f2p_make(tdot[jj * R + m * 32], tdot[(jj + 1) * R + m * 32]), xh, nxh, xlp);
-      }
-      D2 wd[DR];
-#pragma unroll
-      for (int m = 0; m < DR; ++m) {
-        D2 e, o;
-        d2p_lanes(wq[m], e, o);
-        wd[m] = d2_merge(e, o);
+        for (int q = 0; q < DR; ++q)
+          xs_step(sx[q], lo[q][(jj >> 1) & 1],
+                  f2p_make(tdot[jj * P + q * 32], tdot[(jj + 1) * P + q * 32]), xh, xl, xd.s2);
       }
       if (M == 1) {
+        unsigned mx = 0u;
 #pragma unroll
-        for (int m = 0; m < DR; ++m) {
-          const float h = __fadd_rn(wd[m].s, wd[m].c);
-          wv[(rb0 + m) * 32 + lane] = make_float2(h, __fsub_rn(wd[m].c, __fsub_rn(h, wd[m].s)));
+        for (int q = 0; q < DR; ++q) {
+          const float2 l2 = f2p_split(f2p_add(lo[q][0], lo[q][1]));
+          const float2 v = xs_value(sx[q], __fadd_rn(l2.x, l2.y), xd);
+          const int r = (rb0 + q) * 32 + lane;
+          qhs[r] = v.x;
+          qls[r] = v.y;
+          mx = max(mx, __float_as_uint(fabsf(v.x)));
         }
+        mx = __reduce_max_sync(0xffffffffu, mx);
+        if (lane == 0) atomicMax(wmax, mx);
       } else {
-        wpf[cg * R + rb0 * 32 + lane] = make_float2(wd[0].s, wd[0].c);
+        const float2 l2 = f2p_split(f2p_add(lo[0][0], lo[0][1]));
+        wpx[cg * R + rb0 * 32 + lane] = make_uint2(sx[0], __float_as_uint(__fadd_rn(l2.x, l2.y)));
       }
     }
     if (M > 1) {
       __syncthreads();
-      if (t < R) {
+      if (t < R) {  // whole warps (R is a multiple of 32)
+        float h = 0.f, l = 0.f;
         if (RESID) {
           double wsum = 0.0;
 #pragma unroll
           for (int q = 0; q < M; ++q) wsum += wpd[q * R + t];
           const int64_t i = i0 + t;
-          float h = 0.f, l = 0.f;
           if (i < d) {
             const double bi = b[i];
             const double ri = bi - wsum;
@@ -651,42 +779,74 @@ __device__ __forceinline__ void pass32n_body(const float* __restrict__ A, int64_
             h = __double2float_rn(ri);
             l = __double2float_rn(ri - (double)h);
           }
-          wv[t] = make_float2(h, l);
         } else {
-          D2 a{wpf[t].x, wpf[t].y};
+          unsigned st = 0u;
+          float lt = 0.f;
 #pragma unroll
-          for (int q = 1; q < M; ++q) a = d2_merge(a, D2{wpf[q * R + t].x, wpf[q * R + t].y});
-          const float h = __fadd_rn(a.s, a.c);
-          wv[t] = make_float2(h, __fsub_rn(a.c, __fsub_rn(h, a.s)));
+          for (int q = 0; q < M; ++q) {
+            const uint2 e = wpx[q * R + t];
+            st += e.x;
+            lt = __fadd_rn(lt, __uint_as_float(e.y));
+          }
+          const float2 v = xs_value(st, lt, xd);
+          h = v.x;
+          l = v.y;
         }
+        qhs[t] = h;
+        qls[t] = l;
+        const unsigned mx = __reduce_max_sync(0xffffffffu, __float_as_uint(fabsf(h)));
+        if (lane == 0) atomicMax(wmax, mx);
       }
     }
     __syncthreads();
     // ---- column phase
     {
-      const float* tcol = tl + w * CC * R + lane;
+      const float* ca = tl + jc * P + g * RPT;
+      const float* qa = qhs + g * RPT;
+      const float* qb = qls + g * RPT;
+      float4 av[RPT / 4];
 #pragma unroll
-      for (int m = 0; m < RB; ++m) {
-        const float2 wm = wv[m * 32 + lane];
-        const f2p wh = f2p_make(wm.x, wm.x), nwh = f2p_make(-wm.x, -wm.x), wl = f2p_make(wm.y, wm.y);
+      for (int v = 0; v < RPT / 4; ++v) av[v] = *reinterpret_cast<const float4*>(ca + 4 * v);
+      int k = kc;
+      if (RESID) {
+        float ct = 0.f;
 #pragma unroll
-        for (int c = 0; c < CC / 2; ++c)
-          d2p_fma(acc[c], f2p_make(tcol[2 * c * R + m * 32], tcol[(2 * c + 1) * R + m * 32]), wh, nwh, wl);
+        for (int v = 0; v < RPT / 4; ++v)
+          ct = fmaxf(ct, fmaxf(fmaxf(fabsf(av[v].x), fabsf(av[v].y)), fmaxf(fabsf(av[v].z), fabsf(av[v].w))));
+        cm = fmaxf(cm, ct);
+        k = p32_exp_bound(__float_as_uint(ct)) + 3 + MG;
       }
+      // |a_ij qh_i| < 2^(ecol + eq + 2) = 2^(k - 1 - MG)
+      const XSig xc = xsig_make(k + p32_exp_bound(*wmax));
+      unsigned sx = 0u - (unsigned)RPT * xc.sb;
+      f2p lo0 = 0ull, lo1 = 0ull;
+#pragma unroll
+      for (int v = 0; v < RPT / 4; ++v) {
+        const float4 h4 = *reinterpret_cast<const float4*>(qa + 4 * v);
+        const float4 l4 = *reinterpret_cast<const float4*>(qb + 4 * v);
+        xs_step(sx, lo0, f2p_make(av[v].x, av[v].y), f2p_make(h4.x, h4.y), f2p_make(l4.x, l4.y), xc.s2);
+        xs_step(sx, lo1, f2p_make(av[v].z, av[v].w), f2p_make(h4.z, h4.w), f2p_make(l4.z, l4.w), xc.s2);
+      }
+      xs_flush(acc, sx, f2p_add(lo0, lo1), xc);
     }
   }
-  // ---- per-CTA partials: sum each column's accumulator over the 32 lanes
-  double* out = part + (int64_t)cta * (n + 2);
+  // ---- per-CTA partials: each column's G row groups summed in FP64
+  double* out = part + (int64_t)cta * (RESID ? pass_out_len(n) : (int64_t)n + 2);
+  __syncthreads();  // the last tile's reads of the merge space and the tiles are done
+  wpd[t] = (double)acc.s + (double)acc.c;  // t = g NC + jc
+  float* cmx = tiles;                       // T floats
+  if (RESID) cmx[t] = cm;
+  __syncthreads();
+  if (t < n) {
+    double s = 0.0;
+    float mx = 0.f;
 #pragma unroll
-  for (int c = 0; c < CC; ++c) {
-    D2 lo, hi;
-    d2p_lanes(acc[c / 2], lo, hi);
-    D2 a = (c & 1) ? hi : lo;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-      a = d2_merge(a, D2{__shfl_xor_sync(0xffffffffu, a.s, o), __shfl_xor_sync(0xffffffffu, a.c, o)});
-    const int j = w * CC + c;
-    if (lane == 0 && j < n) out[j] = (double)a.s + (double)a.c;
+    for (int gg = 0; gg < G; ++gg) {
+      s += wpd[gg * NC + t];
+      if (RESID) mx = fmaxf(mx, cmx[gg * NC + t]);
+    }
+    out[t] = s;
+    if (RESID) out[n + 2 + t] = (double)mx;
   }
   if (RESID) {
     __shared__ double sred[2][T / 32];

@@ -116,19 +116,25 @@ __device__ __forceinline__ void pass_body(const TA* __restrict__ A, int64_t lda,
 // out[j] = sum over CTAs of part[cta][j] (j < len), fixed order: block b
 // covers outputs 32b .. 32b+31 (lane = output); warp w sums CTAs w, w+8, ...;
 // the 8 warp sums are added in warp order.
+// Entries j < nsum are summed over the CTAs, the rest (nonnegative column
+// maxima) reduced by max.
 __device__ __forceinline__ void pass_reduce_body(const double* __restrict__ part, int nctas, int len,
-                                                 double* __restrict__ out, int blk) {
+                                                 int nsum, double* __restrict__ out, int blk) {
   __shared__ double ws[8][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int j = blk * 32 + lane;
+  const bool sum = j < nsum;
   double s = 0.0;
   if (j < len)
-    for (int q = warp; q < nctas; q += 8) s += part[(int64_t)q * len + j];
+    for (int q = warp; q < nctas; q += 8) {
+      const double v = part[(int64_t)q * len + j];
+      s = sum ? s + v : fmax(s, v);
+    }
   ws[warp][lane] = s;
   __syncthreads();
   if (warp == 0 && j < len) {
     double t = 0.0;
-    for (int w = 0; w < 8; ++w) t += ws[w][lane];
+    for (int w = 0; w < 8; ++w) t = sum ? t + ws[w][lane] : fmax(t, ws[w][lane]);
     out[j] = t;
   }
 }
