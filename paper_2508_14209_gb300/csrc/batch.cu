@@ -261,6 +261,7 @@ constexpr int kGather = 6;
 struct BatchCtl {
   double rr, relres, rr_prev, relres_prev, relres_sns, gain;
   int iters, conv, ref, by_rule;
+  int stop;  // stalled without the evidence of convergence: no more steps
 };
 
 // After the first FP64 residual pass: ||r||^2 and the relative residual of
@@ -287,6 +288,7 @@ __global__ void __launch_bounds__(256) batch_ref_init_kernel(const BatchJob* __r
     c.conv = refine ? 0 : 1;
     c.ref = 0;
     c.by_rule = 0;
+    c.stop = 0;
     if (!c.conv) any = 1;
   }
   __syncthreads();
@@ -304,7 +306,7 @@ __global__ void batch_outer_arm_kernel(const BatchJob* __restrict__ jobs, int ni
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nitems; j += gridDim.x * blockDim.x) {
     const BatchJob& J = jobs[j];
     BatchCtl& c = ctl[j];
-    c.ref = c.conv ? 0 : 1;
+    c.ref = (c.conv || c.stop) ? 0 : 1;
     refining[j] = c.ref;
     for (int q = 0; q < kScCount; ++q) J.sc[q] = 0.0;
     J.sc[2] = c.ref ? 1.0 : 0.0;
@@ -355,8 +357,10 @@ __global__ void batch_post_inner_kernel(const BatchJob* __restrict__ jobs, int n
 // End of an outer step: the rechecked problems' new residuals; converged
 // when the solve ended by its gain rule and the FP64 residual confirms the
 // predicted decrease to tol * ||r||^2, or when the relative residual moved
-// by at most tol; then the outer loop's condition (some problem left,
-// fewer than max_iter steps taken).
+// by at most tol while the inner iterations so far stay within
+// kStallIters * n (a stall after more is a preconditioner too poor to trust:
+// the problem stops unconverged); then the outer loop's condition (some
+// problem left, fewer than max_iter steps taken).
 __global__ void __launch_bounds__(256) batch_outer_check_kernel(const BatchJob* __restrict__ jobs,
                                                                 int nitems, BatchCtl* __restrict__ ctl,
                                                                 const int* __restrict__ recheck, double tol,
@@ -374,10 +378,13 @@ __global__ void __launch_bounds__(256) batch_outer_check_kernel(const BatchJob* 
       const double predicted = c.rr_prev - c.gain;
       c.rr = rr;
       c.relres = relres;
-      if ((c.by_rule && fabs(rr - predicted) <= tol * rr) || fabs(c.relres_prev - relres) <= tol * relres)
+      const bool stalled = fabs(c.relres_prev - relres) <= tol * relres;
+      if ((c.by_rule && fabs(rr - predicted) <= tol * rr) || (stalled && c.iters <= kStallIters * J.n))
         c.conv = 1;
+      else if (stalled)
+        c.stop = 1;
     }
-    if (!c.conv) any = 1;
+    if (!c.conv && !c.stop) any = 1;
   }
   __syncthreads();
   if (threadIdx.x == 0) {

@@ -758,13 +758,17 @@ int ms_lstsq(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, const 
       // Converged when the solve ended by its gain rule and the true FP64
       // residual confirms the decrease the CG recurrences predicted (no loss
       // to the inner arithmetic), or when the relative residual no longer
-      // moves by more than tol.
+      // moves by more than tol while the inner iterations so far stay within
+      // kStallIters * n.  A stall after more iterations means a
+      // preconditioner too poor to trust the stall: stop, unconverged.
       const double predicted = rr_prev - h[6];
+      const bool stalled = std::fabs(relres_prev - relres) <= tol * relres;
       if ((h[7] != 0.0 && std::fabs(rr - predicted) <= tol * rr) ||
-          std::fabs(relres_prev - relres) <= tol * relres) {
+          (stalled && inner_total <= kStallIters * n)) {
         converged = 1;
         break;
       }
+      if (stalled) break;
     }
     iters = inner_total;
     if (!converged) status = MSK_ENOCONV;

@@ -295,6 +295,17 @@ __device__ __forceinline__ void p32_cp8(float* dst, const float* src, int bytes)
                : "memory");
 }
 
+// Copy of W whole floats (no zero fill) to the shared address dst.
+template <int W>
+__device__ __forceinline__ void p32_cp_whole(unsigned dst, const float* src) {
+  if constexpr (W == 4)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+  else if constexpr (W == 2)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
+
 // Copy width (floats per cp.async) usable for A: 4 when A is 16-byte aligned
 // and lda a multiple of 4, 2 when 8-byte aligned with lda even, else 1.
 __host__ __device__ __forceinline__ int pass32_copy_width(const float* A, int64_t lda) {
@@ -323,6 +334,14 @@ __device__ __forceinline__ void p32n_issue(const float* __restrict__ A, int64_t 
     const int rbytes = left >= W ? 4 * W : (left > 0 ? (int)left * 4 : 0);
     const float* src = A + i + (int64_t)j0 * lda;
     const int64_t step = (int64_t)JS * lda;
+    if (n == NC && i0 + R <= d) {
+      // a whole tile: every copy full, shared offsets known at compile time
+      const unsigned d0 = p32_smem_addr(buf + j0 * P + r);
+#pragma unroll
+      for (int k = 0; k < KT; ++k) p32_cp_whole<W>(d0 + 4u * (unsigned)(k * JS * P), src + k * step);
+      p32_commit();
+      return;
+    }
     float* dst = buf + j0 * P + r;
     int j = j0;
 #pragma unroll 8
@@ -567,17 +586,33 @@ __device__ __forceinline__ void pass32g_body(const float* __restrict__ A, int64_
   }
 }
 
+// Dot phase of the operator pass (not RESID): warp w takes rows w RW .. w RW
+// + RW - 1 of the tile (RW = R / 8) with LR = 32 / RW lanes per row; lane
+// (rs, cl) = (lane mod RW, lane / RW) sums the DCL = NC / LR columns
+// dot_col(cl, k), k = 0 .. DCL - 1: runs of SB = RW / 4 consecutive columns,
+// run cl of every LR runs.  At a column pitch of 4 mod 32 the 32 lanes of one
+// load (fixed k) touch banks RW cl + rs + const, all distinct; a row's LR
+// partial sums meet by shuffles, with no shared-memory merge and no barrier.
+template <int NC>
+struct DotMap {
+  static constexpr int R = pass32n_tile(NC) / NC, RW = R / 8, LR = 32 / RW, SB = RW / 4, DCL = NC / LR;
+  static_assert(RW >= 4 && RW <= 32 && DCL % 2 == 0, "dot map");
+};
+template <int NC>
+__host__ __device__ constexpr int dot_col(int cl, int k) {
+  return DotMap<NC>::SB * cl + k % DotMap<NC>::SB + (k / DotMap<NC>::SB) * DotMap<NC>::SB * DotMap<NC>::LR;
+}
+
 // Specialised body for NC = pass32_class(n) staged columns (n <= NC real).
 // Tile: R = TE / NC rows (RB = R / 32 row blocks of 32 rows), columns at
 // pitch P = pass32n_pitch(NC) in shared memory.
-//   dot phase   : warp w takes row blocks rb0 .. rb0 + DR - 1 and the DC
-//                 columns of column group cg (M = 8 / min(RB, 8) groups share a
-//                 row block; their partials are merged through shared memory);
-//                 lane = row, so a warp reads 32 consecutive rows of a column.
-//                 RESID: FP64, one DFMA per element.  Else the extraction
-//                 (xs_step) with one sigma for the pass, from the column
-//                 maxima of |A| that the residual pass recorded (cmax) and
-//                 the largest |ph_j| of each column.
+//   dot phase   : RESID: warp w takes row blocks rb0 .. rb0 + DR - 1 and
+//                 the DC columns of column group cg (M = 8 / min(RB, 8) groups
+//                 share a row block; their partials are merged through shared
+//                 memory); lane = row; FP64, one DFMA per element.  Else the
+//                 lanes of DotMap, by the extraction (xs_step) with one sigma
+//                 for the pass, from the column maxima of |A| that the
+//                 residual pass recorded (cmax) and the largest |ph_j|.
 //   column phase: thread (jc, g) = (t mod NC, t / NC) takes column jc over
 //                 the RPT rows g RPT .. of the tile (G = T / NC row groups),
 //                 by the extraction with sigma from the column's maximum of
@@ -606,6 +641,7 @@ __device__ __forceinline__ void pass32n_body(const float* __restrict__ A, int64_
   constexpr int WPB = 8 / M;                 // warps per column group
   constexpr int G = T / NC, RPT = R / G;     // column phase: row groups, rows per thread
   constexpr int MG = RPT <= 16 ? 2 : 3;      // RPT 2^(22 - MG) <= 2^24
+  constexpr int DLR = DotMap<NC>::LR;        // operator pass: lanes per row
   static_assert(RPT % 4 == 0 && RPT <= 32 && G * NC == T, "column-phase shape");
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   float* tiles = reinterpret_cast<float*>(smem);
@@ -613,7 +649,6 @@ __device__ __forceinline__ void pass32n_body(const float* __restrict__ A, int64_
   double* vd = reinterpret_cast<double*>(vreg);   // RESID: x
   float4* pvx = reinterpret_cast<float4*>(vreg);  // else (ph0, ph1, pl0, pl1) per column pair
   double* wpd = reinterpret_cast<double*>(vreg + 8 * NC);  // T: merge space
-  uint2* wpx = reinterpret_cast<uint2*>(wpd);
   float* qhs = reinterpret_cast<float*>(wpd + T);  // R: w_i = qhs[i] + qls[i]
   float* qls = qhs + R;
   __shared__ unsigned s_wmax[2];  // by tile parity: bits of the largest |qh_i|
@@ -632,16 +667,20 @@ __device__ __forceinline__ void pass32n_body(const float* __restrict__ A, int64_
   if (RESID) {
     for (int j = t; j < NC; j += T) vd[j] = j < n ? vin[j] : 0.0;
   } else {
+    // entry h = (k2, cl) of the dot phase's table: columns dot_col(cl, 2 k2)
+    // and dot_col(cl, 2 k2 + 1)
     for (int h = t; h < NC / 2; h += T) {
-      const double x0 = 2 * h < n ? vin[2 * h] : 0.0, x1 = 2 * h + 1 < n ? vin[2 * h + 1] : 0.0;
+      const int cl = h % DLR, k = 2 * (h / DLR);
+      const int c0 = dot_col<NC>(cl, k), c1 = dot_col<NC>(cl, k + 1);
+      const double x0 = c0 < n ? vin[c0] : 0.0, x1 = c1 < n ? vin[c1] : 0.0;
       const float h0 = __double2float_rn(x0), h1 = __double2float_rn(x1);
       pvx[h] = make_float4(h0, h1, __double2float_rn(x0 - (double)h0), __double2float_rn(x1 - (double)h1));
       int e = -1000;
-      if (2 * h < n)
-        e = p32_exp_bound(__float_as_uint(__double2float_ru(cmax[2 * h]))) +
+      if (c0 < n)
+        e = p32_exp_bound(__float_as_uint(__double2float_ru(cmax[c0]))) +
             p32_exp_bound(__float_as_uint(fabsf(h0)));
-      if (2 * h + 1 < n)
-        e = max(e, p32_exp_bound(__float_as_uint(__double2float_ru(cmax[2 * h + 1]))) +
+      if (c1 < n)
+        e = max(e, p32_exp_bound(__float_as_uint(__double2float_ru(cmax[c1]))) +
                        p32_exp_bound(__float_as_uint(fabsf(h1))));
       atomicMax(&s_e, e);
     }
@@ -668,13 +707,14 @@ __device__ __forceinline__ void pass32n_body(const float* __restrict__ A, int64_
   for (int64_t m = 0;; ++m) {
     const int64_t tile = cta + m * nctas;
     if (tile >= ntiles) break;
-    __syncthreads();  // the stage refilled next, qhs/qls and s_wmax[(m + 1) & 1] are free again
+    p32_wait<S - 2>();  // this thread's copies of tile m have landed
+    // everyone's have, and tile m - 1 is consumed: its stage (refilled next),
+    // qhs/qls and s_wmax[(m + 1) & 1] are free
+    __syncthreads();
     if (t == 0) s_wmax[(m + 1) & 1] = 0u;
     const int64_t next = tile + (int64_t)(S - 1) * nctas;
     if (next < ntiles) issue(next * R, tiles + (int)((m + S - 1) % S) * TP);
     else p32_commit();
-    p32_wait<S - 1>();
-    __syncthreads();
     const float* tl = tiles + (int)(m % S) * TP;
     const int64_t i0 = tile * R;
     unsigned* wmax = &s_wmax[m & 1];
@@ -726,71 +766,50 @@ __device__ __forceinline__ void pass32n_body(const float* __restrict__ A, int64_
         wpd[cg * R + rb0 * 32 + lane] = wd[0];
       }
     } else {
-      // column pairs (jj, jj + 1) as the two lanes; two rests per row
-      unsigned sx[DR];
-      f2p lo[DR][2];
+      // lane (rs, cl) of DotMap: column pairs (k, k + 1) as the two lanes
+      constexpr int RW = DotMap<NC>::RW, DCL = DotMap<NC>::DCL;
+      const int rs = lane % RW, cl = lane / RW, r = w * RW + rs;
+      const float* ta = tl + (size_t)(DotMap<NC>::SB * cl) * P + r;
+      unsigned sx = 0u - (unsigned)DCL * xd.sb;
+      f2p lo[2] = {0ull, 0ull};
 #pragma unroll
-      for (int q = 0; q < DR; ++q) {
-        sx[q] = 0u - (unsigned)DC * xd.sb;
-        lo[q][0] = 0ull;
-        lo[q][1] = 0ull;
+      for (int k = 0; k < DCL; k += 2) {
+        const float4 xv = pvx[(k / 2) * DLR + cl];
+        xs_step(sx, lo[(k >> 1) & 1], f2p_make(ta[dot_col<NC>(0, k) * P], ta[dot_col<NC>(0, k + 1) * P]),
+                f2p_make(xv.x, xv.y), f2p_make(xv.z, xv.w), xd.s2);
       }
+      const float2 l2 = f2p_split(f2p_add(lo[0], lo[1]));
+      float ls = __fadd_rn(l2.x, l2.y);
 #pragma unroll
-      for (int jj = 0; jj < DC; jj += 2) {
-        const float4 xv = pvx[(cg * DC + jj) / 2];
-        const f2p xh = f2p_make(xv.x, xv.y), xl = f2p_make(xv.z, xv.w);
-#pragma unroll
-        for (int q = 0; q < DR; ++q)
-          xs_step(sx[q], lo[q][(jj >> 1) & 1],
-                  f2p_make(tdot[jj * P + q * 32], tdot[(jj + 1) * P + q * 32]), xh, xl, xd.s2);
+      for (int o = RW; o < 32; o <<= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        ls = __fadd_rn(ls, __shfl_xor_sync(0xffffffffu, ls, o));
       }
-      if (M == 1) {
-        unsigned mx = 0u;
-#pragma unroll
-        for (int q = 0; q < DR; ++q) {
-          const float2 l2 = f2p_split(f2p_add(lo[q][0], lo[q][1]));
-          const float2 v = xs_value(sx[q], __fadd_rn(l2.x, l2.y), xd);
-          const int r = (rb0 + q) * 32 + lane;
-          qhs[r] = v.x;
-          qls[r] = v.y;
-          mx = max(mx, __float_as_uint(fabsf(v.x)));
-        }
-        mx = __reduce_max_sync(0xffffffffu, mx);
-        if (lane == 0) atomicMax(wmax, mx);
-      } else {
-        const float2 l2 = f2p_split(f2p_add(lo[0][0], lo[0][1]));
-        wpx[cg * R + rb0 * 32 + lane] = make_uint2(sx[0], __float_as_uint(__fadd_rn(l2.x, l2.y)));
+      unsigned mx = 0u;
+      if (cl == 0) {
+        const float2 v = xs_value(sx, ls, xd);
+        qhs[r] = v.x;
+        qls[r] = v.y;
+        mx = __float_as_uint(fabsf(v.x));
       }
+      mx = __reduce_max_sync(0xffffffffu, mx);
+      if (lane == 0) atomicMax(wmax, mx);
     }
-    if (M > 1) {
+    if (RESID && M > 1) {
       __syncthreads();
       if (t < R) {  // whole warps (R is a multiple of 32)
         float h = 0.f, l = 0.f;
-        if (RESID) {
-          double wsum = 0.0;
+        double wsum = 0.0;
 #pragma unroll
-          for (int q = 0; q < M; ++q) wsum += wpd[q * R + t];
-          const int64_t i = i0 + t;
-          if (i < d) {
-            const double bi = b[i];
-            const double ri = bi - wsum;
-            s1 = fma(ri, ri, s1);
-            s2 = fma(bi, bi, s2);
-            h = __double2float_rn(ri);
-            l = __double2float_rn(ri - (double)h);
-          }
-        } else {
-          unsigned st = 0u;
-          float lt = 0.f;
-#pragma unroll
-          for (int q = 0; q < M; ++q) {
-            const uint2 e = wpx[q * R + t];
-            st += e.x;
-            lt = __fadd_rn(lt, __uint_as_float(e.y));
-          }
-          const float2 v = xs_value(st, lt, xd);
-          h = v.x;
-          l = v.y;
+        for (int q = 0; q < M; ++q) wsum += wpd[q * R + t];
+        const int64_t i = i0 + t;
+        if (i < d) {
+          const double bi = b[i];
+          const double ri = bi - wsum;
+          s1 = fma(ri, ri, s1);
+          s2 = fma(bi, bi, s2);
+          h = __double2float_rn(ri);
+          l = __double2float_rn(ri - (double)h);
         }
         qhs[t] = h;
         qls[t] = l;

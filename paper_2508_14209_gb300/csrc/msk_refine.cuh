@@ -10,6 +10,13 @@
 
 namespace msk {
 
+// A stall of the relative residual between outer steps counts as
+// convergence only while the inner CG iterations so far stay within
+// kStallIters * n: CG ends in at most n steps in exact arithmetic and a
+// well-preconditioned solve takes far fewer; after more, the preconditioner
+// is too poor for a stall to show that x sits at the minimiser.
+constexpr int kStallIters = 4;
+
 // ---------------------------------------------------------------------------
 // Row-tiled FP64 passes over an FP64 A (tiles of kPR rows, whole rows in
 // shared memory).  Passes over an FP32 A are in msk_pass.cuh.
