@@ -144,10 +144,14 @@ __global__ void batch_gemm_reduce_kernel(const BatchJob* __restrict__ jobs) {
 // the cluster's first CTA (the refined path forms x0 = R^{-1} c after the
 // explicit inverse instead).
 __global__ void __launch_bounds__(kQrThreads) batch_qr_kernel(const BatchJob* __restrict__ jobs,
-                                                             size_t smem_cap, int solve) {
+                                                             size_t smem_cap, int solve, int flow,
+                                                             int* tflag) {
   extern __shared__ __align__(16) double bqr_dyn[];
   const BatchJob& J = jobs[blockIdx.y];
-  if (qr_smem_bytes(J.p, J.ncol, (int)cg::this_cluster().num_blocks()) <= smem_cap)
+  const int CL = (int)cg::this_cluster().num_blocks();
+  if (flow && qr_flow_smem_bytes(J.p, J.ncol, CL) <= smem_cap)
+    qr_cluster_flow_body(J.Z, J.p, J.ncol, J.p, bqr_dyn, tflag);
+  else if (qr_smem_bytes(J.p, J.ncol, CL) <= smem_cap)
     qr_cluster_smem_body(J.Z, J.p, J.ncol, J.p, bqr_dyn);
   else
     qr_cluster_body(J.Z, J.p, J.ncol, J.p);
@@ -657,9 +661,19 @@ int msk_batch_lstsq(const msk_batch_item* items, int nitems, int refine, double 
   const int round_len = (int)std::min<long long>(16, std::max<long long>(1, tune_get("batch.round", kRound)));
   const unsigned gblocks = (unsigned)((nitems + 255) / 256);
   const dim3 rgrid((unsigned)((pass_out_len(P.max_n) + 31) / 32), nitems);
+  // cluster QR: the flow form where it fits (knob "qr.flow"), else the
+  // look-ahead on-chip form, else the global-memory form
+  const int qflow = tune_get("qr.flow", 0) != 0 ? 1 : 0;
   size_t qsm = 0;
-  for (const BatchJob& J : P.jobs)
-    if (qr_smem_fits(J.p, J.ncol, 16)) qsm = std::max(qsm, qr_smem_bytes(J.p, J.ncol, 16));
+  for (const BatchJob& J : P.jobs) {
+    if (qflow && qr_flow_fits(J.p, J.ncol, 16)) qsm = std::max(qsm, qr_flow_smem_bytes(J.p, J.ncol, 16));
+    else if (qr_smem_fits(J.p, J.ncol, 16)) qsm = std::max(qsm, qr_smem_bytes(J.p, J.ncol, 16));
+  }
+  int* qtflag = nullptr;
+  if (qflow) {
+    const int frc = tc_timeout_flag(&qtflag);
+    if (frc) return frc;
+  }
   // Function attributes before any capture begins.
   MSK_CUDA(cudaFuncSetAttribute(batch_qr_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   if (qsm) MSK_ALLOW_SMEM(batch_qr_kernel);
@@ -689,7 +703,7 @@ int msk_batch_lstsq(const msk_batch_item* items, int nitems, int refine, double 
     std::memcpy(&tb, &tol, sizeof(tb));
     push(tb);
     push(P.max_yk), push(P.max_pk), push(P.max_k), push(P.max_npad), push(P.max_n), push(P.max_nt);
-    push(P.total_items), push((int64_t)qsm), push(sms);
+    push(P.total_items), push((int64_t)qsm), push(sms), push(qflow);
     push((int64_t)P.widths.size());
     for (size_t c = 0; c < P.widths.size(); ++c)
       push(P.widths[c]), push((int64_t)P.cs_off[c]), push((int64_t)P.tiles_off[c]), push((int64_t)P.cs[c].size()),
@@ -766,7 +780,8 @@ int msk_batch_lstsq(const msk_batch_item* items, int nitems, int refine, double 
       at[0].val.clusterDim.z = 1;
       cfg.attrs = at;
       cfg.numAttrs = 1;
-      MSK_CUDA(cudaLaunchKernelEx(&cfg, batch_qr_kernel, (const BatchJob*)jobs_dev, qsm, refine ? 0 : 1));
+      MSK_CUDA(cudaLaunchKernelEx(&cfg, batch_qr_kernel, (const BatchJob*)jobs_dev, qsm, refine ? 0 : 1, qflow,
+                                  qtflag));
     }
     if (refine) {  // R^{-1} (the preconditioner) and from it x0 = R^{-1} c
       batch_tri_inverse_kernel<<<dim3((P.max_n + 7) / 8, nitems), 256, 0, s>>>(jobs_dev);

@@ -181,6 +181,8 @@ int launch_oz_prepare_g(uint64_t gkey, int64_t p, int64_t k, int64_t ncol, void*
                         cudaStream_t st);
 // qr.cu
 int launch_householder_qr(double* W, int64_t m, int64_t c, int64_t ldw, cudaStream_t st);
+// Whether the cluster QR of an m x c matrix on CL CTAs runs its flow form.
+bool qr_use_flow(int64_t m, int64_t c, int CL);
 int launch_trsv_upper(const double* R, int64_t n, int64_t ldr, const double* rhs, double* x,
                       int* status, bool transposed, cudaStream_t st);
 int launch_cholesky(double* Gm, int64_t n, int64_t ldg, double* R, int64_t ldr, int* status,

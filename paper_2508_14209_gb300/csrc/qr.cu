@@ -27,16 +27,27 @@
 namespace msk {
 
 
-// smem_cap: dynamic shared memory of the launch; the on-chip form runs when
-// the owned columns fit in it.
+// smem_cap: dynamic shared memory of the launch; flow != 0: the flow form
+// (sized for it); else the look-ahead on-chip form when the owned columns
+// fit in smem_cap, the global-memory form otherwise.  tflag: set when a
+// bounded wait of the flow form expires.
 __global__ void __launch_bounds__(kQrThreads) qr_cluster_kernel(double* __restrict__ W, int m, int c,
-                                                              int64_t ldw, size_t smem_cap) {
+                                                              int64_t ldw, size_t smem_cap, int flow,
+                                                              int* tflag) {
   extern __shared__ __align__(16) double qr_dyn[];
   const int CL = (int)cg::this_cluster().num_blocks();
-  if (qr_smem_bytes(m, c, CL) <= smem_cap)
+  if (flow)
+    qr_cluster_flow_body(W, m, c, ldw, qr_dyn, tflag);
+  else if (qr_smem_bytes(m, c, CL) <= smem_cap)
     qr_cluster_smem_body(W, m, c, ldw, qr_dyn);
   else
     qr_cluster_body(W, m, c, ldw);
+}
+
+// The flow form (knob "qr.flow", default off: measured slower) when its
+// shared memory fits.
+bool qr_use_flow(int64_t m, int64_t c, int CL) {
+  return tune_get("qr.flow", 0) != 0 && qr_flow_fits((int)m, (int)c, CL);
 }
 
 int launch_householder_qr(double* W, int64_t m, int64_t c, int64_t ldw, cudaStream_t st) {
@@ -76,10 +87,18 @@ int launch_householder_qr(double* W, int64_t m, int64_t c, int64_t ldw, cudaStre
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  const size_t smem = qr_smem_fits((int)m, (int)c, CL) ? qr_smem_bytes((int)m, (int)c, CL) : 0;
+  const bool flow = qr_use_flow(m, c, CL);
+  const size_t smem = flow ? qr_flow_smem_bytes((int)m, (int)c, CL)
+                           : (qr_smem_fits((int)m, (int)c, CL) ? qr_smem_bytes((int)m, (int)c, CL) : 0);
+  int* tflag = nullptr;
+  if (flow) {
+    const int frc = tc_timeout_flag(&tflag);
+    if (frc) return frc;
+  }
   if (smem) MSK_ALLOW_SMEM(qr_cluster_kernel);
   cfg.dynamicSmemBytes = smem;
-  MSK_CUDA(cudaLaunchKernelEx(&cfg, qr_cluster_kernel, W, (int)m, (int)c, ldw, smem));
+  MSK_CUDA(cudaLaunchKernelEx(&cfg, qr_cluster_kernel, W, (int)m, (int)c, ldw, smem, flow ? 1 : 0,
+                              tflag));
   return MSK_OK;
 }
 

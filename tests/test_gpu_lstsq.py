@@ -52,6 +52,30 @@ def test_householder_r_matches_oracle(msk, orc, m, c):
     assert np.allclose(R.T @ R, Z.T @ Z, rtol=0, atol=8 * m * EPS64 * nz * nz)
 
 
+# The cluster QR's two on-chip forms: the flow form (per-reflector mbarriers,
+# deferred updates; the default) and the look-ahead form behind one split
+# cluster barrier per column (knob qr.flow = 0) both match the oracle.
+@pytest.mark.parametrize("m,c", [(9, 9), (64, 17), (129, 65), (512, 129), (1024, 257), (300, 17),
+                                 (40, 40)])
+@pytest.mark.parametrize("flow", [0, 1])
+def test_householder_forms_match_oracle(msk, orc, m, c, flow):
+    Z = np.random.default_rng(m * 13 + c).standard_normal((m, c))
+    W = dev_colmajor(Z, msk)
+    msk.tune_set("qr.flow", flow)
+    try:
+        msk.msk_householder_qr(W)
+        torch.cuda.synchronize()
+    finally:
+        msk.tune_clear("qr.flow")
+    assert msk.msk_take_timeout() == 0
+    Wh = W.cpu().numpy()
+    R = Wh[:c, :c]
+    nz = np.linalg.norm(Z)
+    assert np.all(Wh[np.tril_indices(m, -1, c)] == 0.0)
+    assert np.allclose(R, orc.householder_r(Z), rtol=0, atol=4 * m * EPS64 * nz)
+    assert np.allclose(R.T @ R, Z.T @ Z, rtol=0, atol=8 * m * EPS64 * nz * nz)
+
+
 def test_trsv_and_zero_pivot(msk):
     rng = np.random.default_rng(3)
     n = 200
