@@ -694,6 +694,13 @@ __device__ __forceinline__ void pass32n_body(const float* __restrict__ A, int64_
   // |a_ij ph_j| < 2^(s_e + 2) = 2^(k - 1)
   const XSig xd = xsig_make(RESID ? 0 : s_e + 3);
   const int rb0 = (w % WPB) * DR, cg = w / WPB;
+  // operator pass at <= 16 columns per lane: this lane's (ph, pl) pairs in
+  // registers for the whole pass (they are the same in every tile)
+  float4 vreg_x[DotMap<NC>::DCL <= 16 ? DotMap<NC>::DCL / 2 : 1];
+  if constexpr (!RESID && DotMap<NC>::DCL <= 16) {
+#pragma unroll
+    for (int k2 = 0; k2 < DotMap<NC>::DCL / 2; ++k2) vreg_x[k2] = pvx[k2 * DLR + (lane / DotMap<NC>::RW)];
+  }
   D2 acc{0.f, 0.f};  // column jc over this thread's rows of every tile
   float cm = 0.f;    // RESID: running maximum of |A| in column jc
   double s1 = 0.0, s2 = 0.0;
@@ -774,7 +781,9 @@ __device__ __forceinline__ void pass32n_body(const float* __restrict__ A, int64_
       f2p lo[2] = {0ull, 0ull};
 #pragma unroll
       for (int k = 0; k < DCL; k += 2) {
-        const float4 xv = pvx[(k / 2) * DLR + cl];
+        float4 xv;
+        if constexpr (DCL <= 16) xv = vreg_x[k / 2];
+        else xv = pvx[(k / 2) * DLR + cl];
         xs_step(sx, lo[(k >> 1) & 1], f2p_make(ta[dot_col<NC>(0, k) * P], ta[dot_col<NC>(0, k + 1) * P]),
                 f2p_make(xv.x, xv.y), f2p_make(xv.z, xv.w), xd.s2);
       }
