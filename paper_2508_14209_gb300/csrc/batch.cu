@@ -347,7 +347,8 @@ __global__ void batch_post_inner_kernel(const BatchJob* __restrict__ jobs, int n
     const BatchJob& J = jobs[j];
     c.iters += (int)J.sc[4];
     if (J.sc[5] != 0.0) {
-      c.conv = 1;
+      if (c.iters <= kStallIters * J.n) c.conv = 1;
+      else c.stop = 1;
     } else {
       recheck[j] = 1;
       c.rr_prev = c.rr;
@@ -361,10 +362,10 @@ __global__ void batch_post_inner_kernel(const BatchJob* __restrict__ jobs, int n
 // End of an outer step: the rechecked problems' new residuals; converged
 // when the solve ended by its gain rule and the FP64 residual confirms the
 // predicted decrease to tol * ||r||^2, or when the relative residual moved
-// by at most tol while the inner iterations so far stay within
-// kStallIters * n (a stall after more is a preconditioner too poor to trust:
-// the problem stops unconverged); then the outer loop's condition (some
-// problem left, fewer than max_iter steps taken).
+// by at most tol, in either case while the inner iterations so far stay
+// within kStallIters * n (after more, a preconditioner too poor to trust
+// either test: the problem stops unconverged); then the outer loop's
+// condition (some problem left, fewer than max_iter steps taken).
 __global__ void __launch_bounds__(256) batch_outer_check_kernel(const BatchJob* __restrict__ jobs,
                                                                 int nitems, BatchCtl* __restrict__ ctl,
                                                                 const int* __restrict__ recheck, double tol,
@@ -382,11 +383,10 @@ __global__ void __launch_bounds__(256) batch_outer_check_kernel(const BatchJob* 
       const double predicted = c.rr_prev - c.gain;
       c.rr = rr;
       c.relres = relres;
-      const bool stalled = fabs(c.relres_prev - relres) <= tol * relres;
-      if ((c.by_rule && fabs(rr - predicted) <= tol * rr) || (stalled && c.iters <= kStallIters * J.n))
-        c.conv = 1;
-      else if (stalled)
-        c.stop = 1;
+      if ((c.by_rule && fabs(rr - predicted) <= tol * rr) || fabs(c.relres_prev - relres) <= tol * relres) {
+        if (c.iters <= kStallIters * J.n) c.conv = 1;
+        else c.stop = 1;
+      }
     }
     if (!c.conv && !c.stop) any = 1;
   }

@@ -744,10 +744,14 @@ int ms_lstsq(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, const 
       MSK_CUDA(cudaMemcpyAsync(h, sc, sizeof(h), cudaMemcpyDeviceToHost, st));
       MSK_CUDA(cudaStreamSynchronize(st));
       inner_total += (int)h[4];
+      // every convergence test below is trusted only while the inner
+      // iterations stay within kStallIters * n; beyond that the solve stops
+      // unconverged when a test fires
+      const bool trusted = inner_total <= kStallIters * n;
       if (h[5] != 0.0) {
         // even the first step gains no more than the floor: x is the
         // minimiser to within tol; keep it (relres is its FP64 residual)
-        converged = 1;
+        converged = trusted ? 1 : 0;
         break;
       }
       axpy_kernel<<<1, 512, 0, st>>>((int)n, s.dlt, x);
@@ -758,17 +762,15 @@ int ms_lstsq(const void* A, int dtype, int64_t d, int64_t n, int64_t lda, const 
       // Converged when the solve ended by its gain rule and the true FP64
       // residual confirms the decrease the CG recurrences predicted (no loss
       // to the inner arithmetic), or when the relative residual no longer
-      // moves by more than tol while the inner iterations so far stay within
-      // kStallIters * n.  A stall after more iterations means a
-      // preconditioner too poor to trust the stall: stop, unconverged.
+      // moves by more than tol, in either case while the inner iterations
+      // so far stay within kStallIters * n.  After more, the preconditioner
+      // is too poor to trust either test: stop, unconverged.
       const double predicted = rr_prev - h[6];
-      const bool stalled = std::fabs(relres_prev - relres) <= tol * relres;
       if ((h[7] != 0.0 && std::fabs(rr - predicted) <= tol * rr) ||
-          (stalled && inner_total <= kStallIters * n)) {
-        converged = 1;
+          std::fabs(relres_prev - relres) <= tol * relres) {
+        converged = trusted ? 1 : 0;
         break;
       }
-      if (stalled) break;
     }
     iters = inner_total;
     if (!converged) status = MSK_ENOCONV;

@@ -10,11 +10,11 @@
 
 namespace msk {
 
-// A stall of the relative residual between outer steps counts as
-// convergence only while the inner CG iterations so far stay within
-// kStallIters * n: CG ends in at most n steps in exact arithmetic and a
-// well-preconditioned solve takes far fewer; after more, the preconditioner
-// is too poor for a stall to show that x sits at the minimiser.
+// The refinement's convergence tests count only while the inner CG
+// iterations so far stay within kStallIters * n: CG ends in at most n steps
+// in exact arithmetic and a well-preconditioned solve takes far fewer; after
+// more, the preconditioner is too poor for a stall or a small CG gain to
+// show that x sits at the minimiser, and the solve stops unconverged.
 constexpr int kStallIters = 4;
 
 // ---------------------------------------------------------------------------
