@@ -96,6 +96,30 @@ def test_countsketch_f32(msk, orc, strategy, d, n, k, with_b, lda_pad):
     assert np.all(np.abs(Y - Yo) <= tol)
 
 
+# FP32 sketches with few buckets run the shared-memory-privatised kernel
+# (k <= 256 by default, any k that fits with cs.f32.priv = 2; rows >= 16 k;
+# k x cs floats per CTA, cs >= 4 columns per slice): one slice (k = 512),
+# four slices (k = 2048, 33 columns), a ragged last chunk, lda padding; the
+# knob cs.f32.priv = 0 gives the tile kernels on the same input.
+@pytest.mark.parametrize("d,n,k,with_b,lda_pad", [(40000, 16, 512, True, 0), (150001, 32, 2048, True, 3),
+                                                 (70001, 9, 300, False, 1), (200000, 33, 2048, False, 0),
+                                                 (16384, 1, 512, True, 0), (50000, 8, 128, True, 2)])
+@pytest.mark.parametrize("priv", [2, 1, 0])
+def test_countsketch_f32_private(msk, orc, d, n, k, with_b, lda_pad, priv):
+    seed = 0x5EED0006 + d
+    A, b, Ad, bd = _inputs(d, n, with_b, torch.float32, seed, lda_pad)
+    msk.tune_set("cs.f32.priv", priv)
+    try:
+        Y = msk.cs_sketch(Ad, k, seed, b=bd).cpu().numpy().astype(np.float64)
+    finally:
+        msk.tune_clear("cs.f32.priv")
+    An = A.numpy()
+    bn = None if b is None else b.numpy().astype(np.float32).astype(np.float64)
+    Yo = orc.countsketch(An, k, seed, b=bn)
+    tol = 1e-5 * orc.bucket_abs_sums(An, k, seed, b=bn)
+    assert np.all(np.abs(Y - Yo) <= tol)
+
+
 def test_countsketch_row_pitch(msk, orc):
     # Y with a leading dimension larger than ncol: the padding is left alone
     d, n, k, seed = 5000, 9, 100, 17
