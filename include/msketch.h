@@ -101,7 +101,7 @@ typedef enum {
 } msk_sketch_kind;
 
 #define MSK_OK 0
-#define MSK_ENOCONV 1001  /* refinement stopped at max_iter (x is returned) */
+#define MSK_ENOCONV 1001  /* refinement stopped unconverged (x is returned) */
 #define MSK_ENOMEM 1002   /* ws too small, or a request over the memory budget */
 #define MSK_ETIMEOUT 1003 /* a bounded device wait gave up */
 #define MSK_ECUDA 1004    /* a CUDA runtime call failed */
@@ -364,14 +364,18 @@ size_t msk_lstsq_workspace(int64_t d, int64_t n, int64_t k, int64_t p,
  *     residual r = b - A x and g = A^T r in FP64 (one pass over A), then runs
  *     conjugate gradients on A^T A d = g preconditioned by R11^T R11 (one pass
  *     over A per iteration; FP64 for FP64 A, double-single arithmetic on the
- *     FP32 units for FP32 A) until the preconditioned residual drops by 1e-6,
- *     and sets x += d.  Stops when the relative residual changes by at most
- *     tol * relres between outer steps, or after max_iter outer steps.
+ *     FP32 units for FP32 A) until a step lowers ||r||^2 by no more than
+ *     0.05 tol ||r||^2, and sets x += d.  Converged when the next FP64
+ *     residual confirms the decrease the CG steps predicted (to tol ||r||^2),
+ *     when the relative residual moves by at most tol * relres between outer
+ *     steps, or when the first CG step already gains less than that floor;
+ *     each test counts only within 4n inner iterations.  Stops unconverged
+ *     when a test fires after more, or after max_iter outer steps.
  *   A : device column-major d x n (lda), dtype F64 or F32; b : device double[d].
  *   x : device double[n] (output).
  *   info : host msk_lstsq_info* or NULL; when non-NULL the stream is
  *     synchronised and relres fields are filled.
- * Returns MSK_OK; MSK_ENOCONV if refinement hit max_iter; j+1 if R11 has an
+ * Returns MSK_OK; MSK_ENOCONV if refinement stopped unconverged; j+1 if R11 has an
  * exactly zero pivot at column j; negative for bad arguments (-1 A, -2 dtype,
  * -3 d < n, -4 n < 1, -5 lda, -6 b, -7 k < n+1, -8 p < n+1 or p > k,
  * -10 gemm_prec, -11 refine, -14 x, MSK_ENOMEM ws). */
@@ -528,14 +532,14 @@ size_t msk_batch_item_bound(const msk_batch_item *item, int refine);
  * FP32 CountSketch, split-BF16 tensor-core Gaussian stage with FP32
  * accumulators drained into double-single registers, FP64 Householder QR and
  * solve (Algorithm 1), and with refine = 1 the refinement of ms_lstsq (FP64
- * residual passes, double-single CG passes) until each problem's relative
- * residual changes by at most tol * relres, or max_iter outer steps.  Each
+ * residual passes, double-single CG passes) with its convergence tests and
+ * stops, per problem.  Each
  * stage is one launch over all problems, and the whole batch — the stages,
  * the outer refinement loop and the inner CG loop — is one CUDA-graph launch
  * whose loops are device-driven while nodes, so the host waits once, for the
  * results.  items: host array of nitems; infos: host array of nitems or
  * NULL.  Synchronises `stream`.  ws: 256-byte aligned, msk_batch_workspace
- * bytes.  Returns MSK_OK, MSK_ENOCONV if some problem hit max_iter, or -1
+ * bytes.  Returns MSK_OK, MSK_ENOCONV if some problem stopped unconverged, or -1
  * (bad item), -2 (nitems < 1), -3 (bad refine), MSK_ENOMEM. */
 int msk_batch_lstsq(const msk_batch_item *items, int nitems, int refine,
                     double tol, int32_t max_iter, msk_lstsq_info *infos,
