@@ -8,6 +8,7 @@
     python -m paper_2508_14209_gb300.cases rcq     --d 8388608 --n 128 --log10-sigma -6
     python -m paper_2508_14209_gb300.cases srht    --d 8388608 --n 128
     python -m paper_2508_14209_gb300.cases qr      --p 512 --ncol 129
+    python -m paper_2508_14209_gb300.cases batchmix --nprob 32 [--tol 1e-7]
 
 Each case draws its seeded synthetic input once on the GPU (the generators of
 the `inputs` module), runs the library call `--reps` times and prints one JSON
@@ -30,7 +31,11 @@ def main(argv=None):
     import paper_2508_14209_gb300 as msk
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["sketch", "gemm", "refined", "ne", "sns", "rcq", "srht", "host", "qr"])
+    ap.add_argument("case", choices=["sketch", "gemm", "refined", "ne", "sns", "rcq", "srht", "host", "qr",
+                                     "batchmix"])
+    ap.add_argument("--nprob", type=int, default=32,
+                    help="batchmix: requests in the batch (n cycling 16, 32, 64, 128; d log-uniform in "
+                         "[2^14, 2^21]; FP32 A with sigma from 1 to 10^log10-sigma)")
     ap.add_argument("--d", type=int, default=1 << 20)
     ap.add_argument("--n", type=int, default=64)
     ap.add_argument("--dtype", choices=["f64", "f32"], default="f64")
@@ -93,6 +98,26 @@ def main(argv=None):
         call = lambda: msk.srht_sketch(A, k, a.seed, Y=Y, ws=ws)  # noqa: E731
         m = a.d.bit_length() - 1
         out.update(d=a.d, n=a.n, k=k, adds_per_call=a.d * a.n * m)
+    elif a.case == "batchmix":
+        # one batch shaped like the served trace: msk_batch_lstsq, refined
+        import numpy as np
+
+        rng = np.random.default_rng(a.seed)
+        prob = []
+        for j in range(a.nprob):
+            n = (16, 32, 64, 128)[j % 4]
+            d = int(2 ** rng.uniform(14, 21))
+            A, b, _ = inputs.ls_problem(d, n, a.log10_sigma, seed=a.seed + j, dtype=torch.float32, device=dev)
+            prob.append((A, b, a.seed + j))
+        ws = msk.workspace(msk.msk_batch_workspace(prob, True), dev)
+        res = {}
+
+        def call():
+            r = msk.msk_batch_lstsq(prob, refine=True, tol=a.tol, max_iter=4, ws=ws)
+            res["r"] = {"converged": sum(int(i["converged"]) for i in r[1]),
+                        "inner_iters_mean": float(np.mean([i["iters"] for i in r[1]]))}
+        out.update(nprob=a.nprob, tol=a.tol, rows=sum(p_[0].shape[0] for p_ in prob),
+                   bytes_per_pass=sum(p_[0].shape[0] * p_[0].shape[1] * 4 for p_ in prob))
     elif a.case == "qr":
         # Householder QR of a p x ncol FP64 matrix (the sketched [SA Sb]),
         # restored from a saved copy before every call (copy included)
@@ -179,7 +204,7 @@ def main(argv=None):
     ev[1].record()
     torch.cuda.synchronize()
     out["ms_per_call"] = round(ev[0].elapsed_time(ev[1]) / a.reps, 5)
-    if a.case in ("refined", "ne", "sns", "rcq"):
+    if a.case in ("refined", "ne", "sns", "rcq", "batchmix"):
         out["info"] = res["r"]
     print(json.dumps(out), flush=True)
 
