@@ -2,31 +2,27 @@
 // of the sketch-and-precondition refinement: A preconditioned by the R of the
 // sketched QR, as in the preconditioned normal equations of Section 6.3):
 //   RESID = true : r_i = b_i - A_i x in FP64 (one DFMA per element);
-//                  accumulates g = A^T r, ||r||^2, ||b||^2.
-//   RESID = false: w_i = A_i p and v = A^T w, both in double-single.
-// Every product of A with a column vector is accumulated as a compensated
-// pair (s, c) of binary32 numbers: s carries the running sum, TwoSum (Knuth)
-// returns its exact rounding error, the exact product error comes from one
-// FMA (Dekker), and all errors are summed into c — the Dot2 scheme of Ogita,
-// Rump and Oishi (SIAM J. Sci. Comput. 2005), about twice the working
-// precision (~48 bits) at 11 binary32 operations per multiply-add.  GB300's
-// FP64 rate is about 1/64 of its FP32 rate, so this is ~5x cheaper than DFMA.
+//                  accumulates g = A^T r, ||r||^2, ||b||^2 and (specialised
+//                  bodies) the column maxima of |A|.
+//   RESID = false: w_i = A_i p and v = A^T w, both to about 44 bits.
+// Two ways of summing products to about twice binary32's precision on the
+// FP32 units (GB300's FP64 rate is about 1/64 of its FP32 rate):
+//   Dot2 (Ogita, Rump and Oishi, SIAM J. Sci. Comput. 2005): a compensated
+//     pair (s, c), TwoSum (Knuth) for the rounding error of s, one FMA
+//     (Dekker) for the product's; 11 binary32 operations per term.  The
+//     generic body (n > 256) uses it.
+//   error-free extraction (xs_step; Rump, Ogita and Oishi 2008): each product
+//     on an integer grid by one FMA against 1.5 2^k, the grid parts summed
+//     exactly as integers, the part below the grid into a binary32 rest;
+//     5 binary32 operations and one integer add per term.  The specialised
+//     bodies' operator pass and both column phases use it.
 //
-// Tiling.  A CTA of kP32Threads threads walks row tiles t = cta, cta + nctas,
-// ... of R rows (R a power of two, R * n ~ 8192), staged column-major in shared
-// memory (stride R) by cp.async, two buffers deep so that the next tile streams
-// in while the current one is computed.  Rows beyond d are zero-filled by the
-// copy itself.
-//   dot phase   : thread (r, q) = (t mod R, t / R) sums columns q, q + Q, ...
-//                 of row r (Q = T / R threads per row; rows t, t + T, ... when
-//                 R >= T); the Q partials are merged through shared memory.
-//                 A warp reads 32 consecutive rows of one column: no conflicts.
-//   column phase: thread (g, j) = (t mod G, t / G) accumulates column j over
-//                 rows g + G * ((x + j) mod (R / G)), x = 0 .. R/G - 1 (G row
-//                 groups, G * n <= T).  The rotation by j puts the 32 lanes of a
-//                 warp in 32 different banks although the stride R is a
-//                 multiple of 32.  Accumulators live in registers across tiles
-//                 and are merged over the G groups once per CTA.
+// The generic body (pass32g_body) tiles R rows (a power of two, R n ~ 8192)
+// column-major in shared memory by cp.async, two buffers deep; a thread (r, q)
+// sums columns q, q + Q, ... of row r with the Q partials merged through
+// shared memory, and a thread (g, j) accumulates column j over a rotated set
+// of rows (32 lanes in 32 banks).  The specialised bodies (pass32n_body,
+// n <= 256 as the next power of two) are described where they are defined.
 // Output: part[cta][0..n) the CTA's vector partial, part[cta][n], [n+1] the
 // scalars (RESID) or zeros; summed in fixed order by pass_reduce_body.
 #pragma once
@@ -111,7 +107,7 @@ __device__ __forceinline__ D2 d2_merge(D2 a, D2 b) {
 // Two binary32 lanes in one 64-bit register for the packed FP32x2
 // instructions of sm_100+ (add/sub/mul/fma .rn.f32x2): each instruction does
 // the same operation on both lanes, halving the instruction count of the
-// compensated sums below.
+// extraction steps below.
 typedef unsigned long long f2p;
 __device__ __forceinline__ f2p f2p_make(float lo, float hi) {
   f2p r;
@@ -143,28 +139,6 @@ __device__ __forceinline__ f2p f2p_fma(f2p a, f2p b, f2p c) {
   asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
   return r;
 }
-struct D2P {
-  f2p s, c;  // two independent compensated sums
-};
-// acc += a * (xh + xl) lane-wise, nxh = -xh: the Dot2 step of d2_fma with
-// ph = a xh carried negated (nph = -ph exactly, rounding is sign-symmetric)
-// so that the exact product error is one FMA: a xh + nph.
-__device__ __forceinline__ void d2p_fma(D2P& acc, f2p a, f2p xh, f2p nxh, f2p xl) {
-  const f2p nph = f2p_mul(a, nxh);
-  const f2p pe = f2p_fma(a, xh, nph);
-  const f2p s = f2p_sub(acc.s, nph);
-  const f2p v = f2p_sub(s, acc.s);
-  const f2p e = f2p_sub(f2p_sub(acc.s, f2p_sub(s, v)), f2p_add(nph, v));
-  acc.s = s;
-  acc.c = f2p_add(acc.c, f2p_add(e, f2p_fma(a, xl, pe)));
-}
-// The two lanes of a packed sum as scalar pairs.
-__device__ __forceinline__ void d2p_lanes(const D2P& a, D2& lo, D2& hi) {
-  const float2 s = f2p_split(a.s), c = f2p_split(a.c);
-  lo = D2{s.x, c.x};
-  hi = D2{s.y, c.y};
-}
-
 // Extraction of a sum of products into an exact integer part and a small
 // rest: the error-free transformation of Rump, Ogita and Oishi ("Accurate
 // floating-point summation", SIAM J. Sci. Comput. 2008) with each product
